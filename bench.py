@@ -1,0 +1,365 @@
+#!/usr/bin/env python
+"""Benchmark of the parallel Kalman filter + RTS smoother on GB300.
+
+Metric: smoothed steps/s (steps of a sequence whose filtering and smoothing
+posteriors have all been computed), one step of the benchmark = one full pass
+of the hot path (filtering elements built from y, forward scan, smoothing
+elements built from the filtered moments, reverse scan) over one sequence.
+
+Workload (default): 2-D Wiener-velocity tracking model, nx = 4, ny = 2,
+dt = 0.1, q = 1, R = I, m0 = 0, P0 = I, T = 2^20 steps, synthetic data
+simulated from the model with a fixed seed (one independent sequence per
+rank under torchrun: weak scaling, no collective on the data path).
+
+    python bench.py [--steps K] [--warmup W] [--T T]
+    python bench.py --impl reference      # the FP64 CPU oracle, same metric
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "smoothed steps/s"
+UNIT = "steps/s"
+FP32_LANES_PER_SM = 128
+NUM_SMS = 152
+SM_MAX_MHZ = 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--T", type=int, default=1 << 20)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- work model
+def bytes_per_step(nx: int, ny: int) -> dict:
+    """Algorithmic DRAM bytes per step of each kernel (FP32), fused path:
+    the forward scan reads y and writes the filtered mean + covariance; the
+    reverse scan reads those and writes the smoothed ones."""
+    post = 4 * (nx + nx * nx)
+    return {"filter": 4 * ny + post, "smoother": 2 * post}
+
+
+def flops_per_step(N: int, M: int) -> dict:
+    """Floating-point operations per step of each kernel's per-step work
+    (FMA = 2): the forward scan folds one measurement element into its block
+    aggregate (rank-M Lemma 4) and later applies it to the running filtered
+    posterior; the reverse scan builds the Lemma 5 element twice (fold and
+    application), folds it (Lemma 6) and applies it.  Block-level scan,
+    look-back and element-building overheads are not counted."""
+    s = N * (N + 1) // 2
+    sm = M * (M + 1) // 2
+    chol = M * M * M // 3 + 3 * M
+    meas = 2 * (N * M + sm) + M
+    fold = 2 * (3 * N * N * M + M * N * N + 2 * N * sm + sm * N + 2 * N ** 3 + s * N + 2 * s * M
+                + N * N + 3 * N * M + sm) + chol
+    adv = 2 * (N * N * M + sm * N + 2 * N * sm + 3 * N * M + N * N + s * M + N ** 3 + s * N) + chol
+    sel = 2 * (N ** 3 + s * N + N ** 3 // 6 + N * N * (N - 1) + 2 * N * N + s * N) + 2 * N * N + N
+    scomb = 2 * (N ** 3 + s * N + N * N + N ** 3)
+    sadv = 2 * (N ** 3 + N * N + s * N)
+    return {"filter": fold + adv + 2 * meas, "smoother": 2 * sel + scomb + sadv}
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1].split()[0]))
+                smax.append(float(parts[2].split()[0]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- CPU oracle
+def cpu_oracle_rate(seq, seconds: float) -> dict:
+    """The FP64 oracle (sequential KF + RTS, one core) on the same sequence,
+    repeated until `seconds` of CPU work have run (at least once)."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        oracle.kf_rts(seq.model, seq.y)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return {"value": reps * seq.T / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{reps} full passes over the T={seq.T} sequence ({el:.1f} s, 1 thread)"}
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1905_13002_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources; else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(kernel)
+    if not e or e.get("source_hash") != source_hash():
+        return None
+    return e.get("dram_bytes_per_launch_full")
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    seq = workloads.tracking_sequence(args.T, seed=workloads.SEED_BASE + 2)
+    import oracle
+    oracle.build()
+    # Each step: a bounded sample of the workload (a prefix of the sequence
+    # sized so that W + K steps take about a minute or less).
+    Ts = min(args.T, 1 << 18)
+    sub = workloads.Sequence(seq.model, seq.y[:Ts])
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.kf_rts(sub.model, sub.y)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    ms = 1e3 * statistics.mean(times)
+    value = Ts / (ms / 1e3)
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "wiener_velocity_2d nx=4 ny=2 dt=0.1 q=1 R=I", "T": args.T,
+                      "T_sample_per_step": Ts},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": f"first {Ts} steps of the T={args.T} sequence per step"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+# ---------------------------------------------------------------- our arm
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_1905_13002_gb300 as ks
+    from paper_1905_13002_gb300 import _build
+
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if local == 0:
+        _build.build()
+    if world > 1:
+        dist.barrier()
+
+    T = args.T
+    seq = workloads.tracking_sequence(T, seed=workloads.SEED_BASE + 2 + rank)
+    m = seq.model
+    model = ks.Model.create(m.F, m.Q, m.H, m.R, m.m0, m.P0, u=m.u, d=m.d, device=dev)
+    y = torch.as_tensor(seq.y, dtype=torch.float32, device=dev)
+    ws = ks.alloc_workspace(model, T, ks.KS_WS_ELEMENTS)
+    fm = torch.empty(T, 4, device=dev)
+    fP = torch.empty(T, 4, 4, device=dev)
+    sm = torch.empty(T, 4, device=dev)
+    sP = torch.empty(T, 4, 4, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+    stream = torch.cuda.current_stream()
+
+    def step(events=None):
+        ks.smooth(model, y, ws, fmean=fm, fcov=fP, smean=sm, scov=sP, events=events)
+
+    for _ in range(max(args.warmup, 3)):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    if ks.status(ws) != ks.KS_OK:
+        raise SystemExit("device status not OK after warm-up")
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    for i in range(args.steps):
+        flush.zero_()                       # L2 flushed between timed steps, outside the events
+        step(evs[i])
+    torch.cuda.synchronize()
+    time.sleep(0.3)
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    st = ks.status(ws)
+    if st != ks.KS_OK:
+        raise SystemExit(f"device status {st} after the timed steps")
+
+    tot = [e[0].elapsed_time(e[3]) for e in evs]
+    kf = [e[1].elapsed_time(e[2]) for e in evs]
+    ksm = [e[2].elapsed_time(e[3]) for e in evs]
+    ms = statistics.mean(tot)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = T * world / (ms / 1e3)
+
+    # ---- end to end through the public API with host buffers
+    y_h = torch.as_tensor(seq.y, dtype=torch.float32).pin_memory()
+    sm_h = torch.empty(T, 4, dtype=torch.float32).pin_memory()
+    sP_h = torch.empty(T, 4, 4, dtype=torch.float32).pin_memory()
+    y_d = torch.empty_like(y)
+    e2e_times = []
+    for i in range(args.warmup + args.steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        y_d.copy_(y_h, non_blocking=True)
+        ks.smooth(model, y_d, ws, smean=sm, scov=sP, keep_filtered=False)
+        sm_h.copy_(sm, non_blocking=True)
+        sP_h.copy_(sP, non_blocking=True)
+        b.record()
+        b.synchronize()
+        if i >= args.warmup:
+            e2e_times.append(a.elapsed_time(b))
+    e2e_ms = statistics.mean(e2e_times)
+    if ks.status(ws) != ks.KS_OK:
+        raise SystemExit("device status not OK after the end-to-end steps")
+    e2e = {"value": T * world / (e2e_ms / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": int(y_h.numel() * 4),
+           "d2h_bytes_per_step": int((sm_h.numel() + sP_h.numel()) * 4)}
+
+    # ---- roofline of the dominant kernel
+    hbm, which = peaks()
+    bps = bytes_per_step(4, 2)
+    fps = flops_per_step(4, 2)
+    kernels = {"filter": statistics.mean(kf), "smoother": statistics.mean(ksm)}
+    dom = max(kernels, key=kernels.get)
+    dur_s = kernels[dom] / 1e3
+    gbs = bps[dom] * T / dur_s / 1e9
+    alu_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    tfl = fps[dom] * T / dur_s / 1e12
+    kname = {"filter": "filter_scan_kernel", "smoother": "smoother_scan_kernel"}[dom]
+    traffic = recorded_traffic(kname)
+    if tfl / alu_peak >= gbs / hbm:
+        roof = {"bound": "alu", "achieved": tfl, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": tfl / alu_peak, "traffic": traffic}
+    else:
+        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                "frac": gbs / hbm, "traffic": traffic}
+    roof.update({"kernel": kname, "peak_source": which if roof["bound"] == "hbm" else
+                 "152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                 "ms_per_launch": kernels[dom], "hbm_frac": gbs / hbm, "alu_frac": tfl / alu_peak,
+                 "bytes_per_step": bps[dom], "flops_per_step": fps[dom],
+                 "kernels_ms": {k: round(v, 4) for k, v in kernels.items()}})
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "wiener_velocity_2d nx=4 ny=2 dt=0.1 q=1 R=I m0=0 P0=I", "T": T,
+                      "sequences_per_gpu": 1, "parallelism": f"replicas{world}",
+                      "l2": "flushed between timed steps (256 MiB memset outside the events)"},
+           "clocks": {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+           "gpu_launches": 3 * args.steps, "e2e": e2e, "roofline": roof}
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_oracle_rate(seq, args.cpu_seconds)
+    print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

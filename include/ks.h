@@ -1,0 +1,196 @@
+/*
+ * ks.h -- C ABI of the GB300 temporally parallel Kalman filter / RTS smoother.
+ *
+ * The library computes the filtering and smoothing posteriors of a
+ * linear/Gaussian state-space model (Section IV)
+ *
+ *     x_k = F x_{k-1} + u + q_{k-1},   q ~ N(0, Q),
+ *     y_k = H x_k + d + r_k,           r ~ N(0, R),   x_0 ~ N(m0, P0),
+ *
+ * as two all-prefix-sums (Section II-B):
+ *   - Lemma 3 builds one filtering element a_k = (A_k, b_k, C_k, eta_k, J_k)
+ *     per measurement; Lemma 4's operator combines them; by Theorem 1 the
+ *     prefix a_1 (x) ... (x) a_k has b = filtered mean, C = filtered covariance.
+ *   - Lemma 5 builds one smoothing element (E_k, g_k, L_k) per step from the
+ *     filtered moments; Lemma 6's operator combines them; by Theorem 2 the
+ *     suffix a_k (x) ... (x) a_n has g = smoothed mean, L = smoothed covariance.
+ * The scans use block-level elements (Section III-C): each thread folds a
+ * contiguous block of steps, blocks are scanned within a thread block, and
+ * thread blocks are chained by a decoupled look-back.
+ *
+ * Conventions (all entry points)
+ * ------------------------------
+ * - Arithmetic: FP32 on the GPU; the k = 1 element (prior m0, P0) in FP64.
+ * - Memory: every pointer argument documented "device" must point to memory
+ *   the current CUDA device can read/write (cudaMalloc, torch CUDA tensors).
+ *   The caller owns every buffer; the library allocates no device memory and
+ *   keeps no global state between calls.  Scratch lives in the caller's
+ *   workspace `ws` (opaque, size from ks_workspace_bytes, 256-byte aligned).
+ * - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream).  Calls are stream-ordered and asynchronous, make no host
+ *   synchronisation, and may be captured into a CUDA graph.
+ * - Layouts: matrices row-major; filtered/smoothed means are [T][nx],
+ *   covariances [T][nx][nx] (full, symmetric), all FP32.
+ * - Sizes: 1 <= T <= 2^31 - 1.  Supported (nx, ny) pairs are listed by
+ *   ks_supported(); others return KS_EUNSUPPORTED.
+ * - Errors: every call returns KS_OK (0) or a negative code.  Argument and
+ *   launch errors are returned immediately.  Errors found on the device
+ *   (non-finite values, a failed factorisation, a look-back wait that timed
+ *   out) are recorded in the workspace's status word and reported by
+ *   ks_status().  Calls on one workspace must not overlap on the device.
+ */
+#ifndef KS_H
+#define KS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define KS_OK 0
+#define KS_EINVAL (-1)        /* bad argument: size, null or misaligned pointer */
+#define KS_ECUDA (-2)         /* a CUDA launch or copy failed */
+#define KS_ENUMERIC (-3)      /* device: non-finite value or failed factorisation */
+#define KS_ETIMEOUT (-4)      /* device: bounded look-back wait ran out */
+#define KS_EUNSUPPORTED (-5)  /* (nx, ny) not compiled into this library */
+
+/* Workspace purposes for ks_workspace_bytes(). */
+#define KS_WS_SMOOTH 0        /* ks_smooth / ks_filter_scan / ks_smooth_scan scratch */
+#define KS_WS_ELEMENTS 1      /* additionally the materialised element arrays of ks_build_elements */
+
+/*
+ * Time-invariant linear/Gaussian model of Section IV.  F [nx][nx],
+ * u [nx], Q [nx][nx], H [ny][nx], d [ny], R [ny][ny] are DEVICE pointers to
+ * FP32 row-major arrays; u and d may be NULL (zero).  m0 [nx] and P0
+ * [nx][nx] are DEVICE pointers to FP64 arrays.  Q, R and P0 must be
+ * symmetric positive definite (R, P0) / semidefinite with F P F^T + Q
+ * definite (Q).  time_varying must be 0.
+ */
+typedef struct ks_model {
+    int32_t nx;
+    int32_t ny;
+    int32_t time_varying;
+    int32_t reserved;
+    const float *F, *u, *Q, *H, *d, *R;
+    const double *m0, *P0;
+} ks_model;
+
+/* Layout of the materialised filtering elements written by ks_build_elements
+ * (Lemma 3) into the workspace: structure of arrays, component-major.  The
+ * c-th scalar component of element k (0-based step) is the float at
+ *     (float*)((char*)ws + offset_X) + c * ld + k
+ * with components row-major within A [nx*nx], b [nx], C [nx*nx], eta [nx],
+ * J [nx*nx]. */
+typedef struct ks_elements_layout {
+    int64_t ld;          /* floats between consecutive components (>= T, multiple of 64) */
+    int64_t offset_A, offset_b, offset_C, offset_eta, offset_J;  /* bytes from ws */
+} ks_elements_layout;
+
+/* Library version, for the binding's load check. */
+int ks_version(void);
+
+/* 1 if the (nx, ny) pair is compiled in, else 0. */
+int ks_supported(int nx, int ny);
+
+/* Human-readable text of a status code; never NULL. */
+const char *ks_strerror(int code);
+
+/*
+ * Bytes of workspace needed for sequences of up to T steps of model `m`
+ * (only m->nx, m->ny are read; host pointer).  purpose = KS_WS_SMOOTH or
+ * KS_WS_ELEMENTS.  Returns 0 for invalid arguments.
+ */
+size_t ks_workspace_bytes(const ks_model *m, int64_t T, int purpose);
+
+/*
+ * Zero the workspace's status word and scan state (stream-ordered).  Call
+ * once on a fresh workspace before its first use.
+ */
+int ks_workspace_init(void *ws, size_t ws_bytes, void *stream);
+
+/*
+ * Element offsets of ks_build_elements' output inside a KS_WS_ELEMENTS
+ * workspace (host call, no device work).
+ */
+int ks_elements_layout_get(const ks_model *m, int64_t T, ks_elements_layout *out);
+
+/*
+ * Lemma 3 (Section IV-A): build the T filtering elements (A_k, b_k, C_k,
+ * eta_k, J_k) from the measurements y [T][ny] (device, FP32) into the
+ * workspace, in the layout of ks_elements_layout_get.  k = 1 is built in
+ * FP64 from (m0, P0) with A_1 = 0 and eta_1 = 0, J_1 = 0; for k > 1 the model
+ * being time-invariant, A, C, J are the same for every k and only b_k, eta_k
+ * depend on y_k.  C and J are stored symmetrised.
+ * ws must hold ks_workspace_bytes(m, T, KS_WS_ELEMENTS) bytes.
+ */
+int ks_build_elements(const ks_model *m, const float *y, int64_t T,
+                      void *ws, size_t ws_bytes, void *stream);
+
+/*
+ * Forward filtering scan over the elements built by ks_build_elements:
+ * inclusive all-prefix-sums under Lemma 4's operator (Theorem 1).  Writes the
+ * filtered means fmean [T][nx] = b of each prefix and covariances
+ * fcov [T][nx][nx] = C of each prefix (device, FP32).
+ */
+int ks_filter_scan(const ks_model *m, int64_t T, void *ws, size_t ws_bytes,
+                   float *fmean, float *fcov, void *stream);
+
+/*
+ * Reverse smoothing scan (Lemmas 5 and 6, Theorem 2): builds the smoothing
+ * elements from the filtered moments fmean [T][nx], fcov [T][nx][nx]
+ * (device) as it loads them, computes the suffix sums
+ * a_k (x) a_{k+1} (x) ... (x) a_T (earlier element on the left) and writes
+ * smoothed means smean [T][nx] and covariances scov [T][nx][nx] (device).
+ */
+int ks_smooth_scan(const ks_model *m, int64_t T, const float *fmean, const float *fcov,
+                   void *ws, size_t ws_bytes, float *smean, float *scov, void *stream);
+
+/*
+ * End to end: filtering elements built from y as the forward scan loads
+ * them (no materialised element arrays), forward scan writing
+ * fmean/fcov, then the reverse smoothing scan writing smean/scov.
+ * y [T][ny], fmean [T][nx], fcov [T][nx][nx], smean, scov: device, FP32.
+ * fmean and fcov may be NULL, in which case the filtered moments are kept
+ * in the workspace only (which then needs ks_workspace_bytes(m, T,
+ * KS_WS_ELEMENTS) bytes).
+ */
+int ks_smooth(const ks_model *m, const float *y, int64_t T, void *ws, size_t ws_bytes,
+              float *fmean, float *fcov, float *smean, float *scov, void *stream);
+
+/*
+ * ks_smooth with per-kernel timing: `events` points to 4 cudaEvent_t handles
+ * (passed as void*; any may be NULL) that are recorded on `stream` before the
+ * model preparation, before the forward scan kernel, between the two scans
+ * and after the reverse scan kernel.  Otherwise identical to ks_smooth.
+ */
+int ks_smooth_traced(const ks_model *m, const float *y, int64_t T, void *ws, size_t ws_bytes,
+                     float *fmean, float *fcov, float *smean, float *scov, void *stream,
+                     void *const *events);
+
+/*
+ * Synchronise `stream`, read the workspace's device status word, clear it,
+ * and return KS_OK, KS_ENUMERIC or KS_ETIMEOUT (or KS_ECUDA if the stream
+ * reported an error).  ws: device.
+ */
+int ks_status(void *ws, void *stream);
+
+/*
+ * Batched Lemma 4 / Lemma 6 operators on `count` independent element pairs,
+ * for operator-level testing and for callers that run their own scans.
+ * Elements are packed per element (no padding) in device memory, FP32:
+ *   filter element  = A[nx*nx] b[nx] C[nx*nx] eta[nx] J[nx*nx]
+ *   smoother element = E[nx*nx] g[nx] L[nx*nx]
+ * out[i] = left[i] (x) right[i].  C, J, L of the results are symmetrised.
+ */
+int ks_filter_combine_batch(int nx, int64_t count, const float *left, const float *right,
+                            float *out, void *ws, size_t ws_bytes, void *stream);
+int ks_smoother_combine_batch(int nx, int64_t count, const float *left, const float *right,
+                              float *out, void *ws, size_t ws_bytes, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KS_H */

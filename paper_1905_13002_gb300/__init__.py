@@ -1,0 +1,282 @@
+"""GB300 temporally parallel Kalman filter / RTS smoother.
+
+Python binding of ``libks`` (C ABI in ``include/ks.h``), the CUDA
+implementation of the parallel linear/Gaussian filter and smoother of
+Särkkä & García-Fernández, "Temporal Parallelization of Bayesian Smoothers"
+(Section IV): Lemma 3 / Lemma 4 elements and operator scanned forward
+(Theorem 1), Lemma 5 / Lemma 6 elements and operator scanned in reverse
+(Theorem 2).
+
+This module only marshals arguments: it passes torch CUDA tensors (device
+memory) and the current torch stream to the library, whose kernels do every
+step.  There is no CPU fallback; if the library is not built, every call
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+__all__ = [
+    "KsError", "Model", "lib", "workspace_bytes", "alloc_workspace", "smooth", "build_elements",
+    "elements", "filter_scan", "smooth_scan", "status", "filter_combine_batch",
+    "smoother_combine_batch", "supported", "KS_WS_SMOOTH", "KS_WS_ELEMENTS",
+]
+
+KS_OK, KS_EINVAL, KS_ECUDA, KS_ENUMERIC, KS_ETIMEOUT, KS_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
+KS_WS_SMOOTH, KS_WS_ELEMENTS = 0, 1
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "libks.so")
+
+
+class KsError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        msg = lib().ks_strerror(code).decode() if _lib is not None else str(code)
+        super().__init__(f"{what}: {msg} (code {code})" if what else f"{msg} (code {code})")
+
+
+class _KsModel(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("time_varying", ctypes.c_int32),
+                ("reserved", ctypes.c_int32),
+                ("F", ctypes.c_void_p), ("u", ctypes.c_void_p), ("Q", ctypes.c_void_p),
+                ("H", ctypes.c_void_p), ("d", ctypes.c_void_p), ("R", ctypes.c_void_p),
+                ("m0", ctypes.c_void_p), ("P0", ctypes.c_void_p)]
+
+
+class _KsLayout(ctypes.Structure):
+    _fields_ = [("ld", ctypes.c_int64), ("offset_A", ctypes.c_int64), ("offset_b", ctypes.c_int64),
+                ("offset_C", ctypes.c_int64), ("offset_eta", ctypes.c_int64),
+                ("offset_J", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libks.so (built in-tree by ``__graft_entry__.build()``)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libks is not built ({LIB_PATH} missing); run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, sz, i64, i32 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int64, ctypes.c_int
+        M = ctypes.POINTER(_KsModel)
+        sig = {
+            "ks_version": ([], i32),
+            "ks_supported": ([i32, i32], i32),
+            "ks_strerror": ([i32], ctypes.c_char_p),
+            "ks_workspace_bytes": ([M, i64, i32], sz),
+            "ks_workspace_init": ([vp, sz, vp], i32),
+            "ks_elements_layout_get": ([M, i64, ctypes.POINTER(_KsLayout)], i32),
+            "ks_build_elements": ([M, vp, i64, vp, sz, vp], i32),
+            "ks_filter_scan": ([M, i64, vp, sz, vp, vp, vp], i32),
+            "ks_smooth_scan": ([M, i64, vp, vp, vp, sz, vp, vp, vp], i32),
+            "ks_smooth": ([M, vp, i64, vp, sz, vp, vp, vp, vp, vp], i32),
+            "ks_smooth_traced": ([M, vp, i64, vp, sz, vp, vp, vp, vp, vp, ctypes.POINTER(vp)], i32),
+            "ks_status": ([vp, vp], i32),
+            "ks_filter_combine_batch": ([i32, i64, vp, vp, vp, vp, sz, vp], i32),
+            "ks_smoother_combine_batch": ([i32, i64, vp, vp, vp, vp, sz, vp], i32),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, what: str):
+    if rc != KS_OK:
+        raise KsError(rc, what)
+
+
+def _p(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev(x, dtype, device):
+    t = torch.as_tensor(x, dtype=dtype, device=device)
+    return t.contiguous()
+
+
+@dataclass
+class Model:
+    """Device-resident time-invariant linear/Gaussian model (Section IV).
+
+    F [nx,nx], u [nx], Q [nx,nx], H [ny,nx], d [ny], R [ny,ny] are FP32;
+    m0 [nx], P0 [nx,nx] are FP64 (the k = 1 element is built in FP64).
+    """
+
+    F: torch.Tensor
+    Q: torch.Tensor
+    H: torch.Tensor
+    R: torch.Tensor
+    m0: torch.Tensor
+    P0: torch.Tensor
+    u: torch.Tensor | None = None
+    d: torch.Tensor | None = None
+
+    @classmethod
+    def create(cls, F, Q, H, R, m0, P0, u=None, d=None, device="cuda") -> "Model":
+        f32, f64 = torch.float32, torch.float64
+        return cls(F=_dev(F, f32, device), Q=_dev(Q, f32, device), H=_dev(H, f32, device),
+                   R=_dev(R, f32, device), m0=_dev(m0, f64, device), P0=_dev(P0, f64, device),
+                   u=None if u is None else _dev(u, f32, device),
+                   d=None if d is None else _dev(d, f32, device))
+
+    @property
+    def nx(self) -> int:
+        return int(self.F.shape[0])
+
+    @property
+    def ny(self) -> int:
+        return int(self.H.shape[0])
+
+    def struct(self) -> _KsModel:
+        return _KsModel(self.nx, self.ny, 0, 0, self.F.data_ptr(),
+                        0 if self.u is None else self.u.data_ptr(), self.Q.data_ptr(),
+                        self.H.data_ptr(), 0 if self.d is None else self.d.data_ptr(),
+                        self.R.data_ptr(), self.m0.data_ptr(), self.P0.data_ptr())
+
+
+def supported(nx: int, ny: int) -> bool:
+    return bool(lib().ks_supported(nx, ny))
+
+
+def workspace_bytes(model: Model, T: int, purpose: int = KS_WS_SMOOTH) -> int:
+    m = model.struct()
+    n = lib().ks_workspace_bytes(ctypes.byref(m), T, purpose)
+    if n == 0:
+        raise KsError(KS_EUNSUPPORTED if not supported(model.nx, model.ny) else KS_EINVAL,
+                      "ks_workspace_bytes")
+    return int(n)
+
+
+def alloc_workspace(model: Model, T: int, purpose: int = KS_WS_SMOOTH, stream=None) -> torch.Tensor:
+    """A zero-initialised workspace tensor (uint8, on the model's device)."""
+    nbytes = workspace_bytes(model, T, purpose)
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=model.F.device)
+    _check(lib().ks_workspace_init(_p(ws), nbytes, _stream(stream)), "ks_workspace_init")
+    return ws
+
+
+def _out(shape, like, out):
+    if out is not None:
+        return out
+    return torch.empty(shape, dtype=torch.float32, device=like.device)
+
+
+def smooth(model: Model, y: torch.Tensor, ws: torch.Tensor | None = None, *, fmean=None, fcov=None,
+           smean=None, scov=None, keep_filtered: bool = True, stream=None, events=None):
+    """End to end (``ks_smooth``): returns (fmean, fcov, smean, scov).
+
+    With ``keep_filtered=False`` the filtered moments stay in the workspace
+    (which must then be a KS_WS_ELEMENTS workspace) and None is returned for
+    them.  ``events``: 4 recorded-or-fresh torch.cuda.Event objects to time
+    the kernels (``ks_smooth_traced``).
+    """
+    T = int(y.shape[0])
+    purpose = KS_WS_SMOOTH if keep_filtered else KS_WS_ELEMENTS
+    ws = alloc_workspace(model, T, purpose, stream) if ws is None else ws
+    if keep_filtered:
+        fmean = _out((T, model.nx), y, fmean)
+        fcov = _out((T, model.nx, model.nx), y, fcov)
+    else:
+        fmean = fcov = None
+    smean = _out((T, model.nx), y, smean)
+    scov = _out((T, model.nx, model.nx), y, scov)
+    m = model.struct()
+    args = (ctypes.byref(m), _p(y), T, _p(ws), ws.numel(), _p(fmean), _p(fcov), _p(smean), _p(scov),
+            _stream(stream))
+    if events is None:
+        _check(lib().ks_smooth(*args), "ks_smooth")
+    else:
+        for e in events:
+            if e is not None and not e.cuda_event:   # torch creates events lazily
+                e.record(torch.cuda.current_stream() if stream is None else stream)
+        handles = (ctypes.c_void_p * 4)(*[ctypes.c_void_p(e.cuda_event) if e is not None else None
+                                          for e in events])
+        _check(lib().ks_smooth_traced(*args, handles), "ks_smooth_traced")
+    return fmean, fcov, smean, scov
+
+
+def build_elements(model: Model, y: torch.Tensor, ws: torch.Tensor, stream=None):
+    """Lemma 3 elements into the workspace (``ks_build_elements``)."""
+    m = model.struct()
+    _check(lib().ks_build_elements(ctypes.byref(m), _p(y), int(y.shape[0]), _p(ws), ws.numel(),
+                                   _stream(stream)), "ks_build_elements")
+
+
+def elements(model: Model, T: int, ws: torch.Tensor) -> dict:
+    """Views of the materialised elements: A, C, J [T,nx,nx]; b, eta [T,nx]."""
+    m = model.struct()
+    lay = _KsLayout()
+    _check(lib().ks_elements_layout_get(ctypes.byref(m), T, ctypes.byref(lay)), "ks_elements_layout_get")
+    n = model.nx
+    f = ws.view(torch.float32) if ws.numel() % 4 == 0 else None
+
+    def comp(off, k):
+        return f[off // 4: off // 4 + k * lay.ld].view(k, lay.ld)[:, :T]
+
+    return {"A": comp(lay.offset_A, n * n).T.reshape(T, n, n),
+            "b": comp(lay.offset_b, n).T.reshape(T, n),
+            "C": comp(lay.offset_C, n * n).T.reshape(T, n, n),
+            "eta": comp(lay.offset_eta, n).T.reshape(T, n),
+            "J": comp(lay.offset_J, n * n).T.reshape(T, n, n)}
+
+
+def filter_scan(model: Model, T: int, ws: torch.Tensor, *, fmean=None, fcov=None, stream=None):
+    """Forward scan over materialised elements (``ks_filter_scan``)."""
+    fmean = _out((T, model.nx), ws, fmean)
+    fcov = _out((T, model.nx, model.nx), ws, fcov)
+    m = model.struct()
+    _check(lib().ks_filter_scan(ctypes.byref(m), T, _p(ws), ws.numel(), _p(fmean), _p(fcov),
+                                _stream(stream)), "ks_filter_scan")
+    return fmean, fcov
+
+
+def smooth_scan(model: Model, fmean: torch.Tensor, fcov: torch.Tensor, ws: torch.Tensor | None = None, *,
+                smean=None, scov=None, stream=None):
+    """Reverse scan from filtered moments (``ks_smooth_scan``)."""
+    T = int(fmean.shape[0])
+    ws = alloc_workspace(model, T, KS_WS_SMOOTH, stream) if ws is None else ws
+    smean = _out((T, model.nx), fmean, smean)
+    scov = _out((T, model.nx, model.nx), fmean, scov)
+    m = model.struct()
+    _check(lib().ks_smooth_scan(ctypes.byref(m), T, _p(fmean), _p(fcov), _p(ws), ws.numel(), _p(smean),
+                                _p(scov), _stream(stream)), "ks_smooth_scan")
+    return smean, scov
+
+
+def status(ws: torch.Tensor, stream=None) -> int:
+    """Synchronise, read and clear the device status word (``ks_status``)."""
+    return int(lib().ks_status(_p(ws), _stream(stream)))
+
+
+def _combine(fn, name, nx, left, right, ws, stream):
+    count = int(left.shape[0])
+    out = torch.empty_like(left)
+    if ws is None:
+        ws = torch.zeros(256, dtype=torch.uint8, device=left.device)
+    _check(fn(nx, count, _p(left), _p(right), _p(out), _p(ws), ws.numel(), _stream(stream)), name)
+    return out, ws
+
+
+def filter_combine_batch(nx: int, left: torch.Tensor, right: torch.Tensor, ws=None, stream=None):
+    """Lemma 4 on packed element pairs [count, 3nx^2+2nx]; returns (out, ws)."""
+    return _combine(lib().ks_filter_combine_batch, "ks_filter_combine_batch", nx, left, right, ws, stream)
+
+
+def smoother_combine_batch(nx: int, left: torch.Tensor, right: torch.Tensor, ws=None, stream=None):
+    """Lemma 6 on packed element pairs [count, 2nx^2+nx]; returns (out, ws)."""
+    return _combine(lib().ks_smoother_combine_batch, "ks_smoother_combine_batch", nx, left, right, ws,
+                    stream)

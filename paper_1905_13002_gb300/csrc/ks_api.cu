@@ -1,0 +1,167 @@
+// ks_api.cu -- extern "C" entry points of include/ks.h: dispatch to the
+// compiled (nx, ny) instantiations, workspace queries and status handling.
+#include <cuda_runtime.h>
+
+#include "../../include/ks.h"
+#include "ks_impl.cuh"
+
+namespace ks {
+
+extern const VTable kImpl_4_2;
+
+static const VTable* const kImpls[] = {&kImpl_4_2};
+
+const VTable* find_impl(int nx, int ny) {
+    for (const VTable* v : kImpls)
+        if (v->nx == nx && v->ny == ny) return v;
+    return nullptr;
+}
+
+static const VTable* find_nx(int nx) {
+    for (const VTable* v : kImpls)
+        if (v->nx == nx) return v;
+    return nullptr;
+}
+
+static int check_nx_ny(const ks_model* m, const VTable** out) {
+    if (!m) return KS_EINVAL;
+    if (m->nx < 1 || m->ny < 1) return KS_EINVAL;
+    const VTable* v = find_impl(m->nx, m->ny);
+    if (!v) return KS_EUNSUPPORTED;
+    *out = v;
+    return KS_OK;
+}
+
+}  // namespace ks
+
+using namespace ks;
+
+extern "C" {
+
+int ks_version(void) { return 100; }
+
+int ks_supported(int nx, int ny) { return find_impl(nx, ny) != nullptr ? 1 : 0; }
+
+const char* ks_strerror(int code) {
+    switch (code) {
+        case KS_OK: return "ok";
+        case KS_EINVAL: return "invalid argument (size, null or misaligned pointer, workspace too small)";
+        case KS_ECUDA: return "CUDA launch or copy failed";
+        case KS_ENUMERIC: return "non-finite value or failed factorisation on the device";
+        case KS_ETIMEOUT: return "look-back wait on the device ran out";
+        case KS_EUNSUPPORTED: return "(nx, ny) not compiled into this library, or time-varying model";
+        default: return "unknown status code";
+    }
+}
+
+size_t ks_workspace_bytes(const ks_model* m, int64_t T, int purpose) {
+    const VTable* v = nullptr;
+    if (check_nx_ny(m, &v) || T < 1 || T > 0x7fffffffLL) return 0;
+    const Layout L = v->layout(T);
+    if (purpose == KS_WS_SMOOTH) return L.bytes_smooth;
+    if (purpose == KS_WS_ELEMENTS) return L.bytes_elements;
+    return 0;
+}
+
+int ks_workspace_init(void* ws, size_t ws_bytes, void* stream) {
+    if (!ws || ws_bytes < 256 || (reinterpret_cast<uintptr_t>(ws) & 255u) != 0) return KS_EINVAL;
+    return cudaMemsetAsync(ws, 0, 256, static_cast<cudaStream_t>(stream)) == cudaSuccess ? KS_OK : KS_ECUDA;
+}
+
+int ks_elements_layout_get(const ks_model* m, int64_t T, ks_elements_layout* out) {
+    const VTable* v = nullptr;
+    int rc = check_nx_ny(m, &v);
+    if (rc) return rc;
+    if (!out || T < 1 || T > 0x7fffffffLL) return KS_EINVAL;
+    const Layout L = v->layout(T);
+    const int64_t n = m->nx, f = 4 * L.ld;
+    out->ld = L.ld;
+    out->offset_A = (int64_t)L.off_elems;
+    out->offset_b = out->offset_A + n * n * f;
+    out->offset_C = out->offset_b + n * f;
+    out->offset_eta = out->offset_C + n * n * f;
+    out->offset_J = out->offset_eta + n * f;
+    return KS_OK;
+}
+
+int ks_build_elements(const ks_model* m, const float* y, int64_t T, void* ws, size_t ws_bytes, void* stream) {
+    const VTable* v = nullptr;
+    int rc = check_nx_ny(m, &v);
+    if (rc) return rc;
+    return v->build_elements(m, y, T, ws, ws_bytes, static_cast<cudaStream_t>(stream));
+}
+
+int ks_filter_scan(const ks_model* m, int64_t T, void* ws, size_t ws_bytes, float* fmean, float* fcov,
+                   void* stream) {
+    const VTable* v = nullptr;
+    int rc = check_nx_ny(m, &v);
+    if (rc) return rc;
+    return v->filter_scan(m, T, ws, ws_bytes, fmean, fcov, static_cast<cudaStream_t>(stream));
+}
+
+int ks_smooth_scan(const ks_model* m, int64_t T, const float* fmean, const float* fcov, void* ws,
+                   size_t ws_bytes, float* smean, float* scov, void* stream) {
+    const VTable* v = nullptr;
+    int rc = check_nx_ny(m, &v);
+    if (rc) return rc;
+    return v->smooth_scan(m, T, fmean, fcov, ws, ws_bytes, smean, scov, static_cast<cudaStream_t>(stream));
+}
+
+int ks_smooth(const ks_model* m, const float* y, int64_t T, void* ws, size_t ws_bytes, float* fmean,
+              float* fcov, float* smean, float* scov, void* stream) {
+    const VTable* v = nullptr;
+    int rc = check_nx_ny(m, &v);
+    if (rc) return rc;
+    return v->smooth(m, y, T, ws, ws_bytes, fmean, fcov, smean, scov, static_cast<cudaStream_t>(stream),
+                     nullptr);
+}
+
+int ks_smooth_traced(const ks_model* m, const float* y, int64_t T, void* ws, size_t ws_bytes, float* fmean,
+                     float* fcov, float* smean, float* scov, void* stream, void* const* events) {
+    const VTable* v = nullptr;
+    int rc = check_nx_ny(m, &v);
+    if (rc) return rc;
+    return v->smooth(m, y, T, ws, ws_bytes, fmean, fcov, smean, scov, static_cast<cudaStream_t>(stream),
+                     events);
+}
+
+int ks_status(void* ws, void* stream) {
+    if (!ws) return KS_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uint32_t h = 0;
+    if (cudaMemcpyAsync(&h, ws, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess) return KS_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return KS_ECUDA;
+    if (cudaMemsetAsync(ws, 0, sizeof(h), s) != cudaSuccess) return KS_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return KS_ECUDA;
+    if (h & ST_TIMEOUT) return KS_ETIMEOUT;
+    if (h & ST_NUMERIC) return KS_ENUMERIC;
+    return KS_OK;
+}
+
+static int combine_args(int nx, int64_t count, const float* l, const float* r, float* o, void* ws,
+                        size_t ws_bytes) {
+    if (nx < 1 || count < 0 || !ws || ws_bytes < 256 || (reinterpret_cast<uintptr_t>(ws) & 255u) != 0)
+        return KS_EINVAL;
+    if (count > 0 && (!l || !r || !o)) return KS_EINVAL;
+    return KS_OK;
+}
+
+int ks_filter_combine_batch(int nx, int64_t count, const float* left, const float* right, float* out,
+                            void* ws, size_t ws_bytes, void* stream) {
+    int rc = combine_args(nx, count, left, right, out, ws, ws_bytes);
+    if (rc) return rc;
+    const VTable* v = find_nx(nx);
+    if (!v) return KS_EUNSUPPORTED;
+    return v->fcomb_batch(count, left, right, out, ws, static_cast<cudaStream_t>(stream));
+}
+
+int ks_smoother_combine_batch(int nx, int64_t count, const float* left, const float* right, float* out,
+                              void* ws, size_t ws_bytes, void* stream) {
+    int rc = combine_args(nx, count, left, right, out, ws, ws_bytes);
+    if (rc) return rc;
+    const VTable* v = find_nx(nx);
+    if (!v) return KS_EUNSUPPORTED;
+    return v->scomb_batch(count, left, right, out, ws, static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,246 @@
+// ks_impl.cuh -- host side of one (nx, ny) instantiation: workspace layout,
+// argument checks and kernel launches behind the C ABI of include/ks.h.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "../../include/ks.h"
+#include "ks_scan.cuh"
+
+namespace ks {
+
+// Polls of a look-back flag before a wait is declared lost (sleeps grow to
+// ~1 us, so this is roughly one second).
+constexpr uint32_t kSpinLimit = 1000000u;
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct Layout {
+    int64_t T = 0, ld = 0;
+    int ntf = 0, nts = 0;
+    size_t off_const = 0, off_flags = 0, flags_bytes = 0;
+    size_t off_fagg = 0, off_fpre = 0, off_sagg = 0, off_spre = 0;
+    size_t off_elems = 0, off_fmean = 0, off_fcov = 0;
+    size_t bytes_smooth = 0, bytes_elements = 0;
+};
+
+// Function table of one instantiation.
+struct VTable {
+    int nx, ny;
+    Layout (*layout)(int64_t T);
+    int (*build_elements)(const ks_model*, const float*, int64_t, void*, size_t, cudaStream_t);
+    int (*filter_scan)(const ks_model*, int64_t, void*, size_t, float*, float*, cudaStream_t);
+    int (*smooth_scan)(const ks_model*, int64_t, const float*, const float*, void*, size_t, float*, float*,
+                       cudaStream_t);
+    int (*smooth)(const ks_model*, const float*, int64_t, void*, size_t, float*, float*, float*, float*,
+                  cudaStream_t, void* const*);
+    int (*fcomb_batch)(int64_t, const float*, const float*, float*, void*, cudaStream_t);
+    int (*scomb_batch)(int64_t, const float*, const float*, float*, void*, cudaStream_t);
+};
+
+inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+inline int launch_status() {
+    return cudaGetLastError() == cudaSuccess ? KS_OK : KS_ECUDA;
+}
+
+template <int N, int M>
+struct Impl {
+    static constexpr int FNT = 128, FCH = 16;   // forward scan: threads, steps per thread
+    static constexpr int SNT = 128, SCH = 16;   // reverse scan
+    static constexpr int64_t FTILE = (int64_t)FNT * FCH, STILE = (int64_t)SNT * SCH;
+    static constexpr int NCOMP = 3 * N * N + 2 * N;   // scalars of one filtering element
+
+    static Layout layout(int64_t T) {
+        Layout L;
+        L.T = T;
+        L.ld = (int64_t)align_up((size_t)T, 64);
+        L.ntf = (int)((T + FTILE - 1) / FTILE);
+        L.nts = (int)((T + STILE - 1) / STILE);
+        size_t off = 256;                                   // status word + reserved
+        L.off_const = off;
+        off = align_up(off + sizeof(ModelConst<N, M>), 256);
+        L.off_flags = off;                                  // [fcounter, scounter, 2 pad][fflags][sflags]
+        L.flags_bytes = 16 + 4 * (size_t)(L.ntf + L.nts);
+        off = align_up(off + L.flags_bytes, 256);
+        L.off_fagg = off;
+        off = align_up(off + sizeof(FElem<N>) * (size_t)L.ntf, 256);
+        L.off_fpre = off;
+        off = align_up(off + sizeof(FState<N>) * (size_t)L.ntf, 256);
+        L.off_sagg = off;
+        off = align_up(off + sizeof(SElem<N>) * (size_t)L.nts, 256);
+        L.off_spre = off;
+        off = align_up(off + sizeof(SState<N>) * (size_t)L.nts, 256);
+        L.bytes_smooth = off;
+        L.off_elems = off;
+        off = align_up(off + 4 * (size_t)NCOMP * (size_t)L.ld, 256);
+        L.off_fmean = off;
+        off = align_up(off + 4 * (size_t)N * (size_t)T, 256);
+        L.off_fcov = off;
+        off = align_up(off + 4 * (size_t)N * N * (size_t)T, 256);
+        L.bytes_elements = off;
+        return L;
+    }
+
+    static ModelConst<N, M>* mconst(void* ws, const Layout& L) {
+        return reinterpret_cast<ModelConst<N, M>*>(static_cast<char*>(ws) + L.off_const);
+    }
+    static uint32_t* status(void* ws) { return static_cast<uint32_t*>(ws); }
+
+    static ScanState fstate(void* ws, const Layout& L) {
+        char* b = static_cast<char*>(ws);
+        ScanState s;
+        s.counter = reinterpret_cast<uint32_t*>(b + L.off_flags);
+        s.flags = reinterpret_cast<uint32_t*>(b + L.off_flags + 16);
+        s.agg = reinterpret_cast<float*>(b + L.off_fagg);
+        s.pre = reinterpret_cast<float*>(b + L.off_fpre);
+        s.status = status(ws);
+        s.spin_limit = kSpinLimit;
+        return s;
+    }
+    static ScanState sstate(void* ws, const Layout& L) {
+        char* b = static_cast<char*>(ws);
+        ScanState s;
+        s.counter = reinterpret_cast<uint32_t*>(b + L.off_flags + 4);
+        s.flags = reinterpret_cast<uint32_t*>(b + L.off_flags + 16 + 4 * (size_t)L.ntf);
+        s.agg = reinterpret_cast<float*>(b + L.off_sagg);
+        s.pre = reinterpret_cast<float*>(b + L.off_spre);
+        s.status = status(ws);
+        s.spin_limit = kSpinLimit;
+        return s;
+    }
+
+    static int check_model(const ks_model* m) {
+        if (!m || !m->F || !m->Q || !m->H || !m->R || !m->m0 || !m->P0) return KS_EINVAL;
+        if (m->time_varying != 0) return KS_EUNSUPPORTED;
+        return KS_OK;
+    }
+
+    static int check_common(const ks_model* m, int64_t T, void* ws, size_t ws_bytes, size_t need) {
+        int rc = check_model(m);
+        if (rc) return rc;
+        if (T < 1 || T > 0x7fffffffLL) return KS_EINVAL;
+        if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) != 0 || ws_bytes < need) return KS_EINVAL;
+        return KS_OK;
+    }
+
+    static int prep(const ks_model* m, const float* y, void* ws, const Layout& L, cudaStream_t st) {
+        prep_kernel<N, M><<<1, 32, 0, st>>>(m->F, m->u, m->Q, m->H, m->d, m->R, m->m0, m->P0, y,
+                                            mconst(ws, L), status(ws));
+        return launch_status();
+    }
+
+    static int reset_flags(void* ws, const Layout& L, cudaStream_t st) {
+        return cudaMemsetAsync(static_cast<char*>(ws) + L.off_flags, 0, L.flags_bytes, st) == cudaSuccess
+                   ? KS_OK : KS_ECUDA;
+    }
+
+    static int launch_filter(void* ws, const Layout& L, const float* y, const float* el, float* fm,
+                             float* fc, bool from_y, cudaStream_t st) {
+        ScanState s = fstate(ws, L);
+        if (from_y)
+            filter_scan_kernel<N, M, FNT, FCH, true><<<L.ntf, FNT, 0, st>>>(mconst(ws, L), y, nullptr, L.ld,
+                                                                          L.T, fm, fc, s);
+        else
+            filter_scan_kernel<N, M, FNT, FCH, false><<<L.ntf, FNT, 0, st>>>(mconst(ws, L), nullptr, el, L.ld,
+                                                                           L.T, fm, fc, s);
+        return launch_status();
+    }
+
+    static int launch_smoother(void* ws, const Layout& L, const float* fm, const float* fc, float* sm,
+                               float* sc, cudaStream_t st) {
+        smoother_scan_kernel<N, M, SNT, SCH><<<L.nts, SNT, 0, st>>>(mconst(ws, L), fm, fc, L.T, sm, sc,
+                                                                   sstate(ws, L));
+        return launch_status();
+    }
+
+    static int build_elements(const ks_model* m, const float* y, int64_t T, void* ws, size_t ws_bytes,
+                              cudaStream_t st) {
+        const Layout L = layout(T);
+        int rc = check_common(m, T, ws, ws_bytes, L.bytes_elements);
+        if (rc) return rc;
+        if (!y || !aligned16(y)) return KS_EINVAL;
+        if ((rc = prep(m, y, ws, L, st))) return rc;
+        float* el = reinterpret_cast<float*>(static_cast<char*>(ws) + L.off_elems);
+        const int blocks = (int)std::min<int64_t>((T + 255) / 256, 152 * 8);
+        build_elements_kernel<N, M><<<blocks, 256, 0, st>>>(mconst(ws, L), y, T, el, L.ld);
+        return launch_status();
+    }
+
+    static int filter_scan(const ks_model* m, int64_t T, void* ws, size_t ws_bytes, float* fm, float* fc,
+                           cudaStream_t st) {
+        const Layout L = layout(T);
+        int rc = check_common(m, T, ws, ws_bytes, L.bytes_elements);
+        if (rc) return rc;
+        if (!fm || !fc || !aligned16(fm) || !aligned16(fc)) return KS_EINVAL;
+        if ((rc = reset_flags(ws, L, st))) return rc;
+        const float* el = reinterpret_cast<const float*>(static_cast<char*>(ws) + L.off_elems);
+        return launch_filter(ws, L, nullptr, el, fm, fc, false, st);
+    }
+
+    static int smooth_scan(const ks_model* m, int64_t T, const float* fm, const float* fc, void* ws,
+                           size_t ws_bytes, float* sm, float* sc, cudaStream_t st) {
+        const Layout L = layout(T);
+        int rc = check_common(m, T, ws, ws_bytes, L.bytes_smooth);
+        if (rc) return rc;
+        if (!fm || !fc || !sm || !sc || !aligned16(fm) || !aligned16(fc) || !aligned16(sm) || !aligned16(sc))
+            return KS_EINVAL;
+        if ((rc = prep(m, nullptr, ws, L, st))) return rc;
+        if ((rc = reset_flags(ws, L, st))) return rc;
+        return launch_smoother(ws, L, fm, fc, sm, sc, st);
+    }
+
+    static int record(void* const* ev, int i, cudaStream_t st) {
+        if (!ev || !ev[i]) return KS_OK;
+        return cudaEventRecord(static_cast<cudaEvent_t>(ev[i]), st) == cudaSuccess ? KS_OK : KS_ECUDA;
+    }
+
+    static int smooth(const ks_model* m, const float* y, int64_t T, void* ws, size_t ws_bytes, float* fm,
+                      float* fc, float* sm, float* sc, cudaStream_t st, void* const* ev) {
+        const Layout L = layout(T);
+        const bool own = (fm == nullptr) || (fc == nullptr);
+        int rc = check_common(m, T, ws, ws_bytes, own ? L.bytes_elements : L.bytes_smooth);
+        if (rc) return rc;
+        if (!y || !sm || !sc || !aligned16(y) || !aligned16(sm) || !aligned16(sc)) return KS_EINVAL;
+        if (own) {
+            fm = reinterpret_cast<float*>(static_cast<char*>(ws) + L.off_fmean);
+            fc = reinterpret_cast<float*>(static_cast<char*>(ws) + L.off_fcov);
+        } else if (!aligned16(fm) || !aligned16(fc)) {
+            return KS_EINVAL;
+        }
+        if ((rc = record(ev, 0, st))) return rc;
+        if ((rc = prep(m, y, ws, L, st))) return rc;
+        if ((rc = reset_flags(ws, L, st))) return rc;
+        if ((rc = record(ev, 1, st))) return rc;
+        if ((rc = launch_filter(ws, L, y, nullptr, fm, fc, true, st))) return rc;
+        if ((rc = record(ev, 2, st))) return rc;
+        if ((rc = launch_smoother(ws, L, fm, fc, sm, sc, st))) return rc;
+        return record(ev, 3, st);
+    }
+
+    static int fcomb_batch(int64_t count, const float* l, const float* r, float* o, void* ws, cudaStream_t st) {
+        if (count <= 0) return KS_OK;
+        const int blocks = (int)std::min<int64_t>((count + 127) / 128, 152 * 16);
+        filter_combine_batch_kernel<N><<<blocks, 128, 0, st>>>(l, r, o, count, status(ws));
+        return launch_status();
+    }
+
+    static int scomb_batch(int64_t count, const float* l, const float* r, float* o, void*, cudaStream_t st) {
+        if (count <= 0) return KS_OK;
+        const int blocks = (int)std::min<int64_t>((count + 127) / 128, 152 * 16);
+        smoother_combine_batch_kernel<N><<<blocks, 128, 0, st>>>(l, r, o, count);
+        return launch_status();
+    }
+
+    static constexpr VTable vtable() {
+        return VTable{N, M, &layout, &build_elements, &filter_scan, &smooth_scan, &smooth,
+                      &fcomb_batch, &scomb_batch};
+    }
+};
+
+// Registry (one entry per compiled (nx, ny)).
+const VTable* find_impl(int nx, int ny);
+
+}  // namespace ks

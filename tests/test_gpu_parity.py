@@ -1,0 +1,223 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Every comparison is element by element over all steps on seeded inputs.
+Tolerance: tests/parity.py (1e-4 normwise per step for FP32 at nx <= 8).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import lemmas as L
+import parity
+import pins
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ks():
+    from paper_1905_13002_gb300 import _build
+    _build.build()
+    import paper_1905_13002_gb300 as ks
+    return ks
+
+
+def gpu_model(ks, m):
+    return ks.Model.create(m.F, m.Q, m.H, m.R, m.m0, m.P0, u=m.u, d=m.d, device="cuda")
+
+
+def run_smooth(ks, m, y):
+    model = gpu_model(ks, m)
+    yt = torch.as_tensor(np.asarray(y), dtype=torch.float32, device="cuda")
+    ws = ks.alloc_workspace(model, yt.shape[0])
+    out = ks.smooth(model, yt, ws)
+    assert ks.status(ws) == ks.KS_OK
+    return out
+
+
+def check(ks, m, y, tol=parity.TOL):
+    got = run_smooth(ks, m, y)
+    ref = oracle.kf_rts(m, np.asarray(y, dtype=np.float64))
+    e = parity.errors(got, ref)
+    assert max(e.values()) < tol, e
+    return e
+
+
+# Sizes span one tile (2048 steps) and many, with ragged tails, and the
+# degenerate T = 1 and T = 2.
+@pytest.mark.parametrize("T", [1, 2, 3, 15, 16, 17, 33, 511, 2047, 2048, 2049, 4096, 4097, 6150, 20001])
+def test_tracking_model_sizes(ks, T):
+    seq = workloads.tracking_sequence(T, seed=1000 + T)
+    check(ks, seq.model, seq.y)
+
+
+def test_single_sequence_T1024(ks):
+    seq = workloads.config_single()
+    e = check(ks, seq.model, seq.y)
+    print("T=1024 errors", e)
+
+
+def test_long_sequence_T2pow20(ks):
+    seq = workloads.config_long()
+    e = check(ks, seq.model, seq.y)
+    print("T=2^20 errors", e)
+
+
+def test_paper_experiment_model(ks):
+    """Section V's printed parameters: sigma = 0.5 (R = 0.25 I), m0 = (0, 0, 1, -1)."""
+    rng = np.random.default_rng(77)
+    m = workloads.wiener_velocity(2, dt=0.1, q=1.0, r=0.25, m0=np.array([0.0, 0.0, 1.0, -1.0]))
+    _, y = workloads.simulate(m, 3000, rng)
+    check(ks, m, y)
+
+
+def test_random_model_with_offsets(ks):
+    """A dense random stable model with non-zero u and d."""
+    rng = np.random.default_rng(78)
+    m0 = workloads.random_stable(4, 2, rng)
+    m = workloads.make_model(m0.F, m0.Q, m0.H, m0.R, rng.standard_normal(4), 2.0 * np.eye(4),
+                             u=0.3 * rng.standard_normal(4), d=0.5 * rng.standard_normal(2))
+    _, y = workloads.simulate(m, 9000, rng)
+    check(ks, m, y)
+
+
+def test_materialised_elements_match_lemma3(ks):
+    seq = workloads.tracking_sequence(300, seed=5)
+    m = seq.model
+    model = gpu_model(ks, m)
+    y = torch.as_tensor(seq.y, dtype=torch.float32, device="cuda")
+    ws = ks.alloc_workspace(model, 300, ks.KS_WS_ELEMENTS)
+    ks.build_elements(model, y, ws)
+    assert ks.status(ws) == ks.KS_OK
+    got = {k: v.cpu().numpy().astype(np.float64) for k, v in ks.elements(model, 300, ws).items()}
+    ref = L.filter_elements(m, seq.y)
+    for name in ("A", "b", "C", "eta", "J"):
+        r = np.array([getattr(e, name) for e in ref])
+        scale = max(np.abs(r).max(), 1e-30)
+        assert np.abs(got[name] - r).max() / scale < 1e-5, name
+
+
+@pytest.mark.parametrize("T", [1, 2, 2049, 70000])
+def test_filter_scan_over_materialised_elements(ks, T):
+    seq = workloads.tracking_sequence(T, seed=2000 + T)
+    m = seq.model
+    model = gpu_model(ks, m)
+    y = torch.as_tensor(seq.y, dtype=torch.float32, device="cuda")
+    ws = ks.alloc_workspace(model, T, ks.KS_WS_ELEMENTS)
+    ks.build_elements(model, y, ws)
+    fm, fP = ks.filter_scan(model, T, ws)
+    assert ks.status(ws) == ks.KS_OK
+    rfm, rfP = oracle.kf(m, seq.y)
+    assert parity.mean_err(fm.cpu().numpy(), rfm, rfP) < parity.TOL
+    assert parity.cov_err(fP.cpu().numpy(), rfP) < parity.TOL
+
+
+@pytest.mark.parametrize("T", [1, 3, 2048, 50001])
+def test_smooth_scan_from_given_filtered_moments(ks, T):
+    """ks_smooth_scan on FP32 filtered moments vs the oracle's RTS pass on the
+    very same (FP32-rounded) moments."""
+    seq = workloads.tracking_sequence(T, seed=3000 + T)
+    m = seq.model
+    rfm, rfP = oracle.kf(m, seq.y)
+    fm32 = rfm.astype(np.float32)
+    fP32 = rfP.astype(np.float32)
+    rsm, rsP = oracle.rts(m, fm32.astype(np.float64), fP32.astype(np.float64))
+    model = gpu_model(ks, m)
+    sm, sP = ks.smooth_scan(model, torch.as_tensor(fm32, device="cuda"), torch.as_tensor(fP32, device="cuda"))
+    torch.cuda.synchronize()
+    assert parity.mean_err(sm.cpu().numpy(), rsm, rsP) < parity.TOL
+    assert parity.cov_err(sP.cpu().numpy(), rsP) < parity.TOL
+
+
+def _pack_f(e):
+    return np.concatenate([e.A.ravel(), e.b, e.C.ravel(), e.eta, e.J.ravel()])
+
+
+def _pack_s(e):
+    return np.concatenate([e.E.ravel(), e.g, e.L.ravel()])
+
+
+def test_filter_operator_batch_matches_lemma4(ks):
+    rng = np.random.default_rng(11)
+    n, cnt = 4, 500
+    lefts, rights, refs = [], [], []
+    for i in range(cnt):
+        a = L.FElem(rng.standard_normal((n, n)) / 2, rng.standard_normal(n), pins.rand_spd(n, rng, 0.5),
+                    rng.standard_normal(n), pins.rand_psd(n, rng, scale=0.7))
+        b = L.FElem(rng.standard_normal((n, n)) / 2, rng.standard_normal(n), pins.rand_spd(n, rng, 0.5),
+                    rng.standard_normal(n), pins.rand_psd(n, rng, rank=2, scale=0.7))
+        a32 = L.FElem(*(x.astype(np.float32).astype(np.float64) for x in a))
+        b32 = L.FElem(*(x.astype(np.float32).astype(np.float64) for x in b))
+        lefts.append(_pack_f(a32)); rights.append(_pack_f(b32)); refs.append(_pack_f(L.filter_combine(a32, b32)))
+    lt = torch.as_tensor(np.array(lefts), dtype=torch.float32, device="cuda")
+    rt = torch.as_tensor(np.array(rights), dtype=torch.float32, device="cuda")
+    out, ws = ks.filter_combine_batch(n, lt, rt)
+    assert ks.status(ws) == ks.KS_OK
+    got = out.cpu().numpy().astype(np.float64)
+    ref = np.array(refs)
+    rel = np.abs(got - ref).max(1) / np.abs(ref).max(1)
+    assert rel.max() < 1e-4, rel.max()
+
+
+def test_smoother_operator_batch_matches_lemma6(ks):
+    rng = np.random.default_rng(12)
+    n, cnt = 4, 500
+    lefts, rights, refs = [], [], []
+    for i in range(cnt):
+        a = L.SElem(rng.standard_normal((n, n)) / 2, rng.standard_normal(n), pins.rand_spd(n, rng))
+        b = L.SElem(rng.standard_normal((n, n)) / 2, rng.standard_normal(n), pins.rand_spd(n, rng))
+        a32 = L.SElem(*(x.astype(np.float32).astype(np.float64) for x in a))
+        b32 = L.SElem(*(x.astype(np.float32).astype(np.float64) for x in b))
+        lefts.append(_pack_s(a32)); rights.append(_pack_s(b32)); refs.append(_pack_s(L.smoother_combine(a32, b32)))
+    lt = torch.as_tensor(np.array(lefts), dtype=torch.float32, device="cuda")
+    rt = torch.as_tensor(np.array(rights), dtype=torch.float32, device="cuda")
+    out, _ = ks.smoother_combine_batch(n, lt, rt)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().astype(np.float64)
+    ref = np.array(refs)
+    rel = np.abs(got - ref).max(1) / np.abs(ref).max(1)
+    assert rel.max() < 1e-5, rel.max()
+
+
+def test_non_finite_measurement_is_reported(ks):
+    seq = workloads.tracking_sequence(5000, seed=4)
+    y = seq.y.copy()
+    y[1234, 0] = np.nan
+    model = gpu_model(ks, seq.model)
+    yt = torch.as_tensor(y, dtype=torch.float32, device="cuda")
+    ws = ks.alloc_workspace(model, 5000)
+    ks.smooth(model, yt, ws)
+    assert ks.status(ws) == ks.KS_ENUMERIC
+    assert ks.status(ws) == ks.KS_OK          # the status word was cleared
+
+
+def test_bad_arguments_raise(ks):
+    seq = workloads.tracking_sequence(100, seed=4)
+    model = gpu_model(ks, seq.model)
+    y = torch.as_tensor(seq.y, dtype=torch.float32, device="cuda")
+    small = torch.zeros(256, dtype=torch.uint8, device="cuda")
+    with pytest.raises(ks.KsError) as ei:
+        ks.smooth(model, y, small)
+    assert ei.value.code == ks.KS_EINVAL
+    mis = torch.empty(2 * 100 + 1, dtype=torch.float32, device="cuda")[1:].view(100, 2)
+    with pytest.raises(ks.KsError) as ei:
+        ks.smooth(model, mis)
+    assert ei.value.code == ks.KS_EINVAL
+
+
+def test_repeated_calls_agree(ks):
+    """Two calls on the same workspace agree (the look-back may combine tiles
+    in a different grouping from run to run, so agreement is to rounding)."""
+    seq = workloads.tracking_sequence(100000, seed=6)
+    model = gpu_model(ks, seq.model)
+    y = torch.as_tensor(seq.y, dtype=torch.float32, device="cuda")
+    ws = ks.alloc_workspace(model, 100000)
+    a = [t.clone() for t in ks.smooth(model, y, ws)]
+    b = ks.smooth(model, y, ws)
+    assert ks.status(ws) == ks.KS_OK
+    ref = oracle.kf_rts(seq.model, seq.y)
+    ea = parity.errors(a, ref)
+    eb = parity.errors(b, ref)
+    assert max(ea.values()) < parity.TOL and max(eb.values()) < parity.TOL
