@@ -21,7 +21,7 @@ struct Layout {
     int64_t T = 0, ld = 0;
     int ntf = 0, nts = 0;
     size_t off_const = 0, off_flags = 0, flags_bytes = 0;
-    size_t off_fagg = 0, off_fpre = 0, off_sagg = 0, off_spre = 0;
+    size_t off_fagg = 0, off_fpre = 0, off_sagg = 0, off_spre = 0, off_sblk = 0;
     size_t off_elems = 0, off_fmean = 0, off_fcov = 0;
     size_t bytes_smooth = 0, bytes_elements = 0;
 };
@@ -48,8 +48,8 @@ inline int launch_status() {
 
 template <int N, int M>
 struct Impl {
-    static constexpr int FNT = 128, FCH = 16;   // forward scan: threads, steps per thread
-    static constexpr int SNT = 128, SCH = 16;   // reverse scan
+    static constexpr int FNT = 128, FCH = 32;   // forward scan: threads, steps per thread
+    static constexpr int SNT = 128, SCH = FCH;  // reverse scan (same block grid)
     static constexpr int64_t FTILE = (int64_t)FNT * FCH, STILE = (int64_t)SNT * SCH;
     static constexpr int NCOMP = 3 * N * N + 2 * N;   // scalars of one filtering element
 
@@ -73,6 +73,8 @@ struct Impl {
         off = align_up(off + sizeof(SElem<N>) * (size_t)L.nts, 256);
         L.off_spre = off;
         off = align_up(off + sizeof(SState<N>) * (size_t)L.nts, 256);
+        L.off_sblk = off;                                   // smoothing aggregate per forward block
+        off = align_up(off + sizeof(SElem<N>) * (size_t)((T + FCH - 1) / FCH), 256);
         L.bytes_smooth = off;
         L.off_elems = off;
         off = align_up(off + 4 * (size_t)NCOMP * (size_t)L.ld, 256);
@@ -126,9 +128,12 @@ struct Impl {
         return KS_OK;
     }
 
+    // Model constants (and the k = 1 element when y is given); also zeroes the
+    // scans' tile counters and flags, which every scan launch needs.
     static int prep(const ks_model* m, const float* y, void* ws, const Layout& L, cudaStream_t st) {
-        prep_kernel<N, M><<<1, 32, 0, st>>>(m->F, m->u, m->Q, m->H, m->d, m->R, m->m0, m->P0, y,
-                                            mconst(ws, L), status(ws));
+        uint32_t* z = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + L.off_flags);
+        prep_kernel<N, M><<<1, 128, 0, st>>>(m->F, m->u, m->Q, m->H, m->d, m->R, m->m0, m->P0, y,
+                                             mconst(ws, L), status(ws), z, (int)(L.flags_bytes / 4));
         return launch_status();
     }
 
@@ -137,22 +142,48 @@ struct Impl {
                    ? KS_OK : KS_ECUDA;
     }
 
+    // Dynamic shared memory above 48 KB needs an explicit opt-in per kernel.
+    template <class K>
+    static bool allow_smem(K kernel, int bytes) {
+        return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess;
+    }
+
+    static float* sblk(void* ws, const Layout& L) {
+        return reinterpret_cast<float*>(static_cast<char*>(ws) + L.off_sblk);
+    }
+
     static int launch_filter(void* ws, const Layout& L, const float* y, const float* el, float* fm,
                              float* fc, bool from_y, cudaStream_t st) {
         ScanState s = fstate(ws, L);
-        if (from_y)
-            filter_scan_kernel<N, M, FNT, FCH, true><<<L.ntf, FNT, 0, st>>>(mconst(ws, L), y, nullptr, L.ld,
-                                                                          L.T, fm, fc, s);
-        else
-            filter_scan_kernel<N, M, FNT, FCH, false><<<L.ntf, FNT, 0, st>>>(mconst(ws, L), nullptr, el, L.ld,
-                                                                           L.T, fm, fc, s);
+        constexpr int smem = filter_dyn_smem<N, FNT>();
+        if (from_y) {   // fused path: also folds the smoothing block aggregates
+            auto k = filter_scan_kernel<N, M, FNT, FCH, true, true>;
+            static const bool ok = allow_smem(k, smem);
+            if (!ok) return KS_ECUDA;
+            k<<<L.ntf, FNT, smem, st>>>(mconst(ws, L), y, nullptr, L.ld, L.T, fm, fc, s, sblk(ws, L));
+        } else {
+            auto k = filter_scan_kernel<N, M, FNT, FCH, false, false>;
+            static const bool ok = allow_smem(k, smem);
+            if (!ok) return KS_ECUDA;
+            k<<<L.ntf, FNT, smem, st>>>(mconst(ws, L), nullptr, el, L.ld, L.T, fm, fc, s, nullptr);
+        }
         return launch_status();
     }
 
     static int launch_smoother(void* ws, const Layout& L, const float* fm, const float* fc, float* sm,
-                               float* sc, cudaStream_t st) {
-        smoother_scan_kernel<N, M, SNT, SCH><<<L.nts, SNT, 0, st>>>(mconst(ws, L), fm, fc, L.T, sm, sc,
-                                                                   sstate(ws, L));
+                               float* sc, bool from_agg, cudaStream_t st) {
+        constexpr int smem = smoother_dyn_smem<N, SNT>();
+        if (from_agg) {
+            auto k = smoother_scan_kernel<N, M, SNT, SCH, true>;
+            static const bool ok = allow_smem(k, smem);
+            if (!ok) return KS_ECUDA;
+            k<<<L.nts, SNT, smem, st>>>(mconst(ws, L), fm, fc, L.T, sm, sc, sstate(ws, L), sblk(ws, L));
+        } else {
+            auto k = smoother_scan_kernel<N, M, SNT, SCH, false>;
+            static const bool ok = allow_smem(k, smem);
+            if (!ok) return KS_ECUDA;
+            k<<<L.nts, SNT, smem, st>>>(mconst(ws, L), fm, fc, L.T, sm, sc, sstate(ws, L), nullptr);
+        }
         return launch_status();
     }
 
@@ -188,8 +219,7 @@ struct Impl {
         if (!fm || !fc || !sm || !sc || !aligned16(fm) || !aligned16(fc) || !aligned16(sm) || !aligned16(sc))
             return KS_EINVAL;
         if ((rc = prep(m, nullptr, ws, L, st))) return rc;
-        if ((rc = reset_flags(ws, L, st))) return rc;
-        return launch_smoother(ws, L, fm, fc, sm, sc, st);
+        return launch_smoother(ws, L, fm, fc, sm, sc, false, st);
     }
 
     static int record(void* const* ev, int i, cudaStream_t st) {
@@ -212,11 +242,10 @@ struct Impl {
         }
         if ((rc = record(ev, 0, st))) return rc;
         if ((rc = prep(m, y, ws, L, st))) return rc;
-        if ((rc = reset_flags(ws, L, st))) return rc;
         if ((rc = record(ev, 1, st))) return rc;
         if ((rc = launch_filter(ws, L, y, nullptr, fm, fc, true, st))) return rc;
         if ((rc = record(ev, 2, st))) return rc;
-        if ((rc = launch_smoother(ws, L, fm, fc, sm, sc, st))) return rc;
+        if ((rc = launch_smoother(ws, L, fm, fc, sm, sc, true, st))) return rc;
         return record(ev, 3, st);
     }
 

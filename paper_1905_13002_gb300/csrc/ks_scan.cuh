@@ -19,6 +19,7 @@
 // status word and the kernel finishes with a zero prefix instead of hanging.
 #pragma once
 
+#include "ks_async.cuh"
 #include "ks_ops.cuh"
 
 namespace ks {
@@ -44,6 +45,26 @@ KS_DEV T shfl_up_t(const T& x, int d) {
     float* py = reinterpret_cast<float*>(&y);
 #pragma unroll
     for (int i = 0; i < (int)(sizeof(T) / 4); ++i) py[i] = __shfl_up_sync(kFull, px[i], d);
+    return y;
+}
+
+template <class T>
+KS_DEV T shfl_down_t(const T& x, int d) {
+    T y;
+    const float* px = reinterpret_cast<const float*>(&x);
+    float* py = reinterpret_cast<float*>(&y);
+#pragma unroll
+    for (int i = 0; i < (int)(sizeof(T) / 4); ++i) py[i] = __shfl_down_sync(kFull, px[i], d);
+    return y;
+}
+
+template <class T>
+KS_DEV T shfl_t(const T& x, int src) {
+    T y;
+    const float* px = reinterpret_cast<const float*>(&x);
+    float* py = reinterpret_cast<float*>(&y);
+#pragma unroll
+    for (int i = 0; i < (int)(sizeof(T) / 4); ++i) py[i] = __shfl_sync(kFull, px[i], src);
     return y;
 }
 
@@ -194,188 +215,207 @@ KS_DEV void load_const(const ModelConst<N, M>* __restrict__ g, ModelConst<N, M>&
 }
 
 // ---------------------------------------------------------------- prep
-// Model constants.  k > 1 quantities in FP32 (Lemma 3 with the Cholesky
-// factor of S); the k = 1 element (Kalman prediction and update from
-// N(m0, P0), Lemma 3) in FP64.  One thread: the work is O(N^3).
+// Model constants, one thread block.  k > 1 quantities in FP32 (Lemma 3 with
+// the Cholesky factor of S); the k = 1 element (Kalman prediction and update
+// from N(m0, P0), Lemma 3) in FP64.  Every matrix product is spread over the
+// block, one output entry per thread, so the FP64 chain is a few products
+// deep.  The block also zeroes the scans' tile counters and flags.
 template <int N, int M>
-__global__ void prep_kernel(const float* __restrict__ F, const float* __restrict__ u,
-                            const float* __restrict__ Q, const float* __restrict__ H,
-                            const float* __restrict__ d, const float* __restrict__ R,
-                            const double* __restrict__ m0, const double* __restrict__ P0,
-                            const float* __restrict__ y, ModelConst<N, M>* __restrict__ out,
-                            uint32_t* __restrict__ status) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    ModelConst<N, M> mc;
-    bool ok = true;
-    float Hm[M][N], Fm[N][N], Qs[N][N], Rs[M][M], uv[N], dv[M];
-    for (int a = 0; a < N; ++a) {
-        uv[a] = u ? u[a] : 0.f;
-        for (int b = 0; b < N; ++b) { Fm[a][b] = F[a * N + b]; Qs[a][b] = Q[a * N + b]; }
+struct PrepSmem {
+    float F[N][N], Q[N][N], H[M][N], R[M][M], u[N], d[M];
+    float HQ[M][N], HF[M][N], S[M][M], Lsi[M][M], tmp[M][N], K[N][M];
+    double m0[N], P0[N][N], mm[N], FP[N][N], Pm[N][N], HP[M][N], S1[M][M], L1[M][M], t1[M][N], e1[M],
+        z[M];
+    int ok;
+};
+
+template <int N, int M>
+__global__ void __launch_bounds__(128) prep_kernel(const float* __restrict__ F, const float* __restrict__ u,
+                                                   const float* __restrict__ Q, const float* __restrict__ H,
+                                                   const float* __restrict__ d, const float* __restrict__ R,
+                                                   const double* __restrict__ m0, const double* __restrict__ P0,
+                                                   const float* __restrict__ y, ModelConst<N, M>* __restrict__ out,
+                                                   uint32_t* __restrict__ status, uint32_t* __restrict__ zero,
+                                                   int nzero) {
+    __shared__ PrepSmem<N, M> p;
+    __shared__ ModelConst<N, M> mc;
+    const int t = threadIdx.x, nt = blockDim.x;
+    for (int i = t; i < nzero; i += nt) zero[i] = 0u;
+    if (t == 0) p.ok = 1;
+    for (int e = t; e < N * N; e += nt) {
+        const int a = e / N, b = e % N;
+        p.F[a][b] = F[e];
+        p.Q[a][b] = 0.5f * (Q[a * N + b] + Q[b * N + a]);
+        p.P0[a][b] = P0[e];
     }
-    for (int q = 0; q < M; ++q) {
-        dv[q] = d ? d[q] : 0.f;
-        for (int a = 0; a < N; ++a) Hm[q][a] = H[q * N + a];
-        for (int p = 0; p < M; ++p) Rs[q][p] = R[q * M + p];
+    for (int e = t; e < M * N; e += nt) p.H[e / N][e % N] = H[e];
+    for (int e = t; e < M * M; e += nt) {
+        const int a = e / M, b = e % M;
+        p.R[a][b] = 0.5f * (R[a * M + b] + R[b * M + a]);
     }
-    for (int a = 0; a < N; ++a) {
-        mc.u[a] = uv[a];
-        for (int b = 0; b < N; ++b) mc.F[a * N + b] = Fm[a][b];
-        for (int b = 0; b <= a; ++b) mc.Q[sidx(a, b)] = 0.5f * (Qs[a][b] + Qs[b][a]);
+    for (int e = t; e < N; e += nt) { p.u[e] = u ? u[e] : 0.f; p.m0[e] = m0[e]; }
+    for (int e = t; e < M; e += nt) p.d[e] = d ? d[e] : 0.f;
+    __syncthreads();
+    // ---- FP32, k > 1: HQ = H Q, HF = H F, and the FP64 k = 1 prediction
+    for (int e = t; e < M * N; e += nt) {
+        const int q = e / N, a = e % N;
+        float s = 0.f, h = 0.f;
+        for (int c = 0; c < N; ++c) { s = fmaf(p.H[q][c], p.Q[c][a], s); h = fmaf(p.H[q][c], p.F[c][a], h); }
+        p.HQ[q][a] = s;
+        p.HF[q][a] = h;
     }
-    // S = H Q H^T + R, S = Ls Ls^T, Lsi = Ls^{-1}
-    float HQ[M][N], S[M][M], Ls[M][M], Lsi[M][M];
-    for (int q = 0; q < M; ++q)
-        for (int a = 0; a < N; ++a) {
-            float s = 0.f;
-            for (int c = 0; c < N; ++c) s = fmaf(Hm[q][c], mc.Q[sidx(c, a)], s);
-            HQ[q][a] = s;
-        }
-    for (int q = 0; q < M; ++q)
-        for (int p = 0; p < M; ++p) {
-            float s = 0.5f * (Rs[q][p] + Rs[p][q]);
-            for (int c = 0; c < N; ++c) s = fmaf(HQ[q][c], Hm[p][c], s);
-            S[q][p] = s;
-        }
-    for (int j = 0; j < M; ++j) {
-        float s = S[j][j];
-        for (int l = 0; l < j; ++l) s -= Ls[j][l] * Ls[j][l];
-        ok = ok && (s > 0.f);
-        Ls[j][j] = sqrtf(fmaxf(s, 1e-37f));
-        for (int i = j + 1; i < M; ++i) {
-            float t = S[i][j];
-            for (int l = 0; l < j; ++l) t -= Ls[i][l] * Ls[j][l];
-            Ls[i][j] = t / Ls[j][j];
-        }
-        for (int i = 0; i < j; ++i) Ls[i][j] = 0.f;
+    for (int e = t; e < N * N; e += nt) {          // FP = F P0
+        const int a = e / N, b = e % N;
+        double s = 0.0;
+        for (int c = 0; c < N; ++c) s += (double)p.F[a][c] * p.P0[c][b];
+        p.FP[a][b] = s;
     }
-    for (int c = 0; c < M; ++c)
-        for (int i = 0; i < M; ++i) {
-            if (i < c) { Lsi[i][c] = 0.f; continue; }
-            float t = (i == c) ? 1.f : 0.f;
-            for (int l = c; l < i; ++l) t -= Ls[i][l] * Lsi[l][c];
-            Lsi[i][c] = t / Ls[i][i];
-        }
-    // tmp = Lsi H Q  (so K = tmp^T Lsi and K S K^T = tmp^T tmp)
-    float tmp[M][N], HF[M][N];
-    for (int q = 0; q < M; ++q)
-        for (int a = 0; a < N; ++a) {
-            float s = 0.f, h = 0.f;
-            for (int p = 0; p <= q; ++p) s = fmaf(Lsi[q][p], HQ[p][a], s);
-            for (int c = 0; c < N; ++c) h = fmaf(Hm[q][c], Fm[c][a], h);
-            tmp[q][a] = s;
-            HF[q][a] = h;
-        }
-    float K[N][M];
-    for (int a = 0; a < N; ++a)
-        for (int q = 0; q < M; ++q) {
-            float s = 0.f;
-            for (int p = q; p < M; ++p) s = fmaf(tmp[p][a], Lsi[p][q], s);
-            K[a][q] = s;
-            mc.K[a * M + q] = s;
-        }
-    for (int q = 0; q < M; ++q) {
-        for (int p = 0; p < M; ++p) mc.Lsi[q * M + p] = Lsi[q][p];
-        float s = dv[q];
-        for (int c = 0; c < N; ++c) s = fmaf(Hm[q][c], uv[c], s);
-        mc.hud[q] = s;
-        for (int a = 0; a < N; ++a) {
-            float t = 0.f;
-            for (int p = 0; p <= q; ++p) t = fmaf(Lsi[q][p], HF[p][a], t);
-            mc.U[q * N + a] = t;
-        }
+    for (int e = t; e < N; e += nt) {              // m- = F m0 + u
+        double s = p.u[e];
+        for (int c = 0; c < N; ++c) s += (double)p.F[e][c] * p.m0[c];
+        p.mm[e] = s;
     }
-    for (int a = 0; a < N; ++a)
-        for (int b = 0; b < N; ++b) {
-            float s = Fm[a][b];
-            for (int q = 0; q < M; ++q) s = fmaf(-K[a][q], HF[q][b], s);
-            mc.A[a * N + b] = s;
-        }
-    for (int a = 0; a < N; ++a)
-        for (int b = 0; b <= a; ++b) {
-            float s = mc.Q[sidx(a, b)];
-            for (int q = 0; q < M; ++q) s = fmaf(-tmp[q][a], tmp[q][b], s);
-            mc.C[sidx(a, b)] = s;
-        }
-    // ---- k = 1 in FP64: m- = F m0 + u, P- = F P0 F^T + Q, S1 = H P- H^T + R,
-    //      K1 = P- H^T S1^{-1}, b1 = m- + K1 (y1 - H m- - d), C1 = P- - K1 S1 K1^T
-    //      (skipped when no measurements are given: the smoother needs none of it)
-    for (int a = 0; a < N; ++a) mc.b1[a] = 0.f;
-    for (int a = 0; a < sym_size(N); ++a) mc.C1[a] = 0.f;
-    if (y != nullptr) {
-        double mm[N], FP[N][N], Pm[N][N], HP[M][N], S1[M][M], L1[M][M], t1[M][N], e1[M], z[M];
-        for (int a = 0; a < N; ++a) {
-            double s = uv[a];
-            for (int c = 0; c < N; ++c) s += (double)Fm[a][c] * m0[c];
-            mm[a] = s;
-        }
-        for (int a = 0; a < N; ++a)
-            for (int b = 0; b < N; ++b) {
-                double s = 0.0;
-                for (int c = 0; c < N; ++c) s += (double)Fm[a][c] * P0[c * N + b];
-                FP[a][b] = s;
-            }
-        for (int a = 0; a < N; ++a)
-            for (int b = 0; b < N; ++b) {
-                double s = 0.5 * ((double)Qs[a][b] + (double)Qs[b][a]);
-                for (int c = 0; c < N; ++c) s += FP[a][c] * (double)Fm[b][c];
-                Pm[a][b] = s;
-            }
-        for (int q = 0; q < M; ++q)
-            for (int a = 0; a < N; ++a) {
-                double s = 0.0;
-                for (int c = 0; c < N; ++c) s += (double)Hm[q][c] * Pm[c][a];
-                HP[q][a] = s;
-            }
-        for (int q = 0; q < M; ++q)
-            for (int p = 0; p < M; ++p) {
-                double s = 0.5 * ((double)Rs[q][p] + (double)Rs[p][q]);
-                for (int c = 0; c < N; ++c) s += HP[q][c] * (double)Hm[p][c];
-                S1[q][p] = s;
-            }
+    __syncthreads();
+    for (int e = t; e < M * M; e += nt) {          // S = H Q H^T + R
+        const int q = e / M, r = e % M;
+        float s = p.R[q][r];
+        for (int c = 0; c < N; ++c) s = fmaf(p.HQ[q][c], p.H[r][c], s);
+        p.S[q][r] = s;
+    }
+    for (int e = t; e < N * N; e += nt) {          // P- = F P0 F^T + Q
+        const int a = e / N, b = e % N;
+        double s = 0.5 * ((double)p.Q[a][b] + (double)p.Q[b][a]);
+        for (int c = 0; c < N; ++c) s += p.FP[a][c] * (double)p.F[b][c];
+        p.Pm[a][b] = s;
+    }
+    __syncthreads();
+    if (t == 0) {                                  // Cholesky of S, L_S^{-1}
+        float Ls[M][M];
+        bool ok = true;
         for (int j = 0; j < M; ++j) {
-            double s = S1[j][j];
-            for (int l = 0; l < j; ++l) s -= L1[j][l] * L1[j][l];
-            ok = ok && (s > 0.0);
-            L1[j][j] = sqrt(s > 0.0 ? s : 1e-300);
+            float s = p.S[j][j];
+            for (int l = 0; l < j; ++l) s -= Ls[j][l] * Ls[j][l];
+            ok = ok && (s > 0.f);
+            Ls[j][j] = sqrtf(fmaxf(s, 1e-37f));
             for (int i = j + 1; i < M; ++i) {
-                double t = S1[i][j];
-                for (int l = 0; l < j; ++l) t -= L1[i][l] * L1[j][l];
-                L1[i][j] = t / L1[j][j];
+                float q = p.S[i][j];
+                for (int l = 0; l < j; ++l) q -= Ls[i][l] * Ls[j][l];
+                Ls[i][j] = q / Ls[j][j];
             }
         }
-        // t1 = L1^{-1} H P-  (K1 S1 K1^T = t1^T t1),  z = L1^{-1} e1
-        for (int a = 0; a < N; ++a)
+        for (int c = 0; c < M; ++c)
+            for (int i = 0; i < M; ++i) {
+                if (i < c) { p.Lsi[i][c] = 0.f; continue; }
+                float q = (i == c) ? 1.f : 0.f;
+                for (int l = c; l < i; ++l) q -= Ls[i][l] * p.Lsi[l][c];
+                p.Lsi[i][c] = q / Ls[i][i];
+            }
+        if (!ok) p.ok = 0;
+    }
+    for (int e = t; e < M * N; e += nt) {          // HP = H P-
+        const int q = e / N, a = e % N;
+        double s = 0.0;
+        for (int c = 0; c < N; ++c) s += (double)p.H[q][c] * p.Pm[c][a];
+        p.HP[q][a] = s;
+    }
+    __syncthreads();
+    for (int e = t; e < M * N; e += nt) {          // tmp = L_S^{-1} H Q, U = L_S^{-1} H F
+        const int q = e / N, a = e % N;
+        float s = 0.f, v = 0.f;
+        for (int r = 0; r <= q; ++r) { s = fmaf(p.Lsi[q][r], p.HQ[r][a], s); v = fmaf(p.Lsi[q][r], p.HF[r][a], v); }
+        p.tmp[q][a] = s;
+        mc.U[q * N + a] = v;
+    }
+    for (int e = t; e < M * M; e += nt) {          // S1 = H P- H^T + R
+        const int q = e / M, r = e % M;
+        double s = 0.5 * ((double)p.R[q][r] + (double)p.R[r][q]);
+        for (int c = 0; c < N; ++c) s += p.HP[q][c] * (double)p.H[r][c];
+        p.S1[q][r] = s;
+    }
+    for (int e = t; e < M; e += nt) {
+        float s = p.d[e];
+        for (int c = 0; c < N; ++c) s = fmaf(p.H[e][c], p.u[c], s);
+        mc.hud[e] = s;
+        for (int r = 0; r < M; ++r) mc.Lsi[e * M + r] = p.Lsi[e][r];
+    }
+    __syncthreads();
+    for (int e = t; e < N * M; e += nt) {          // K = tmp^T L_S^{-1}
+        const int a = e / M, q = e % M;
+        float s = 0.f;
+        for (int r = q; r < M; ++r) s = fmaf(p.tmp[r][a], p.Lsi[r][q], s);
+        p.K[a][q] = s;
+        mc.K[a * M + q] = s;
+    }
+    if (t == 0 && y != nullptr) {                  // FP64 Cholesky of S1 and the innovation solve
+        bool ok = true;
+        for (int j = 0; j < M; ++j) {
+            double s = p.S1[j][j];
+            for (int l = 0; l < j; ++l) s -= p.L1[j][l] * p.L1[j][l];
+            ok = ok && (s > 0.0);
+            p.L1[j][j] = sqrt(s > 0.0 ? s : 1e-300);
+            for (int i = j + 1; i < M; ++i) {
+                double q = p.S1[i][j];
+                for (int l = 0; l < j; ++l) q -= p.L1[i][l] * p.L1[j][l];
+                p.L1[i][j] = q / p.L1[j][j];
+            }
+        }
+        for (int q = 0; q < M; ++q) {
+            double s = (double)y[q] - (double)p.d[q];
+            for (int c = 0; c < N; ++c) s -= (double)p.H[q][c] * p.mm[c];
+            for (int l = 0; l < q; ++l) s -= p.L1[q][l] * p.z[l];
+            p.z[q] = s / p.L1[q][q];
+        }
+        if (!ok) p.ok = 0;
+    }
+    __syncthreads();
+    for (int e = t; e < N * N; e += nt) {          // A = F - K H F ; C = Q - tmp^T tmp ; copies
+        const int a = e / N, b = e % N;
+        float s = p.F[a][b];
+        for (int q = 0; q < M; ++q) s = fmaf(-p.K[a][q], p.HF[q][b], s);
+        mc.A[a * N + b] = s;
+        mc.F[a * N + b] = p.F[a][b];
+        if (b <= a) {
+            float c = p.Q[a][b];
+            for (int q = 0; q < M; ++q) c = fmaf(-p.tmp[q][a], p.tmp[q][b], c);
+            mc.C[sidx(a, b)] = c;
+            mc.Q[sidx(a, b)] = p.Q[a][b];
+        }
+    }
+    for (int e = t; e < N; e += nt) mc.u[e] = p.u[e];
+    if (y != nullptr) {
+        for (int a = t; a < N; a += nt) {          // t1 = L1^{-1} H P- (column a)
             for (int q = 0; q < M; ++q) {
-                double t = HP[q][a];
-                for (int l = 0; l < q; ++l) t -= L1[q][l] * t1[l][a];
-                t1[q][a] = t / L1[q][q];
+                double s = p.HP[q][a];
+                for (int l = 0; l < q; ++l) s -= p.L1[q][l] * p.t1[l][a];
+                p.t1[q][a] = s / p.L1[q][q];
             }
-        for (int q = 0; q < M; ++q) {
-            double s = (double)y[q] - (double)dv[q];
-            for (int c = 0; c < N; ++c) s -= (double)Hm[q][c] * mm[c];
-            e1[q] = s;
         }
-        for (int q = 0; q < M; ++q) {
-            double t = e1[q];
-            for (int l = 0; l < q; ++l) t -= L1[q][l] * z[l];
-            z[q] = t / L1[q][q];
-        }
-        // b1 = m- + K1 e1 = m- + t1^T z   (K1 = t1^T L1^{-1})
-        for (int a = 0; a < N; ++a) {
-            double s = mm[a];
-            for (int q = 0; q < M; ++q) s += t1[q][a] * z[q];
-            mc.b1[a] = (float)s;
-        }
-        for (int a = 0; a < N; ++a)
-            for (int b = 0; b <= a; ++b) {
-                double s = 0.5 * (Pm[a][b] + Pm[b][a]);
-                for (int q = 0; q < M; ++q) s -= t1[q][a] * t1[q][b];
+        __syncthreads();
+        for (int e = t; e < N * N; e += nt) {      // b1 = m- + t1^T z ; C1 = P- - t1^T t1
+            const int a = e / N, b = e % N;
+            if (b == 0) {
+                double s = p.mm[a];
+                for (int q = 0; q < M; ++q) s += p.t1[q][a] * p.z[q];
+                mc.b1[a] = (float)s;
+            }
+            if (b <= a) {
+                double s = 0.5 * (p.Pm[a][b] + p.Pm[b][a]);
+                for (int q = 0; q < M; ++q) s -= p.t1[q][a] * p.t1[q][b];
                 mc.C1[sidx(a, b)] = (float)s;
             }
+        }
+    } else {
+        for (int e = t; e < N; e += nt) mc.b1[e] = 0.f;
+        for (int e = t; e < sym_size(N); e += nt) mc.C1[e] = 0.f;
     }
-    for (int i = 0; i < 4; ++i) mc.pad[i] = 0.f;
-    *out = mc;
-    if (!ok) atomicOr(status, ST_NUMERIC);
+    if (t < 4) mc.pad[t] = 0.f;
+    __syncthreads();
+    {
+        const float* src = reinterpret_cast<const float*>(&mc);
+        float* dst = reinterpret_cast<float*>(out);
+        for (int i = t; i < (int)(sizeof(ModelConst<N, M>) / 4); i += nt) dst[i] = src[i];
+    }
+    if (t == 0 && !p.ok) atomicOr(status, ST_NUMERIC);
 }
 
 // ---------------------------------------------------------------- Lemma 3 materialised
@@ -417,20 +457,309 @@ __global__ void __launch_bounds__(256) build_elements_kernel(const ModelConst<N,
     }
 }
 
+// ---------------------------------------------------------------- staging
+// Outputs (and, for the reverse scan, inputs) of each thread's block of steps
+// are staged in shared memory in groups of G steps and moved with per-thread
+// bulk copies (TMA), so that global traffic is contiguous 16-byte-aligned
+// runs instead of one scattered row per step.  Used when a mean row (4 nx
+// bytes) is a multiple of 16 bytes; otherwise rows go straight to memory.
+template <int N>
+struct Stage {
+    static constexpr bool kOn = (N % 4) == 0;
+    static constexpr int G = 4;                                   // steps per group
+    static constexpr int kMeanB = 4 * N, kCovB = 4 * N * N;       // bytes per step
+    static constexpr int kBuf = G * (kMeanB + kCovB);             // one group
+    // per-thread stride: an odd number of 16-byte units keeps the 8 threads of
+    // a quarter warp on distinct banks for 16-byte accesses
+    __host__ __device__ static constexpr int pad_odd(int b) { return ((b / 16) % 2 == 1) ? b : b + 16; }
+};
+
+template <int N>
+KS_DEV void stage_write(char* buf, int slot, const float (&m)[N], const float (&S)[sym_size(N)]) {
+    constexpr int G = Stage<N>::G;
+    float* pm = reinterpret_cast<float*>(buf) + slot * N;
+    float* pc = reinterpret_cast<float*>(buf + G * Stage<N>::kMeanB) + slot * N * N;
+#pragma unroll
+    for (int i = 0; i < N; i += 4) *reinterpret_cast<float4*>(pm + i) = make_float4(m[i], m[i + 1], m[i + 2], m[i + 3]);
+#pragma unroll
+    for (int a = 0; a < N; ++a)
+#pragma unroll
+        for (int i = 0; i < N; i += 4)
+            *reinterpret_cast<float4*>(pc + a * N + i) =
+                make_float4(S[sidx(a, i)], S[sidx(a, i + 1)], S[sidx(a, i + 2)], S[sidx(a, i + 3)]);
+}
+
+template <int N>
+KS_DEV void stage_read(const char* buf, int slot, float (&m)[N], float (&S)[sym_size(N)]) {
+    constexpr int G = Stage<N>::G;
+    const float* pm = reinterpret_cast<const float*>(buf) + slot * N;
+    const float* pc = reinterpret_cast<const float*>(buf + G * Stage<N>::kMeanB) + slot * N * N;
+#pragma unroll
+    for (int i = 0; i < N; i += 4) {
+        const float4 t = *reinterpret_cast<const float4*>(pm + i);
+        m[i] = t.x; m[i + 1] = t.y; m[i + 2] = t.z; m[i + 3] = t.w;
+    }
+#pragma unroll
+    for (int a = 0; a < N; ++a)
+#pragma unroll
+        for (int i = 0; i < N; i += 4) {
+            const float4 t = *reinterpret_cast<const float4*>(pc + a * N + i);
+            if (i <= a) S[sidx(a, i)] = t.x;
+            if (i + 1 <= a) S[sidx(a, i + 1)] = t.y;
+            if (i + 2 <= a) S[sidx(a, i + 2)] = t.z;
+            if (i + 3 <= a) S[sidx(a, i + 3)] = t.w;
+        }
+}
+
+// Group of `cnt` steps starting at step k0 (mean rows then covariance rows of
+// the group in `buf`) to global memory.
+template <int N>
+KS_DEV void stage_flush(char* buf, float* mean, float* cov, int64_t k0, int cnt) {
+    constexpr int G = Stage<N>::G;
+    fence_proxy_async();
+    bulk_store(mean + k0 * N, buf, (uint32_t)(cnt * Stage<N>::kMeanB));
+    bulk_store(cov + k0 * N * N, buf + G * Stage<N>::kMeanB, (uint32_t)(cnt * Stage<N>::kCovB));
+    bulk_commit();
+}
+
+template <int N>
+KS_DEV void stage_fetch(char* buf, const float* mean, const float* cov, int64_t k0, int cnt, uint64_t* mb) {
+    constexpr int G = Stage<N>::G;
+    fence_proxy_async();
+    mbar_expect_tx(mb, (uint32_t)(cnt * (Stage<N>::kMeanB + Stage<N>::kCovB)));
+    bulk_load(buf, mean + k0 * N, (uint32_t)(cnt * Stage<N>::kMeanB), mb);
+    bulk_load(buf + G * Stage<N>::kMeanB, cov + k0 * N * N, (uint32_t)(cnt * Stage<N>::kCovB), mb);
+}
+
+// ---------------------------------------------------------------- look-back
+// Decoupled look-back by one warp over windows of 32 predecessor tiles.  Lane
+// l inspects tile base - l.  If some tile in the window has published its
+// inclusive prefix, the nearest one (lane p) is used and the aggregates of
+// the p tiles after it are reduced in log2(p) shuffle levels; otherwise all
+// 32 aggregates are reduced and the window moves back.  Returns (in lane 0)
+// the exclusive prefix of `tile`, in prefix form.
+//   Op::combine(x, y)   x (x) y for general elements, x earlier in scan order
+//   Op::advance(st, e)  prefix-form state (x) general element
+template <class Op>
+KS_DEV typename Op::State lookback_warp(const ScanState& ss, int tile, int lane, bool& bad, bool& timeout) {
+    using E = typename Op::Elem;
+    using S = typename Op::State;
+    constexpr int AF = sizeof(E) / 4, PF = sizeof(S) / 4;
+    S ex;
+    E run;
+    bool have_run = false;
+    int base = tile - 1;
+    while (true) {
+        const int j = base - lane;
+        uint32_t f = 0u;
+        if (j >= 0) f = wait_flag(ss.flags + j, ss.spin_limit);
+        const bool lost = (j >= 0) && (f == 0u);
+        if (__any_sync(kFull, lost)) {
+            timeout = true;
+            Op::zero_state(ex);
+            return ex;
+        }
+        const unsigned pm = __ballot_sync(kFull, (j >= 0) && (f == kFlagPre));
+        const int p = pm ? (__ffs(pm) - 1) : 32;
+        E x;
+        if (lane < p && j >= 0) x = load_cg<E>(ss.agg + (int64_t)j * AF);
+        else Op::identity(x);
+#pragma unroll 1
+        for (int d = 1; d < p; d <<= 1) {
+            const E o = shfl_down_t(x, d);      // lane + d holds an earlier tile
+            if ((lane & (2 * d - 1)) == 0) x = Op::combine(o, x, bad);
+        }
+        if (p < 32) {
+            if (lane == 0) {
+                ex = load_cg<S>(ss.pre + (int64_t)(base - p) * PF);
+                if (p > 0) Op::advance(ex, x, bad);
+                if (have_run) Op::advance(ex, run, bad);
+            }
+            return ex;
+        }
+        if (lane == 0) {
+            run = have_run ? Op::combine(x, run, bad) : x;
+            have_run = true;
+        }
+        base -= 32;
+    }
+}
+
+template <int N>
+struct FilterOp {
+    using Elem = FElem<N>;
+    using State = FState<N>;
+    KS_DEV static Elem combine(const Elem& a, const Elem& b, bool& bad) { return fcombine<N>(a, b, bad); }
+    KS_DEV static void advance(State& s, const Elem& e, bool& bad) { fadvance<N>(s, e, bad); }
+    KS_DEV static void identity(Elem& e) { set_identity<N>(e); }
+    KS_DEV static void zero_state(State& s) {
+#pragma unroll
+        for (int a = 0; a < N; ++a) s.b[a] = 0.f;
+#pragma unroll
+        for (int a = 0; a < sym_size(N); ++a) s.C[a] = 0.f;
+    }
+    KS_DEV static State state_of(const Elem& e) {   // element with A = 0
+        State s;
+#pragma unroll
+        for (int a = 0; a < N; ++a) s.b[a] = e.b[a];
+#pragma unroll
+        for (int a = 0; a < sym_size(N); ++a) s.C[a] = e.C[a];
+        return s;
+    }
+};
+
+// Reverse-scan operator in scan (reversed-time) order: x (x)_r y = y (x) x.
+template <int N>
+struct SmootherOp {
+    using Elem = SElem<N>;
+    using State = SState<N>;
+    KS_DEV static Elem combine(const Elem& a, const Elem& b, bool&) { return scombine<N>(b, a); }
+    KS_DEV static void advance(State& s, const Elem& e, bool&) { sadvance<N>(e, s); }
+    KS_DEV static void identity(Elem& e) { set_identity<N>(e); }
+    KS_DEV static void zero_state(State& s) {
+#pragma unroll
+        for (int a = 0; a < N; ++a) s.g[a] = 0.f;
+#pragma unroll
+        for (int a = 0; a < sym_size(N); ++a) s.L[a] = 0.f;
+    }
+    KS_DEV static State state_of(const Elem& e) {   // element with E = 0
+        State s;
+#pragma unroll
+        for (int a = 0; a < N; ++a) s.g[a] = e.g[a];
+#pragma unroll
+        for (int a = 0; a < sym_size(N); ++a) s.L[a] = e.L[a];
+        return s;
+    }
+};
+
+// Phase 2 shared by both scans: warp scan of the per-thread block elements,
+// scan of the warp totals (last warp, NW lanes), publication of the tile
+// aggregate and the look-back.  On return every thread of a valid block has
+// `st` = the prefix entering its block and `has` = whether there is one (only
+// the very first block of the sequence has none).
+template <class Op, int NT>
+struct BlockScan {
+    static constexpr int NW = NT / 32;
+    using E = typename Op::Elem;
+    using S = typename Op::State;
+    struct Smem {
+        E wtot[NW];
+        E wincl[NW];
+        E lexcl[NT];     // per-thread in-warp exclusive prefix, parked across the look-back
+        E tagg;
+        S texcl;
+        int has;
+    };
+
+    KS_DEV static void run(Smem& sm, const ScanState& ss, int tile, const E& acc, S& st, bool& has,
+                           bool& bad) {
+        const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+        constexpr int AF = sizeof(E) / 4, PF = sizeof(S) / 4;
+        E incl = acc;
+#pragma unroll 1
+        for (int d = 1; d < 32; d <<= 1) {
+            const E o = shfl_up_t(incl, d);
+            if (lane >= d) incl = Op::combine(o, incl, bad);
+        }
+        {
+            const E lane_excl = shfl_up_t(incl, 1);
+            sm.lexcl[tid] = lane_excl;
+        }
+        if (lane == 31) sm.wtot[warp] = incl;
+        __syncthreads();
+        if (warp == NW - 1) {
+            {
+                E x;
+                if (lane < NW) x = sm.wtot[lane];
+                else Op::identity(x);
+#pragma unroll 1
+                for (int d = 1; d < NW; d <<= 1) {
+                    const E o = shfl_up_t(x, d);
+                    if (lane >= d && lane < NW) x = Op::combine(o, x, bad);
+                }
+                if (lane < NW) sm.wincl[lane] = x;
+                if (lane == NW - 1) sm.tagg = x;
+            }
+            __syncwarp();
+            bool timeout = false;
+            S ex;
+            if (tile == 0) {
+                if (lane == 0) {
+                    store_plain(ss.pre, Op::state_of(sm.tagg));
+                    st_release(ss.flags, kFlagPre);
+                }
+            } else {
+                if (lane == 0) {
+                    store_plain(ss.agg + (int64_t)tile * AF, sm.tagg);
+                    st_release(ss.flags + tile, kFlagAgg);
+                }
+                ex = lookback_warp<Op>(ss, tile, lane, bad, timeout);
+                if (lane == 0) {
+                    S inc = ex;
+                    Op::advance(inc, sm.tagg, bad);
+                    store_plain(ss.pre + (int64_t)tile * PF, inc);
+                    st_release(ss.flags + tile, kFlagPre);
+                }
+            }
+            if (timeout && lane == 0) atomicOr(ss.status, ST_TIMEOUT);
+            if (lane == 0) {
+                if (tile != 0) sm.texcl = ex;
+                sm.has = (tile != 0) ? 1 : 0;
+            }
+        }
+        __syncthreads();
+        has = sm.has != 0;
+        if (has) st = sm.texcl;
+        if (warp > 0) {
+            const E& wp = sm.wincl[warp - 1];
+            if (has) Op::advance(st, wp, bad);
+            else { st = Op::state_of(wp); has = true; }
+        }
+        if (lane > 0) {
+            const E& le = sm.lexcl[tid];
+            if (has) Op::advance(st, le, bad);
+            else { st = Op::state_of(le); has = true; }
+        }
+    }
+};
+
+// Lemma 5 element from a filtered mean and covariance (k = n when `last`).
+template <int N, int M>
+KS_DEV void build_selem_from(const ModelConst<N, M>& mc, const float (&xb)[N], const float (&P)[sym_size(N)],
+                             bool last, SElem<N>& e, bool& bad) {
+    if (last) {  // Lemma 5, k = n: E = 0, g = xbar_n, L = P_n
+#pragma unroll
+        for (int a = 0; a < N * N; ++a) e.E[a] = 0.f;
+#pragma unroll
+        for (int a = 0; a < N; ++a) e.g[a] = xb[a];
+#pragma unroll
+        for (int a = 0; a < sym_size(N); ++a) e.L[a] = P[a];
+    } else {
+        smoother_element<N, M>(mc, xb, P, e, bad);
+    }
+}
+
 // ---------------------------------------------------------------- forward scan
-template <int N, int M, int NT, int CH, bool FROM_Y>
+// With SAGG the same pass also builds each step's Lemma 5 smoothing element
+// from the posterior it has just produced and folds the thread's block of
+// them (Lemma 6, associativity lets the fold run forward), writing one
+// smoothing block aggregate per thread to `sagg` for the reverse scan.
+template <int N, int M, int NT, int CH, bool FROM_Y, bool SAGG>
 __global__ void __launch_bounds__(NT) filter_scan_kernel(const ModelConst<N, M>* __restrict__ mcg,
                                                          const float* __restrict__ y,
                                                          const float* __restrict__ el, int64_t ld,
                                                          int64_t T, float* __restrict__ fmean,
-                                                         float* __restrict__ fcov, ScanState ss) {
-    constexpr int NW = NT / 32;
+                                                         float* __restrict__ fcov, ScanState ss,
+                                                         float* __restrict__ sagg) {
+    using BS = BlockScan<FilterOp<N>, NT>;
+    using SG = Stage<N>;
     constexpr int64_t TILE = (int64_t)NT * CH;
+    constexpr int OSTR = SG::pad_odd(SG::kBuf);
     __shared__ ModelConst<N, M> mc;
-    __shared__ FElem<N> wtot[NW];
-    __shared__ FState<N> texcl;
-    __shared__ int s_tile, s_has;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    __shared__ typename BS::Smem bsm;
+    __shared__ int s_tile;
+    extern __shared__ __align__(16) char dsm[];
+    const int tid = threadIdx.x, lane = tid & 31;
     load_const<N, M>(mcg, mc, tid, NT);
     if (tid == 0) s_tile = (int)atomicAdd(ss.counter, 1u);
     __syncthreads();
@@ -471,102 +800,19 @@ __global__ void __launch_bounds__(NT) filter_scan_kernel(const ModelConst<N, M>*
         }
     }
 
-    // ---- phase 2: warp scan, warp-total scan, look-back
-    FElem<N> incl = acc;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        FElem<N> o = shfl_up_t(incl, d);
-        if (lane >= d) incl = fcombine<N>(o, incl, bad);
-    }
-    const FElem<N> lane_excl = shfl_up_t(incl, 1);
-    if (lane == 31) wtot[warp] = incl;
-    __syncthreads();
-    FElem<N> wpre;
-    if (warp > 0) {
-        wpre = wtot[0];
-        for (int w = 1; w < warp; ++w) wpre = fcombine<N>(wpre, wtot[w], bad);
-    }
-    if (tid == NT - 1) {
-        FElem<N> tagg = (NW > 1) ? fcombine<N>(wpre, wtot[NW - 1], bad) : wtot[0];
-        FState<N> ex;
-        int has = 0;
-        constexpr int AF = sizeof(FElem<N>) / 4, PF = sizeof(FState<N>) / 4;
-        if (tile == 0) {
-            FState<N> inc;
-#pragma unroll
-            for (int a = 0; a < N; ++a) inc.b[a] = tagg.b[a];
-#pragma unroll
-            for (int a = 0; a < sym_size(N); ++a) inc.C[a] = tagg.C[a];
-            store_plain(ss.pre, inc);
-            st_release(ss.flags, kFlagPre);
-#pragma unroll
-            for (int a = 0; a < N; ++a) ex.b[a] = 0.f;
-#pragma unroll
-            for (int a = 0; a < sym_size(N); ++a) ex.C[a] = 0.f;
-        } else {
-            store_plain(ss.agg + (int64_t)tile * AF, tagg);
-            st_release(ss.flags + tile, kFlagAgg);
-            FElem<N> run;
-            bool have_run = false;
-            int j = tile - 1;
-            while (true) {
-                const uint32_t f = wait_flag(ss.flags + j, ss.spin_limit);
-                if (f == 0u) {
-                    atomicOr(ss.status, ST_TIMEOUT);
-#pragma unroll
-                    for (int a = 0; a < N; ++a) ex.b[a] = 0.f;
-#pragma unroll
-                    for (int a = 0; a < sym_size(N); ++a) ex.C[a] = 0.f;
-                    break;
-                }
-                if (f == kFlagPre) {
-                    ex = load_cg<FState<N>>(ss.pre + (int64_t)j * PF);
-                    if (have_run) fadvance<N>(ex, run, bad);
-                    break;
-                }
-                const FElem<N> a = load_cg<FElem<N>>(ss.agg + (int64_t)j * AF);
-                run = have_run ? fcombine<N>(a, run, bad) : a;
-                have_run = true;
-                --j;
-            }
-            has = 1;
-            FState<N> inc = ex;
-            fadvance<N>(inc, tagg, bad);
-            store_plain(ss.pre + (int64_t)tile * PF, inc);
-            st_release(ss.flags + tile, kFlagPre);
-        }
-        texcl = ex;
-        s_has = has;
-    }
-    __syncthreads();
+    // ---- phase 2
+    FState<N> st;
+    bool has = false;
+    BS::run(bsm, ss, tile, acc, st, has, bad);
 
-    // ---- phase 3: prefix entering this thread's block, then step by step
+    // ---- phase 3: step through the block from the incoming posterior
     if (valid) {
-        FState<N> st = texcl;
-        bool has = s_has != 0;
-        if (warp > 0) {
-            if (has) {
-                fadvance<N>(st, wpre, bad);
-            } else {
-#pragma unroll
-                for (int a = 0; a < N; ++a) st.b[a] = wpre.b[a];
-#pragma unroll
-                for (int a = 0; a < sym_size(N); ++a) st.C[a] = wpre.C[a];
-                has = true;
-            }
-        }
-        if (lane > 0) {
-            if (has) {
-                fadvance<N>(st, lane_excl, bad);
-            } else {
-#pragma unroll
-                for (int a = 0; a < N; ++a) st.b[a] = lane_excl.b[a];
-#pragma unroll
-                for (int a = 0; a < sym_size(N); ++a) st.C[a] = lane_excl.C[a];
-                has = true;
-            }
-        }
+        char* obuf = dsm + tid * OSTR;
+        int gcnt = 0;
+        int64_t gk = k0;
+        bool pending = false;
         float probe = 0.f;
+        SElem<N> sacc;
 #pragma unroll 1
         for (int i = 0; i < CH; ++i) {
             const int64_t k = k0 + i;
@@ -587,18 +833,36 @@ __global__ void __launch_bounds__(NT) filter_scan_kernel(const ModelConst<N, M>*
             } else {
                 const FElem<N> e = load_soa<N>(el, ld, k);
                 if (!has) {
-#pragma unroll
-                    for (int a = 0; a < N; ++a) st.b[a] = e.b[a];
-#pragma unroll
-                    for (int a = 0; a < sym_size(N); ++a) st.C[a] = e.C[a];
+                    st = FilterOp<N>::state_of(e);
                     has = true;
                 } else {
                     fadvance<N>(st, e, bad);
                 }
             }
-            store_posterior<N>(fmean, fcov, k, st.b, st.C);
             probe += finite_probe<N>(st.b, st.C);
+            if constexpr (SAGG) {
+                SElem<N> e;
+                build_selem_from<N, M>(mc, st.b, st.C, k == T - 1, e, bad);
+                sacc = (i == 0) ? e : scombine<N>(sacc, e);
+            }
+            if constexpr (SG::kOn) {
+                if (gcnt == 0 && pending) bulk_wait_read_all();
+                stage_write<N>(obuf, gcnt, st.b, st.C);
+                ++gcnt;
+                if (gcnt == SG::G || k == T - 1 || i == CH - 1) {
+                    stage_flush<N>(obuf, fmean, fcov, gk, gcnt);
+                    pending = true;
+                    gk += gcnt;
+                    gcnt = 0;
+                }
+            } else {
+                store_posterior<N>(fmean, fcov, k, st.b, st.C);
+            }
         }
+        if constexpr (SG::kOn) {
+            if (pending) bulk_wait_all();
+        }
+        if constexpr (SAGG) store_plain(sagg + (k0 / CH) * (int64_t)(sizeof(SElem<N>) / 4), sacc);
         bad |= !isfinite(probe);
     }
     if (__any_sync(kFull, bad) && lane == 0) atomicOr(ss.status, ST_NUMERIC);
@@ -608,178 +872,189 @@ __global__ void __launch_bounds__(NT) filter_scan_kernel(const ModelConst<N, M>*
 // Tiles and threads walk the reversed sequence r = T-1-k; in that order the
 // scan operator is x (x)_r y = y (x) x (Lemma 6 with the earlier time step
 // on the left), so the inclusive r-prefixes are Theorem 2's suffix sums.
-template <int N, int M>
-KS_DEV void build_selem(const ModelConst<N, M>& mc, const float* __restrict__ fmean,
-                        const float* __restrict__ fcov, int64_t T, int64_t k, SElem<N>& e, bool& bad) {
-    float xb[N], P[sym_size(N)];
-    load_posterior<N>(fmean, fcov, k, xb, P);
-    if (k == T - 1) {  // Lemma 5, k = n: E = 0, g = xbar_n, L = P_n
-#pragma unroll
-        for (int a = 0; a < N * N; ++a) e.E[a] = 0.f;
-#pragma unroll
-        for (int a = 0; a < N; ++a) e.g[a] = xb[a];
-#pragma unroll
-        for (int a = 0; a < sym_size(N); ++a) e.L[a] = P[a];
-    } else {
-        smoother_element<N, M>(mc, xb, P, e, bad);
-    }
-}
+// Per-thread source of filtered moments for the reverse scan: either staged
+// groups of G steps fetched by bulk copies (double-buffered), or direct rows.
+template <int N>
+struct RevReader {
+    using SG = Stage<N>;
+    static constexpr int BSTR = SG::pad_odd(SG::kBuf);
+    static constexpr int TSTR = 2 * BSTR + 16;      // per thread: odd number of 16-byte units
+    char* base;
+    uint64_t* mb;
+    uint32_t par0, par1;
+    int64_t khi;      // first (latest) step of the thread's block
+    int cnt;          // steps in the block
+    int ngroups;
 
-template <int N, int M, int NT, int CH>
+    KS_DEV void init(char* b, uint64_t* mbar, int64_t k_hi, int count) {
+        base = b;
+        mb = mbar;
+        par0 = par1 = 0u;
+        khi = k_hi;
+        cnt = count;
+        ngroups = (count + SG::G - 1) / SG::G;
+    }
+    KS_DEV char* buf(int g) const { return base + (g & 1) * BSTR; }
+    // group g covers steps khi - g*G down to max(khi - g*G - G + 1, khi - cnt + 1)
+    KS_DEV int64_t glo(int g) const {
+        const int64_t lo = khi - (int64_t)g * SG::G - SG::G + 1;
+        const int64_t lim = khi - cnt + 1;
+        return lo > lim ? lo : lim;
+    }
+    KS_DEV int gcount(int g) const { return (int)(khi - (int64_t)g * SG::G - glo(g) + 1); }
+    KS_DEV void fetch(const float* fm, const float* fc, int g) {
+        if (g < ngroups) stage_fetch<N>(buf(g), fm, fc, glo(g), gcount(g), mb + (g & 1));
+    }
+    KS_DEV bool wait(int g, uint32_t limit) {
+        const bool odd = (g & 1) != 0;
+        const bool ok = mbar_wait(mb + (g & 1), odd ? par1 : par0, limit);
+        if (odd) par1 ^= 1u; else par0 ^= 1u;
+        return ok;
+    }
+};
+
+// Blocks of CH steps start at multiples of CH from step 0 (the forward
+// scan's grid); the reverse scan visits them last block first.  With FROM_AGG
+// each thread's block aggregate comes from the forward scan (`sagg`);
+// otherwise it is folded here from the filtered moments.
+template <int N, int M, int NT, int CH, bool FROM_AGG>
 __global__ void __launch_bounds__(NT) smoother_scan_kernel(const ModelConst<N, M>* __restrict__ mcg,
                                                            const float* __restrict__ fmean,
                                                            const float* __restrict__ fcov, int64_t T,
                                                            float* __restrict__ smean,
-                                                           float* __restrict__ scov, ScanState ss) {
-    constexpr int NW = NT / 32;
-    constexpr int64_t TILE = (int64_t)NT * CH;
+                                                           float* __restrict__ scov, ScanState ss,
+                                                           const float* __restrict__ sagg) {
+    using BS = BlockScan<SmootherOp<N>, NT>;
+    using SG = Stage<N>;
+    using RR = RevReader<N>;
     __shared__ ModelConst<N, M> mc;
-    __shared__ SElem<N> wtot[NW];
-    __shared__ SState<N> texcl;
-    __shared__ int s_tile, s_has;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    __shared__ typename BS::Smem bsm;
+    __shared__ int s_tile;
+    __shared__ uint64_t mbars[SG::kOn ? 2 * NT : 1];
+    extern __shared__ __align__(16) char dsm[];
+    const int tid = threadIdx.x, lane = tid & 31;
     load_const<N, M>(mcg, mc, tid, NT);
     if (tid == 0) s_tile = (int)atomicAdd(ss.counter, 1u);
+    if constexpr (SG::kOn) {
+        mbar_init(&mbars[2 * tid], 1);
+        mbar_init(&mbars[2 * tid + 1], 1);
+        fence_proxy_async();
+    }
     __syncthreads();
     const int tile = s_tile;
-    const int64_t r0 = tile * TILE + (int64_t)tid * CH;
-    const bool valid = r0 < T;
-    bool bad = false;
+    const int64_t nblk = (T + CH - 1) / CH;
+    const int64_t c = nblk - 1 - ((int64_t)tile * NT + tid);    // forward block index
+    const bool valid = c >= 0;
+    const int64_t klo = c * CH;
+    const int64_t khi = valid ? ((klo + CH < T ? klo + CH : T) - 1) : -1;
+    const int cnt = valid ? (int)(khi - klo + 1) : 0;
+    bool bad = false, lost = false;
+    constexpr uint32_t kWait = 4000000u;
+    RR rd;
+    if constexpr (SG::kOn) rd.init(dsm + tid * RR::TSTR, &mbars[2 * tid], khi, cnt);
 
     // ---- phase 1: a_{k_lo} (x) ... (x) a_{k_hi} over this thread's steps
     SElem<N> acc;
-    if (!valid) {
-        set_identity<N>(acc);
-    } else {
-        build_selem<N, M>(mc, fmean, fcov, T, T - 1 - r0, acc, bad);
+    set_identity<N>(acc);
+    if constexpr (FROM_AGG) {
+        if (valid) acc = load_cg<SElem<N>>(sagg + c * (int64_t)(sizeof(SElem<N>) / 4));
+    } else if (valid) {
+        if constexpr (SG::kOn) {
+            rd.fetch(fmean, fcov, 0);
+            rd.fetch(fmean, fcov, 1);
+            bool first = true;
 #pragma unroll 1
-        for (int i = 1; i < CH; ++i) {
-            const int64_t r = r0 + i;
-            if (r >= T) break;
-            SElem<N> e;
-            build_selem<N, M>(mc, fmean, fcov, T, T - 1 - r, e, bad);
-            acc = scombine<N>(e, acc);
+            for (int g = 0; g < rd.ngroups; ++g) {
+                lost |= !rd.wait(g, kWait);
+                const int gc = rd.gcount(g);
+                const int64_t lo = rd.glo(g);
+#pragma unroll 1
+                for (int s = gc - 1; s >= 0; --s) {
+                    float xb[N], P[sym_size(N)];
+                    stage_read<N>(rd.buf(g), s, xb, P);
+                    SElem<N> e;
+                    build_selem_from<N, M>(mc, xb, P, lo + s == T - 1, e, bad);
+                    acc = first ? e : scombine<N>(e, acc);
+                    first = false;
+                }
+                rd.fetch(fmean, fcov, g + 2);
+            }
+        } else {
+#pragma unroll 1
+            for (int i = 0; i < cnt; ++i) {
+                const int64_t k = khi - i;
+                float xb[N], P[sym_size(N)];
+                load_posterior<N>(fmean, fcov, k, xb, P);
+                SElem<N> e;
+                build_selem_from<N, M>(mc, xb, P, k == T - 1, e, bad);
+                acc = (i == 0) ? e : scombine<N>(e, acc);
+            }
         }
     }
 
     // ---- phase 2
-    SElem<N> incl = acc;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        SElem<N> o = shfl_up_t(incl, d);
-        if (lane >= d) incl = scombine<N>(incl, o);
-    }
-    const SElem<N> lane_excl = shfl_up_t(incl, 1);
-    if (lane == 31) wtot[warp] = incl;
-    __syncthreads();
-    SElem<N> wpre;
-    if (warp > 0) {
-        wpre = wtot[0];
-        for (int w = 1; w < warp; ++w) wpre = scombine<N>(wtot[w], wpre);
-    }
-    if (tid == NT - 1) {
-        SElem<N> tagg = (NW > 1) ? scombine<N>(wtot[NW - 1], wpre) : wtot[0];
-        SState<N> ex;
-        int has = 0;
-        constexpr int AF = sizeof(SElem<N>) / 4, PF = sizeof(SState<N>) / 4;
-        if (tile == 0) {
-            SState<N> inc;
-#pragma unroll
-            for (int a = 0; a < N; ++a) inc.g[a] = tagg.g[a];
-#pragma unroll
-            for (int a = 0; a < sym_size(N); ++a) inc.L[a] = tagg.L[a];
-            store_plain(ss.pre, inc);
-            st_release(ss.flags, kFlagPre);
-#pragma unroll
-            for (int a = 0; a < N; ++a) ex.g[a] = 0.f;
-#pragma unroll
-            for (int a = 0; a < sym_size(N); ++a) ex.L[a] = 0.f;
-        } else {
-            store_plain(ss.agg + (int64_t)tile * AF, tagg);
-            st_release(ss.flags + tile, kFlagAgg);
-            SElem<N> run;
-            bool have_run = false;
-            int j = tile - 1;
-            while (true) {
-                const uint32_t f = wait_flag(ss.flags + j, ss.spin_limit);
-                if (f == 0u) {
-                    atomicOr(ss.status, ST_TIMEOUT);
-#pragma unroll
-                    for (int a = 0; a < N; ++a) ex.g[a] = 0.f;
-#pragma unroll
-                    for (int a = 0; a < sym_size(N); ++a) ex.L[a] = 0.f;
-                    break;
-                }
-                if (f == kFlagPre) {
-                    ex = load_cg<SState<N>>(ss.pre + (int64_t)j * PF);
-                    if (have_run) sadvance<N>(run, ex);
-                    break;
-                }
-                const SElem<N> a = load_cg<SElem<N>>(ss.agg + (int64_t)j * AF);
-                run = have_run ? scombine<N>(run, a) : a;
-                have_run = true;
-                --j;
-            }
-            has = 1;
-            SState<N> inc = ex;
-            sadvance<N>(tagg, inc);
-            store_plain(ss.pre + (int64_t)tile * PF, inc);
-            st_release(ss.flags + tile, kFlagPre);
-        }
-        texcl = ex;
-        s_has = has;
-    }
-    __syncthreads();
+    SState<N> st;
+    bool has = false;
+    BS::run(bsm, ss, tile, acc, st, has, bad);
 
     // ---- phase 3
     if (valid) {
-        SState<N> st = texcl;
-        bool has = s_has != 0;
-        if (warp > 0) {
-            if (has) {
-                sadvance<N>(wpre, st);
-            } else {
-#pragma unroll
-                for (int a = 0; a < N; ++a) st.g[a] = wpre.g[a];
-#pragma unroll
-                for (int a = 0; a < sym_size(N); ++a) st.L[a] = wpre.L[a];
-                has = true;
-            }
-        }
-        if (lane > 0) {
-            if (has) {
-                sadvance<N>(lane_excl, st);
-            } else {
-#pragma unroll
-                for (int a = 0; a < N; ++a) st.g[a] = lane_excl.g[a];
-#pragma unroll
-                for (int a = 0; a < sym_size(N); ++a) st.L[a] = lane_excl.L[a];
-                has = true;
-            }
-        }
         float probe = 0.f;
+        if constexpr (SG::kOn) {
+            rd.fetch(fmean, fcov, 0);
+            rd.fetch(fmean, fcov, 1);
 #pragma unroll 1
-        for (int i = 0; i < CH; ++i) {
-            const int64_t r = r0 + i;
-            if (r >= T) break;
-            const int64_t k = T - 1 - r;
-            SElem<N> e;
-            build_selem<N, M>(mc, fmean, fcov, T, k, e, bad);
-            if (!has) {  // only k = T-1: E_n = 0
-#pragma unroll
-                for (int a = 0; a < N; ++a) st.g[a] = e.g[a];
-#pragma unroll
-                for (int a = 0; a < sym_size(N); ++a) st.L[a] = e.L[a];
-                has = true;
-            } else {
-                sadvance<N>(e, st);
+            for (int g = 0; g < rd.ngroups; ++g) {
+                lost |= !rd.wait(g, kWait);
+                const int gc = rd.gcount(g);
+                const int64_t lo = rd.glo(g);
+                char* b = rd.buf(g);
+#pragma unroll 1
+                for (int s = gc - 1; s >= 0; --s) {
+                    float xb[N], P[sym_size(N)];
+                    stage_read<N>(b, s, xb, P);
+                    SElem<N> e;
+                    build_selem_from<N, M>(mc, xb, P, lo + s == T - 1, e, bad);
+                    if (!has) { st = SmootherOp<N>::state_of(e); has = true; }   // only k = T-1
+                    else sadvance<N>(e, st);
+                    stage_write<N>(b, s, st.g, st.L);     // the slot's input is already in registers
+                    probe += finite_probe<N>(st.g, st.L);
+                }
+                stage_flush<N>(b, smean, scov, lo, gc);
+                if (g + 2 < rd.ngroups) {
+                    bulk_wait_read_all();
+                    rd.fetch(fmean, fcov, g + 2);
+                }
             }
-            store_posterior<N>(smean, scov, k, st.g, st.L);
-            probe += finite_probe<N>(st.g, st.L);
+            bulk_wait_all();
+        } else {
+#pragma unroll 1
+            for (int i = 0; i < cnt; ++i) {
+                const int64_t k = khi - i;
+                float xb[N], P[sym_size(N)];
+                load_posterior<N>(fmean, fcov, k, xb, P);
+                SElem<N> e;
+                build_selem_from<N, M>(mc, xb, P, k == T - 1, e, bad);
+                if (!has) { st = SmootherOp<N>::state_of(e); has = true; }
+                else sadvance<N>(e, st);
+                store_posterior<N>(smean, scov, k, st.g, st.L);
+                probe += finite_probe<N>(st.g, st.L);
+            }
         }
         bad |= !isfinite(probe);
     }
+    if (lost) atomicOr(ss.status, ST_TIMEOUT);
     if (__any_sync(kFull, bad) && lane == 0) atomicOr(ss.status, ST_NUMERIC);
+}
+
+// Dynamic shared memory of the two scans (bytes).
+template <int N, int NT>
+constexpr int filter_dyn_smem() {
+    return Stage<N>::kOn ? NT * Stage<N>::pad_odd(Stage<N>::kBuf) : 16;
+}
+template <int N, int NT>
+constexpr int smoother_dyn_smem() {
+    return Stage<N>::kOn ? NT * RevReader<N>::TSTR : 16;
 }
 
 // ---------------------------------------------------------------- operator batches
