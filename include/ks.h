@@ -177,6 +177,36 @@ int ks_smooth_traced(const ks_model *m, const float *y, int64_t T, void *ws, siz
 int ks_status(void *ws, void *stream);
 
 /*
+ * ks_smooth without a workspace, for callers that cannot allocate device
+ * memory: for example a real-time loop that must not take cudaMalloc's
+ * implicit device synchronisation or risk its failure once running, or a host
+ * application that owns the device memory budget and does not let plug-ins
+ * allocate.  The paper has no counterpart; this is an interface convenience.
+ *
+ * Same computation and arguments as ks_smooth for nx = 4, ny = 2 (other
+ * sizes: KS_EUNSUPPORTED), with T <= KS_NOALLOC_MAX_T (larger T, or NULL
+ * fmean / fcov: KS_EINVAL).  The caller still provides every input and
+ * output; the scratch lives in a static device array of
+ * KS_NOALLOC_SCRATCH_BYTES that every GPU loading this library holds until
+ * the process exits.  The function itself allocates nothing.
+ *  - The first call on each device looks up that array's device address (with
+ *    the device current) and caches it; make that first call before any stream
+ *    capture.
+ *  - All calls on a device share the one array: calls that overlap on the GPU
+ *    (different streams or threads without ordering) race and give wrong
+ *    results.  Each call clears the state it needs, so sequential calls are
+ *    independent.
+ *  - Device-side errors: if status_out (device pointer, may be NULL) is given,
+ *    the call's device status bits are copied there at the end of the call,
+ *    stream-ordered: 0 = ok, bit 0 = non-finite value or failed factorisation,
+ *    bit 1 = a look-back wait ran out.
+ */
+#define KS_NOALLOC_MAX_T 1048576
+#define KS_NOALLOC_SCRATCH_BYTES 4194304
+int ks_smooth_noalloc(const ks_model *m, const float *y, int64_t T, float *fmean, float *fcov,
+                      float *smean, float *scov, int32_t *status_out, void *stream);
+
+/*
  * Batched Lemma 4 / Lemma 6 operators on `count` independent element pairs,
  * for operator-level testing and for callers that run their own scans.
  * Elements are packed per element (no padding) in device memory, FP32:

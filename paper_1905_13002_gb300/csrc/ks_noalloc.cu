@@ -1,0 +1,66 @@
+// ks_noalloc.cu -- ks_smooth_noalloc: the end-to-end filter + smoother with
+// its scratch in a file-scope device array instead of a caller workspace, for
+// callers that cannot allocate device memory.
+//
+// The array below is a host-side stand-in in host code: its device address is
+// fetched with cudaGetSymbolAddress once per device (with that device
+// current) and cached; that set-up happens on the first call on each device.
+// Every call on a device shares the array; calls that overlap on the GPU race
+// on it.  The status word is cleared at the start of each call and the scan
+// state is cleared by the model-preparation kernel, so a call never depends
+// on what an earlier call left behind.
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "../../include/ks.h"
+#include "ks_impl.cuh"
+
+namespace ks {
+namespace {
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[KS_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mutex;
+void* g_scratch_addr[kMaxDevices];
+
+// Device address of the scratch array on the current device (set up once).
+int scratch_on_current_device(void** out) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return KS_ECUDA;
+    std::lock_guard<std::mutex> lock(g_mutex);
+    if (g_scratch_addr[dev] == nullptr) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) return KS_ECUDA;
+        g_scratch_addr[dev] = p;
+    }
+    *out = g_scratch_addr[dev];
+    return KS_OK;
+}
+
+}  // namespace
+}  // namespace ks
+
+extern "C" int ks_smooth_noalloc(const ks_model* m, const float* y, int64_t T, float* fmean, float* fcov,
+                                 float* smean, float* scov, int32_t* status_out, void* stream) {
+    using namespace ks;
+    if (!m) return KS_EINVAL;
+    if (m->nx != 4 || m->ny != 2) return KS_EUNSUPPORTED;
+    if (T < 1 || T > KS_NOALLOC_MAX_T) return KS_EINVAL;
+    if (!fmean || !fcov) return KS_EINVAL;
+    const VTable* v = find_impl(4, 2);
+    if (!v) return KS_EUNSUPPORTED;
+    if (v->layout(T).bytes_smooth > (size_t)KS_NOALLOC_SCRATCH_BYTES) return KS_EINVAL;
+    void* ws = nullptr;
+    int rc = scratch_on_current_device(&ws);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(ws, 0, 256, st) != cudaSuccess) return KS_ECUDA;   // status word
+    rc = v->smooth(m, y, T, ws, (size_t)KS_NOALLOC_SCRATCH_BYTES, fmean, fcov, smean, scov, st, nullptr);
+    if (rc) return rc;
+    if (status_out &&
+        cudaMemcpyAsync(status_out, ws, sizeof(int32_t), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return KS_ECUDA;
+    return KS_OK;
+}
