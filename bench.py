@@ -74,11 +74,13 @@ def bytes_per_step(nx: int, ny: int) -> dict:
 
 def flops_per_step(N: int, M: int) -> dict:
     """Floating-point operations per step of each kernel's per-step work
-    (FMA = 2): the forward scan folds one measurement element into its block
-    aggregate (rank-M Lemma 4) and later applies it to the running filtered
-    posterior; the reverse scan builds the Lemma 5 element twice (fold and
-    application), folds it (Lemma 6) and applies it.  Block-level scan,
-    look-back and element-building overheads are not counted."""
+    (FMA = 2).  The forward scan folds one measurement element into its block
+    aggregate (rank-M form of Lemma 4), applies it to the running filtered
+    posterior, and -- fused into the same pass -- builds the step's Lemma 5
+    smoothing element from that posterior and folds it into the block's
+    smoothing aggregate (Lemma 6).  The reverse scan rebuilds the Lemma 5
+    element and applies it to the running smoothed posterior.  Block-level
+    scan and look-back overheads are not counted."""
     s = N * (N + 1) // 2
     sm = M * (M + 1) // 2
     chol = M * M * M // 3 + 3 * M
@@ -89,7 +91,7 @@ def flops_per_step(N: int, M: int) -> dict:
     sel = 2 * (N ** 3 + s * N + N ** 3 // 6 + N * N * (N - 1) + 2 * N * N + s * N) + 2 * N * N + N
     scomb = 2 * (N ** 3 + s * N + N * N + N ** 3)
     sadv = 2 * (N ** 3 + N * N + s * N)
-    return {"filter": fold + adv + 2 * meas, "smoother": 2 * sel + scomb + sadv}
+    return {"filter": fold + adv + 2 * meas + sel + scomb, "smoother": sel + sadv}
 
 
 # ---------------------------------------------------------------- clocks

@@ -7,9 +7,11 @@
 
 namespace ks {
 
+extern const VTable kImpl_2_1;
 extern const VTable kImpl_4_2;
+extern const VTable kImpl_6_3;
 
-static const VTable* const kImpls[] = {&kImpl_4_2};
+static const VTable* const kImpls[] = {&kImpl_2_1, &kImpl_4_2, &kImpl_6_3};
 
 const VTable* find_impl(int nx, int ny) {
     for (const VTable* v : kImpls)

@@ -221,3 +221,22 @@ def test_repeated_calls_agree(ks):
     ea = parity.errors(a, ref)
     eb = parity.errors(b, ref)
     assert max(ea.values()) < parity.TOL and max(eb.values()) < parity.TOL
+
+
+@pytest.mark.parametrize("dim,T", [(1, 3000), (1, 1), (3, 2500), (3, 4097)])
+def test_other_state_sizes_wiener(ks, dim, T):
+    """nx = 2 (ny = 1) and nx = 6 (ny = 3) Wiener-velocity models."""
+    rng = np.random.default_rng(300 + dim + T)
+    m = workloads.wiener_velocity(dim, dt=0.1, q=float(rng.uniform(0.5, 2)), r=float(rng.uniform(0.1, 1)))
+    _, y = workloads.simulate(m, T, rng)
+    check(ks, m, y)
+
+
+@pytest.mark.parametrize("T", [1, 700, 5000])
+def test_random_stable_nx8(ks, T):
+    if not ks.supported(8, 4):
+        pytest.skip("nx = 8 is not compiled into this library")
+    rng = np.random.default_rng(400 + T)
+    m = workloads.random_stable(8, 4, rng)
+    _, y = workloads.simulate(m, T, rng)
+    check(ks, m, y)
