@@ -77,6 +77,25 @@ typedef struct ks_model {
     const double *m0, *P0;
 } ks_model;
 
+/*
+ * B independent time-invariant models for a batch of sequences laid end to
+ * end.  Every array holds one model per sequence, sequence-major: F [B][nx][nx],
+ * u [B][nx] (or NULL), Q [B][nx][nx], H [B][ny][nx], d [B][ny] (or NULL),
+ * R [B][ny][ny] FP32; m0 [B][nx], P0 [B][nx][nx] FP64.  offsets [B+1] (int64)
+ * gives each sequence's first step on the concatenated axis: offsets[0] = 0,
+ * strictly increasing (every sequence has at least one step), offsets[B] =
+ * the total number of steps.  All pointers are DEVICE pointers.
+ */
+typedef struct ks_model_batch {
+    int32_t nx;
+    int32_t ny;
+    int32_t B;
+    int32_t reserved;
+    const float *F, *u, *Q, *H, *d, *R;
+    const double *m0, *P0;
+    const int64_t *offsets;
+} ks_model_batch;
+
 /* Layout of the materialised filtering elements written by ks_build_elements
  * (Lemma 3) into the workspace: structure of arrays, component-major.  The
  * c-th scalar component of element k (0-based step) is the float at
@@ -158,6 +177,20 @@ int ks_smooth_scan(const ks_model *m, int64_t T, const float *fmean, const float
  */
 int ks_smooth(const ks_model *m, const float *y, int64_t T, void *ws, size_t ws_bytes,
               float *fmean, float *fcov, float *smean, float *scov, void *stream);
+
+/*
+ * Batched end to end: one forward and one reverse scan over the B sequences
+ * laid end to end (segmented scans; no combine crosses into a neighbouring
+ * sequence's result because each sequence's first filtering element has
+ * A_1 = 0 and its last smoothing element has E_n = 0).  y [total_T][ny] and
+ * the outputs [total_T][nx], [total_T][nx][nx] are concatenated in sequence
+ * order (device, FP32).  ws: ks_workspace_bytes_batch(nx, ny, B, total_T)
+ * bytes.  An inconsistent offsets table is reported by ks_status as
+ * KS_EINVAL.
+ */
+size_t ks_workspace_bytes_batch(int nx, int ny, int B, int64_t total_T);
+int ks_smooth_batch(const ks_model_batch *mb, const float *y, int64_t total_T, void *ws, size_t ws_bytes,
+                    float *fmean, float *fcov, float *smean, float *scov, void *stream);
 
 /*
  * ks_smooth with per-kernel timing: `events` points to 4 cudaEvent_t handles

@@ -21,7 +21,7 @@ from dataclasses import dataclass
 import torch
 
 __all__ = [
-    "KsError", "Model", "lib", "workspace_bytes", "alloc_workspace", "smooth", "build_elements",
+    "KsError", "Model", "ModelBatch", "smooth_batch", "workspace_bytes_batch", "lib", "workspace_bytes", "alloc_workspace", "smooth", "build_elements",
     "elements", "filter_scan", "smooth_scan", "status", "filter_combine_batch",
     "smoother_combine_batch", "supported", "KS_WS_SMOOTH", "KS_WS_ELEMENTS",
 ]
@@ -45,6 +45,14 @@ class _KsModel(ctypes.Structure):
                 ("F", ctypes.c_void_p), ("u", ctypes.c_void_p), ("Q", ctypes.c_void_p),
                 ("H", ctypes.c_void_p), ("d", ctypes.c_void_p), ("R", ctypes.c_void_p),
                 ("m0", ctypes.c_void_p), ("P0", ctypes.c_void_p)]
+
+
+class _KsModelBatch(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("B", ctypes.c_int32),
+                ("reserved", ctypes.c_int32),
+                ("F", ctypes.c_void_p), ("u", ctypes.c_void_p), ("Q", ctypes.c_void_p),
+                ("H", ctypes.c_void_p), ("d", ctypes.c_void_p), ("R", ctypes.c_void_p),
+                ("m0", ctypes.c_void_p), ("P0", ctypes.c_void_p), ("offsets", ctypes.c_void_p)]
 
 
 class _KsLayout(ctypes.Structure):
@@ -78,6 +86,8 @@ def lib():
             "ks_smooth": ([M, vp, i64, vp, sz, vp, vp, vp, vp, vp], i32),
             "ks_smooth_traced": ([M, vp, i64, vp, sz, vp, vp, vp, vp, vp, ctypes.POINTER(vp)], i32),
             "ks_status": ([vp, vp], i32),
+            "ks_workspace_bytes_batch": ([i32, i32, i32, i64], sz),
+            "ks_smooth_batch": ([ctypes.POINTER(_KsModelBatch), vp, i64, vp, sz, vp, vp, vp, vp, vp], i32),
             "ks_filter_combine_batch": ([i32, i64, vp, vp, vp, vp, sz, vp], i32),
             "ks_smoother_combine_batch": ([i32, i64, vp, vp, vp, vp, sz, vp], i32),
         }
@@ -280,3 +290,86 @@ def smoother_combine_batch(nx: int, left: torch.Tensor, right: torch.Tensor, ws=
     """Lemma 6 on packed element pairs [count, 2nx^2+nx]; returns (out, ws)."""
     return _combine(lib().ks_smoother_combine_batch, "ks_smoother_combine_batch", nx, left, right, ws,
                     stream)
+
+
+@dataclass
+class ModelBatch:
+    """B time-invariant models for sequences laid end to end (``ks_smooth_batch``).
+
+    Per-sequence arrays stacked on a leading axis of length B (FP32; m0, P0
+    FP64) and the int64 ``offsets`` [B+1] of each sequence's first step.
+    """
+
+    F: torch.Tensor
+    Q: torch.Tensor
+    H: torch.Tensor
+    R: torch.Tensor
+    m0: torch.Tensor
+    P0: torch.Tensor
+    offsets: torch.Tensor
+    u: torch.Tensor | None = None
+    d: torch.Tensor | None = None
+
+    @classmethod
+    def create(cls, models, lengths, device="cuda") -> "ModelBatch":
+        """``models``: objects with F, Q, H, R, m0, P0 (and optionally u, d) of
+        one common (nx, ny); ``lengths``: steps of each sequence (>= 1)."""
+        import numpy as np
+        f32, f64 = torch.float32, torch.float64
+
+        def stack(name, dtype):
+            return _dev(np.stack([np.asarray(getattr(m, name)) for m in models]), dtype, device)
+
+        has_u = any(getattr(m, "u", None) is not None and np.any(np.asarray(m.u) != 0) for m in models)
+        has_d = any(getattr(m, "d", None) is not None and np.any(np.asarray(m.d) != 0) for m in models)
+        off = np.concatenate([[0], np.cumsum(np.asarray(lengths, dtype=np.int64))])
+        return cls(F=stack("F", f32), Q=stack("Q", f32), H=stack("H", f32), R=stack("R", f32),
+                   m0=stack("m0", f64), P0=stack("P0", f64),
+                   offsets=torch.as_tensor(off, dtype=torch.int64, device=device),
+                   u=stack("u", f32) if has_u else None, d=stack("d", f32) if has_d else None)
+
+    @property
+    def nx(self) -> int:
+        return int(self.F.shape[1])
+
+    @property
+    def ny(self) -> int:
+        return int(self.H.shape[1])
+
+    @property
+    def B(self) -> int:
+        return int(self.F.shape[0])
+
+    def struct(self) -> _KsModelBatch:
+        return _KsModelBatch(self.nx, self.ny, self.B, 0, self.F.data_ptr(),
+                             0 if self.u is None else self.u.data_ptr(), self.Q.data_ptr(),
+                             self.H.data_ptr(), 0 if self.d is None else self.d.data_ptr(),
+                             self.R.data_ptr(), self.m0.data_ptr(), self.P0.data_ptr(),
+                             self.offsets.data_ptr())
+
+
+def workspace_bytes_batch(nx: int, ny: int, B: int, total_T: int) -> int:
+    n = lib().ks_workspace_bytes_batch(nx, ny, B, total_T)
+    if n == 0:
+        raise KsError(KS_EUNSUPPORTED if not supported(nx, ny) else KS_EINVAL, "ks_workspace_bytes_batch")
+    return int(n)
+
+
+def smooth_batch(batch: ModelBatch, y: torch.Tensor, ws: torch.Tensor | None = None, *, fmean=None,
+                 fcov=None, smean=None, scov=None, stream=None):
+    """Batched end to end (``ks_smooth_batch``) over ``y`` [total_T, ny]
+    (sequences concatenated); returns concatenated (fmean, fcov, smean, scov)."""
+    T = int(y.shape[0])
+    n = batch.nx
+    if ws is None:
+        nbytes = workspace_bytes_batch(n, batch.ny, batch.B, T)
+        ws = torch.empty(nbytes, dtype=torch.uint8, device=y.device)
+        _check(lib().ks_workspace_init(_p(ws), nbytes, _stream(stream)), "ks_workspace_init")
+    fmean = _out((T, n), y, fmean)
+    fcov = _out((T, n, n), y, fcov)
+    smean = _out((T, n), y, smean)
+    scov = _out((T, n, n), y, scov)
+    mb = batch.struct()
+    _check(lib().ks_smooth_batch(ctypes.byref(mb), _p(y), T, _p(ws), ws.numel(), _p(fmean), _p(fcov),
+                                 _p(smean), _p(scov), _stream(stream)), "ks_smooth_batch")
+    return fmean, fcov, smean, scov

@@ -59,7 +59,7 @@ const char* ks_strerror(int code) {
 size_t ks_workspace_bytes(const ks_model* m, int64_t T, int purpose) {
     const VTable* v = nullptr;
     if (check_nx_ny(m, &v) || T < 1 || T > 0x7fffffffLL) return 0;
-    const Layout L = v->layout(T);
+    const Layout L = v->layout(T, 1);
     if (purpose == KS_WS_SMOOTH) return L.bytes_smooth;
     if (purpose == KS_WS_ELEMENTS) return L.bytes_elements;
     return 0;
@@ -75,7 +75,7 @@ int ks_elements_layout_get(const ks_model* m, int64_t T, ks_elements_layout* out
     int rc = check_nx_ny(m, &v);
     if (rc) return rc;
     if (!out || T < 1 || T > 0x7fffffffLL) return KS_EINVAL;
-    const Layout L = v->layout(T);
+    const Layout L = v->layout(T, 1);
     const int64_t n = m->nx, f = 4 * L.ld;
     out->ld = L.ld;
     out->offset_A = (int64_t)L.off_elems;
@@ -127,6 +127,21 @@ int ks_smooth_traced(const ks_model* m, const float* y, int64_t T, void* ws, siz
                      events);
 }
 
+size_t ks_workspace_bytes_batch(int nx, int ny, int B, int64_t total_T) {
+    const VTable* v = find_impl(nx, ny);
+    if (!v || B < 1 || total_T < B || total_T > 0x7fffffffLL) return 0;
+    return v->layout(total_T, B).bytes_smooth;
+}
+
+int ks_smooth_batch(const ks_model_batch* mb, const float* y, int64_t total_T, void* ws, size_t ws_bytes,
+                    float* fmean, float* fcov, float* smean, float* scov, void* stream) {
+    if (!mb || mb->nx < 1 || mb->ny < 1) return KS_EINVAL;
+    const VTable* v = find_impl(mb->nx, mb->ny);
+    if (!v) return KS_EUNSUPPORTED;
+    return v->smooth_batch(mb, y, total_T, ws, ws_bytes, fmean, fcov, smean, scov,
+                           static_cast<cudaStream_t>(stream));
+}
+
 int ks_status(void* ws, void* stream) {
     if (!ws) return KS_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -135,6 +150,7 @@ int ks_status(void* ws, void* stream) {
     if (cudaStreamSynchronize(s) != cudaSuccess) return KS_ECUDA;
     if (cudaMemsetAsync(ws, 0, sizeof(h), s) != cudaSuccess) return KS_ECUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return KS_ECUDA;
+    if (h & ST_BADARG) return KS_EINVAL;
     if (h & ST_TIMEOUT) return KS_ETIMEOUT;
     if (h & ST_NUMERIC) return KS_ENUMERIC;
     return KS_OK;

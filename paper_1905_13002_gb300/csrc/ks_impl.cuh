@@ -19,6 +19,7 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct Layout {
     int64_t T = 0, ld = 0;
+    int B = 1;
     int ntf = 0, nts = 0;
     size_t off_const = 0, off_flags = 0, flags_bytes = 0;
     size_t off_fagg = 0, off_fpre = 0, off_sagg = 0, off_spre = 0, off_sblk = 0;
@@ -29,13 +30,15 @@ struct Layout {
 // Function table of one instantiation.
 struct VTable {
     int nx, ny;
-    Layout (*layout)(int64_t T);
+    Layout (*layout)(int64_t T, int B);
     int (*build_elements)(const ks_model*, const float*, int64_t, void*, size_t, cudaStream_t);
     int (*filter_scan)(const ks_model*, int64_t, void*, size_t, float*, float*, cudaStream_t);
     int (*smooth_scan)(const ks_model*, int64_t, const float*, const float*, void*, size_t, float*, float*,
                        cudaStream_t);
     int (*smooth)(const ks_model*, const float*, int64_t, void*, size_t, float*, float*, float*, float*,
                   cudaStream_t, void* const*);
+    int (*smooth_batch)(const ks_model_batch*, const float*, int64_t, void*, size_t, float*, float*, float*,
+                        float*, cudaStream_t);
     int (*fcomb_batch)(int64_t, const float*, const float*, float*, void*, cudaStream_t);
     int (*scomb_batch)(int64_t, const float*, const float*, float*, void*, cudaStream_t);
 };
@@ -53,15 +56,16 @@ struct Impl {
     static constexpr int64_t FTILE = (int64_t)FNT * FCH, STILE = (int64_t)SNT * SCH;
     static constexpr int NCOMP = 3 * N * N + 2 * N;   // scalars of one filtering element
 
-    static Layout layout(int64_t T) {
+    static Layout layout(int64_t T, int B = 1) {
         Layout L;
         L.T = T;
+        L.B = B;
         L.ld = (int64_t)align_up((size_t)T, 64);
         L.ntf = (int)((T + FTILE - 1) / FTILE);
         L.nts = (int)((T + STILE - 1) / STILE);
         size_t off = 256;                                   // status word + reserved
-        L.off_const = off;
-        off = align_up(off + sizeof(ModelConst<N, M>), 256);
+        L.off_const = off;                                  // one ModelConst per segment
+        off = align_up(off + sizeof(ModelConst<N, M>) * (size_t)B, 256);
         L.off_flags = off;                                  // [fcounter, scounter, 2 pad][fflags][sflags]
         L.flags_bytes = 16 + 4 * (size_t)(L.ntf + L.nts);
         off = align_up(off + L.flags_bytes, 256);
@@ -133,9 +137,12 @@ struct Impl {
     static int prep(const ks_model* m, const float* y, void* ws, const Layout& L, cudaStream_t st) {
         uint32_t* z = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + L.off_flags);
         prep_kernel<N, M><<<1, 128, 0, st>>>(m->F, m->u, m->Q, m->H, m->d, m->R, m->m0, m->P0, y,
-                                             mconst(ws, L), status(ws), z, (int)(L.flags_bytes / 4));
+                                             mconst(ws, L), status(ws), z, (int)(L.flags_bytes / 4), nullptr,
+                                             L.T);
         return launch_status();
     }
+
+    static Segs<N, M> no_segs() { return Segs<N, M>{nullptr, nullptr, 1}; }
 
     static int reset_flags(void* ws, const Layout& L, cudaStream_t st) {
         return cudaMemsetAsync(static_cast<char*>(ws) + L.off_flags, 0, L.flags_bytes, st) == cudaSuccess
@@ -152,38 +159,38 @@ struct Impl {
         return reinterpret_cast<float*>(static_cast<char*>(ws) + L.off_sblk);
     }
 
-    static int launch_filter(void* ws, const Layout& L, const float* y, const float* el, float* fm,
-                             float* fc, bool from_y, cudaStream_t st) {
-        ScanState s = fstate(ws, L);
+    template <bool SEG>
+    static int launch_filter_fused(void* ws, const Layout& L, const float* y, float* fm, float* fc,
+                                   Segs<N, M> segs, cudaStream_t st) {
         constexpr int smem = filter_dyn_smem<N, FNT>();
-        if (from_y) {   // fused path: also folds the smoothing block aggregates
-            auto k = filter_scan_kernel<N, M, FNT, FCH, true, true>;
-            static const bool ok = allow_smem(k, smem);
-            if (!ok) return KS_ECUDA;
-            k<<<L.ntf, FNT, smem, st>>>(mconst(ws, L), y, nullptr, L.ld, L.T, fm, fc, s, sblk(ws, L));
-        } else {
-            auto k = filter_scan_kernel<N, M, FNT, FCH, false, false>;
-            static const bool ok = allow_smem(k, smem);
-            if (!ok) return KS_ECUDA;
-            k<<<L.ntf, FNT, smem, st>>>(mconst(ws, L), nullptr, el, L.ld, L.T, fm, fc, s, nullptr);
-        }
+        auto k = filter_scan_kernel<N, M, FNT, FCH, true, true, SEG>;
+        static const bool ok = allow_smem(k, smem);
+        if (!ok) return KS_ECUDA;
+        k<<<L.ntf, FNT, smem, st>>>(mconst(ws, L), y, nullptr, L.ld, L.T, fm, fc, fstate(ws, L), sblk(ws, L),
+                                    segs);
         return launch_status();
     }
 
+    static int launch_filter_soa(void* ws, const Layout& L, const float* el, float* fm, float* fc,
+                                 cudaStream_t st) {
+        constexpr int smem = filter_dyn_smem<N, FNT>();
+        auto k = filter_scan_kernel<N, M, FNT, FCH, false, false, false>;
+        static const bool ok = allow_smem(k, smem);
+        if (!ok) return KS_ECUDA;
+        k<<<L.ntf, FNT, smem, st>>>(mconst(ws, L), nullptr, el, L.ld, L.T, fm, fc, fstate(ws, L), nullptr,
+                                    no_segs());
+        return launch_status();
+    }
+
+    template <bool FROM_AGG, bool SEG>
     static int launch_smoother(void* ws, const Layout& L, const float* fm, const float* fc, float* sm,
-                               float* sc, bool from_agg, cudaStream_t st) {
+                               float* sc, Segs<N, M> segs, cudaStream_t st) {
         constexpr int smem = smoother_dyn_smem<N, SNT>();
-        if (from_agg) {
-            auto k = smoother_scan_kernel<N, M, SNT, SCH, true>;
-            static const bool ok = allow_smem(k, smem);
-            if (!ok) return KS_ECUDA;
-            k<<<L.nts, SNT, smem, st>>>(mconst(ws, L), fm, fc, L.T, sm, sc, sstate(ws, L), sblk(ws, L));
-        } else {
-            auto k = smoother_scan_kernel<N, M, SNT, SCH, false>;
-            static const bool ok = allow_smem(k, smem);
-            if (!ok) return KS_ECUDA;
-            k<<<L.nts, SNT, smem, st>>>(mconst(ws, L), fm, fc, L.T, sm, sc, sstate(ws, L), nullptr);
-        }
+        auto k = smoother_scan_kernel<N, M, SNT, SCH, FROM_AGG, SEG>;
+        static const bool ok = allow_smem(k, smem);
+        if (!ok) return KS_ECUDA;
+        k<<<L.nts, SNT, smem, st>>>(mconst(ws, L), fm, fc, L.T, sm, sc, sstate(ws, L),
+                                    FROM_AGG ? sblk(ws, L) : nullptr, segs);
         return launch_status();
     }
 
@@ -208,7 +215,7 @@ struct Impl {
         if (!fm || !fc || !aligned16(fm) || !aligned16(fc)) return KS_EINVAL;
         if ((rc = reset_flags(ws, L, st))) return rc;
         const float* el = reinterpret_cast<const float*>(static_cast<char*>(ws) + L.off_elems);
-        return launch_filter(ws, L, nullptr, el, fm, fc, false, st);
+        return launch_filter_soa(ws, L, el, fm, fc, st);
     }
 
     static int smooth_scan(const ks_model* m, int64_t T, const float* fm, const float* fc, void* ws,
@@ -219,7 +226,7 @@ struct Impl {
         if (!fm || !fc || !sm || !sc || !aligned16(fm) || !aligned16(fc) || !aligned16(sm) || !aligned16(sc))
             return KS_EINVAL;
         if ((rc = prep(m, nullptr, ws, L, st))) return rc;
-        return launch_smoother(ws, L, fm, fc, sm, sc, false, st);
+        return launch_smoother<false, false>(ws, L, fm, fc, sm, sc, no_segs(), st);
     }
 
     static int record(void* const* ev, int i, cudaStream_t st) {
@@ -243,10 +250,32 @@ struct Impl {
         if ((rc = record(ev, 0, st))) return rc;
         if ((rc = prep(m, y, ws, L, st))) return rc;
         if ((rc = record(ev, 1, st))) return rc;
-        if ((rc = launch_filter(ws, L, y, nullptr, fm, fc, true, st))) return rc;
+        if ((rc = launch_filter_fused<false>(ws, L, y, fm, fc, no_segs(), st))) return rc;
         if ((rc = record(ev, 2, st))) return rc;
-        if ((rc = launch_smoother(ws, L, fm, fc, sm, sc, true, st))) return rc;
+        if ((rc = launch_smoother<true, false>(ws, L, fm, fc, sm, sc, no_segs(), st))) return rc;
         return record(ev, 3, st);
+    }
+
+    // B sequences laid end to end (offsets in mb->offsets), T steps in total.
+    static int smooth_batch(const ks_model_batch* mb, const float* y, int64_t T, void* ws, size_t ws_bytes,
+                            float* fm, float* fc, float* sm, float* sc, cudaStream_t st) {
+        if (!mb || !mb->F || !mb->Q || !mb->H || !mb->R || !mb->m0 || !mb->P0 || !mb->offsets)
+            return KS_EINVAL;
+        if (mb->B < 1 || mb->B > T || T < 1 || T > 0x7fffffffLL) return KS_EINVAL;
+        const Layout L = layout(T, mb->B);
+        if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) != 0 || ws_bytes < L.bytes_smooth) return KS_EINVAL;
+        if (!y || !fm || !fc || !sm || !sc) return KS_EINVAL;
+        if (!aligned16(y) || !aligned16(fm) || !aligned16(fc) || !aligned16(sm) || !aligned16(sc))
+            return KS_EINVAL;
+        uint32_t* z = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + L.off_flags);
+        prep_kernel<N, M><<<mb->B, 128, 0, st>>>(mb->F, mb->u, mb->Q, mb->H, mb->d, mb->R, mb->m0, mb->P0, y,
+                                                 mconst(ws, L), status(ws), z, (int)(L.flags_bytes / 4),
+                                                 mb->offsets, T);
+        int rc = launch_status();
+        if (rc) return rc;
+        const Segs<N, M> segs{mconst(ws, L), mb->offsets, mb->B};
+        if ((rc = launch_filter_fused<true>(ws, L, y, fm, fc, segs, st))) return rc;
+        return launch_smoother<true, true>(ws, L, fm, fc, sm, sc, segs, st);
     }
 
     static int fcomb_batch(int64_t count, const float* l, const float* r, float* o, void* ws, cudaStream_t st) {
@@ -264,7 +293,7 @@ struct Impl {
     }
 
     static constexpr VTable vtable() {
-        return VTable{N, M, &layout, &build_elements, &filter_scan, &smooth_scan, &smooth,
+        return VTable{N, M, &layout, &build_elements, &filter_scan, &smooth_scan, &smooth, &smooth_batch,
                       &fcomb_batch, &scomb_batch};
     }
 };

@@ -51,7 +51,7 @@ extern "C" int ks_smooth_noalloc(const ks_model* m, const float* y, int64_t T, f
     if (!fmean || !fcov) return KS_EINVAL;
     const VTable* v = find_impl(4, 2);
     if (!v) return KS_EUNSUPPORTED;
-    if (v->layout(T).bytes_smooth > (size_t)KS_NOALLOC_SCRATCH_BYTES) return KS_EINVAL;
+    if (v->layout(T, 1).bytes_smooth > (size_t)KS_NOALLOC_SCRATCH_BYTES) return KS_EINVAL;
     void* ws = nullptr;
     int rc = scratch_on_current_device(&ws);
     if (rc) return rc;

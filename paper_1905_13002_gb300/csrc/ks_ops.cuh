@@ -20,7 +20,7 @@ __host__ __device__ constexpr int sidx(int i, int j) {
 }
 
 // Device status bits (combined with atomicOr into the workspace status word).
-enum : uint32_t { ST_NUMERIC = 1u, ST_TIMEOUT = 2u };
+enum : uint32_t { ST_NUMERIC = 1u, ST_TIMEOUT = 2u, ST_BADARG = 4u };
 
 // ---------------------------------------------------------------- elements
 // Filtering element of Lemma 3: f(x|z) = N(x; A z + b, C), g(z) ∝ N_I(z; eta, J).

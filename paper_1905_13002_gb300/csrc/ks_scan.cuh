@@ -214,12 +214,82 @@ KS_DEV void load_const(const ModelConst<N, M>* __restrict__ g, ModelConst<N, M>&
     for (int i = tid; i < (int)(sizeof(ModelConst<N, M>) / 4); i += nt) dst[i] = __ldg(src + i);
 }
 
+// ---------------------------------------------------------------- segments
+// Scans may run over several independent sequences laid end to end (segment
+// s = steps [off[s], off[s+1]) of the concatenated axis).  No combine needs
+// to know where a segment starts: a segment's first filtering element has
+// A_1 = 0 (Lemma 3), so any prefix combined with it yields exactly that
+// segment's own (b_1, C_1), and its last smoothing element has E_n = 0
+// (Lemma 5), so any suffix combined after it is discarded.  Only the element
+// builders need each step's segment (its model constants, whether the step
+// is a segment's first or last).  A single sequence is the case off = {0, T}
+// with its constants in shared memory.
+template <int N, int M>
+struct Segs {
+    const ModelConst<N, M>* mcg;   // per-segment constants [B] (batched)
+    const int64_t* off;            // [B+1] (batched), else nullptr
+    int B;
+};
+
+template <int N, int M, bool SEG>
+struct Cursor {
+    const ModelConst<N, M>* mc;
+    int64_t start, end;
+    int s;
+
+    KS_DEV void seek(const Segs<N, M>& g, const ModelConst<N, M>* single, int64_t k, int64_t T) {
+        if constexpr (!SEG) {
+            mc = single;
+            start = 0;
+            end = T;
+            s = 0;
+        } else {
+            int lo = 0, hi = g.B - 1;          // largest s with off[s] <= k
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (__ldg(g.off + mid) <= k) lo = mid;
+                else hi = mid - 1;
+            }
+            s = lo;
+            start = __ldg(g.off + s);
+            end = __ldg(g.off + s + 1);
+            mc = g.mcg + s;
+        }
+    }
+    // The loops stop at the table's ends, so an inconsistent table (reported
+    // by the preparation kernel) cannot take a cursor out of bounds.
+    KS_DEV void forward(const Segs<N, M>& g, int64_t k) {
+        if constexpr (SEG) {
+            while (k >= end && s < g.B - 1) {
+                ++s;
+                start = end;
+                end = __ldg(g.off + s + 1);
+                mc = g.mcg + s;
+            }
+        }
+    }
+    KS_DEV void backward(const Segs<N, M>& g, int64_t k) {
+        if constexpr (SEG) {
+            while (k < start && s > 0) {
+                --s;
+                end = start;
+                start = __ldg(g.off + s);
+                mc = g.mcg + s;
+            }
+        }
+    }
+    KS_DEV bool first(int64_t k) const { return k == start; }
+    KS_DEV bool last(int64_t k) const { return k == end - 1; }
+};
+
 // ---------------------------------------------------------------- prep
 // Model constants, one thread block.  k > 1 quantities in FP32 (Lemma 3 with
 // the Cholesky factor of S); the k = 1 element (Kalman prediction and update
 // from N(m0, P0), Lemma 3) in FP64.  Every matrix product is spread over the
 // block, one output entry per thread, so the FP64 chain is a few products
-// deep.  The block also zeroes the scans' tile counters and flags.
+// deep.  Block s prepares segment s (batched: the model arrays hold one model
+// per segment and `off` gives the segments' first steps); block 0 also zeroes
+// the scans' tile counters and flags and checks the segment table.
 template <int N, int M>
 struct PrepSmem {
     float F[N][N], Q[N][N], H[M][N], R[M][M], u[N], d[M];
@@ -236,11 +306,31 @@ __global__ void __launch_bounds__(128) prep_kernel(const float* __restrict__ F, 
                                                    const double* __restrict__ m0, const double* __restrict__ P0,
                                                    const float* __restrict__ y, ModelConst<N, M>* __restrict__ out,
                                                    uint32_t* __restrict__ status, uint32_t* __restrict__ zero,
-                                                   int nzero) {
+                                                   int nzero, const int64_t* __restrict__ off, int64_t T) {
     __shared__ PrepSmem<N, M> p;
     __shared__ ModelConst<N, M> mc;
     const int t = threadIdx.x, nt = blockDim.x;
-    for (int i = t; i < nzero; i += nt) zero[i] = 0u;
+    const int sg = blockIdx.x;
+    if (sg == 0)
+        for (int i = t; i < nzero; i += nt) zero[i] = 0u;
+    if (off != nullptr && t == 0) {
+        const int64_t a = off[sg], b = off[sg + 1];
+        const bool okseg = (a < b) && (sg != 0 || a == 0) && (sg != (int)gridDim.x - 1 || b == T);
+        if (!okseg) atomicOr(status, ST_BADARG);
+    }
+    F += (size_t)sg * N * N;
+    Q += (size_t)sg * N * N;
+    H += (size_t)sg * M * N;
+    R += (size_t)sg * M * M;
+    m0 += (size_t)sg * N;
+    P0 += (size_t)sg * N * N;
+    if (u) u += (size_t)sg * N;
+    if (d) d += (size_t)sg * M;
+    if (y && off) {   // an empty or out-of-range segment has no first measurement
+        const int64_t a = off[sg], b = off[sg + 1];
+        y = (a >= 0 && a < b && a < T) ? y + a * M : nullptr;
+    }
+    out += sg;
     if (t == 0) p.ok = 1;
     for (int e = t; e < N * N; e += nt) {
         const int a = e / N, b = e % N;
@@ -744,13 +834,14 @@ KS_DEV void build_selem_from(const ModelConst<N, M>& mc, const float (&xb)[N], c
 // from the posterior it has just produced and folds the thread's block of
 // them (Lemma 6, associativity lets the fold run forward), writing one
 // smoothing block aggregate per thread to `sagg` for the reverse scan.
-template <int N, int M, int NT, int CH, bool FROM_Y, bool SAGG>
+template <int N, int M, int NT, int CH, bool FROM_Y, bool SAGG, bool SEG>
 __global__ void __launch_bounds__(NT) filter_scan_kernel(const ModelConst<N, M>* __restrict__ mcg,
                                                          const float* __restrict__ y,
                                                          const float* __restrict__ el, int64_t ld,
                                                          int64_t T, float* __restrict__ fmean,
                                                          float* __restrict__ fcov, ScanState ss,
-                                                         float* __restrict__ sagg) {
+                                                         float* __restrict__ sagg, Segs<N, M> segs) {
+    static_assert(FROM_Y || !SEG, "segmented scans build their elements from y");
     using BS = BlockScan<FilterOp<N>, NT>;
     using SG = Stage<N>;
     constexpr int64_t TILE = (int64_t)NT * CH;
@@ -770,25 +861,37 @@ __global__ void __launch_bounds__(NT) filter_scan_kernel(const ModelConst<N, M>*
 
     // ---- phase 1: fold this thread's block of steps
     FElem<N> acc;
+    Cursor<N, M, SEG> cur;
     if (!valid) {
         set_identity<N>(acc);
     } else if constexpr (FROM_Y) {
-        if (k0 == 0) {
-            first_element<N, M>(mc, acc);
+        cur.seek(segs, &mc, k0, T);
+        if (cur.first(k0)) {
+            first_element<N, M>(*cur.mc, acc);
         } else {
             float yk[M], b[N], w[M];
             load_meas<M>(y, k0, yk);
-            meas_element<N, M>(mc, yk, b, w);
-            expand_meas<N, M>(mc, b, w, acc);
+            meas_element<N, M>(*cur.mc, yk, b, w);
+            expand_meas<N, M>(*cur.mc, b, w, acc);
         }
 #pragma unroll 1
         for (int i = 1; i < CH; ++i) {
             const int64_t k = k0 + i;
             if (k >= T) break;
-            float yk[M], b[N], w[M];
-            load_meas<M>(y, k, yk);
-            meas_element<N, M>(mc, yk, b, w);
-            acc = fcombine_meas<N, M>(acc, mc, b, w, bad);
+            cur.forward(segs, k);
+            if (cur.first(k)) {   // acc (x) a_1 = (0, b_1, C_1, eta_acc, J_acc) since A_1 = 0, eta_1 = J_1 = 0
+#pragma unroll
+                for (int a = 0; a < N * N; ++a) acc.A[a] = 0.f;
+#pragma unroll
+                for (int a = 0; a < N; ++a) acc.b[a] = cur.mc->b1[a];
+#pragma unroll
+                for (int a = 0; a < sym_size(N); ++a) acc.C[a] = cur.mc->C1[a];
+            } else {
+                float yk[M], b[N], w[M];
+                load_meas<M>(y, k, yk);
+                meas_element<N, M>(*cur.mc, yk, b, w);
+                acc = fcombine_meas<N, M>(acc, *cur.mc, b, w, bad);
+            }
         }
     } else {
         acc = load_soa<N>(el, ld, k0);
@@ -813,22 +916,24 @@ __global__ void __launch_bounds__(NT) filter_scan_kernel(const ModelConst<N, M>*
         bool pending = false;
         float probe = 0.f;
         SElem<N> sacc;
+        if constexpr (FROM_Y) cur.seek(segs, &mc, k0, T);
 #pragma unroll 1
         for (int i = 0; i < CH; ++i) {
             const int64_t k = k0 + i;
             if (k >= T) break;
             if constexpr (FROM_Y) {
-                if (!has) {  // only step k = 0: the first element has A_1 = 0
+                cur.forward(segs, k);
+                if (cur.first(k)) {  // posterior (x) a_1 = (b_1, C_1): A_1 = 0
 #pragma unroll
-                    for (int a = 0; a < N; ++a) st.b[a] = mc.b1[a];
+                    for (int a = 0; a < N; ++a) st.b[a] = cur.mc->b1[a];
 #pragma unroll
-                    for (int a = 0; a < sym_size(N); ++a) st.C[a] = mc.C1[a];
+                    for (int a = 0; a < sym_size(N); ++a) st.C[a] = cur.mc->C1[a];
                     has = true;
                 } else {
                     float yk[M], b[N], w[M];
                     load_meas<M>(y, k, yk);
-                    meas_element<N, M>(mc, yk, b, w);
-                    fadvance_meas<N, M>(st, mc, b, w, bad);
+                    meas_element<N, M>(*cur.mc, yk, b, w);
+                    fadvance_meas<N, M>(st, *cur.mc, b, w, bad);
                 }
             } else {
                 const FElem<N> e = load_soa<N>(el, ld, k);
@@ -842,7 +947,7 @@ __global__ void __launch_bounds__(NT) filter_scan_kernel(const ModelConst<N, M>*
             probe += finite_probe<N>(st.b, st.C);
             if constexpr (SAGG) {
                 SElem<N> e;
-                build_selem_from<N, M>(mc, st.b, st.C, k == T - 1, e, bad);
+                build_selem_from<N, M>(*cur.mc, st.b, st.C, cur.last(k), e, bad);
                 sacc = (i == 0) ? e : scombine<N>(sacc, e);
             }
             if constexpr (SG::kOn) {
@@ -917,13 +1022,13 @@ struct RevReader {
 // scan's grid); the reverse scan visits them last block first.  With FROM_AGG
 // each thread's block aggregate comes from the forward scan (`sagg`);
 // otherwise it is folded here from the filtered moments.
-template <int N, int M, int NT, int CH, bool FROM_AGG>
+template <int N, int M, int NT, int CH, bool FROM_AGG, bool SEG>
 __global__ void __launch_bounds__(NT) smoother_scan_kernel(const ModelConst<N, M>* __restrict__ mcg,
                                                            const float* __restrict__ fmean,
                                                            const float* __restrict__ fcov, int64_t T,
                                                            float* __restrict__ smean,
                                                            float* __restrict__ scov, ScanState ss,
-                                                           const float* __restrict__ sagg) {
+                                                           const float* __restrict__ sagg, Segs<N, M> segs) {
     using BS = BlockScan<SmootherOp<N>, NT>;
     using SG = Stage<N>;
     using RR = RevReader<N>;
@@ -959,6 +1064,8 @@ __global__ void __launch_bounds__(NT) smoother_scan_kernel(const ModelConst<N, M
     if constexpr (FROM_AGG) {
         if (valid) acc = load_cg<SElem<N>>(sagg + c * (int64_t)(sizeof(SElem<N>) / 4));
     } else if (valid) {
+        Cursor<N, M, SEG> cur;
+        cur.seek(segs, &mc, khi, T);
         if constexpr (SG::kOn) {
             rd.fetch(fmean, fcov, 0);
             rd.fetch(fmean, fcov, 1);
@@ -972,8 +1079,9 @@ __global__ void __launch_bounds__(NT) smoother_scan_kernel(const ModelConst<N, M
                 for (int s = gc - 1; s >= 0; --s) {
                     float xb[N], P[sym_size(N)];
                     stage_read<N>(rd.buf(g), s, xb, P);
+                    cur.backward(segs, lo + s);
                     SElem<N> e;
-                    build_selem_from<N, M>(mc, xb, P, lo + s == T - 1, e, bad);
+                    build_selem_from<N, M>(*cur.mc, xb, P, cur.last(lo + s), e, bad);
                     acc = first ? e : scombine<N>(e, acc);
                     first = false;
                 }
@@ -985,8 +1093,9 @@ __global__ void __launch_bounds__(NT) smoother_scan_kernel(const ModelConst<N, M
                 const int64_t k = khi - i;
                 float xb[N], P[sym_size(N)];
                 load_posterior<N>(fmean, fcov, k, xb, P);
+                cur.backward(segs, k);
                 SElem<N> e;
-                build_selem_from<N, M>(mc, xb, P, k == T - 1, e, bad);
+                build_selem_from<N, M>(*cur.mc, xb, P, cur.last(k), e, bad);
                 acc = (i == 0) ? e : scombine<N>(e, acc);
             }
         }
@@ -1000,6 +1109,8 @@ __global__ void __launch_bounds__(NT) smoother_scan_kernel(const ModelConst<N, M
     // ---- phase 3
     if (valid) {
         float probe = 0.f;
+        Cursor<N, M, SEG> cur;
+        cur.seek(segs, &mc, khi, T);
         if constexpr (SG::kOn) {
             rd.fetch(fmean, fcov, 0);
             rd.fetch(fmean, fcov, 1);
@@ -1013,8 +1124,9 @@ __global__ void __launch_bounds__(NT) smoother_scan_kernel(const ModelConst<N, M
                 for (int s = gc - 1; s >= 0; --s) {
                     float xb[N], P[sym_size(N)];
                     stage_read<N>(b, s, xb, P);
+                    cur.backward(segs, lo + s);
                     SElem<N> e;
-                    build_selem_from<N, M>(mc, xb, P, lo + s == T - 1, e, bad);
+                    build_selem_from<N, M>(*cur.mc, xb, P, cur.last(lo + s), e, bad);
                     if (!has) { st = SmootherOp<N>::state_of(e); has = true; }   // only k = T-1
                     else sadvance<N>(e, st);
                     stage_write<N>(b, s, st.g, st.L);     // the slot's input is already in registers
@@ -1033,8 +1145,9 @@ __global__ void __launch_bounds__(NT) smoother_scan_kernel(const ModelConst<N, M
                 const int64_t k = khi - i;
                 float xb[N], P[sym_size(N)];
                 load_posterior<N>(fmean, fcov, k, xb, P);
+                cur.backward(segs, k);
                 SElem<N> e;
-                build_selem_from<N, M>(mc, xb, P, k == T - 1, e, bad);
+                build_selem_from<N, M>(*cur.mc, xb, P, cur.last(k), e, bad);
                 if (!has) { st = SmootherOp<N>::state_of(e); has = true; }
                 else sadvance<N>(e, st);
                 store_posterior<N>(smean, scov, k, st.g, st.L);

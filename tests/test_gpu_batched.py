@@ -1,0 +1,92 @@
+"""GPU parity of the segmented (batched) scans: many sequences of uneven
+length laid end to end, each checked against the FP64 oracle on its own."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import parity
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ks():
+    from paper_1905_13002_gb300 import _build
+    _build.build()
+    import paper_1905_13002_gb300 as ks
+    return ks
+
+
+def make_batch(dim, lengths, seed):
+    rng = np.random.default_rng(seed)
+    seqs = []
+    for T in lengths:
+        m = workloads.wiener_velocity(dim, dt=0.1, q=float(rng.uniform(0.5, 2)), r=float(rng.uniform(0.1, 1)))
+        _, y = workloads.simulate(m, int(T), rng)
+        seqs.append(workloads.Sequence(m, y))
+    return seqs
+
+
+def run_and_check(ks, seqs):
+    batch = ks.ModelBatch.create([s.model for s in seqs], [s.T for s in seqs])
+    y = torch.as_tensor(np.concatenate([s.y for s in seqs]), dtype=torch.float32, device="cuda")
+    ws = torch.empty(ks.workspace_bytes_batch(batch.nx, batch.ny, batch.B, y.shape[0]), dtype=torch.uint8,
+                     device="cuda")
+    assert ks.lib().ks_workspace_init(ks._p(ws), ws.numel(), ks._stream(None)) == 0
+    out = [t.cpu().numpy() for t in ks.smooth_batch(batch, y, ws)]
+    assert ks.status(ws) == ks.KS_OK
+    worst = 0.0
+    o = 0
+    for s in seqs:
+        ref = oracle.kf_rts(s.model, s.y)
+        e = parity.errors([x[o:o + s.T] for x in out], ref)
+        worst = max(worst, max(e.values()))
+        o += s.T
+    assert worst < parity.TOL, worst
+    return worst
+
+
+# Lengths put boundaries inside thread blocks (32 steps) and tiles (4096),
+# include one-step sequences, and sequences shorter than a block.
+EDGE = [1, 2, 31, 32, 33, 1, 127, 128, 129, 5000, 1, 4096, 4097, 3, 8191, 64]
+
+
+@pytest.mark.parametrize("dim", [1, 2, 3])
+def test_edge_lengths(ks, dim):
+    run_and_check(ks, make_batch(dim, EDGE, 10 + dim))
+
+
+@pytest.mark.parametrize("dim", [1, 2, 3])
+def test_log_uniform_lengths(ks, dim):
+    rng = np.random.default_rng(20 + dim)
+    lengths = workloads.batch_lengths(120, rng, 256, 16384)
+    run_and_check(ks, make_batch(dim, lengths, 30 + dim))
+
+
+def test_single_sequence_batch_equals_plain_call(ks):
+    seqs = make_batch(2, [20000], 7)
+    run_and_check(ks, seqs)
+
+
+def test_batched_config_sample(ks):
+    """The batched workload's own generator (mixed nx), one call per nx group."""
+    seqs = workloads.config_batched(B=96)
+    for nx in (2, 4, 6):
+        group = [s for s in seqs if s.model.nx == nx]
+        if group:
+            run_and_check(ks, group)
+
+
+def test_bad_offsets_reported(ks):
+    seqs = make_batch(2, [100, 200], 9)
+    batch = ks.ModelBatch.create([s.model for s in seqs], [s.T for s in seqs])
+    y = torch.as_tensor(np.concatenate([s.y for s in seqs]), dtype=torch.float32, device="cuda")
+    ws = torch.zeros(ks.workspace_bytes_batch(4, 2, 2, 300), dtype=torch.uint8, device="cuda")
+    # The second sequence is made empty (offsets 0, 300, 300): every offset
+    # stays within [0, T], so all accesses are in bounds, and the device check
+    # flags the table as inconsistent.
+    batch.offsets[1] = 300
+    ks.smooth_batch(batch, y, ws)
+    assert ks.status(ws) == ks.KS_EINVAL
