@@ -51,6 +51,10 @@ def parse():
     ap.add_argument("--T", type=int, default=1 << 20)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="long", choices=["long", "batched"],
+                    help="long: one T=2^20 nx=4 sequence per GPU (default); batched: 4096 sequences, "
+                         "lengths log-uniform in [256, 16384], nx in {2,4,6}")
+    ap.add_argument("--batch", type=int, default=4096)
     return ap.parse_args()
 
 
@@ -226,6 +230,9 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
+    if args.workload == "batched":
+        run_batched(args, rank, world, local)
+        return
 
     import torch
     import torch.distributed as dist
@@ -285,6 +292,7 @@ def main():
         raise SystemExit(f"device status {st} after the timed steps")
 
     tot = [e[0].elapsed_time(e[3]) for e in evs]
+    lat = {"p50_ms": float(np.percentile(tot, 50)), "p99_ms": float(np.percentile(tot, 99))}
     kf = [e[1].elapsed_time(e[2]) for e in evs]
     ksm = [e[2].elapsed_time(e[3]) for e in evs]
     ms = statistics.mean(tot)
@@ -355,9 +363,188 @@ def main():
                       "sequences_per_gpu": 1, "parallelism": f"replicas{world}",
                       "l2": "flushed between timed steps (256 MiB memset outside the events)"},
            "clocks": {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
-           "gpu_launches": 3 * args.steps, "e2e": e2e, "roofline": roof}
+           "gpu_launches": 3 * args.steps, "latency": lat, "e2e": e2e, "roofline": roof}
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_oracle_rate(seq, args.cpu_seconds)
+    print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------- batched workload
+def cpu_oracle_batched(seqs, seconds: float) -> dict:
+    """The FP64 oracle over the batch's sequences on all host cores (one
+    sequence per task; the C oracle releases the GIL), on a bounded sample:
+    sequences in order until `seconds` have elapsed."""
+    from concurrent.futures import ThreadPoolExecutor
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    done_steps = 0
+    done = 0
+    with ThreadPoolExecutor(max_workers=cores) as ex:
+        i = 0
+        while i < len(seqs) and time.perf_counter() - t0 < seconds:
+            chunk = seqs[i:i + 4 * cores]
+            list(ex.map(lambda q: oracle.kf_rts(q.model, q.y), chunk))
+            done_steps += sum(q.T for q in chunk)
+            done += len(chunk)
+            i += len(chunk)
+    el = time.perf_counter() - t0
+    return {"value": done_steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {done} of {len(seqs)} sequences ({done_steps} steps, {el:.1f} s, {cores} threads)"}
+
+
+def run_batched(args, rank, world, local):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1905_13002_gb300 as ks
+    from paper_1905_13002_gb300 import _build
+
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if local == 0:
+        _build.build()
+    if world > 1:
+        dist.barrier()
+    seqs = workloads.config_batched(B=args.batch, seed=workloads.SEED_BASE + 3 + rank)
+    total = sum(q.T for q in seqs)
+    groups = []
+    for nx in sorted({q.model.nx for q in seqs}):
+        g = [q for q in seqs if q.model.nx == nx]
+        batch = ks.ModelBatch.create([q.model for q in g], [q.T for q in g], device=dev)
+        y = torch.as_tensor(np.concatenate([q.y for q in g]), dtype=torch.float32, device=dev)
+        T = int(y.shape[0])
+        ws = torch.zeros(ks.workspace_bytes_batch(batch.nx, batch.ny, batch.B, T), dtype=torch.uint8,
+                         device=dev)
+        outs = [torch.empty(T, nx, device=dev), torch.empty(T, nx, nx, device=dev),
+                torch.empty(T, nx, device=dev), torch.empty(T, nx, nx, device=dev)]
+        groups.append({"nx": nx, "B": batch.B, "T": T, "batch": batch, "y": y, "ws": ws, "outs": outs,
+                       "stream": torch.cuda.Stream(device=dev)})
+    def step():
+        main = torch.cuda.current_stream()      # the capture stream while a graph is recorded
+        for g in groups:
+            g["stream"].wait_stream(main)
+            with torch.cuda.stream(g["stream"]):
+                fm, fP, sm, sP = g["outs"]
+                ks.smooth_batch(g["batch"], g["y"], g["ws"], fmean=fm, fcov=fP, smean=sm, scov=sP)
+        for g in groups:
+            main.wait_stream(g["stream"])
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    for g in groups:
+        if ks.status(g["ws"]) != ks.KS_OK:
+            raise SystemExit(f"device status not OK (nx={g['nx']})")
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(2):
+        graph.replay()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    clocks.start()
+    time.sleep(0.3)
+    times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        graph.replay()
+        b.record()
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+    time.sleep(0.3)
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    for g in groups:
+        if ks.status(g["ws"]) != ks.KS_OK:
+            raise SystemExit(f"device status not OK after timing (nx={g['nx']})")
+    ms = statistics.mean(times)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = total * world / (ms / 1e3)
+
+    # the plain single-sequence scan, one call per sequence, same GPU
+    plain = []
+    for q in seqs:
+        m = q.model
+        model = ks.Model.create(m.F, m.Q, m.H, m.R, m.m0, m.P0, device=dev)
+        yq = torch.as_tensor(q.y, dtype=torch.float32, device=dev)
+        wsq = ks.alloc_workspace(model, q.T)
+        o = [torch.empty(q.T, m.nx, device=dev), torch.empty(q.T, m.nx, m.nx, device=dev),
+             torch.empty(q.T, m.nx, device=dev), torch.empty(q.T, m.nx, m.nx, device=dev)]
+        plain.append((model, yq, wsq, o))
+
+    def plain_pass():
+        for model, yq, wsq, o in plain:
+            ks.smooth(model, yq, wsq, fmean=o[0], fcov=o[1], smean=o[2], scov=o[3])
+
+    plain_pass()
+    torch.cuda.synchronize()
+    ptimes = []
+    for _ in range(3):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        plain_pass()
+        b.record()
+        b.synchronize()
+        ptimes.append(a.elapsed_time(b))
+    pms = statistics.median(ptimes)
+
+    # roofline over the whole graph step: algorithmic bytes and flops of all groups
+    hbm, which = peaks()
+    nbytes = 0
+    nflops = 0
+    for g in groups:
+        bps = bytes_per_step(g["nx"], g["nx"] // 2)
+        fps = flops_per_step(g["nx"], g["nx"] // 2)
+        nbytes += (bps["filter"] + bps["smoother"]) * g["T"]
+        nflops += (fps["filter"] + fps["smoother"]) * g["T"]
+    dur = ms / 1e3
+    gbs = nbytes / dur / 1e9
+    tfl = nflops / dur / 1e12
+    alu_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    if tfl / alu_peak >= gbs / hbm:
+        roof = {"bound": "alu", "achieved": tfl, "peak": alu_peak, "unit": "TFLOP/s", "frac": tfl / alu_peak}
+    else:
+        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm}
+    roof.update({"traffic": None, "kernel": "whole graph step (3 groups x (prep + 2 scans))",
+                 "hbm_frac": gbs / hbm, "alu_frac": tfl / alu_peak})
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "batched: log-uniform T in [256,16384], nx in {2,4,6} Wiener-velocity, "
+                                  "q~U[0.5,2], R=rI r~U[0.1,1]", "sequences": len(seqs), "total_steps": total,
+                      "groups": [{"nx": g["nx"], "B": g["B"], "T": g["T"]} for g in groups],
+                      "launch": "one CUDA graph: 3 segmented ks_smooth_batch calls on 3 streams",
+                      "l2": "flushed between timed steps (256 MiB memset outside the events)"},
+           "clocks": {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+           "gpu_launches": 9 * args.steps,
+           "latency": {"p50_ms": float(np.percentile(times, 50)), "p99_ms": float(np.percentile(times, 99))},
+           "plain_scan": {"value": total / (pms / 1e3), "unit": UNIT, "ms_per_pass": pms,
+                          "how": "ks_smooth once per sequence, sequentially on one stream"},
+           "roofline": roof}
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_oracle_batched(seqs, args.cpu_seconds)
     print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()
