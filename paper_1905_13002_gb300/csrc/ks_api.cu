@@ -10,8 +10,10 @@ namespace ks {
 extern const VTable kImpl_2_1;
 extern const VTable kImpl_4_2;
 extern const VTable kImpl_6_3;
+extern const VTable kImpl_8_4;
+extern const VTable kImpl_32_8;
 
-static const VTable* const kImpls[] = {&kImpl_2_1, &kImpl_4_2, &kImpl_6_3};
+static const VTable* const kImpls[] = {&kImpl_2_1, &kImpl_4_2, &kImpl_6_3, &kImpl_8_4, &kImpl_32_8};
 
 const VTable* find_impl(int nx, int ny) {
     for (const VTable* v : kImpls)

@@ -1,0 +1,191 @@
+// ks_gimpl.cuh -- host side of the one-warp-per-chain instantiations (larger
+// nx): workspace layout and launches behind the same C ABI as ks_impl.cuh.
+#pragma once
+
+#include "ks_gscan.cuh"
+#include "ks_impl.cuh"
+
+namespace ks {
+
+template <int N, int M, int NW, int CH>
+struct GImpl {
+    static constexpr int FS = grp::Dim<N>::FSLOT, SS = grp::Dim<N>::SSLOT;
+    static constexpr int64_t TILE = (int64_t)NW * CH;
+    using SM = grp::GSmem<N, M, NW>;
+
+    static size_t prep_smem() { return sizeof(PrepSmem<N, M>) + sizeof(ModelConst<N, M>) + 16; }
+
+    static Layout layout(int64_t T, int B = 1) {
+        Layout L;
+        L.T = T;
+        L.B = B;
+        L.ld = 0;
+        const int64_t nch = (T + CH - 1) / CH;
+        L.ntf = L.nts = (int)((nch + NW - 1) / NW);
+        size_t off = 256;
+        L.off_const = off;
+        off = align_up(off + sizeof(ModelConst<N, M>) * (size_t)B, 256);
+        L.off_flags = off;
+        L.flags_bytes = 16 + 4 * (size_t)(L.ntf + L.nts);
+        off = align_up(off + L.flags_bytes, 256);
+        L.off_fagg = off;                                   // filter: agg, pre, tile prefixes, chains
+        off = align_up(off + 4 * (size_t)FS * L.ntf * 3, 256);
+        L.off_fpre = off;
+        off = align_up(off + 4 * (size_t)FS * (size_t)(L.ntf * NW) * 2, 256);
+        L.off_sagg = off;                                   // smoother: agg, pre, tile prefixes, chains
+        off = align_up(off + 4 * (size_t)SS * L.nts * 3, 256);
+        L.off_spre = off;
+        off = align_up(off + 4 * (size_t)SS * (size_t)(L.nts * NW) * 2, 256);
+        L.off_sblk = off;
+        L.bytes_smooth = off;
+        L.off_elems = off;
+        L.off_fmean = off;
+        off = align_up(off + 4 * (size_t)N * (size_t)T, 256);
+        L.off_fcov = off;
+        off = align_up(off + 4 * (size_t)N * N * (size_t)T, 256);
+        L.bytes_elements = off;
+        return L;
+    }
+
+    static ModelConst<N, M>* mconst(void* ws, const Layout& L) {
+        return reinterpret_cast<ModelConst<N, M>*>(static_cast<char*>(ws) + L.off_const);
+    }
+    static uint32_t* status(void* ws) { return static_cast<uint32_t*>(ws); }
+
+    static void states(void* ws, const Layout& L, ScanState& fs, grp::GBuf& fb, ScanState& ss, grp::GBuf& sb) {
+        char* b = static_cast<char*>(ws);
+        fs.counter = reinterpret_cast<uint32_t*>(b + L.off_flags);
+        fs.flags = reinterpret_cast<uint32_t*>(b + L.off_flags + 16);
+        float* fa = reinterpret_cast<float*>(b + L.off_fagg);
+        fs.agg = fa;
+        fs.pre = fa + (size_t)FS * L.ntf;
+        fb.tex = fa + (size_t)FS * L.ntf * 2;
+        fb.chains = reinterpret_cast<float*>(b + L.off_fpre);
+        fs.status = status(ws);
+        fs.spin_limit = kSpinLimit;
+        ss.counter = reinterpret_cast<uint32_t*>(b + L.off_flags + 4);
+        ss.flags = reinterpret_cast<uint32_t*>(b + L.off_flags + 16 + 4 * (size_t)L.ntf);
+        float* sa = reinterpret_cast<float*>(b + L.off_sagg);
+        ss.agg = sa;
+        ss.pre = sa + (size_t)SS * L.nts;
+        sb.tex = sa + (size_t)SS * L.nts * 2;
+        sb.chains = reinterpret_cast<float*>(b + L.off_spre);
+        ss.status = status(ws);
+        ss.spin_limit = kSpinLimit;
+    }
+
+    template <class K>
+    static bool allow_smem(K kernel, int bytes) {
+        return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess;
+    }
+
+    static int prep(const float* F, const float* u, const float* Q, const float* H, const float* d,
+                    const float* R, const double* m0, const double* P0, const float* y, int B,
+                    const int64_t* off, void* ws, const Layout& L, cudaStream_t st) {
+        const int smem = (int)prep_smem();
+        auto k = prep_kernel<N, M>;
+        static const bool ok = allow_smem(k, smem);
+        if (!ok) return KS_ECUDA;
+        uint32_t* z = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + L.off_flags);
+        k<<<B, 128, smem, st>>>(F, u, Q, H, d, R, m0, P0, y, mconst(ws, L), status(ws), z,
+                                (int)(L.flags_bytes / 4), off, L.T);
+        return launch_status();
+    }
+
+    template <bool SEG>
+    static int scans(void* ws, const Layout& L, const float* y, float* fm, float* fc, float* sm, float* sc,
+                     Segs<N, M> segs, cudaStream_t st, void* const* ev, bool filter, bool smoother) {
+        ScanState fs, ss;
+        grp::GBuf fb, sb;
+        states(ws, L, fs, fb, ss, sb);
+        constexpr int smem = SM::BYTES;
+        if (filter) {
+            auto k = grp::gfilter_kernel<N, M, NW, CH, SEG>;
+            static const bool ok = allow_smem(k, smem);
+            if (!ok) return KS_ECUDA;
+            k<<<L.ntf, NW * 32, smem, st>>>(mconst(ws, L), y, L.T, fm, fc, fs, fb, segs);
+            int rc = launch_status();
+            if (rc) return rc;
+        }
+        if (ev && ev[2] && cudaEventRecord(static_cast<cudaEvent_t>(ev[2]), st) != cudaSuccess) return KS_ECUDA;
+        if (smoother) {
+            auto k = grp::gsmoother_kernel<N, M, NW, CH, SEG>;
+            static const bool ok = allow_smem(k, smem);
+            if (!ok) return KS_ECUDA;
+            k<<<L.nts, NW * 32, smem, st>>>(mconst(ws, L), fm, fc, L.T, sm, sc, ss, sb, segs);
+            int rc = launch_status();
+            if (rc) return rc;
+        }
+        return KS_OK;
+    }
+
+    static int check(const ks_model* m, int64_t T, void* ws, size_t ws_bytes, size_t need) {
+        if (!m || !m->F || !m->Q || !m->H || !m->R || !m->m0 || !m->P0) return KS_EINVAL;
+        if (m->time_varying != 0) return KS_EUNSUPPORTED;
+        if (T < 1 || T > 0x7fffffffLL) return KS_EINVAL;
+        if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) != 0 || ws_bytes < need) return KS_EINVAL;
+        return KS_OK;
+    }
+
+    static int build_elements(const ks_model*, const float*, int64_t, void*, size_t, cudaStream_t) {
+        return KS_EUNSUPPORTED;   // materialised elements are offered for the register-resident sizes
+    }
+    static int filter_scan(const ks_model*, int64_t, void*, size_t, float*, float*, cudaStream_t) {
+        return KS_EUNSUPPORTED;
+    }
+
+    static int smooth_scan(const ks_model* m, int64_t T, const float* fm, const float* fc, void* ws,
+                           size_t ws_bytes, float* sm, float* sc, cudaStream_t st) {
+        const Layout L = layout(T);
+        int rc = check(m, T, ws, ws_bytes, L.bytes_smooth);
+        if (rc) return rc;
+        if (!fm || !fc || !sm || !sc) return KS_EINVAL;
+        if ((rc = prep(m->F, m->u, m->Q, m->H, m->d, m->R, m->m0, m->P0, nullptr, 1, nullptr, ws, L, st)))
+            return rc;
+        return scans<false>(ws, L, nullptr, const_cast<float*>(fm), const_cast<float*>(fc), sm, sc,
+                            Segs<N, M>{nullptr, nullptr, 1}, st, nullptr, false, true);
+    }
+
+    static int smooth(const ks_model* m, const float* y, int64_t T, void* ws, size_t ws_bytes, float* fm,
+                      float* fc, float* sm, float* sc, cudaStream_t st, void* const* ev) {
+        const Layout L = layout(T);
+        const bool own = (fm == nullptr) || (fc == nullptr);
+        int rc = check(m, T, ws, ws_bytes, own ? L.bytes_elements : L.bytes_smooth);
+        if (rc) return rc;
+        if (!y || !sm || !sc) return KS_EINVAL;
+        if (own) {
+            fm = reinterpret_cast<float*>(static_cast<char*>(ws) + L.off_fmean);
+            fc = reinterpret_cast<float*>(static_cast<char*>(ws) + L.off_fcov);
+        }
+        if (ev && ev[0] && cudaEventRecord(static_cast<cudaEvent_t>(ev[0]), st) != cudaSuccess) return KS_ECUDA;
+        if ((rc = prep(m->F, m->u, m->Q, m->H, m->d, m->R, m->m0, m->P0, y, 1, nullptr, ws, L, st))) return rc;
+        if (ev && ev[1] && cudaEventRecord(static_cast<cudaEvent_t>(ev[1]), st) != cudaSuccess) return KS_ECUDA;
+        if ((rc = scans<false>(ws, L, y, fm, fc, sm, sc, Segs<N, M>{nullptr, nullptr, 1}, st, ev, true, true)))
+            return rc;
+        if (ev && ev[3] && cudaEventRecord(static_cast<cudaEvent_t>(ev[3]), st) != cudaSuccess) return KS_ECUDA;
+        return KS_OK;
+    }
+
+    static int smooth_batch(const ks_model_batch* mb, const float* y, int64_t T, void* ws, size_t ws_bytes,
+                            float* fm, float* fc, float* sm, float* sc, cudaStream_t st) {
+        if (!mb || !mb->F || !mb->Q || !mb->H || !mb->R || !mb->m0 || !mb->P0 || !mb->offsets)
+            return KS_EINVAL;
+        if (mb->B < 1 || mb->B > T || T < 1 || T > 0x7fffffffLL) return KS_EINVAL;
+        const Layout L = layout(T, mb->B);
+        if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) != 0 || ws_bytes < L.bytes_smooth) return KS_EINVAL;
+        if (!y || !fm || !fc || !sm || !sc) return KS_EINVAL;
+        int rc = prep(mb->F, mb->u, mb->Q, mb->H, mb->d, mb->R, mb->m0, mb->P0, y, mb->B, mb->offsets, ws, L, st);
+        if (rc) return rc;
+        return scans<true>(ws, L, y, fm, fc, sm, sc, Segs<N, M>{mconst(ws, L), mb->offsets, mb->B}, st, nullptr,
+                           true, true);
+    }
+
+    static int no_comb(int64_t, const float*, const float*, float*, void*, cudaStream_t) { return KS_EUNSUPPORTED; }
+
+    static constexpr VTable vtable() {
+        return VTable{N, M, &layout, &build_elements, &filter_scan, &smooth_scan, &smooth, &smooth_batch,
+                      &no_comb, &no_comb};
+    }
+};
+
+}  // namespace ks

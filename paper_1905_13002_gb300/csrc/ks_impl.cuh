@@ -56,6 +56,8 @@ struct Impl {
     static constexpr int64_t FTILE = (int64_t)FNT * FCH, STILE = (int64_t)SNT * SCH;
     static constexpr int NCOMP = 3 * N * N + 2 * N;   // scalars of one filtering element
 
+    static constexpr size_t prep_smem() { return sizeof(PrepSmem<N, M>) + sizeof(ModelConst<N, M>) + 16; }
+
     static Layout layout(int64_t T, int B = 1) {
         Layout L;
         L.T = T;
@@ -136,7 +138,7 @@ struct Impl {
     // scans' tile counters and flags, which every scan launch needs.
     static int prep(const ks_model* m, const float* y, void* ws, const Layout& L, cudaStream_t st) {
         uint32_t* z = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + L.off_flags);
-        prep_kernel<N, M><<<1, 128, 0, st>>>(m->F, m->u, m->Q, m->H, m->d, m->R, m->m0, m->P0, y,
+        prep_kernel<N, M><<<1, 128, prep_smem(), st>>>(m->F, m->u, m->Q, m->H, m->d, m->R, m->m0, m->P0, y,
                                              mconst(ws, L), status(ws), z, (int)(L.flags_bytes / 4), nullptr,
                                              L.T);
         return launch_status();
@@ -268,7 +270,7 @@ struct Impl {
         if (!aligned16(y) || !aligned16(fm) || !aligned16(fc) || !aligned16(sm) || !aligned16(sc))
             return KS_EINVAL;
         uint32_t* z = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + L.off_flags);
-        prep_kernel<N, M><<<mb->B, 128, 0, st>>>(mb->F, mb->u, mb->Q, mb->H, mb->d, mb->R, mb->m0, mb->P0, y,
+        prep_kernel<N, M><<<mb->B, 128, prep_smem(), st>>>(mb->F, mb->u, mb->Q, mb->H, mb->d, mb->R, mb->m0, mb->P0, y,
                                                  mconst(ws, L), status(ws), z, (int)(L.flags_bytes / 4),
                                                  mb->offsets, T);
         int rc = launch_status();

@@ -307,8 +307,10 @@ __global__ void __launch_bounds__(128) prep_kernel(const float* __restrict__ F, 
                                                    const float* __restrict__ y, ModelConst<N, M>* __restrict__ out,
                                                    uint32_t* __restrict__ status, uint32_t* __restrict__ zero,
                                                    int nzero, const int64_t* __restrict__ off, int64_t T) {
-    __shared__ PrepSmem<N, M> p;
-    __shared__ ModelConst<N, M> mc;
+    extern __shared__ __align__(16) char prep_dsm[];
+    PrepSmem<N, M>& p = *reinterpret_cast<PrepSmem<N, M>*>(prep_dsm);
+    ModelConst<N, M>& mc =
+        *reinterpret_cast<ModelConst<N, M>*>(prep_dsm + ((sizeof(PrepSmem<N, M>) + 15) / 16) * 16);
     const int t = threadIdx.x, nt = blockDim.x;
     const int sg = blockIdx.x;
     if (sg == 0)

@@ -90,3 +90,13 @@ def test_bad_offsets_reported(ks):
     batch.offsets[1] = 300
     ks.smooth_batch(batch, y, ws)
     assert ks.status(ws) == ks.KS_EINVAL
+
+
+def test_random_stable_nx8_batch(ks):
+    rng = np.random.default_rng(77)
+    seqs = []
+    for T in [1, 5, 31, 32, 33, 127, 128, 129, 3000, 1, 700]:
+        m = workloads.random_stable(8, 4, rng)
+        _, y = workloads.simulate(m, T, rng)
+        seqs.append(workloads.Sequence(m, y))
+    run_and_check(ks, seqs)

@@ -240,3 +240,36 @@ def test_random_stable_nx8(ks, T):
     m = workloads.random_stable(8, 4, rng)
     _, y = workloads.simulate(m, T, rng)
     check(ks, m, y)
+
+
+@pytest.mark.parametrize("T", [1, 63, 64, 65, 193, 1000])
+def test_random_stable_nx32_sizes(ks, T):
+    """nx = 32 (one warp per chain): edge sizes around a chain (64 steps) and
+    a tile (3 chains)."""
+    rng = np.random.default_rng(500 + T)
+    m = workloads.random_stable(32, 8, rng)
+    _, y = workloads.simulate(m, T, rng)
+    e = check(ks, m, y, tol=parity.TOL_NX32)
+    print(f"nx=32 T={T} errors", e)
+
+
+def test_precision_workload_nx32(ks):
+    """The nx = 32, ny = 8, T = 65536 random stable workload against the FP64 oracle."""
+    seq = workloads.config_precision()
+    e = check(ks, seq.model, seq.y, tol=parity.TOL_NX32)
+    print("nx=32 T=65536 errors", e)
+
+
+@pytest.mark.parametrize("T", [1, 2048, 9000])
+def test_smooth_scan_nx8_from_given_moments(ks, T):
+    rng = np.random.default_rng(600 + T)
+    m = workloads.random_stable(8, 4, rng)
+    _, y = workloads.simulate(m, T, rng)
+    rfm, rfP = oracle.kf(m, y)
+    fm32, fP32 = rfm.astype(np.float32), rfP.astype(np.float32)
+    rsm, rsP = oracle.rts(m, fm32.astype(np.float64), fP32.astype(np.float64))
+    model = gpu_model(ks, m)
+    sm, sP = ks.smooth_scan(model, torch.as_tensor(fm32, device="cuda"), torch.as_tensor(fP32, device="cuda"))
+    torch.cuda.synchronize()
+    assert parity.mean_err(sm.cpu().numpy(), rsm, rsP) < parity.TOL
+    assert parity.cov_err(sP.cpu().numpy(), rsP) < parity.TOL
