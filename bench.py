@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--T", type=int, default=1 << 20)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="long", choices=["long", "batched"],
+    ap.add_argument("--workload", default="long", choices=["long", "batched", "precision"],
                     help="long: one T=2^20 nx=4 sequence per GPU (default); batched: 4096 sequences, "
                          "lengths log-uniform in [256, 16384], nx in {2,4,6}")
     ap.add_argument("--batch", type=int, default=4096)
@@ -76,7 +76,7 @@ def bytes_per_step(nx: int, ny: int) -> dict:
     return {"filter": 4 * ny + post, "smoother": 2 * post}
 
 
-def flops_per_step(N: int, M: int) -> dict:
+def flops_per_step(N: int, M: int, fused_smoothing: bool = True) -> dict:
     """Floating-point operations per step of each kernel's per-step work
     (FMA = 2).  The forward scan folds one measurement element into its block
     aggregate (rank-M form of Lemma 4), applies it to the running filtered
@@ -95,7 +95,10 @@ def flops_per_step(N: int, M: int) -> dict:
     sel = 2 * (N ** 3 + s * N + N ** 3 // 6 + N * N * (N - 1) + 2 * N * N + s * N) + 2 * N * N + N
     scomb = 2 * (N ** 3 + s * N + N * N + N ** 3)
     sadv = 2 * (N ** 3 + N * N + s * N)
-    return {"filter": fold + adv + 2 * meas + sel + scomb, "smoother": sel + sadv}
+    if fused_smoothing:
+        return {"filter": fold + adv + 2 * meas + sel + scomb, "smoother": sel + sadv}
+    # warp-per-chain kernels (nx >= 8): the reverse scan folds its own blocks
+    return {"filter": fold + adv + 2 * meas, "smoother": 2 * sel + scomb + sadv}
 
 
 # ---------------------------------------------------------------- clocks
@@ -233,7 +236,10 @@ def main():
     if args.workload == "batched":
         run_batched(args, rank, world, local)
         return
+    run_single(args, rank, world, local, precision=args.workload == "precision")
 
+
+def run_single(args, rank, world, local, precision):
     import torch
     import torch.distributed as dist
 
@@ -243,22 +249,32 @@ def main():
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
     if local == 0:
         _build.build()
     if world > 1:
         dist.barrier()
-
-    T = args.T
-    seq = workloads.tracking_sequence(T, seed=workloads.SEED_BASE + 2 + rank)
+    if precision:
+        T = 65536 if args.T == (1 << 20) else args.T
+        seq = workloads.config_precision(T=T)
+        if rank:
+            rng = np.random.default_rng(np.random.PCG64(workloads.SEED_BASE + 4 + rank))
+            _, y = workloads.simulate(seq.model, T, rng)
+            seq = workloads.Sequence(seq.model, y)
+        wl = "random_stable nx=32 ny=8 F=O diag(U[0.9,0.99]) Q=0.1I H~N(0,1/32) R=0.5I"
+    else:
+        T = args.T
+        seq = workloads.tracking_sequence(T, seed=workloads.SEED_BASE + 2 + rank)
+        wl = "wiener_velocity_2d nx=4 ny=2 dt=0.1 q=1 R=I m0=0 P0=I"
+    dev = torch.device("cuda", local)
     m = seq.model
+    nx, ny = m.nx, m.ny
     model = ks.Model.create(m.F, m.Q, m.H, m.R, m.m0, m.P0, u=m.u, d=m.d, device=dev)
     y = torch.as_tensor(seq.y, dtype=torch.float32, device=dev)
     ws = ks.alloc_workspace(model, T, ks.KS_WS_ELEMENTS)
-    fm = torch.empty(T, 4, device=dev)
-    fP = torch.empty(T, 4, 4, device=dev)
-    sm = torch.empty(T, 4, device=dev)
-    sP = torch.empty(T, 4, 4, device=dev)
+    fm = torch.empty(T, nx, device=dev)
+    fP = torch.empty(T, nx, nx, device=dev)
+    sm = torch.empty(T, nx, device=dev)
+    sP = torch.empty(T, nx, nx, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
     stream = torch.cuda.current_stream()
 
@@ -304,8 +320,8 @@ def main():
 
     # ---- end to end through the public API with host buffers
     y_h = torch.as_tensor(seq.y, dtype=torch.float32).pin_memory()
-    sm_h = torch.empty(T, 4, dtype=torch.float32).pin_memory()
-    sP_h = torch.empty(T, 4, 4, dtype=torch.float32).pin_memory()
+    sm_h = torch.empty(T, nx, dtype=torch.float32).pin_memory()
+    sP_h = torch.empty(T, nx, nx, dtype=torch.float32).pin_memory()
     y_d = torch.empty_like(y)
     e2e_times = []
     for i in range(args.warmup + args.steps):
@@ -330,15 +346,16 @@ def main():
 
     # ---- roofline of the dominant kernel
     hbm, which = peaks()
-    bps = bytes_per_step(4, 2)
-    fps = flops_per_step(4, 2)
+    bps = bytes_per_step(nx, ny)
+    fps = flops_per_step(nx, ny, fused_smoothing=nx <= 6)
     kernels = {"filter": statistics.mean(kf), "smoother": statistics.mean(ksm)}
     dom = max(kernels, key=kernels.get)
     dur_s = kernels[dom] / 1e3
     gbs = bps[dom] * T / dur_s / 1e9
     alu_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
     tfl = fps[dom] * T / dur_s / 1e12
-    kname = {"filter": "filter_scan_kernel", "smoother": "smoother_scan_kernel"}[dom]
+    kname = ({"filter": "filter_scan_kernel", "smoother": "smoother_scan_kernel"} if nx <= 6 else
+             {"filter": "gfilter_kernel", "smoother": "gsmoother_kernel"})[dom]
     traffic = recorded_traffic(kname)
     if tfl / alu_peak >= gbs / hbm:
         roof = {"bound": "alu", "achieved": tfl, "peak": alu_peak, "unit": "TFLOP/s",
@@ -359,7 +376,7 @@ def main():
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": "wiener_velocity_2d nx=4 ny=2 dt=0.1 q=1 R=I m0=0 P0=I", "T": T,
+           "config": {"workload": wl, "T": T,
                       "sequences_per_gpu": 1, "parallelism": f"replicas{world}",
                       "l2": "flushed between timed steps (256 MiB memset outside the events)"},
            "clocks": {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},

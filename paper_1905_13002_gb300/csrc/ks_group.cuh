@@ -17,10 +17,12 @@ constexpr unsigned kFullMask = 0xffffffffu;
 
 template <int N>
 struct Dim {
-    // Row pitch (floats).  Broadcast reads (all lanes, one address) and column
-    // reads (lane r reads column r) are bank-conflict free at any pitch; the
-    // pitch only has to hold 2 ny scalars per row in the rank-ny products.
-    static constexpr int NP = N < 8 ? 8 : N;
+    // Row pitch (floats), odd: lane r reading its own row (address r NP + k)
+    // then hits bank (r + k) mod 32, distinct across the warp; broadcast reads
+    // (one address) and column reads (lane r reads column r) are conflict free
+    // at any pitch.  It also holds the 2 ny scalars per row of the rank-ny
+    // products (ny <= nx / 2 here).
+    static constexpr int NP = N + 1;
     static constexpr int MAT = N * NP;          // one matrix
     static constexpr int FSLOT = 3 * MAT + 2 * NP;   // A, C, J, b, eta
     static constexpr int SSLOT = 2 * MAT + NP;       // E, L, g

@@ -136,15 +136,20 @@ __global__ void __launch_bounds__(NW * 32) gfilter_kernel(const ModelConst<N, M>
         int a = 0;
         copy_floats_cg(X[0].p, T0, FS);
 #pragma unroll 1
-        for (int t = 1; t < w; ++t) {
-            fcombine<N>(r, X[a], FSlot<N>{const_cast<float*>(T0) + (size_t)t * 2 * FS}, X[a ^ 1], s, bad);
+        for (int t = 1; t < w; ++t) {                    // operands staged in shared memory
+            copy_floats_cg(X[2].p, T0 + (size_t)t * 2 * FS, FS);
+            fcombine<N>(r, X[a], X[2], X[a ^ 1], s, bad);
             a ^= 1;
         }
         if (w >= 1) copy_floats(chE, X[a].p, FS);        // E_w = T_0 (x) ... (x) T_{w-1}
         if (w == L) {
             float* agg = ss.agg + (size_t)tile * FS;
-            if (w >= 1) fcombine<N>(r, X[a], FSlot<N>{chT}, FSlot<N>{agg}, s, bad);
-            else copy_floats(agg, X[0].p, FS);
+            if (w >= 1) {
+                copy_floats_cg(X[2].p, chT, FS);
+                fcombine<N>(r, X[a], X[2], X[a ^ 1], s, bad);
+                a ^= 1;
+            }
+            copy_floats(agg, X[a].p, FS);
             float* tex = gb.tex + (size_t)tile * FS;
             float* pre = ss.pre + (size_t)tile * FS;
             if (tile == 0) {
@@ -186,7 +191,10 @@ __global__ void __launch_bounds__(NW * 32) gfilter_kernel(const ModelConst<N, M>
                     --j;
                 }
                 __threadfence_block();
-                fadvance<N>(r, FSlot<N>{tex}, FSlot<N>{agg}, FSlot<N>{pre}, s, bad);
+                copy_floats(X[2].p, tex, FS);
+                copy_floats(X[0].p, agg, FS);
+                fadvance<N>(r, X[2], X[0], X[1], s, bad);
+                copy_floats(pre, X[1].p, FS);
                 publish_flag(ss.flags + tile, kFlagPre);
             }
         }
@@ -200,8 +208,13 @@ __global__ void __launch_bounds__(NW * 32) gfilter_kernel(const ModelConst<N, M>
         bool has = false;
         if (tile != 0) {
             const float* tex = gb.tex + (size_t)tile * FS;
-            if (w >= 1) fadvance<N>(r, FSlot<N>{const_cast<float*>(tex)}, FSlot<N>{chE}, X[0], s, bad);
-            else copy_floats(X[0].p, tex, FS);
+            if (w >= 1) {
+                copy_floats(X[2].p, tex, FS);
+                copy_floats(X[1].p, chE, FS);
+                fadvance<N>(r, X[2], X[1], X[0], s, bad);
+            } else {
+                copy_floats(X[0].p, tex, FS);
+            }
             has = true;
         } else if (w >= 1) {
             copy_floats(X[0].p, chE, FS);        // E_w has A = 0 (it starts with the first element)
@@ -313,14 +326,19 @@ __global__ void __launch_bounds__(NW * 32) gsmoother_kernel(const ModelConst<N, 
         copy_floats_cg(X[0].p, T0, SS);
 #pragma unroll 1
         for (int t = 1; t < w; ++t) {       // E_w = T_{w-1} (x) ... (x) T_0 in time order
-            scombine<N, false>(r, SSlot<N>{const_cast<float*>(T0) + (size_t)t * 2 * SS}, X[a], X[a ^ 1], s);
+            copy_floats_cg(X[2].p, T0 + (size_t)t * 2 * SS, SS);
+            scombine<N, false>(r, X[2], X[a], X[a ^ 1], s);
             a ^= 1;
         }
         if (w >= 1) copy_floats(chE, X[a].p, SS);
         if (w == L) {
             float* agg = ss.agg + (size_t)tile * SS;
-            if (w >= 1) scombine<N, false>(r, SSlot<N>{chT}, X[a], SSlot<N>{agg}, s);
-            else copy_floats(agg, X[0].p, SS);
+            if (w >= 1) {
+                copy_floats_cg(X[2].p, chT, SS);
+                scombine<N, false>(r, X[2], X[a], X[a ^ 1], s);
+                a ^= 1;
+            }
+            copy_floats(agg, X[a].p, SS);
             float* tex = gb.tex + (size_t)tile * SS;
             float* pre = ss.pre + (size_t)tile * SS;
             if (tile == 0) {
@@ -362,7 +380,10 @@ __global__ void __launch_bounds__(NW * 32) gsmoother_kernel(const ModelConst<N, 
                     --j;
                 }
                 __threadfence_block();
-                scombine<N, true>(r, SSlot<N>{agg}, SSlot<N>{tex}, SSlot<N>{pre}, s);
+                copy_floats(X[2].p, tex, SS);
+                copy_floats(X[0].p, agg, SS);
+                scombine<N, true>(r, X[0], X[2], X[1], s);
+                copy_floats(pre, X[1].p, SS);
                 publish_flag(ss.flags + tile, kFlagPre);
             }
         }
@@ -376,8 +397,13 @@ __global__ void __launch_bounds__(NW * 32) gsmoother_kernel(const ModelConst<N, 
         bool has = false;
         if (tile != 0) {
             const float* tex = gb.tex + (size_t)tile * SS;
-            if (w >= 1) scombine<N, true>(r, SSlot<N>{chE}, SSlot<N>{const_cast<float*>(tex)}, X[0], s);
-            else copy_floats(X[0].p, tex, SS);
+            if (w >= 1) {
+                copy_floats(X[2].p, tex, SS);
+                copy_floats(X[1].p, chE, SS);
+                scombine<N, true>(r, X[1], X[2], X[0], s);
+            } else {
+                copy_floats(X[0].p, tex, SS);
+            }
             has = true;
         } else if (w >= 1) {
             copy_floats(X[0].p, chE, SS);        // E = 0: it ends with the sequence's last element
