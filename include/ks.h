@@ -33,6 +33,11 @@
  *   covariances [T][nx][nx] (full, symmetric), all FP32.
  * - Sizes: 1 <= T <= 2^31 - 1.  Supported (nx, ny) pairs are listed by
  *   ks_supported(); others return KS_EUNSUPPORTED.
+ * - nx = 32: the operators' dense products run on the tensor cores (3xTF32,
+ *   FP32 accumulate) and the inverses of Lemmas 4 and 5 get one FP64-residual
+ *   refinement step when their estimated condition number exceeds 1e3.
+ *   ks_smooth and ks_smooth_scan then want fmean, fcov, smean and scov
+ *   16-byte aligned (KS_EINVAL otherwise).
  * - Errors: every call returns KS_OK (0) or a negative code.  Argument and
  *   launch errors are returned immediately.  Errors found on the device
  *   (non-finite values, a failed factorisation, a look-back wait that timed

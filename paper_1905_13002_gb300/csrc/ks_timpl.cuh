@@ -1,0 +1,158 @@
+// ks_timpl.cuh -- host side of the nx = 32 tensor-core scans: workspace
+// layout and launches behind the same C ABI as ks_impl.cuh.  Segmented
+// batches at this size run on the CUDA-core group kernels (ks_gimpl.cuh).
+#pragma once
+
+#include "ks_gimpl.cuh"
+#include "ks_tscan.cuh"
+
+namespace ks {
+
+template <int N, int M, int NW, int CH>
+struct TImpl {
+    static constexpr int FR = tc::Rec<N>::F, SR = tc::Rec<N>::S;
+    using FSM = tc::TSmem<N, M, NW, tc::FConst<N, M>>;
+    using SSM = tc::TSmem<N, M, NW, tc::SConst<N, M>>;
+
+    static Layout layout(int64_t T) {
+        Layout L;
+        L.T = T;
+        L.B = 1;
+        L.ld = 0;
+        const int64_t nch = (T + CH - 1) / CH;
+        L.ntf = L.nts = (int)((nch + NW - 1) / NW);
+        const size_t nchp = (size_t)L.ntf * NW;
+        size_t off = 256;
+        L.off_const = off;
+        off = align_up(off + sizeof(ModelConst<N, M>), 256);
+        L.off_flags = off;
+        L.flags_bytes = 16 + 4 * (size_t)(L.ntf + L.nts);
+        off = align_up(off + L.flags_bytes, 256);
+        L.off_fagg = off;                                   // filter: agg, pre, tile prefixes
+        off = align_up(off + 4 * (size_t)FR * L.ntf * 3, 256);
+        L.off_fpre = off;                                   // filter chains
+        off = align_up(off + 4 * (size_t)FR * nchp * 2, 256);
+        L.off_sagg = off;                                   // smoother: agg, pre, tile prefixes
+        off = align_up(off + 4 * (size_t)SR * L.nts * 3, 256);
+        L.off_spre = off;                                   // smoother chains
+        off = align_up(off + 4 * (size_t)SR * nchp * 2, 256);
+        L.off_sblk = off;                                   // smoothing elements, one per step
+        off = align_up(off + 4 * (size_t)SR * (size_t)T, 256);
+        L.bytes_smooth = off;
+        L.off_elems = off;
+        L.off_fmean = off;
+        off = align_up(off + 4 * (size_t)N * (size_t)T, 256);
+        L.off_fcov = off;
+        off = align_up(off + 4 * (size_t)N * N * (size_t)T, 256);
+        L.bytes_elements = off;
+        return L;
+    }
+
+    static void states(void* ws, const Layout& L, ScanState& fs, tc::TBuf& fb, ScanState& ss, tc::TBuf& sb) {
+        char* b = static_cast<char*>(ws);
+        uint32_t* status = static_cast<uint32_t*>(ws);
+        fs.counter = reinterpret_cast<uint32_t*>(b + L.off_flags);
+        fs.flags = reinterpret_cast<uint32_t*>(b + L.off_flags + 16);
+        float* fa = reinterpret_cast<float*>(b + L.off_fagg);
+        fs.agg = fa;
+        fs.pre = fa + (size_t)FR * L.ntf;
+        fb.tex = fa + (size_t)FR * L.ntf * 2;
+        fb.chains = reinterpret_cast<float*>(b + L.off_fpre);
+        fb.elems = nullptr;
+        fs.status = status;
+        fs.spin_limit = kSpinLimit;
+        ss.counter = reinterpret_cast<uint32_t*>(b + L.off_flags + 4);
+        ss.flags = reinterpret_cast<uint32_t*>(b + L.off_flags + 16 + 4 * (size_t)L.ntf);
+        float* sa = reinterpret_cast<float*>(b + L.off_sagg);
+        ss.agg = sa;
+        ss.pre = sa + (size_t)SR * L.nts;
+        sb.tex = sa + (size_t)SR * L.nts * 2;
+        sb.chains = reinterpret_cast<float*>(b + L.off_spre);
+        sb.elems = reinterpret_cast<float*>(b + L.off_sblk);
+        ss.status = status;
+        ss.spin_limit = kSpinLimit;
+    }
+
+    template <class K>
+    static bool allow_smem(K kernel, int bytes) {
+        return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess;
+    }
+
+    static int scans(void* ws, const Layout& L, const float* y, float* fm, float* fc, float* sm, float* sc,
+                     cudaStream_t st, void* const* ev, bool filter, bool smoother) {
+        ScanState fs, ss;
+        tc::TBuf fb, sb;
+        states(ws, L, fs, fb, ss, sb);
+        const ModelConst<N, M>* mc =
+            reinterpret_cast<const ModelConst<N, M>*>(static_cast<char*>(ws) + L.off_const);
+        if (filter) {
+            auto k = tc::tfilter_kernel<N, M, NW, CH>;
+            static const bool ok = allow_smem(k, (int)sizeof(FSM));
+            if (!ok) return KS_ECUDA;
+            k<<<L.ntf, NW * 32, sizeof(FSM), st>>>(mc, y, L.T, fm, fc, fs, fb);
+            int rc = launch_status();
+            if (rc) return rc;
+        }
+        if (ev && ev[2] && cudaEventRecord(static_cast<cudaEvent_t>(ev[2]), st) != cudaSuccess) return KS_ECUDA;
+        if (smoother) {
+            auto k = tc::tsmoother_kernel<N, M, NW, CH>;
+            static const bool ok = allow_smem(k, (int)sizeof(SSM));
+            if (!ok) return KS_ECUDA;
+            k<<<L.nts, NW * 32, sizeof(SSM), st>>>(mc, fm, fc, L.T, sm, sc, ss, sb);
+            int rc = launch_status();
+            if (rc) return rc;
+        }
+        return KS_OK;
+    }
+
+    static int check(const ks_model* m, int64_t T, void* ws, size_t ws_bytes, size_t need) {
+        if (!m || !m->F || !m->Q || !m->H || !m->R || !m->m0 || !m->P0) return KS_EINVAL;
+        if (m->time_varying != 0) return KS_EUNSUPPORTED;
+        if (T < 1 || T > 0x7fffffffLL) return KS_EINVAL;
+        if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) != 0 || ws_bytes < need) return KS_EINVAL;
+        return KS_OK;
+    }
+
+    // The caller's posterior buffers are moved with 16-byte vector accesses.
+    static bool vec_ok(const float* a, const float* b, const float* c, const float* d) {
+        return aligned16(a) && aligned16(b) && aligned16(c) && aligned16(d);
+    }
+
+    static int smooth_scan(const ks_model* m, int64_t T, const float* fm, const float* fc, void* ws,
+                           size_t ws_bytes, float* sm, float* sc, cudaStream_t st) {
+        const Layout L = layout(T);
+        int rc = check(m, T, ws, ws_bytes, L.bytes_smooth);
+        if (rc) return rc;
+        if (!fm || !fc || !sm || !sc) return KS_EINVAL;
+        if (!vec_ok(fm, fc, sm, sc)) return KS_EINVAL;
+        if ((rc = GImpl<N, M, NW, CH>::prep(m->F, m->u, m->Q, m->H, m->d, m->R, m->m0, m->P0, nullptr, 1,
+                                            nullptr, ws, L, st)))
+            return rc;
+        return scans(ws, L, nullptr, const_cast<float*>(fm), const_cast<float*>(fc), sm, sc, st, nullptr, false,
+                     true);
+    }
+
+    static int smooth(const ks_model* m, const float* y, int64_t T, void* ws, size_t ws_bytes, float* fm,
+                      float* fc, float* sm, float* sc, cudaStream_t st, void* const* ev) {
+        const Layout L = layout(T);
+        const bool own = (fm == nullptr) || (fc == nullptr);
+        int rc = check(m, T, ws, ws_bytes, own ? L.bytes_elements : L.bytes_smooth);
+        if (rc) return rc;
+        if (!y || !sm || !sc) return KS_EINVAL;
+        if (own) {
+            fm = reinterpret_cast<float*>(static_cast<char*>(ws) + L.off_fmean);
+            fc = reinterpret_cast<float*>(static_cast<char*>(ws) + L.off_fcov);
+        }
+        if (!vec_ok(fm, fc, sm, sc)) return KS_EINVAL;
+        if (ev && ev[0] && cudaEventRecord(static_cast<cudaEvent_t>(ev[0]), st) != cudaSuccess) return KS_ECUDA;
+        if ((rc = GImpl<N, M, NW, CH>::prep(m->F, m->u, m->Q, m->H, m->d, m->R, m->m0, m->P0, y, 1, nullptr, ws,
+                                            L, st)))
+            return rc;
+        if (ev && ev[1] && cudaEventRecord(static_cast<cudaEvent_t>(ev[1]), st) != cudaSuccess) return KS_ECUDA;
+        if ((rc = scans(ws, L, y, fm, fc, sm, sc, st, ev, true, true))) return rc;
+        if (ev && ev[3] && cudaEventRecord(static_cast<cudaEvent_t>(ev[3]), st) != cudaSuccess) return KS_ECUDA;
+        return KS_OK;
+    }
+};
+
+}  // namespace ks

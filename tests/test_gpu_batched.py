@@ -100,3 +100,14 @@ def test_random_stable_nx8_batch(ks):
         _, y = workloads.simulate(m, T, rng)
         seqs.append(workloads.Sequence(m, y))
     run_and_check(ks, seqs)
+
+
+def test_random_stable_nx32_batch(ks):
+    """nx = 32 batches run on the CUDA-core group kernels."""
+    rng = np.random.default_rng(78)
+    seqs = []
+    for T in [1, 5, 63, 64, 65, 200, 1]:
+        m = workloads.random_stable(32, 8, rng)
+        _, y = workloads.simulate(m, T, rng)
+        seqs.append(workloads.Sequence(m, y))
+    run_and_check(ks, seqs)

@@ -242,15 +242,41 @@ def test_random_stable_nx8(ks, T):
     check(ks, m, y)
 
 
-@pytest.mark.parametrize("T", [1, 63, 64, 65, 193, 1000])
+@pytest.mark.parametrize("T", [1, 2, 31, 32, 33, 95, 96, 97, 289, 1000, 5000])
 def test_random_stable_nx32_sizes(ks, T):
-    """nx = 32 (one warp per chain): edge sizes around a chain (64 steps) and
-    a tile (3 chains)."""
+    """nx = 32 (tensor-core operators, one warp per chain): edge sizes around a
+    chain (32 steps) and a tile (3 chains), and several tiles with a ragged tail."""
     rng = np.random.default_rng(500 + T)
     m = workloads.random_stable(32, 8, rng)
     _, y = workloads.simulate(m, T, rng)
     e = check(ks, m, y, tol=parity.TOL_NX32)
     print(f"nx=32 T={T} errors", e)
+
+
+def test_nx32_ill_conditioned_combine(ks):
+    """Accurate measurements against a large process noise make I + C_i J_j
+    badly conditioned (cond_1 well above the refinement threshold) in the
+    tile-level combines."""
+    rng = np.random.default_rng(515)
+    m = workloads.random_stable(32, 8, rng, q=1.0, r=1e-3)
+    _, y = workloads.simulate(m, 3000, rng)
+    e = check(ks, m, y, tol=parity.TOL_NX32)
+    print("nx=32 ill-conditioned errors", e)
+
+
+@pytest.mark.parametrize("T", [1, 97, 3000])
+def test_smooth_scan_nx32_from_given_moments(ks, T):
+    rng = np.random.default_rng(650 + T)
+    m = workloads.random_stable(32, 8, rng)
+    _, y = workloads.simulate(m, T, rng)
+    rfm, rfP = oracle.kf(m, y)
+    fm32, fP32 = rfm.astype(np.float32), rfP.astype(np.float32)
+    rsm, rsP = oracle.rts(m, fm32.astype(np.float64), fP32.astype(np.float64))
+    model = gpu_model(ks, m)
+    sm, sP = ks.smooth_scan(model, torch.as_tensor(fm32, device="cuda"), torch.as_tensor(fP32, device="cuda"))
+    torch.cuda.synchronize()
+    assert parity.mean_err(sm.cpu().numpy(), rsm, rsP) < parity.TOL_NX32
+    assert parity.cov_err(sP.cpu().numpy(), rsP) < parity.TOL_NX32
 
 
 def test_precision_workload_nx32(ks):
