@@ -6,7 +6,9 @@
 namespace ks {
 namespace {
 
-using TC = TImpl<32, 8, 3, 32>;
+// 3 chains of 72 steps per tile: T = 65536 is then one wave of 304 tiles
+// (two per SM).
+using TC = TImpl<32, 8, 3, 72>;
 using GR = GImpl<32, 8, 3, 64>;
 
 // One layout entry serves both: a single sequence (B = 1) gets the

@@ -28,6 +28,13 @@ namespace tc {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr float kRefineCond = 1.0e3f;
 
+// Unrolling of the k loop of the tensor-core products (code size against
+// cross-step scheduling).
+#ifndef KS_TC_KT_UNROLL
+#define KS_TC_KT_UNROLL 2
+#endif
+constexpr int kMmUnroll = KS_TC_KT_UNROLL;
+
 template <int N>
 struct TD {
     static_assert(N == 32, "the tensor-core operators hold one row per lane");
@@ -80,9 +87,11 @@ KS_DEV uint32_t to_tf32(float x) {
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
     return r;
 }
+// x = hi + lo with hi = tf32(x) rounded to nearest; lo = x - hi is exact in
+// FP32 and handed over as is (the tensor core reads its top 19 bits).
 KS_DEV void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
     hi = to_tf32(x);
-    lo = to_tf32(x - __uint_as_float(hi));
+    lo = __float_as_uint(x - __uint_as_float(hi));
 }
 KS_DEV void mma_tf32(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
     asm volatile(
@@ -110,18 +119,29 @@ KS_DEV void ldsm_x2(uint32_t (&r)[2], const float* p) {
 // op(A)(i, k) = TA ? A[k][i] : A[i][k];  op(B)(k, n) = TB ? B[n][k] : B[k][n].
 // MM x KK times KK x NN, MM a multiple of 16, NN and KK of 8.  C must not
 // alias A or B; it may equal D (each output element reads only its own D).
-// Row-major A and transposed B go through ldmatrix.  Ends with a warp barrier.
+// Row-major A and transposed B go through ldmatrix.  The k loop is outermost
+// and every output tile keeps its two accumulators (hi*hi and the cross terms)
+// live, so each k step issues 3 MT NT independent mma.  Ends with a warp
+// barrier.
 template <int MM, int NN, int KK, int PP, bool TA, bool TB>
 KS_DEV void mm(const float* A, const float* B, float* C, const float* D = nullptr, float sa = 1.f) {
     static_assert(MM % 16 == 0 && NN % 8 == 0 && KK % 8 == 0, "tile shape");
     constexpr int MT = MM / 16, NT = NN / 8, KT = KK / 8;
     const int lane = lane_id(), gid = lane >> 2, tig = lane & 3;
-    uint32_t ah[MT][KT][4], al[MT][KT][4];
+    float big[MT][NT][4], sml[MT][NT][4];
 #pragma unroll
     for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
-        for (int kt = 0; kt < KT; ++kt) {
-            const int i0 = mt * 16, k0 = kt * 8;
+        for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) big[mt][nt][e] = sml[mt][nt][e] = 0.f;
+#pragma unroll kMmUnroll
+    for (int kt = 0; kt < KT; ++kt) {
+        const int k0 = kt * 8;
+        uint32_t ah[MT][4], al[MT][4], bh[NT][2], bl[NT][2];
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt) {
+            const int i0 = mt * 16;
             float a[4];
             if constexpr (!TA) {
                 uint32_t q4[4];
@@ -136,16 +156,24 @@ KS_DEV void mm(const float* A, const float* B, float* C, const float* D = nullpt
                 a[3] = A[(k0 + tig + 4) * PP + i0 + gid + 8];
             }
 #pragma unroll
-            for (int e = 0; e < 4; ++e) split_tf32(sa * a[e], ah[mt][kt][e], al[mt][kt][e]);
+            for (int e = 0; e < 4; ++e) split_tf32(sa * a[e], ah[mt][e], al[mt][e]);
         }
 #pragma unroll
-    for (int nt = 0; nt < NT; ++nt) {
-        uint32_t bh[KT][2], bl[KT][2];
-#pragma unroll
-        for (int kt = 0; kt < KT; ++kt) {
-            const int n0 = nt * 8, k0 = kt * 8;
+        for (int nt = 0; nt < NT; ++nt) {
+            const int n0 = nt * 8;
             float b[2];
             if constexpr (TB) {
+                if (NT % 2 == 0) {
+                    if (nt % 2 == 1) continue;       // loaded with the even tile
+                    uint32_t q4[4];
+                    const int q = lane >> 3, rr = lane & 7;
+                    ldsm_x4(q4, B + (n0 + (q >> 1) * 8 + rr) * PP + k0 + (q & 1) * 4);
+                    split_tf32(__uint_as_float(q4[0]), bh[nt][0], bl[nt][0]);
+                    split_tf32(__uint_as_float(q4[1]), bh[nt][1], bl[nt][1]);
+                    split_tf32(__uint_as_float(q4[2]), bh[nt + 1][0], bl[nt + 1][0]);
+                    split_tf32(__uint_as_float(q4[3]), bh[nt + 1][1], bl[nt + 1][1]);
+                    continue;
+                }
                 uint32_t q2[2];
                 const int q = (lane >> 3) & 1, rr = lane & 7;
                 ldsm_x2(q2, B + (n0 + rr) * PP + k0 + q * 4);
@@ -155,22 +183,26 @@ KS_DEV void mm(const float* A, const float* B, float* C, const float* D = nullpt
                 b[0] = B[(k0 + tig) * PP + n0 + gid];
                 b[1] = B[(k0 + tig + 4) * PP + n0 + gid];
             }
-            split_tf32(b[0], bh[kt][0], bl[kt][0]);
-            split_tf32(b[1], bh[kt][1], bl[kt][1]);
+            split_tf32(b[0], bh[nt][0], bl[nt][0]);
+            split_tf32(b[1], bh[nt][1], bl[nt][1]);
         }
 #pragma unroll
-        for (int mt = 0; mt < MT; ++mt) {
-            float big[4] = {0.f, 0.f, 0.f, 0.f}, sml[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
-            for (int kt = 0; kt < KT; ++kt) {
-                mma_tf32(sml, al[mt][kt], bh[kt]);
-                mma_tf32(sml, ah[mt][kt], bl[kt]);
-                mma_tf32(big, ah[mt][kt], bh[kt]);
+            for (int nt = 0; nt < NT; ++nt) {
+                mma_tf32(sml[mt][nt], al[mt], bh[nt]);
+                mma_tf32(sml[mt][nt], ah[mt], bl[nt]);
+                mma_tf32(big[mt][nt], ah[mt], bh[nt]);
             }
+    }
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) {
             const int r0 = mt * 16 + gid, c0 = nt * 8 + 2 * tig;
             float v[4];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) v[e] = big[e] + sml[e];
+            for (int e = 0; e < 4; ++e) v[e] = big[mt][nt][e] + sml[mt][nt][e];
             if (D) {
                 const float2 d0 = *reinterpret_cast<const float2*>(D + r0 * PP + c0);
                 const float2 d1 = *reinterpret_cast<const float2*>(D + (r0 + 8) * PP + c0);
@@ -182,7 +214,6 @@ KS_DEV void mm(const float* A, const float* B, float* C, const float* D = nullpt
             *reinterpret_cast<float2*>(C + r0 * PP + c0) = make_float2(v[0], v[1]);
             *reinterpret_cast<float2*>(C + (r0 + 8) * PP + c0) = make_float2(v[2], v[3]);
         }
-    }
     __syncwarp();
 }
 
@@ -348,89 +379,149 @@ KS_DEV void gstore_sstate(float* g, const float* L) {
 }
 
 // ---------------------------------------------------------------- inverse
-// Scratch of one warp: vectors (P floats each) and the pivot order.
+// Scratch of one warp: vectors (P floats each), the pivot order and a double
+// buffer for the pivot row.
 template <int N>
 struct VS {
     float* p;
     KS_DEV float* v(int i) const { return p + i * TD<N>::P; }
     KS_DEV float* g() const { return p + 3 * TD<N>::P; }                 // up to 2 P floats
     KS_DEV int* piv() const { return reinterpret_cast<int*>(p + 5 * TD<N>::P); }
+    KS_DEV float* prow() const { return p + 6 * TD<N>::P; }               // 2 N floats
     static constexpr int FLOATS = 8 * TD<N>::P;
+    static_assert(6 * TD<N>::P + 2 * N <= FLOATS, "scratch layout");
 };
 
 // out = Mx^{-1} (out distinct from Mx).  Gauss-Jordan with partial pivoting,
 // in place: lane l holds row l of Mx^T (column l of Mx, so the loads and the
 // final stores are conflict free); at step k the pivot row p_k is the unused
-// row with the largest |entry| in column k, and storage column k changes from
-// column k of the matrix to column p_k of the inverse of Mx^T.  Then
-// (Mx^T)^{-1}[a][b] = W[p_a][q] with p_q = b, i.e. out[p_q][pos(l)] = W[l][q]
-// where pos(l) is the step at which lane l was the pivot.
-template <int N>
-KS_DEV bool gj_inverse(const float* Mx, float* out, int* piv) {
+// row with the largest |entry| in column k (one warp max-reduction over
+// |entry| with its low 5 mantissa bits replaced by the lane, so ties and
+// near-ties go to the lowest lane), the pivot row is broadcast through shared
+// memory, and storage column k changes from column k of the matrix to column
+// p_k of the inverse of Mx^T.  Then (Mx^T)^{-1}[a][b] = W[p_a][q] with
+// p_q = b, i.e. out[p_q][pos(l)] = W[l][q] where pos(l) is the step at which
+// lane l was the pivot.
+// The steps run in blocks of GJ_U inside a rolled loop: after each block the
+// register row is rotated left by GJ_U, so the pivot column of step kb + u is
+// always register u (a compile-time index) and the code stays small enough
+// for the instruction cache; after N steps the rotation is back to the start.
+// PIVOT = false (symmetric positive definite Mx, whose Gauss-Jordan pivots
+// stay positive without row exchanges): p_k = k, no search and no final
+// permutation.
+// Returns the 1-norm condition estimate ||Mx||_1 ||Mx^{-1}||_1 (column sums
+// from the registers); `ok` is cleared on a zero or non-finite pivot.
+constexpr int GJ_U = 4;
+
+// 1 / x: the hardware approximation refined by one Newton-Raphson step
+// y <- y (2 - x y) (relative error a few ulp).
+KS_DEV float recip(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y * fmaf(-x, y, 2.f);
+}
+
+template <int N, bool PIVOT = true>
+KS_DEV float gj_inverse(const float* Mx, float* out, VS<N> vs, bool& ok) {
     constexpr int P = TD<N>::P;
+    static_assert(N % GJ_U == 0 && GJ_U % 2 == 0, "block of steps");
     const int l = lane_id();
+    int* piv = vs.piv();
     float w[N];
 #pragma unroll
     for (int c = 0; c < N; ++c) w[c] = Mx[c * P + l];
-    bool used = false, ok = true;
+    float cm = 0.f;
+#pragma unroll
+    for (int c = 0; c < N; ++c) cm += fabsf(w[c]);
+    bool used = false;
     int pos = 0;
+    float scale = 1.f;
+#pragma unroll 1
+    for (int kb = 0; kb < N; kb += GJ_U) {
 #pragma unroll
-    for (int k = 0; k < N; ++k) {
-        float v = used ? -1.f : fabsf(w[k]);
-        int idx = l;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            const float ov = __shfl_xor_sync(kFull, v, off);
-            const int oi = __shfl_xor_sync(kFull, idx, off);
-            if (ov > v || (ov == v && oi < idx)) {
-                v = ov;
-                idx = oi;
+        for (int u = 0; u < GJ_U; ++u) {
+            float* pr = vs.prow() + (u & 1) * N;
+            int p = kb + u;
+            if constexpr (PIVOT) {
+                const uint32_t key = used ? 0u : ((__float_as_uint(fabsf(w[u])) & ~31u) | (uint32_t)(31 - l));
+                const uint32_t kmax = __reduce_max_sync(kFull, key);
+                p = 31 - (int)(kmax & 31u);
             }
-        }
-        const int p = idx;
-        const bool me = (l == p);
-        if (me) {
-            used = true;
-            pos = k;
-        }
-        if (l == 0) piv[k] = p;
-        const float pv = __shfl_sync(kFull, w[k], p);
-        ok = ok && (fabsf(pv) > 1e-30f) && (fabsf(pv) < 3.0e38f);
-        const float ip = 1.f / pv;
-        const float f = w[k];
+            const bool me = (l == p);
+            if (me) {
+                used = true;
+                pos = kb + u;
+                piv[kb + u] = p;
 #pragma unroll
-        for (int j = 0; j < N; ++j) {
-            if (j == k) continue;
-            const float rp = __shfl_sync(kFull, w[j], p) * ip;
-            w[j] = me ? rp : fmaf(-f, rp, w[j]);
+                for (int j = 0; j < N; j += 4)
+                    *reinterpret_cast<float4*>(pr + j) = make_float4(w[j], w[j + 1], w[j + 2], w[j + 3]);
+            }
+            __syncwarp();
+            float rp[N];
+#pragma unroll
+            for (int j = 0; j < N; j += 4) {
+                const float4 t = *reinterpret_cast<const float4*>(pr + j);
+                rp[j] = t.x;
+                rp[j + 1] = t.y;
+                rp[j + 2] = t.z;
+                rp[j + 3] = t.w;
+            }
+            const float pv = rp[u];
+            ok = ok && (fabsf(pv) > 1e-30f) && (fabsf(pv) < 3.0e38f);
+            const float ip = recip(pv);
+            // rows are kept unscaled: the true row is scale * w, and a lane
+            // takes its scale 1 / pivot when it becomes the pivot row, whose
+            // stored values then stay as they are; the update w -= (f / pivot)
+            // * pivot row is the same for scaled and unscaled rows.
+            const float fp = me ? 0.f : w[u] * ip;
+            if (me) scale = ip;
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                if (j == u) continue;
+                w[j] = fmaf(-fp, rp[j], w[j]);
+            }
+            w[u] = me ? 1.f : -fp;
         }
-        w[k] = me ? ip : -f * ip;
+        float t[GJ_U];
+#pragma unroll
+        for (int u = 0; u < GJ_U; ++u) t[u] = w[u];
+#pragma unroll
+        for (int j = 0; j < N - GJ_U; ++j) w[j] = w[j + GJ_U];
+#pragma unroll
+        for (int u = 0; u < GJ_U; ++u) w[N - GJ_U + u] = t[u];
+    }
+    float ci = 0.f;                         // column pos(l) of the inverse
+#pragma unroll
+    for (int c = 0; c < N; ++c) {
+        w[c] *= scale;
+        ci += fabsf(w[c]);
     }
     __syncwarp();
+    if constexpr (PIVOT) {
 #pragma unroll
-    for (int q = 0; q < N; ++q) out[piv[q] * P + pos] = w[q];
+        for (int q = 0; q < N; q += 4) {
+            const int4 pq = *reinterpret_cast<const int4*>(piv + q);
+            out[pq.x * P + pos] = w[q];
+            out[pq.y * P + pos] = w[q + 1];
+            out[pq.z * P + pos] = w[q + 2];
+            out[pq.w * P + pos] = w[q + 3];
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < N; ++q) out[q * P + l] = w[q];
+    }
     __syncwarp();
-    return ok;
+    const float nm = __uint_as_float(__reduce_max_sync(kFull, __float_as_uint(cm)));
+    const float ni = __uint_as_float(__reduce_max_sync(kFull, __float_as_uint(ci)));
+    return nm * ni;
 }
 
-// One step of refinement when cond_1(Mx) is estimated above kRefineCond:
-// lane l forms column l of R = I - Mx X in FP64, then X[:, l] += X R[:, l].
+// One step of refinement: lane l forms column l of R = I - Mx X in FP64, then
+// X[:, l] += X R[:, l].
 template <int N>
 KS_DEV void refine_inverse(const float* Mx, float* X) {
     constexpr int P = TD<N>::P;
     const int l = lane_id();
-    float cm = 0.f, ci = 0.f;
-#pragma unroll 8
-    for (int k = 0; k < N; ++k) {
-        cm += fabsf(Mx[k * P + l]);
-        ci += fabsf(X[k * P + l]);
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        cm = fmaxf(cm, __shfl_xor_sync(kFull, cm, off));
-        ci = fmaxf(ci, __shfl_xor_sync(kFull, ci, off));
-    }
-    if (!(cm * ci > kRefineCond)) return;   // warp-uniform
     float rc[N];
     {
         double xc[N];
@@ -462,10 +553,14 @@ KS_DEV void refine_inverse(const float* Mx, float* X) {
     __syncwarp();
 }
 
-template <int N>
-KS_DEV bool inverse(const float* Mx, float* X, int* piv) {
-    const bool ok = gj_inverse<N>(Mx, X, piv);
-    refine_inverse<N>(Mx, X);
+// X = Mx^{-1}, refined once when the condition estimate exceeds kRefineCond.
+// Returns false on a zero or non-finite pivot (then nothing is refined).
+// SPD: Mx is symmetric positive definite (no pivot search).
+template <int N, bool SPD = false>
+KS_DEV bool inverse(const float* Mx, float* X, VS<N> vs) {
+    bool ok = true;
+    const float cond = gj_inverse<N, !SPD>(Mx, X, vs, ok);
+    if (ok && cond > kRefineCond && cond < 3.0e38f) refine_inverse<N>(Mx, X);   // warp-uniform
     return ok;
 }
 
@@ -673,7 +768,7 @@ KS_DEV void fadvance(FE& st, const FE& j, Pool<N>& pool, VS<N> vs, bool& bad) {
     mmq<N, false, true>(st.C, j.J, s0);
     add_diag<N>(s0, 1.f);
     vs.v(0)[r] = vrow<N>(st.C)[r] + rdot<N>(st.C, r, vrow<N>(j.J));
-    bad |= !inverse<N>(s0, s1, vs.piv());
+    bad |= !inverse<N>(s0, s1, vs);
     mmq<N, false, false>(j.A, s1, s0);                                // X = A_j M^{-1}
     mmq<N, false, true>(s0, st.C, s1);                                // X C
     vrow<N>(st.C)[r] = rdot<N>(s0, r, vs.v(0)) + vrow<N>(j.C)[r];
@@ -696,7 +791,7 @@ KS_DEV FE fcombine(const FE& i, const FE& j, Pool<N>& pool, VS<N> vs, bool& bad)
     vs.v(0)[r] = vrow<N>(i.C)[r] + rdot<N>(i.C, r, vrow<N>(j.J));    // t = b_i + C_i eta_j
     vs.v(1)[r] = vrow<N>(j.J)[r] - rdot<N>(j.J, r, vrow<N>(i.C));    // v = eta_j - J_j b_i
     float* s1 = pool.get(bad);
-    bad |= !inverse<N>(s0, s1, vs.piv());                             // M^{-1}
+    bad |= !inverse<N>(s0, s1, vs);                             // M^{-1}
     float* s2 = pool.get(bad);
     float* s3 = pool.get(bad);
     mmq<N, false, false>(j.A, s1, s2);                                // X
@@ -738,7 +833,7 @@ KS_DEV SE selem(float* Pm, const SConst<N, M>& c, bool last, Pool<N>& pool, VS<N
     mmq<N, false, true>(FP, c.F, Pp, c.Q);                            // P- = F P F^T + Q
     vs.v(0)[r] = rdot<N>(c.F, r, xb) + c.u[r];                        // F xbar + u
     float* Pi = pool.get(bad);
-    bad |= !inverse<N>(Pp, Pi, vs.piv());
+    bad |= !inverse<N, true>(Pp, Pi, vs);                           // P- is SPD
     mmq<N, true, true>(FP, Pi, Pp);                                   // E = (F P)^T (P-)^{-1}
     mmq<N, false, false>(Pp, FP, Pi, Pm, -1.f);                       // L = P - E F P
     vrow<N>(Pi)[r] = xb[r] - rdot<N>(Pp, r, vs.v(0));                 // g

@@ -37,6 +37,7 @@ struct TSmem {
     float pool[NW * KW * TD<N>::MAT];
     float vs[NW * VS<N>::FLOATS];
     static_assert(NW * KW <= 32, "pool mask");
+    static_assert(NW * KW >= 15, "the tile look-back holds up to 15 buffers");
 };
 
 KS_DEV void tpublish(uint32_t* flag, uint32_t v) {
