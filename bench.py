@@ -101,6 +101,28 @@ def flops_per_step(N: int, M: int, fused_smoothing: bool = True) -> dict:
     return {"filter": fold + adv + 2 * meas, "smoother": 2 * sel + scomb + sadv}
 
 
+def tensor_flops_per_step(N: int, M: int) -> dict:
+    """Algorithmic (FP32-equivalent, FMA = 2) flops per step of the dense
+    products the nx >= 32 kernels run on the tensor cores.  Forward scan: the
+    block fold of a measurement element (3 N^3 and 6 N^2 M products) and its
+    application to the running posterior (2 N^3, 4 N^2 M).  Reverse scan:
+    the Lemma 5 element (4 N^3), its block fold (3 N^3) and its application
+    (2 N^3).  The pivoted inverses (CUDA cores) and the tile-level combines are
+    not counted."""
+    return {"filter": 2 * (5 * N ** 3 + 10 * N * N * M), "smoother": 2 * 9 * N ** 3}
+
+
+def tf32_peak():
+    """Dense TF32 tensor peak of this GPU: the measured bf16 GEMM peak times
+    the nominal TF32 / bf16 ratio (1.1 / 2.25 PFLOP/s)."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["bf16_tflops"]) * 1.1 / 2.25, "measured bf16 GEMM x nominal TF32/bf16 (1.1/2.25)"
+    return 1900.0 * 1.1 / 2.25, "fallback bf16 1.9 PFLOP/s x nominal TF32/bf16 (1.1/2.25)"
+
+
 # ---------------------------------------------------------------- clocks
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -170,10 +192,22 @@ def cpu_oracle_rate(seq, seconds: float) -> dict:
             "sample": f"{reps} full passes over the T={seq.T} sequence ({el:.1f} s, 1 thread)"}
 
 
-def source_hash() -> str:
+# The sources each recorded kernel is built from (its traffic record is
+# dropped when any of them changes).
+KERNEL_SOURCES = {
+    "filter_scan_kernel": ["ks_ops.cuh", "ks_async.cuh", "ks_scan.cuh", "ks_impl.cuh", "ks_inst_4_2.cu"],
+    "smoother_scan_kernel": ["ks_ops.cuh", "ks_async.cuh", "ks_scan.cuh", "ks_impl.cuh", "ks_inst_4_2.cu"],
+    "tfilter_kernel": ["ks_ops.cuh", "ks_scan.cuh", "ks_tc.cuh", "ks_tscan.cuh", "ks_timpl.cuh",
+                       "ks_inst_32_8.cu"],
+    "tsmoother_kernel": ["ks_ops.cuh", "ks_scan.cuh", "ks_tc.cuh", "ks_tscan.cuh", "ks_timpl.cuh",
+                         "ks_inst_32_8.cu"],
+}
+
+
+def source_hash(kernel: str) -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1905_13002_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in sorted(KERNEL_SOURCES.get(kernel, os.listdir(csrc))):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
@@ -188,7 +222,7 @@ def recorded_traffic(kernel: str):
     with open(p) as f:
         d = json.load(f)
     e = d.get(kernel)
-    if not e or e.get("source_hash") != source_hash():
+    if not e or e.get("source_hash") != source_hash(kernel):
         return None
     return e.get("dram_bytes_per_launch_full")
 
@@ -355,19 +389,30 @@ def run_single(args, rank, world, local, precision):
     alu_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
     tfl = fps[dom] * T / dur_s / 1e12
     kname = ({"filter": "filter_scan_kernel", "smoother": "smoother_scan_kernel"} if nx <= 6 else
+             {"filter": "tfilter_kernel", "smoother": "tsmoother_kernel"} if nx >= 32 else
              {"filter": "gfilter_kernel", "smoother": "gsmoother_kernel"})[dom]
     traffic = recorded_traffic(kname)
-    if tfl / alu_peak >= gbs / hbm:
+    if nx >= 32:
+        tpeak, tsrc = tf32_peak()
+        tfs = tensor_flops_per_step(nx, ny)[dom]
+        ttf = tfs * T / dur_s / 1e12
+        roof = {"bound": "tensor", "achieved": ttf, "peak": tpeak, "unit": "TFLOP/s", "frac": ttf / tpeak,
+                "traffic": traffic, "kernel": kname, "peak_source": tsrc, "ms_per_launch": kernels[dom],
+                "split": "3xTF32: 3 TF32 mma per FP32 product, so the tensor pipe issues 3x achieved",
+                "tensor_flops_per_step": tfs, "hbm_frac": gbs / hbm, "bytes_per_step": bps[dom],
+                "kernels_ms": {k: round(v, 4) for k, v in kernels.items()}}
+    elif tfl / alu_peak >= gbs / hbm:
         roof = {"bound": "alu", "achieved": tfl, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": tfl / alu_peak, "traffic": traffic}
     else:
         roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
                 "frac": gbs / hbm, "traffic": traffic}
-    roof.update({"kernel": kname, "peak_source": which if roof["bound"] == "hbm" else
-                 "152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
-                 "ms_per_launch": kernels[dom], "hbm_frac": gbs / hbm, "alu_frac": tfl / alu_peak,
-                 "bytes_per_step": bps[dom], "flops_per_step": fps[dom],
-                 "kernels_ms": {k: round(v, 4) for k, v in kernels.items()}})
+    if nx < 32:
+        roof.update({"kernel": kname, "peak_source": which if roof["bound"] == "hbm" else
+                     "152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                     "ms_per_launch": kernels[dom], "hbm_frac": gbs / hbm, "alu_frac": tfl / alu_peak,
+                     "bytes_per_step": bps[dom], "flops_per_step": fps[dom],
+                     "kernels_ms": {k: round(v, 4) for k, v in kernels.items()}})
 
     if rank != 0:
         if world > 1:
