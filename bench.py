@@ -51,10 +51,15 @@ def parse():
     ap.add_argument("--T", type=int, default=1 << 20)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="long", choices=["long", "batched", "precision"],
+    ap.add_argument("--workload", default="long", choices=["long", "batched", "precision", "serving"],
                     help="long: one T=2^20 nx=4 sequence per GPU (default); batched: 4096 sequences, "
-                         "lengths log-uniform in [256, 16384], nx in {2,4,6}")
+                         "lengths log-uniform in [256, 16384], nx in {2,4,6}; precision: nx=32 T=65536; "
+                         "serving: Poisson request streams, nx in {4,8}, T log-uniform in [64, 2^18]")
     ap.add_argument("--batch", type=int, default=4096)
+    ap.add_argument("--rates", default="100,300,1000,3000,10000", help="serving: request rates (req/s)")
+    ap.add_argument("--duration", type=float, default=10.0, help="serving: seconds of arrivals per rate")
+    ap.add_argument("--streams", type=int, default=2, help="serving: launches in flight")
+    ap.add_argument("--budget-gb", type=float, default=80.0, help="serving: device-memory admission budget")
     return ap.parse_args()
 
 
@@ -269,6 +274,9 @@ def main():
         return
     if args.workload == "batched":
         run_batched(args, rank, world, local)
+        return
+    if args.workload == "serving":
+        run_serving(args, rank, world, local)
         return
     run_single(args, rank, world, local, precision=args.workload == "precision")
 
@@ -606,6 +614,97 @@ def run_batched(args, rank, world, local):
                           "how": "ks_smooth once per sequence, sequentially on one stream"},
            "roofline": roof}
     if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_oracle_batched(seqs, args.cpu_seconds)
+    print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_serving(args, rank, world, local):
+    """Open-loop Poisson request streams through the continuous-batching
+    server, one stream per rate; each rank serves its own stream (replicas)."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_1905_13002_gb300 import _build, serving
+
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if local == 0:
+        _build.build()
+    if world > 1:
+        dist.barrier()
+    models = workloads.serving_models(seed=workloads.SEED_BASE + 5)
+    ys = workloads.serving_measurements(models, 1 << 18, seed=workloads.SEED_BASE + 5 + 100 * rank)
+    pinned = {nx: [torch.from_numpy(y).pin_memory() for y in v] for nx, v in ys.items()}
+    sets = {(nx, nx // 2): serving.ModelSet(models[nx]) for nx in models}
+    budget = int(args.budget_gb * 1e9)
+    rates = [float(r) for r in args.rates.split(",")]
+
+    def requests(rate, n, seed):
+        arr = workloads.serving_arrivals(rate, n, seed)
+        return [serving.Request(i, a.nx, a.nx // 2, a.T, a.model, pinned[a.nx][a.model][:a.T], a.t)
+                for i, a in enumerate(arr)]
+
+    serving.Server(serving.GpuLauncher(sets, streams=args.streams), budget, streams=args.streams).run(
+        requests(rates[0], 64, workloads.SEED_BASE + 5 + 7919 + rank))          # warm-up
+    clk = ClockSampler(local)
+    clk.start()
+    per_rate = {}
+    launches = 0
+    for rate in rates:
+        n = max(1, int(round(rate * args.duration)))
+        rs = requests(rate, n, workloads.SEED_BASE + 5 + 1000 * int(rate) + rank)
+        gl = serving.GpuLauncher(sets, streams=args.streams)
+        srv = serving.Server(gl, budget, streams=args.streams)
+        done = srv.run(rs)
+        launches += srv.stats.launches
+        lg = gl.log
+        dev_rate = {}
+        for nx in sorted({e[0] for e in lg}):
+            e = [x for x in lg if x[0] == nx]
+            dev_rate[str(nx)] = sum(x[2] for x in e) / (sum(x[4] for x in e) / 1e3)
+        lat = [r.latency * 1e3 for r in done]
+        p = serving.percentiles(lat, (50, 99))
+        steps = sum(r.T for r in done)
+        span = max(r.done for r in done) - min(r.arrival for r in done)
+        rate_steps = torch.tensor([steps / span], dtype=torch.float64, device="cuda")
+        if world > 1:
+            dist.all_reduce(rate_steps)
+        per_rate[str(int(rate))] = {
+            "requests": n, "steps": steps, "steps_per_s": float(rate_steps.item()),
+            "offered_steps_per_s": rate * statistics.mean(r.T for r in rs) * world,
+            "p50_ms": p[50], "p99_ms": p[99], "launches": srv.stats.launches,
+            "mean_requests_per_launch": statistics.mean(srv.stats.batch_sizes),
+            "max_reserved_gb": srv.stats.max_reserved / 1e9, "max_in_flight": srv.stats.max_in_flight,
+            "launch_host_ms_mean": 1e3 * statistics.mean(x[3] for x in lg),
+            "launch_device_ms_mean": statistics.mean(x[4] for x in lg),
+            "device_steps_per_s_by_nx": dev_rate}
+    clk_s = clk.stop()
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    top = per_rate[str(int(rates[-1]))]
+    out = {"metric": METRIC, "value": top["steps_per_s"], "unit": UNIT, "n_gpus": world, "steps": len(rates),
+           "warmup": 1, "ms_per_step": top["p50_ms"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "serving: Poisson arrivals, T=round(exp(U[ln64, ln2^18])), nx in {4 (Wiener "
+                                  "velocity, ny=2), 8 (random stable, ny=4)}, 16 models per nx",
+                      "rates": rates, "seconds_per_rate": args.duration, "streams": args.streams,
+                      "budget_gb": args.budget_gb, "parallelism": f"replicas{world}",
+                      "value": "smoothed steps/s at the highest rate (completed steps / (last completion - "
+                               "first arrival)); ms_per_step = its p50 latency",
+                      "latency": "completion (CUDA event after the request's launch) - scheduled arrival"},
+           "clocks": {k: clk_s[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+           "gpu_launches": 3 * launches,
+           "latency": {"p50_ms": top["p50_ms"], "p99_ms": top["p99_ms"]},
+           "rates": per_rate}
+    if world == 1 and not args.no_cpu_baseline:
+        sample = requests(rates[-1], 400, workloads.SEED_BASE + 5 + 31)
+        seqs = [workloads.Sequence(models[r.nx][r.model], ys[r.nx][r.model][:r.T].astype(np.float64))
+                for r in sample]
         out["cpu_baseline"] = cpu_oracle_batched(seqs, args.cpu_seconds)
     print(json.dumps(out))
     if world > 1:

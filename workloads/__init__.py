@@ -221,3 +221,53 @@ def config_batched(B: int = 4096, lo: int = 256, hi: int = 16384,
 
 def to_f32_y(seq: Sequence) -> np.ndarray:
     return np.ascontiguousarray(seq.y.astype(np.float32))
+
+
+# ---------------------------------------------------------------- serving workload
+@dataclass
+class Arrival:
+    """One request of the serving workload: scheduled arrival time (s), the
+    state size, its length and which model of the size's model set it uses."""
+    t: float
+    nx: int
+    T: int
+    model: int
+
+
+def serving_models(n_per_size: int = 16, seed: int = SEED_BASE + 5) -> dict:
+    """Model sets of the serving workload: nx = 4 (2-D Wiener velocity, ny = 2,
+    q ~ U[0.5, 2], R = rI with r ~ U[0.1, 1]) and nx = 8 (random stable, ny = 4,
+    the nx = 32 recipe at nx = 8: F = O diag(U[0.9, 0.99]), Q = 0.1 I,
+    H ~ N(0, 1/8), R = 0.5 I); dt = 0.1, m0 = 0, P0 = I."""
+    rng = np.random.default_rng(np.random.PCG64(seed))
+    out = {4: [], 8: []}
+    for _ in range(n_per_size):
+        out[4].append(wiener_velocity(2, dt=0.1, q=float(rng.uniform(0.5, 2.0)), r=float(rng.uniform(0.1, 1.0))))
+        out[8].append(random_stable(8, 4, rng))
+    return out
+
+
+def serving_arrivals(rate: float, n: int, seed: int, lo: int = 64, hi: int = 1 << 18,
+                     sizes=(4, 8), n_models: int = 16) -> list:
+    """Open-loop Poisson arrivals at ``rate`` requests/s: exponential gaps,
+    T = round(exp(U[ln lo, ln hi])), nx uniform over ``sizes``, model index
+    uniform over the size's set."""
+    rng = np.random.default_rng(np.random.PCG64(seed))
+    t = np.cumsum(rng.exponential(1.0 / rate, size=n))
+    Ts = batch_lengths(n, rng, lo, hi)
+    nxs = rng.choice(np.asarray(sizes), size=n)
+    ms = rng.integers(0, n_models, size=n)
+    return [Arrival(float(t[i]), int(nxs[i]), int(Ts[i]), int(ms[i])) for i in range(n)]
+
+
+def serving_measurements(models: dict, T: int, seed: int = SEED_BASE + 5) -> dict:
+    """One simulated measurement sequence of length T per model (requests
+    use a prefix of their model's sequence): {nx: [y (T, ny) FP32]}."""
+    out = {}
+    for nx, ms in models.items():
+        out[nx] = []
+        for i, m in enumerate(ms):
+            rng = np.random.default_rng(np.random.PCG64(seed * 1000 + nx * 100 + i))
+            _, y = simulate(m, T, rng)
+            out[nx].append(np.ascontiguousarray(y.astype(np.float32)))
+    return out
