@@ -178,7 +178,8 @@ int ks_smooth_scan(const ks_model *m, int64_t T, const float *fmean, const float
  * y [T][ny], fmean [T][nx], fcov [T][nx][nx], smean, scov: device, FP32.
  * fmean and fcov may be NULL, in which case the filtered moments are kept
  * in the workspace only (which then needs ks_workspace_bytes(m, T,
- * KS_WS_ELEMENTS) bytes).
+ * KS_WS_ELEMENTS) bytes).  smean and scov may both be NULL (with fmean and
+ * fcov given): then only the forward scan runs (filtering only).
  */
 int ks_smooth(const ks_model *m, const float *y, int64_t T, void *ws, size_t ws_bytes,
               float *fmean, float *fcov, float *smean, float *scov, void *stream);
@@ -243,6 +244,44 @@ int ks_status(void *ws, void *stream);
 #define KS_NOALLOC_SCRATCH_BYTES 4194304
 int ks_smooth_noalloc(const ks_model *m, const float *y, int64_t T, float *fmean, float *fcov,
                       float *smean, float *scov, int32_t *status_out, void *stream);
+
+/*
+ * Time sharding (Section III-C's block-level elements with one block per
+ * device): a sequence split into consecutive shards, each on its own device,
+ * is smoothed with one exchange of one element per shard and scan:
+ *   1. each shard folds its filtering elements into one element
+ *      (ks_filter_aggregate); the shards' aggregates are exchanged;
+ *   2. shard s combines the aggregates of shards 0..s-1 (ks_filter_combine_batch):
+ *      the result has A = 0 and its (b, C) is the filtered posterior at the step
+ *      before the shard, so the shard's forward scan is ks_smooth(..., smean =
+ *      scov = NULL) with that posterior as the model's (m0, P0) (Lemma 3's
+ *      k = 1 element is exactly "posterior (x) measurement element");
+ *   3. each shard folds its smoothing elements into one element
+ *      (ks_smoother_aggregate); the aggregates are exchanged;
+ *   4. shard s combines those of shards s+1..S-1 (ks_smoother_combine_batch):
+ *      the result has E = 0 and its (g, L) is the smoothed posterior at the
+ *      step after the shard; appended to the shard's filtered moments as one
+ *      extra step, Lemma 5's last-step element turns it into the suffix
+ *      entering the shard, so the shard's reverse scan is ks_smooth_scan over
+ *      T + 1 steps.
+ *
+ * ks_filter_aggregate: out = a_1 (x) ... (x) a_T over the shard's steps
+ * (Lemma 4, packed filter element, device [3nx^2 + 2nx]).  y [T][ny]: the
+ * shard's measurements (device).  first != 0: the shard starts the sequence,
+ * and its first element is Lemma 3's k = 1 element from (m0, P0); otherwise
+ * every element is a measurement element.
+ * ks_smoother_aggregate: out = the fold of the shard's Lemma 5 elements built
+ * from its filtered moments (packed smoother element, device [2nx^2 + nx]);
+ * last != 0: the shard ends the sequence, and its last element is Lemma 5's
+ * k = n element (E = 0).
+ * Workspace: ks_workspace_bytes_aggregate(m, T) bytes, 256-byte aligned.
+ * Offered for nx <= 6 (KS_EUNSUPPORTED otherwise).
+ */
+size_t ks_workspace_bytes_aggregate(const ks_model *m, int64_t T);
+int ks_filter_aggregate(const ks_model *m, const float *y, int64_t T, int first, void *ws,
+                        size_t ws_bytes, float *out, void *stream);
+int ks_smoother_aggregate(const ks_model *m, int64_t T, const float *fmean, const float *fcov,
+                          int last, void *ws, size_t ws_bytes, float *out, void *stream);
 
 /*
  * Batched Lemma 4 / Lemma 6 operators on `count` independent element pairs,

@@ -90,6 +90,9 @@ def lib():
             "ks_smooth_batch": ([ctypes.POINTER(_KsModelBatch), vp, i64, vp, sz, vp, vp, vp, vp, vp], i32),
             "ks_filter_combine_batch": ([i32, i64, vp, vp, vp, vp, sz, vp], i32),
             "ks_smoother_combine_batch": ([i32, i64, vp, vp, vp, vp, sz, vp], i32),
+            "ks_workspace_bytes_aggregate": ([M, i64], sz),
+            "ks_filter_aggregate": ([M, vp, i64, i32, vp, sz, vp, vp], i32),
+            "ks_smoother_aggregate": ([M, i64, vp, vp, i32, vp, sz, vp, vp], i32),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -186,15 +189,19 @@ def _out(shape, like, out):
 
 
 def smooth(model: Model, y: torch.Tensor, ws: torch.Tensor | None = None, *, fmean=None, fcov=None,
-           smean=None, scov=None, keep_filtered: bool = True, stream=None, events=None):
+           smean=None, scov=None, keep_filtered: bool = True, filter_only: bool = False, stream=None,
+           events=None):
     """End to end (``ks_smooth``): returns (fmean, fcov, smean, scov).
 
     With ``keep_filtered=False`` the filtered moments stay in the workspace
     (which must then be a KS_WS_ELEMENTS workspace) and None is returned for
-    them.  ``events``: 4 recorded-or-fresh torch.cuda.Event objects to time
-    the kernels (``ks_smooth_traced``).
+    them.  With ``filter_only=True`` only the forward scan runs and None is
+    returned for the smoothed moments.  ``events``: 4 recorded-or-fresh
+    torch.cuda.Event objects to time the kernels (``ks_smooth_traced``).
     """
     T = int(y.shape[0])
+    if filter_only and not keep_filtered:
+        raise ValueError("filter_only needs keep_filtered")
     purpose = KS_WS_SMOOTH if keep_filtered else KS_WS_ELEMENTS
     ws = alloc_workspace(model, T, purpose, stream) if ws is None else ws
     if keep_filtered:
@@ -202,8 +209,11 @@ def smooth(model: Model, y: torch.Tensor, ws: torch.Tensor | None = None, *, fme
         fcov = _out((T, model.nx, model.nx), y, fcov)
     else:
         fmean = fcov = None
-    smean = _out((T, model.nx), y, smean)
-    scov = _out((T, model.nx, model.nx), y, scov)
+    if filter_only:
+        smean = scov = None
+    else:
+        smean = _out((T, model.nx), y, smean)
+        scov = _out((T, model.nx, model.nx), y, scov)
     m = model.struct()
     args = (ctypes.byref(m), _p(y), T, _p(ws), ws.numel(), _p(fmean), _p(fcov), _p(smean), _p(scov),
             _stream(stream))
@@ -217,6 +227,45 @@ def smooth(model: Model, y: torch.Tensor, ws: torch.Tensor | None = None, *, fme
                                           for e in events])
         _check(lib().ks_smooth_traced(*args, handles), "ks_smooth_traced")
     return fmean, fcov, smean, scov
+
+
+def workspace_bytes_aggregate(model: Model, T: int) -> int:
+    n = lib().ks_workspace_bytes_aggregate(ctypes.byref(model.struct()), T)
+    if n == 0:
+        raise KsError(KS_EUNSUPPORTED if not supported(model.nx, model.ny) else KS_EINVAL,
+                      "ks_workspace_bytes_aggregate")
+    return int(n)
+
+
+def _agg_ws(model: Model, T: int, ws, stream):
+    if ws is not None:
+        return ws
+    nbytes = workspace_bytes_aggregate(model, T)
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=model.F.device)
+    _check(lib().ks_workspace_init(_p(ws), nbytes, _stream(stream)), "ks_workspace_init")
+    return ws
+
+
+def filter_aggregate(model: Model, y: torch.Tensor, first: bool, ws=None, stream=None):
+    """One shard's filtering aggregate (``ks_filter_aggregate``): the packed
+    Lemma 4 fold of its Lemma 3 elements, [3nx^2 + 2nx]; returns (out, ws)."""
+    T = int(y.shape[0])
+    ws = _agg_ws(model, T, ws, stream)
+    out = torch.empty(3 * model.nx * model.nx + 2 * model.nx, dtype=torch.float32, device=y.device)
+    _check(lib().ks_filter_aggregate(ctypes.byref(model.struct()), _p(y), T, int(bool(first)), _p(ws), ws.numel(),
+                                     _p(out), _stream(stream)), "ks_filter_aggregate")
+    return out, ws
+
+
+def smoother_aggregate(model: Model, fmean: torch.Tensor, fcov: torch.Tensor, last: bool, ws=None, stream=None):
+    """One shard's smoothing aggregate (``ks_smoother_aggregate``): the packed
+    Lemma 6 fold of its Lemma 5 elements, [2nx^2 + nx]; returns (out, ws)."""
+    T = int(fmean.shape[0])
+    ws = _agg_ws(model, T, ws, stream)
+    out = torch.empty(2 * model.nx * model.nx + model.nx, dtype=torch.float32, device=fmean.device)
+    _check(lib().ks_smoother_aggregate(ctypes.byref(model.struct()), T, _p(fmean), _p(fcov), int(bool(last)),
+                                       _p(ws), ws.numel(), _p(out), _stream(stream)), "ks_smoother_aggregate")
+    return out, ws
 
 
 def build_elements(model: Model, y: torch.Tensor, ws: torch.Tensor, stream=None):

@@ -129,6 +129,28 @@ int ks_smooth_traced(const ks_model* m, const float* y, int64_t T, void* ws, siz
                      events);
 }
 
+size_t ks_workspace_bytes_aggregate(const ks_model* m, int64_t T) {
+    const VTable* v = nullptr;
+    if (check_nx_ny(m, &v) || T < 1 || T > 0x7fffffffLL) return 0;
+    return v->agg_bytes(T);
+}
+
+int ks_filter_aggregate(const ks_model* m, const float* y, int64_t T, int first, void* ws, size_t ws_bytes,
+                        float* out, void* stream) {
+    const VTable* v = nullptr;
+    int rc = check_nx_ny(m, &v);
+    if (rc) return rc;
+    return v->faggregate(m, y, T, first, ws, ws_bytes, out, static_cast<cudaStream_t>(stream));
+}
+
+int ks_smoother_aggregate(const ks_model* m, int64_t T, const float* fmean, const float* fcov, int last, void* ws,
+                          size_t ws_bytes, float* out, void* stream) {
+    const VTable* v = nullptr;
+    int rc = check_nx_ny(m, &v);
+    if (rc) return rc;
+    return v->saggregate(m, T, fmean, fcov, last, ws, ws_bytes, out, static_cast<cudaStream_t>(stream));
+}
+
 size_t ks_workspace_bytes_batch(int nx, int ny, int B, int64_t total_T) {
     const VTable* v = find_impl(nx, ny);
     if (!v || B < 1 || total_T < B || total_T > 0x7fffffffLL) return 0;

@@ -150,9 +150,10 @@ struct GImpl {
                       float* fc, float* sm, float* sc, cudaStream_t st, void* const* ev) {
         const Layout L = layout(T);
         const bool own = (fm == nullptr) || (fc == nullptr);
+        const bool filter_only = (sm == nullptr) && (sc == nullptr);
         int rc = check(m, T, ws, ws_bytes, own ? L.bytes_elements : L.bytes_smooth);
         if (rc) return rc;
-        if (!y || !sm || !sc) return KS_EINVAL;
+        if (!y || (filter_only && own) || (!filter_only && (!sm || !sc))) return KS_EINVAL;
         if (own) {
             fm = reinterpret_cast<float*>(static_cast<char*>(ws) + L.off_fmean);
             fc = reinterpret_cast<float*>(static_cast<char*>(ws) + L.off_fcov);
@@ -160,7 +161,8 @@ struct GImpl {
         if (ev && ev[0] && cudaEventRecord(static_cast<cudaEvent_t>(ev[0]), st) != cudaSuccess) return KS_ECUDA;
         if ((rc = prep(m->F, m->u, m->Q, m->H, m->d, m->R, m->m0, m->P0, y, 1, nullptr, ws, L, st))) return rc;
         if (ev && ev[1] && cudaEventRecord(static_cast<cudaEvent_t>(ev[1]), st) != cudaSuccess) return KS_ECUDA;
-        if ((rc = scans<false>(ws, L, y, fm, fc, sm, sc, Segs<N, M>{nullptr, nullptr, 1}, st, ev, true, true)))
+        if ((rc = scans<false>(ws, L, y, fm, fc, sm, sc, Segs<N, M>{nullptr, nullptr, 1}, st, ev, true,
+                               !filter_only)))
             return rc;
         if (ev && ev[3] && cudaEventRecord(static_cast<cudaEvent_t>(ev[3]), st) != cudaSuccess) return KS_ECUDA;
         return KS_OK;
@@ -181,10 +183,18 @@ struct GImpl {
     }
 
     static int no_comb(int64_t, const float*, const float*, float*, void*, cudaStream_t) { return KS_EUNSUPPORTED; }
+    static size_t no_agg_bytes(int64_t) { return 0; }
+    static int no_fagg(const ks_model*, const float*, int64_t, int, void*, size_t, float*, cudaStream_t) {
+        return KS_EUNSUPPORTED;
+    }
+    static int no_sagg(const ks_model*, int64_t, const float*, const float*, int, void*, size_t, float*,
+                       cudaStream_t) {
+        return KS_EUNSUPPORTED;
+    }
 
     static constexpr VTable vtable() {
         return VTable{N, M, &layout, &build_elements, &filter_scan, &smooth_scan, &smooth, &smooth_batch,
-                      &no_comb, &no_comb};
+                      &no_comb, &no_comb, &no_agg_bytes, &no_fagg, &no_sagg};
     }
 };
 

@@ -8,6 +8,7 @@
 
 #include "../../include/ks.h"
 #include "ks_scan.cuh"
+#include "ks_shard.cuh"
 
 namespace ks {
 
@@ -41,6 +42,10 @@ struct VTable {
                         float*, cudaStream_t);
     int (*fcomb_batch)(int64_t, const float*, const float*, float*, void*, cudaStream_t);
     int (*scomb_batch)(int64_t, const float*, const float*, float*, void*, cudaStream_t);
+    size_t (*agg_bytes)(int64_t T);
+    int (*faggregate)(const ks_model*, const float*, int64_t, int, void*, size_t, float*, cudaStream_t);
+    int (*saggregate)(const ks_model*, int64_t, const float*, const float*, int, void*, size_t, float*,
+                      cudaStream_t);
 };
 
 inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
@@ -240,9 +245,11 @@ struct Impl {
                       float* fc, float* sm, float* sc, cudaStream_t st, void* const* ev) {
         const Layout L = layout(T);
         const bool own = (fm == nullptr) || (fc == nullptr);
+        const bool filter_only = (sm == nullptr) && (sc == nullptr);
         int rc = check_common(m, T, ws, ws_bytes, own ? L.bytes_elements : L.bytes_smooth);
         if (rc) return rc;
-        if (!y || !sm || !sc || !aligned16(y) || !aligned16(sm) || !aligned16(sc)) return KS_EINVAL;
+        if (!y || !aligned16(y) || (filter_only && own)) return KS_EINVAL;
+        if (!filter_only && (!sm || !sc || !aligned16(sm) || !aligned16(sc))) return KS_EINVAL;
         if (own) {
             fm = reinterpret_cast<float*>(static_cast<char*>(ws) + L.off_fmean);
             fc = reinterpret_cast<float*>(static_cast<char*>(ws) + L.off_fcov);
@@ -254,7 +261,7 @@ struct Impl {
         if ((rc = record(ev, 1, st))) return rc;
         if ((rc = launch_filter_fused<false>(ws, L, y, fm, fc, no_segs(), st))) return rc;
         if ((rc = record(ev, 2, st))) return rc;
-        if ((rc = launch_smoother<true, false>(ws, L, fm, fc, sm, sc, no_segs(), st))) return rc;
+        if (!filter_only && (rc = launch_smoother<true, false>(ws, L, fm, fc, sm, sc, no_segs(), st))) return rc;
         return record(ev, 3, st);
     }
 
@@ -294,9 +301,60 @@ struct Impl {
         return launch_status();
     }
 
+    // ---- time-shard aggregates (ks_shard.cuh): 128 threads x 32 steps per block
+    static constexpr int ANT = 128, ACH = 32;
+
+    static Layout agg_layout(int64_t T) {
+        Layout L{};
+        L.T = T;
+        L.B = 1;
+        const int64_t nblk = (T + (int64_t)ANT * ACH - 1) / ((int64_t)ANT * ACH);
+        L.ntf = L.nts = (int)nblk;
+        size_t off = 256;
+        L.off_const = off;
+        off = align_up(off + sizeof(ModelConst<N, M>), 256);
+        L.off_flags = off;
+        L.flags_bytes = 16;
+        off = align_up(off + L.flags_bytes, 256);
+        L.off_sblk = off;                                   // one packed element per block
+        off = align_up(off + 4 * (size_t)NCOMP * (size_t)nblk, 256);
+        L.bytes_smooth = L.bytes_elements = off;
+        return L;
+    }
+    static size_t agg_bytes(int64_t T) { return agg_layout(T).bytes_smooth; }
+
+    static int faggregate(const ks_model* m, const float* y, int64_t T, int first, void* ws, size_t ws_bytes,
+                          float* out, cudaStream_t st) {
+        const Layout L = agg_layout(T);
+        int rc = check_common(m, T, ws, ws_bytes, L.bytes_smooth);
+        if (rc) return rc;
+        if (!y || !out || !aligned16(y)) return KS_EINVAL;
+        if ((rc = prep(m, y, ws, L, st))) return rc;
+        float* blk = reinterpret_cast<float*>(static_cast<char*>(ws) + L.off_sblk);
+        filter_fold_kernel<N, M, ANT, ACH><<<L.ntf, ANT, 0, st>>>(mconst(ws, L), y, T, first, blk, status(ws));
+        if ((rc = launch_status())) return rc;
+        fold_packed_kernel<FilterFold<N>, ANT><<<1, ANT, 0, st>>>(blk, L.ntf, out, status(ws));
+        return launch_status();
+    }
+
+    static int saggregate(const ks_model* m, int64_t T, const float* fm, const float* fc, int last, void* ws,
+                          size_t ws_bytes, float* out, cudaStream_t st) {
+        const Layout L = agg_layout(T);
+        int rc = check_common(m, T, ws, ws_bytes, L.bytes_smooth);
+        if (rc) return rc;
+        if (!fm || !fc || !out) return KS_EINVAL;
+        if ((rc = prep(m, nullptr, ws, L, st))) return rc;
+        float* blk = reinterpret_cast<float*>(static_cast<char*>(ws) + L.off_sblk);
+        smoother_fold_kernel<N, M, ANT, ACH><<<L.nts, ANT, 0, st>>>(mconst(ws, L), fm, fc, T, last, blk,
+                                                                     status(ws));
+        if ((rc = launch_status())) return rc;
+        fold_packed_kernel<SmootherFold<N>, ANT><<<1, ANT, 0, st>>>(blk, L.nts, out, status(ws));
+        return launch_status();
+    }
+
     static constexpr VTable vtable() {
         return VTable{N, M, &layout, &build_elements, &filter_scan, &smooth_scan, &smooth, &smooth_batch,
-                      &fcomb_batch, &scomb_batch};
+                      &fcomb_batch, &scomb_batch, &agg_bytes, &faggregate, &saggregate};
     }
 };
 

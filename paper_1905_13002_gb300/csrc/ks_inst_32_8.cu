@@ -33,5 +33,8 @@ extern const VTable kImpl_32_8 = VTable{32,
                                         &TC::smooth,
                                         &GR::smooth_batch,
                                         &GR::no_comb,
-                                        &GR::no_comb};
+                                        &GR::no_comb,
+                                        &GR::no_agg_bytes,
+                                        &GR::no_fagg,
+                                        &GR::no_sagg};
 }  // namespace ks

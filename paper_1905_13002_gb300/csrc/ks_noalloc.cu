@@ -48,7 +48,7 @@ extern "C" int ks_smooth_noalloc(const ks_model* m, const float* y, int64_t T, f
     if (!m) return KS_EINVAL;
     if (m->nx != 4 || m->ny != 2) return KS_EUNSUPPORTED;
     if (T < 1 || T > KS_NOALLOC_MAX_T) return KS_EINVAL;
-    if (!fmean || !fcov) return KS_EINVAL;
+    if (!fmean || !fcov || !smean || !scov) return KS_EINVAL;
     const VTable* v = find_impl(4, 2);
     if (!v) return KS_EUNSUPPORTED;
     if (v->layout(T, 1).bytes_smooth > (size_t)KS_NOALLOC_SCRATCH_BYTES) return KS_EINVAL;

@@ -136,20 +136,21 @@ struct TImpl {
                       float* fc, float* sm, float* sc, cudaStream_t st, void* const* ev) {
         const Layout L = layout(T);
         const bool own = (fm == nullptr) || (fc == nullptr);
+        const bool filter_only = (sm == nullptr) && (sc == nullptr);
         int rc = check(m, T, ws, ws_bytes, own ? L.bytes_elements : L.bytes_smooth);
         if (rc) return rc;
-        if (!y || !sm || !sc) return KS_EINVAL;
+        if (!y || (filter_only && own) || (!filter_only && (!sm || !sc))) return KS_EINVAL;
         if (own) {
             fm = reinterpret_cast<float*>(static_cast<char*>(ws) + L.off_fmean);
             fc = reinterpret_cast<float*>(static_cast<char*>(ws) + L.off_fcov);
         }
-        if (!vec_ok(fm, fc, sm, sc)) return KS_EINVAL;
+        if (!vec_ok(fm, fc, filter_only ? fm : sm, filter_only ? fc : sc)) return KS_EINVAL;
         if (ev && ev[0] && cudaEventRecord(static_cast<cudaEvent_t>(ev[0]), st) != cudaSuccess) return KS_ECUDA;
         if ((rc = GImpl<N, M, NW, CH>::prep(m->F, m->u, m->Q, m->H, m->d, m->R, m->m0, m->P0, y, 1, nullptr, ws,
                                             L, st)))
             return rc;
         if (ev && ev[1] && cudaEventRecord(static_cast<cudaEvent_t>(ev[1]), st) != cudaSuccess) return KS_ECUDA;
-        if ((rc = scans(ws, L, y, fm, fc, sm, sc, st, ev, true, true))) return rc;
+        if ((rc = scans(ws, L, y, fm, fc, sm, sc, st, ev, true, !filter_only))) return rc;
         if (ev && ev[3] && cudaEventRecord(static_cast<cudaEvent_t>(ev[3]), st) != cudaSuccess) return KS_ECUDA;
         return KS_OK;
     }
