@@ -246,6 +246,23 @@ int ks_smooth_noalloc(const ks_model *m, const float *y, int64_t T, float *fmean
                       float *smean, float *scov, int32_t *status_out, void *stream);
 
 /*
+ * Marginal log-likelihood (Section III-C: the filtering prefix also carries
+ * p(y_1:k)): one parallel pass over the filtered moments gives every
+ *   log p(y_k | y_1:k-1) = log N(y_k; H (F xbar_{k-1} + u) + d,
+ *                                 H (F P_{k-1} F^T + Q) H^T + R)
+ * (k = 1 from (m0, P0), in FP64), and log p(y_1:T) is their sum.
+ * y [T][ny], fmean [T][nx], fcov [T][nx][nx]: device, FP32 (the filtered
+ * moments of ks_smooth or ks_filter_scan; may be NULL when T = 1).
+ * ll [T] (device FP32, may be NULL): the per-step terms.  total (device, one
+ * double, may be NULL): their sum, accumulated in FP64.  At least one of ll
+ * and total.  status (device uint32): cleared, then set to 1 when a
+ * predictive covariance fails its Cholesky factorisation or a term is not
+ * finite.  Allocates nothing; no workspace.
+ */
+int ks_loglik(const ks_model *m, const float *y, int64_t T, const float *fmean, const float *fcov,
+              float *ll, double *total, uint32_t *status, void *stream);
+
+/*
  * Time sharding (Section III-C's block-level elements with one block per
  * device): a sequence split into consecutive shards, each on its own device,
  * is smoothed with one exchange of one element per shard and scan:

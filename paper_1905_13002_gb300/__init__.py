@@ -91,6 +91,7 @@ def lib():
             "ks_filter_combine_batch": ([i32, i64, vp, vp, vp, vp, sz, vp], i32),
             "ks_smoother_combine_batch": ([i32, i64, vp, vp, vp, vp, sz, vp], i32),
             "ks_workspace_bytes_aggregate": ([M, i64], sz),
+            "ks_loglik": ([M, vp, i64, vp, vp, vp, vp, vp, vp], i32),
             "ks_filter_aggregate": ([M, vp, i64, i32, vp, sz, vp, vp], i32),
             "ks_smoother_aggregate": ([M, i64, vp, vp, i32, vp, sz, vp, vp], i32),
         }
@@ -227,6 +228,19 @@ def smooth(model: Model, y: torch.Tensor, ws: torch.Tensor | None = None, *, fme
                                           for e in events])
         _check(lib().ks_smooth_traced(*args, handles), "ks_smooth_traced")
     return fmean, fcov, smean, scov
+
+
+def loglik(model: Model, y: torch.Tensor, fmean: torch.Tensor | None, fcov: torch.Tensor | None, stream=None):
+    """Marginal log-likelihood (``ks_loglik``) from the filtered moments:
+    returns (per-step log p(y_k | y_1:k-1) [T] FP32, total FP64 [1], status
+    word [1]), all on the device."""
+    T = int(y.shape[0])
+    ll = torch.empty(T, dtype=torch.float32, device=y.device)
+    total = torch.empty(1, dtype=torch.float64, device=y.device)
+    st = torch.empty(1, dtype=torch.int32, device=y.device)
+    _check(lib().ks_loglik(ctypes.byref(model.struct()), _p(y), T, _p(fmean), _p(fcov), _p(ll), _p(total), _p(st),
+                           _stream(stream)), "ks_loglik")
+    return ll, total, st
 
 
 def workspace_bytes_aggregate(model: Model, T: int) -> int:
