@@ -202,10 +202,10 @@ def cpu_oracle_rate(seq, seconds: float) -> dict:
 KERNEL_SOURCES = {
     "filter_scan_kernel": ["ks_ops.cuh", "ks_async.cuh", "ks_scan.cuh", "ks_impl.cuh", "ks_inst_4_2.cu"],
     "smoother_scan_kernel": ["ks_ops.cuh", "ks_async.cuh", "ks_scan.cuh", "ks_impl.cuh", "ks_inst_4_2.cu"],
-    "tfilter_kernel": ["ks_ops.cuh", "ks_scan.cuh", "ks_tc.cuh", "ks_tscan.cuh", "ks_timpl.cuh",
-                       "ks_inst_32_8.cu"],
-    "tsmoother_kernel": ["ks_ops.cuh", "ks_scan.cuh", "ks_tc.cuh", "ks_tscan.cuh", "ks_timpl.cuh",
-                         "ks_inst_32_8.cu"],
+    "tfilter_reduce+spine+apply": ["ks_ops.cuh", "ks_scan.cuh", "ks_tc.cuh", "ks_tscan.cuh", "ks_timpl.cuh",
+                                   "ks_inst_32_8.cu"],
+    "tsmoother_reduce+spine+apply": ["ks_ops.cuh", "ks_scan.cuh", "ks_tc.cuh", "ks_tscan.cuh", "ks_timpl.cuh",
+                                     "ks_inst_32_8.cu"],
 }
 
 
@@ -397,7 +397,7 @@ def run_single(args, rank, world, local, precision):
     alu_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
     tfl = fps[dom] * T / dur_s / 1e12
     kname = ({"filter": "filter_scan_kernel", "smoother": "smoother_scan_kernel"} if nx <= 6 else
-             {"filter": "tfilter_kernel", "smoother": "tsmoother_kernel"} if nx >= 32 else
+             {"filter": "tfilter_reduce+spine+apply", "smoother": "tsmoother_reduce+spine+apply"} if nx >= 32 else
              {"filter": "gfilter_kernel", "smoother": "gsmoother_kernel"})[dom]
     traffic = recorded_traffic(kname)
     if nx >= 32:

@@ -1,5 +1,6 @@
 // ks_timpl.cuh -- host side of the nx = 32 tensor-core scans: workspace
-// layout and launches behind the same C ABI as ks_impl.cuh.  Segmented
+// layout and launches behind the same C ABI as ks_impl.cuh: per scan a
+// reduce launch, log2(tiles) spine launches and an apply launch.  Segmented
 // batches at this size run on the CUDA-core group kernels (ks_gimpl.cuh).
 #pragma once
 
@@ -25,15 +26,15 @@ struct TImpl {
         size_t off = 256;
         L.off_const = off;
         off = align_up(off + sizeof(ModelConst<N, M>), 256);
-        L.off_flags = off;
-        L.flags_bytes = 16 + 4 * (size_t)(L.ntf + L.nts);
+        L.off_flags = off;                                  // zeroed by the preparation kernel
+        L.flags_bytes = 16;
         off = align_up(off + L.flags_bytes, 256);
-        L.off_fagg = off;                                   // filter: agg, pre, tile prefixes
-        off = align_up(off + 4 * (size_t)FR * L.ntf * 3, 256);
+        L.off_fagg = off;                                   // filter: two spine buffers
+        off = align_up(off + 4 * (size_t)FR * L.ntf * 2, 256);
         L.off_fpre = off;                                   // filter chains
         off = align_up(off + 4 * (size_t)FR * nchp * 2, 256);
-        L.off_sagg = off;                                   // smoother: agg, pre, tile prefixes
-        off = align_up(off + 4 * (size_t)SR * L.nts * 3, 256);
+        L.off_sagg = off;                                   // smoother: two spine buffers
+        off = align_up(off + 4 * (size_t)SR * L.nts * 2, 256);
         L.off_spre = off;                                   // smoother chains
         off = align_up(off + 4 * (size_t)SR * nchp * 2, 256);
         L.off_sblk = off;                                   // smoothing elements, one per step
@@ -48,29 +49,18 @@ struct TImpl {
         return L;
     }
 
-    static void states(void* ws, const Layout& L, ScanState& fs, tc::TBuf& fb, ScanState& ss, tc::TBuf& sb) {
+    static void buffers(void* ws, const Layout& L, tc::TBuf& fb, tc::TBuf& sb) {
         char* b = static_cast<char*>(ws);
-        uint32_t* status = static_cast<uint32_t*>(ws);
-        fs.counter = reinterpret_cast<uint32_t*>(b + L.off_flags);
-        fs.flags = reinterpret_cast<uint32_t*>(b + L.off_flags + 16);
-        float* fa = reinterpret_cast<float*>(b + L.off_fagg);
-        fs.agg = fa;
-        fs.pre = fa + (size_t)FR * L.ntf;
-        fb.tex = fa + (size_t)FR * L.ntf * 2;
+        float* fs = reinterpret_cast<float*>(b + L.off_fagg);
+        fb.spine0 = fs;
+        fb.spine1 = fs + (size_t)FR * L.ntf;
         fb.chains = reinterpret_cast<float*>(b + L.off_fpre);
         fb.elems = nullptr;
-        fs.status = status;
-        fs.spin_limit = kSpinLimit;
-        ss.counter = reinterpret_cast<uint32_t*>(b + L.off_flags + 4);
-        ss.flags = reinterpret_cast<uint32_t*>(b + L.off_flags + 16 + 4 * (size_t)L.ntf);
-        float* sa = reinterpret_cast<float*>(b + L.off_sagg);
-        ss.agg = sa;
-        ss.pre = sa + (size_t)SR * L.nts;
-        sb.tex = sa + (size_t)SR * L.nts * 2;
+        float* ss = reinterpret_cast<float*>(b + L.off_sagg);
+        sb.spine0 = ss;
+        sb.spine1 = ss + (size_t)SR * L.nts;
         sb.chains = reinterpret_cast<float*>(b + L.off_spre);
         sb.elems = reinterpret_cast<float*>(b + L.off_sblk);
-        ss.status = status;
-        ss.spin_limit = kSpinLimit;
     }
 
     template <class K>
@@ -80,27 +70,57 @@ struct TImpl {
 
     static int scans(void* ws, const Layout& L, const float* y, float* fm, float* fc, float* sm, float* sc,
                      cudaStream_t st, void* const* ev, bool filter, bool smoother) {
-        ScanState fs, ss;
+        using FSP = tc::SpineSmem<N, tc::kSpineWarps, tc::kSpineBufF>;
+        using SSP = tc::SpineSmem<N, tc::kSpineWarps, tc::kSpineBufS>;
+        constexpr int SW = tc::kSpineWarps;
         tc::TBuf fb, sb;
-        states(ws, L, fs, fb, ss, sb);
+        buffers(ws, L, fb, sb);
+        uint32_t* status = static_cast<uint32_t*>(ws);
         const ModelConst<N, M>* mc =
             reinterpret_cast<const ModelConst<N, M>*>(static_cast<char*>(ws) + L.off_const);
+        int rc;
         if (filter) {
-            auto k = tc::tfilter_kernel<N, M, NW, CH>;
-            static const bool ok = allow_smem(k, (int)sizeof(FSM));
+            auto kr = tc::tfilter_reduce_kernel<N, M, NW, CH>;
+            auto ks = tc::tspine_filter_kernel<N, SW>;
+            auto ka = tc::tfilter_apply_kernel<N, M, NW, CH>;
+            static const bool ok = allow_smem(kr, (int)sizeof(FSM)) && allow_smem(ks, (int)sizeof(FSP)) &&
+                                   allow_smem(ka, (int)sizeof(FSM));
             if (!ok) return KS_ECUDA;
-            k<<<L.ntf, NW * 32, sizeof(FSM), st>>>(mc, y, L.T, fm, fc, fs, fb);
-            int rc = launch_status();
-            if (rc) return rc;
+            kr<<<L.ntf, NW * 32, sizeof(FSM), st>>>(mc, y, L.T, fb, status);
+            if ((rc = launch_status())) return rc;
+            const float* src = fb.spine0;
+            float* dst = fb.spine1;
+            for (int s = 1; s < L.ntf; s <<= 1) {
+                ks<<<(L.ntf + SW - 1) / SW, SW * 32, sizeof(FSP), st>>>(src, dst, L.ntf, s, status);
+                if ((rc = launch_status())) return rc;
+                float* t = const_cast<float*>(src);
+                src = dst;
+                dst = t;
+            }
+            ka<<<L.ntf, NW * 32, sizeof(FSM), st>>>(mc, y, L.T, fm, fc, fb, src, status);
+            if ((rc = launch_status())) return rc;
         }
         if (ev && ev[2] && cudaEventRecord(static_cast<cudaEvent_t>(ev[2]), st) != cudaSuccess) return KS_ECUDA;
         if (smoother) {
-            auto k = tc::tsmoother_kernel<N, M, NW, CH>;
-            static const bool ok = allow_smem(k, (int)sizeof(SSM));
+            auto kr = tc::tsmoother_reduce_kernel<N, M, NW, CH>;
+            auto ks = tc::tspine_smoother_kernel<N, SW>;
+            auto ka = tc::tsmoother_apply_kernel<N, M, NW, CH>;
+            static const bool ok = allow_smem(kr, (int)sizeof(SSM)) && allow_smem(ks, (int)sizeof(SSP)) &&
+                                   allow_smem(ka, (int)sizeof(SSM));
             if (!ok) return KS_ECUDA;
-            k<<<L.nts, NW * 32, sizeof(SSM), st>>>(mc, fm, fc, L.T, sm, sc, ss, sb);
-            int rc = launch_status();
-            if (rc) return rc;
+            kr<<<L.nts, NW * 32, sizeof(SSM), st>>>(mc, fm, fc, L.T, sb, status);
+            if ((rc = launch_status())) return rc;
+            const float* src = sb.spine0;
+            float* dst = sb.spine1;
+            for (int s = 1; s < L.nts; s <<= 1) {
+                ks<<<(L.nts + SW - 1) / SW, SW * 32, sizeof(SSP), st>>>(src, dst, L.nts, s, status);
+                if ((rc = launch_status())) return rc;
+                float* t = const_cast<float*>(src);
+                src = dst;
+                dst = t;
+            }
+            ka<<<L.nts, NW * 32, sizeof(SSM), st>>>(L.T, sm, sc, sb, src, status);
+            if ((rc = launch_status())) return rc;
         }
         return KS_OK;
     }
