@@ -1,5 +1,6 @@
 // ks_gimpl.cuh -- host side of the one-warp-per-chain instantiations (larger
-// nx): workspace layout and launches behind the same C ABI as ks_impl.cuh.
+// nx): workspace layout and launches (reduce, spine levels, apply per scan)
+// behind the same C ABI as ks_impl.cuh.
 #pragma once
 
 #include "ks_gscan.cuh"
@@ -25,18 +26,19 @@ struct GImpl {
         size_t off = 256;
         L.off_const = off;
         off = align_up(off + sizeof(ModelConst<N, M>) * (size_t)B, 256);
-        L.off_flags = off;
-        L.flags_bytes = 16 + 4 * (size_t)(L.ntf + L.nts);
+        L.off_flags = off;                                  // zeroed by the preparation kernel
+        L.flags_bytes = 16;
         off = align_up(off + L.flags_bytes, 256);
-        L.off_fagg = off;                                   // filter: agg, pre, tile prefixes, chains
-        off = align_up(off + 4 * (size_t)FS * L.ntf * 3, 256);
-        L.off_fpre = off;
+        L.off_fagg = off;                                   // filter: two spine buffers
+        off = align_up(off + 4 * (size_t)FS * L.ntf * 2, 256);
+        L.off_fpre = off;                                   // filter chains
         off = align_up(off + 4 * (size_t)FS * (size_t)(L.ntf * NW) * 2, 256);
-        L.off_sagg = off;                                   // smoother: agg, pre, tile prefixes, chains
-        off = align_up(off + 4 * (size_t)SS * L.nts * 3, 256);
-        L.off_spre = off;
+        L.off_sagg = off;                                   // smoother: two spine buffers
+        off = align_up(off + 4 * (size_t)SS * L.nts * 2, 256);
+        L.off_spre = off;                                   // smoother chains
         off = align_up(off + 4 * (size_t)SS * (size_t)(L.nts * NW) * 2, 256);
-        L.off_sblk = off;
+        L.off_sblk = off;                                   // smoothing elements, one slot per step
+        off = align_up(off + 4 * (size_t)SS * (size_t)T, 256);
         L.bytes_smooth = off;
         L.off_elems = off;
         L.off_fmean = off;
@@ -52,26 +54,18 @@ struct GImpl {
     }
     static uint32_t* status(void* ws) { return static_cast<uint32_t*>(ws); }
 
-    static void states(void* ws, const Layout& L, ScanState& fs, grp::GBuf& fb, ScanState& ss, grp::GBuf& sb) {
+    static void buffers(void* ws, const Layout& L, grp::GBuf& fb, grp::GBuf& sb) {
         char* b = static_cast<char*>(ws);
-        fs.counter = reinterpret_cast<uint32_t*>(b + L.off_flags);
-        fs.flags = reinterpret_cast<uint32_t*>(b + L.off_flags + 16);
         float* fa = reinterpret_cast<float*>(b + L.off_fagg);
-        fs.agg = fa;
-        fs.pre = fa + (size_t)FS * L.ntf;
-        fb.tex = fa + (size_t)FS * L.ntf * 2;
+        fb.spine0 = fa;
+        fb.spine1 = fa + (size_t)FS * L.ntf;
         fb.chains = reinterpret_cast<float*>(b + L.off_fpre);
-        fs.status = status(ws);
-        fs.spin_limit = kSpinLimit;
-        ss.counter = reinterpret_cast<uint32_t*>(b + L.off_flags + 4);
-        ss.flags = reinterpret_cast<uint32_t*>(b + L.off_flags + 16 + 4 * (size_t)L.ntf);
         float* sa = reinterpret_cast<float*>(b + L.off_sagg);
-        ss.agg = sa;
-        ss.pre = sa + (size_t)SS * L.nts;
-        sb.tex = sa + (size_t)SS * L.nts * 2;
+        sb.spine0 = sa;
+        sb.spine1 = sa + (size_t)SS * L.nts;
         sb.chains = reinterpret_cast<float*>(b + L.off_spre);
-        ss.status = status(ws);
-        ss.spin_limit = kSpinLimit;
+        fb.elems = nullptr;
+        sb.elems = reinterpret_cast<float*>(b + L.off_sblk);
     }
 
     template <class K>
@@ -92,29 +86,57 @@ struct GImpl {
         return launch_status();
     }
 
+    // Per scan: a reduce launch, log2(tiles) spine launches, an apply launch.
     template <bool SEG>
     static int scans(void* ws, const Layout& L, const float* y, float* fm, float* fc, float* sm, float* sc,
                      Segs<N, M> segs, cudaStream_t st, void* const* ev, bool filter, bool smoother) {
-        ScanState fs, ss;
         grp::GBuf fb, sb;
-        states(ws, L, fs, fb, ss, sb);
+        buffers(ws, L, fb, sb);
         constexpr int smem = SM::BYTES;
+        constexpr int SW = grp::gspine_warps<N>();
+        constexpr int ssmem = grp::GSpineSmem<N, SW>::BYTES;
+        uint32_t* stat = status(ws);
+        int rc;
         if (filter) {
-            auto k = grp::gfilter_kernel<N, M, NW, CH, SEG>;
-            static const bool ok = allow_smem(k, smem);
+            auto kr = grp::gfilter_reduce_kernel<N, M, NW, CH, SEG>;
+            auto ks = grp::gspine_filter_kernel<N, SW>;
+            auto ka = grp::gfilter_apply_kernel<N, M, NW, CH, SEG>;
+            static const bool ok = allow_smem(kr, smem) && allow_smem(ks, ssmem) && allow_smem(ka, smem);
             if (!ok) return KS_ECUDA;
-            k<<<L.ntf, NW * 32, smem, st>>>(mconst(ws, L), y, L.T, fm, fc, fs, fb, segs);
-            int rc = launch_status();
-            if (rc) return rc;
+            kr<<<L.ntf, NW * 32, smem, st>>>(mconst(ws, L), y, L.T, fb, stat, segs);
+            if ((rc = launch_status())) return rc;
+            const float* src = fb.spine0;
+            float* dst = fb.spine1;
+            for (int s = 1; s < L.ntf; s <<= 1) {
+                ks<<<(L.ntf + SW - 1) / SW, SW * 32, ssmem, st>>>(src, dst, L.ntf, s, stat);
+                if ((rc = launch_status())) return rc;
+                float* t = const_cast<float*>(src);
+                src = dst;
+                dst = t;
+            }
+            ka<<<L.ntf, NW * 32, smem, st>>>(mconst(ws, L), y, L.T, fm, fc, fb, src, stat, segs);
+            if ((rc = launch_status())) return rc;
         }
         if (ev && ev[2] && cudaEventRecord(static_cast<cudaEvent_t>(ev[2]), st) != cudaSuccess) return KS_ECUDA;
         if (smoother) {
-            auto k = grp::gsmoother_kernel<N, M, NW, CH, SEG>;
-            static const bool ok = allow_smem(k, smem);
+            auto kr = grp::gsmoother_reduce_kernel<N, M, NW, CH, SEG>;
+            auto ks = grp::gspine_smoother_kernel<N, SW>;
+            auto ka = grp::gsmoother_apply_kernel<N, M, NW, CH>;
+            static const bool ok = allow_smem(kr, smem) && allow_smem(ks, ssmem) && allow_smem(ka, smem);
             if (!ok) return KS_ECUDA;
-            k<<<L.nts, NW * 32, smem, st>>>(mconst(ws, L), fm, fc, L.T, sm, sc, ss, sb, segs);
-            int rc = launch_status();
-            if (rc) return rc;
+            kr<<<L.nts, NW * 32, smem, st>>>(mconst(ws, L), fm, fc, L.T, sb, stat, segs);
+            if ((rc = launch_status())) return rc;
+            const float* src = sb.spine0;
+            float* dst = sb.spine1;
+            for (int s = 1; s < L.nts; s <<= 1) {
+                ks<<<(L.nts + SW - 1) / SW, SW * 32, ssmem, st>>>(src, dst, L.nts, s, stat);
+                if ((rc = launch_status())) return rc;
+                float* t = const_cast<float*>(src);
+                src = dst;
+                dst = t;
+            }
+            ka<<<L.nts, NW * 32, smem, st>>>(L.T, sm, sc, sb, src, stat);
+            if ((rc = launch_status())) return rc;
         }
         return KS_OK;
     }
