@@ -11,8 +11,9 @@ namespace ks {
 template <int N, int M, int NW, int CH>
 struct GImpl {
     static constexpr int FS = grp::Dim<N>::FSLOT, SS = grp::Dim<N>::SSLOT;
-    static constexpr int64_t TILE = (int64_t)NW * CH;
     using SM = grp::GSmem<N, M, NW>;
+    static constexpr int NG = SM::NG;                      // chains per tile (one lane group each)
+    static constexpr int64_t TILE = (int64_t)NG * CH;
 
     static size_t prep_smem() { return sizeof(PrepSmem<N, M>) + sizeof(ModelConst<N, M>) + 16; }
 
@@ -22,7 +23,7 @@ struct GImpl {
         L.B = B;
         L.ld = 0;
         const int64_t nch = (T + CH - 1) / CH;
-        L.ntf = L.nts = (int)((nch + NW - 1) / NW);
+        L.ntf = L.nts = (int)((nch + NG - 1) / NG);
         size_t off = 256;
         L.off_const = off;
         off = align_up(off + sizeof(ModelConst<N, M>) * (size_t)B, 256);
@@ -32,11 +33,11 @@ struct GImpl {
         L.off_fagg = off;                                   // filter: two spine buffers
         off = align_up(off + 4 * (size_t)FS * L.ntf * 2, 256);
         L.off_fpre = off;                                   // filter chains
-        off = align_up(off + 4 * (size_t)FS * (size_t)(L.ntf * NW) * 2, 256);
+        off = align_up(off + 4 * (size_t)FS * (size_t)L.ntf * NG * 2, 256);
         L.off_sagg = off;                                   // smoother: two spine buffers
         off = align_up(off + 4 * (size_t)SS * L.nts * 2, 256);
         L.off_spre = off;                                   // smoother chains
-        off = align_up(off + 4 * (size_t)SS * (size_t)(L.nts * NW) * 2, 256);
+        off = align_up(off + 4 * (size_t)SS * (size_t)L.nts * NG * 2, 256);
         L.off_sblk = off;                                   // smoothing elements, one slot per step
         off = align_up(off + 4 * (size_t)SS * (size_t)T, 256);
         L.bytes_smooth = off;
@@ -95,6 +96,7 @@ struct GImpl {
         constexpr int smem = SM::BYTES;
         constexpr int SW = grp::gspine_warps<N>();
         constexpr int ssmem = grp::GSpineSmem<N, SW>::BYTES;
+        constexpr int SG = grp::GSpineSmem<N, SW>::NG;          // tiles per spine block
         uint32_t* stat = status(ws);
         int rc;
         if (filter) {
@@ -108,7 +110,7 @@ struct GImpl {
             const float* src = fb.spine0;
             float* dst = fb.spine1;
             for (int s = 1; s < L.ntf; s <<= 1) {
-                ks<<<(L.ntf + SW - 1) / SW, SW * 32, ssmem, st>>>(src, dst, L.ntf, s, stat);
+                ks<<<(L.ntf + SG - 1) / SG, SW * 32, ssmem, st>>>(src, dst, L.ntf, s, stat);
                 if ((rc = launch_status())) return rc;
                 float* t = const_cast<float*>(src);
                 src = dst;
@@ -129,7 +131,7 @@ struct GImpl {
             const float* src = sb.spine0;
             float* dst = sb.spine1;
             for (int s = 1; s < L.nts; s <<= 1) {
-                ks<<<(L.nts + SW - 1) / SW, SW * 32, ssmem, st>>>(src, dst, L.nts, s, stat);
+                ks<<<(L.nts + SG - 1) / SG, SW * 32, ssmem, st>>>(src, dst, L.nts, s, stat);
                 if ((rc = launch_status())) return rc;
                 float* t = const_cast<float*>(src);
                 src = dst;

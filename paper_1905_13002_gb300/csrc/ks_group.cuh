@@ -1,9 +1,12 @@
 // ks_group.cuh -- elements of larger state size (nx >= 8), one warp per chain.
 //
-// An element's matrices live in a per-warp shared-memory slot, row-major with
-// a padded row pitch; lane r of the warp computes row r of every result
-// (rows r >= N are idle), reading the other operand's rows from shared memory
-// (all lanes read the same address: broadcast).  Registers hold a few rows.
+// An element's matrices live in a per-chain shared-memory slot, row-major with
+// a padded row pitch; one group of lanes serves one chain and lane r of the
+// group computes row r of every result (rows r >= N are idle), reading the
+// other operand's rows from shared memory (the group reads one address:
+// broadcast).  A group is 8 lanes for N <= 8 (four chains per warp) and the
+// whole warp otherwise; groups synchronise and exchange values with masks
+// of their own lanes only.  Registers hold a few rows.
 // The operators are the same Lemmas 3-6 as the register version in
 // ks_ops.cuh; symmetric results are symmetrised as (X + X^T) / 2.
 #pragma once
@@ -48,7 +51,22 @@ struct SSlot {
     KS_DEV float* g() const { return p + 2 * Dim<N>::MAT; }
 };
 
-KS_DEV void wsync() { __syncwarp(); }
+// Lanes per chain and the mask of the calling lane's group.
+template <int N>
+struct Grp {
+    static constexpr int GS = N <= 8 ? 8 : 32;
+};
+template <int N>
+KS_DEV unsigned gmask() {
+    if constexpr (Grp<N>::GS == 32) {
+        return kFullMask;
+    } else {
+        constexpr unsigned ones = (1u << Grp<N>::GS) - 1u;
+        return ones << ((threadIdx.x & 31) & ~(Grp<N>::GS - 1));
+    }
+}
+template <int N>
+KS_DEV void gsync() { __syncwarp(gmask<N>()); }
 
 // ---------------------------------------------------------------- row kernels
 // Left operands are rows in shared memory (pointers), so that for large N the
@@ -176,11 +194,11 @@ KS_DEV bool gj_inverse(int r, float (&m)[N], float* pr, float* out) {
 #pragma unroll
         for (int c = 0; c < N; ++c)
             if (c == k) v = used ? -1.f : fabsf(m[c]);
-        int idx = threadIdx.x & 31;
+        int idx = r;
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            const float ov = __shfl_xor_sync(kFullMask, v, off);
-            const int oi = __shfl_xor_sync(kFullMask, idx, off);
+        for (int off = Grp<N>::GS / 2; off > 0; off >>= 1) {
+            const float ov = __shfl_xor_sync(gmask<N>(), v, off);
+            const int oi = __shfl_xor_sync(gmask<N>(), idx, off);
             if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
         }
         const int p = idx;
@@ -190,7 +208,7 @@ KS_DEV bool gj_inverse(int r, float (&m)[N], float* pr, float* out) {
             for (int c = 0; c < N; ++c) { pr[c] = m[c]; pr[Dim<N>::NP + c] = inv[c]; }
         }
         if (r == k) src = p;
-        wsync();
+        gsync<N>();
         float piv = 0.f;
 #pragma unroll
         for (int c = 0; c < N; ++c)
@@ -212,15 +230,15 @@ KS_DEV bool gj_inverse(int r, float (&m)[N], float* pr, float* out) {
                 inv[c] = fmaf(-fi, pr[Dim<N>::NP + c], inv[c]);
             }
         }
-        wsync();
+        gsync<N>();
     }
     if (act) store_row<N>(out, r, inv);
-    wsync();
+    gsync<N>();
     float res[N];
     load_row<N>(out, act ? src : 0, res);
-    wsync();
+    gsync<N>();
     if (act) store_row<N>(out, r, res);
-    wsync();
+    gsync<N>();
     return ok;
 }
 
@@ -274,7 +292,7 @@ KS_DEV void fcombine(int r, FSlot<N> i, FSlot<N> j, FSlot<N> o, Scratch<N> s, bo
             s.V(2)[r] = col_dot<N>(s.S(0), r, s.V(1));               // w = Mi^T v
         }
     }
-    wsync();
+    gsync<N>();
     {
         float t1[N], wc[N], an[N];
         row_mul<N>(rowp<N>(s.S(5), rr), i.A(), t1);                  // T1 = (Mi^T J_j) A_i
@@ -288,7 +306,7 @@ KS_DEV void fcombine(int r, FSlot<N> i, FSlot<N> j, FSlot<N> o, Scratch<N> s, bo
             o.eta()[r] = col_dot<N>(i.A(), r, s.V(2)) + i.eta()[r];
         }
     }
-    wsync();
+    gsync<N>();
     {
         float cr[N], jn[N];
         row_mulT<N>(rowp<N>(s.S(2), rr), j.A(), cr);                 // (X C_i) A_j^T
@@ -300,16 +318,16 @@ KS_DEV void fcombine(int r, FSlot<N> i, FSlot<N> j, FSlot<N> o, Scratch<N> s, bo
                 jn[c] += i.J()[r * Dim<N>::NP + c];
             }
         }
-        wsync();                                                     // S2 row r (X C_i) is read by lane r only
+        gsync<N>();                                                     // S2 row r (X C_i) is read by lane r only
         if (act) {
             store_row<N>(s.S(2), r, cr);
             store_row<N>(s.S(3), r, jn);
         }
     }
-    wsync();
+    gsync<N>();
     symmetrise_into<N>(r, s.S(2), o.C());
     symmetrise_into<N>(r, s.S(3), o.J());
-    wsync();
+    gsync<N>();
 }
 
 // o = (b, C) (x) j for a prefix state (A = 0); only b and C of o are formed:
@@ -329,13 +347,13 @@ KS_DEV void fadvance(int r, FSlot<N> st, FSlot<N> j, FSlot<N> o, Scratch<N> s, b
         row_mul<N>(rowp<N>(j.A(), rr), s.S(0), x);
         if (act) store_row<N>(s.S(4), r, x);
     }
-    wsync();
+    gsync<N>();
     {
         float wc[N];
         row_mul<N>(rowp<N>(s.S(4), rr), st.C(), wc);
         if (act) store_row<N>(s.S(2), r, wc);
     }
-    wsync();
+    gsync<N>();
     {
         float cr[N];
         row_mulT<N>(rowp<N>(s.S(2), rr), j.A(), cr);
@@ -344,12 +362,12 @@ KS_DEV void fadvance(int r, FSlot<N> st, FSlot<N> j, FSlot<N> o, Scratch<N> s, b
             for (int c = 0; c < N; ++c) cr[c] += j.C()[r * Dim<N>::NP + c];
             o.b()[r] = dot<N>(rowp<N>(s.S(4), r), s.V(0)) + j.b()[r];
         }
-        wsync();
+        gsync<N>();
         if (act) store_row<N>(s.S(3), r, cr);
     }
-    wsync();
+    gsync<N>();
     symmetrise_into<N>(r, s.S(3), o.C());
-    wsync();
+    gsync<N>();
 }
 
 // Rank-M form for a single measurement element j (constants in `mc`):
@@ -375,7 +393,7 @@ KS_DEV void fcombine_meas(int r, FSlot<N> i, const ModelConst<N, M>& mc, float b
         for (int q = 0; q < M; ++q) s.S(0)[r * NP + q] = cu[q];
         s.V(0)[r] = i.b()[r];
     }
-    wsync();
+    gsync<N>();
     float G[sym_size(M)];                                    // G = I + U CU (every lane)
 #pragma unroll
     for (int q = 0; q < M; ++q)
@@ -411,7 +429,7 @@ KS_DEV void fcombine_meas(int r, FSlot<N> i, const ModelConst<N, M>& mc, float b
         }
         s.V(1)[r] = t_r;
     }
-    wsync();
+    gsync<N>();
     {
         const float* ar = mc.A + rr * N;                     // X[r] = A[r] - (A[r] CUL) UL
         float ac[M];
@@ -439,7 +457,7 @@ KS_DEV void fcombine_meas(int r, FSlot<N> i, const ModelConst<N, M>& mc, float b
             store_row<N>(s.S(2), r, wr);
         }
     }
-    wsync();
+    gsync<N>();
     if (act) o.b()[r] = dot<N>(rowp<N>(s.S(4), r), s.V(1)) + bj;
     if constexpr (!PREFIX) {
         float an[N];
@@ -481,7 +499,7 @@ KS_DEV void fcombine_meas(int r, FSlot<N> i, const ModelConst<N, M>& mc, float b
         row_mul_const_rows<N>(mc.A + rr * N, s.S(2), y);     // Y[r] = A[r] W
         if (act) store_row<N>(s.S(5), r, y);
     }
-    wsync();
+    gsync<N>();
     {
         float cr[N];
         row_mulT_const<N>(rowp<N>(s.S(5), rr), mc.A, cr);    // C_o[r] = Y[r] A^T + C[r]
@@ -504,9 +522,9 @@ KS_DEV void fcombine_meas(int r, FSlot<N> i, const ModelConst<N, M>& mc, float b
             store_row<N>(o.J(), r, jn);                      // VA^T VA + J_i: exactly symmetric
         }
     }
-    wsync();
+    gsync<N>();
     symmetrise_into<N>(r, s.S(0), o.C());
-    wsync();
+    gsync<N>();
 }
 
 // ---------------------------------------------------------------- Lemma 3 rows
@@ -553,7 +571,7 @@ KS_DEV void expand_meas(int r, const ModelConst<N, M>& mc, float b, const float 
         o.eta()[r] = e;
         o.b()[r] = b;
     }
-    wsync();
+    gsync<N>();
 }
 
 // The k = 1 element: A_1 = 0, b_1, C_1 (built in FP64), eta_1 = 0, J_1 = 0.
@@ -568,7 +586,7 @@ KS_DEV void first_elem(int r, const ModelConst<N, M>& mc, FSlot<N> o) {
         o.b()[r] = mc.b1[r];
         o.eta()[r] = 0.f;
     }
-    wsync();
+    gsync<N>();
 }
 
 // acc (x) a_1 for a sequence's first element (A_1 = 0, eta_1 = J_1 = 0):
@@ -582,7 +600,7 @@ KS_DEV void reset_first(int r, const ModelConst<N, M>& mc, FSlot<N> acc) {
         for (int q = 0; q < N; ++q) { pa[q] = 0.f; pc[q] = mc.C1[sidx(r, q)]; }
         acc.b()[r] = mc.b1[r];
     }
-    wsync();
+    gsync<N>();
 }
 
 // Posterior state (b, C) = (b_1, C_1) for a sequence's first step.
@@ -594,7 +612,7 @@ KS_DEV void first_state(int r, const ModelConst<N, M>& mc, FSlot<N> st) {
         for (int q = 0; q < N; ++q) pc[q] = mc.C1[sidx(r, q)];
         st.b()[r] = mc.b1[r];
     }
-    wsync();
+    gsync<N>();
 }
 
 // ---------------------------------------------------------------- Lemma 5 rows
@@ -617,7 +635,7 @@ KS_DEV void selem(int r, const ModelConst<N, M>& mc, const float* P, const float
             }
             o.g()[r] = xb[r];
         }
-        wsync();
+        gsync<N>();
         return;
     }
     {
@@ -628,7 +646,7 @@ KS_DEV void selem(int r, const ModelConst<N, M>& mc, const float* P, const float
             s.V(0)[r] = dot<N>(mc.F + r * N, xb) + mc.u[r];
         }
     }
-    wsync();
+    gsync<N>();
     float pm[N];
     row_mulT_const<N>(rowp<N>(s.S(1), rr), mc.F, pm);       // P-[r] = FP[r] F^T + Q[r]
     if (act) {
@@ -641,7 +659,7 @@ KS_DEV void selem(int r, const ModelConst<N, M>& mc, const float* P, const float
         colT_mul<N>(s.S(1), rr, s.S(0), e);                  // E[r] = (FP^T (P-)^{-1})[r]
         if (act) store_row<N>(o.E(), r, e);
     }
-    wsync();
+    gsync<N>();
     if (act) {
         o.g()[r] = xb[r] - dot<N>(rowp<N>(o.E(), r), s.V(0));
         float l[N];
@@ -650,9 +668,9 @@ KS_DEV void selem(int r, const ModelConst<N, M>& mc, const float* P, const float
         for (int q = 0; q < N; ++q) l[q] = P[r * NP + q] - l[q];
         store_row<N>(s.S(2), r, l);
     }
-    wsync();
+    gsync<N>();
     symmetrise_into<N>(r, s.S(2), o.L());
-    wsync();
+    gsync<N>();
 }
 
 // ---------------------------------------------------------------- Lemma 6 rows
@@ -667,7 +685,7 @@ KS_DEV void scombine(int r, SSlot<N> i, SSlot<N> j, SSlot<N> o, Scratch<N> s) {
         row_mul<N>(rowp<N>(i.E(), rr), j.L(), y);            // Y[r] = E_i[r] L_j
         if (act) store_row<N>(s.S(5), r, y);
     }
-    wsync();
+    gsync<N>();
     {
         float l[N];
         row_mulT<N>(rowp<N>(s.S(5), rr), i.E(), l);          // L[r][c] = Y[r] . E_i[c]
@@ -683,9 +701,9 @@ KS_DEV void scombine(int r, SSlot<N> i, SSlot<N> j, SSlot<N> o, Scratch<N> s) {
         row_mul<N>(rowp<N>(i.E(), rr), j.E(), en);
         if (act) store_row<N>(o.E(), r, en);
     }
-    wsync();
+    gsync<N>();
     symmetrise_into<N>(r, s.S(3), o.L());
-    wsync();
+    gsync<N>();
 }
 
 }  // namespace grp

@@ -1,15 +1,16 @@
-// ks_gscan.cuh -- forward and reverse scans for larger state sizes, one warp
-// per chain of CH consecutive steps (elements in shared-memory slots, see
-// ks_group.cuh).  Each scan runs as three kinds of launch (the paper's
-// block-level elements, Section III-C, one block per tile of NW chains):
-//   reduce   each warp folds its chain into one block element; warp 0 then
-//            combines the tile's chain totals in order, storing each warp's
+// ks_gscan.cuh -- forward and reverse scans for larger state sizes, one lane
+// group per chain of CH consecutive steps (elements in shared-memory slots,
+// see ks_group.cuh: 8 lanes per chain for nx <= 8, a warp otherwise).  Each
+// scan runs as three kinds of launch (the paper's block-level elements,
+// Section III-C, one block per tile of NG chains):
+//   reduce   each group folds its chain into one block element; group 0 then
+//            combines the tile's chain totals in order, storing each chain's
 //            exclusive in-tile prefix, and writes the tile aggregate;
 //   spine    one Kogge-Stone level over the tile aggregates per launch
-//            (log2 tiles launches, one warp per tile, no waiting on other
+//            (log2 tiles launches, one group per tile, no waiting on other
 //            blocks); a left operand that is already a complete prefix is
 //            applied in its prefix-state form;
-//   apply    each warp starts from the prefix entering its chain and applies
+//   apply    each group starts from the prefix entering its chain and applies
 //            its elements one by one, writing one posterior per step.
 // With a full nx x nx combine (a pivoted inverse) per step of a cross-tile
 // walk, a decoupled look-back kept most of each block waiting; the spine
@@ -35,15 +36,20 @@ struct GBuf {
     float* elems;    // T smoothing slots (reverse scan only)
 };
 
-// Copy an element slot (n floats) between two locations, warp-cooperatively.
+// Copy an element slot (n floats) between two locations, by the lanes of the
+// calling chain's group.
+template <int N>
 KS_DEV void copy_floats(float* dst, const float* src, int n) {
-    for (int i = threadIdx.x & 31; i < n; i += 32) dst[i] = src[i];
-    __syncwarp();
+    constexpr int GS = Grp<N>::GS;
+    for (int i = threadIdx.x & (GS - 1); i < n; i += GS) dst[i] = src[i];
+    gsync<N>();
 }
 // The same from data written by other blocks or launches (L2 loads).
+template <int N>
 KS_DEV void copy_floats_cg(float* dst, const float* src, int n) {
-    for (int i = threadIdx.x & 31; i < n; i += 32) dst[i] = __ldcg(src + i);
-    __syncwarp();
+    constexpr int GS = Grp<N>::GS;
+    for (int i = threadIdx.x & (GS - 1); i < n; i += GS) dst[i] = __ldcg(src + i);
+    gsync<N>();
 }
 
 template <int N, int M>
@@ -53,29 +59,41 @@ KS_DEV void load_const_all(const ModelConst<N, M>* __restrict__ g, ModelConst<N,
     for (int i = threadIdx.x; i < (int)(sizeof(ModelConst<N, M>) / 4); i += blockDim.x) dst[i] = __ldg(src + i);
 }
 
-template <int N, int M, int NW>
-struct GSmem {
+// Per-chain buffer: three element slots and the scratch.  With 8-lane groups
+// the stride is padded to 8 (mod 32) words, so the four groups of a warp
+// reading their own row r (word 9 r + j + 8 g) or one broadcast row hit
+// distinct banks.
+template <int N>
+struct GChain {
     static constexpr int FS = Dim<N>::FSLOT, SS = Dim<N>::SSLOT;
     static constexpr int SLOT = FS > SS ? FS : SS;
-    static constexpr int WARP = 3 * SLOT + Scratch<N>::FLOATS;      // three element slots + scratch
-    static constexpr int BYTES = (int)sizeof(ModelConst<N, M>) + NW * WARP * 4 + 16;
+    static constexpr int RAW = 3 * SLOT + Scratch<N>::FLOATS;
+    static constexpr int STRIDE = Grp<N>::GS == 32 ? RAW : RAW + ((8 - RAW % 32) + 32) % 32;
+};
+
+// Shared memory of a scan launch: the model constants and NW warps' chains.
+template <int N, int M, int NW>
+struct GSmem {
+    static constexpr int SLOT = GChain<N>::SLOT;
+    static constexpr int NG = NW * 32 / Grp<N>::GS;                  // chains per block
+    static constexpr int BYTES = (int)sizeof(ModelConst<N, M>) + NG * GChain<N>::STRIDE * 4 + 16;
     static KS_DEV ModelConst<N, M>& mc(char* base) { return *reinterpret_cast<ModelConst<N, M>*>(base); }
-    static KS_DEV float* warp(char* base, int w) {
-        return reinterpret_cast<float*>(base + ((sizeof(ModelConst<N, M>) + 15) / 16) * 16) + w * WARP;
+    static KS_DEV float* chain(char* base, int g) {
+        return reinterpret_cast<float*>(base + ((sizeof(ModelConst<N, M>) + 15) / 16) * 16) + g * GChain<N>::STRIDE;
     }
 };
 
-// Shared memory of a spine launch (no model constants).
+// Shared memory of a spine launch (no model constants): NWS warps' chains.
 template <int N, int NWS>
 struct GSpineSmem {
-    static constexpr int WARP = GSmem<N, 1, 1>::WARP;
-    static constexpr int BYTES = NWS * WARP * 4;
-    static KS_DEV float* warp(char* base, int w) { return reinterpret_cast<float*>(base) + w * WARP; }
+    static constexpr int NG = NWS * 32 / Grp<N>::GS;
+    static constexpr int BYTES = NG * GChain<N>::STRIDE * 4;
+    static KS_DEV float* chain(char* base, int g) { return reinterpret_cast<float*>(base) + g * GChain<N>::STRIDE; }
 };
 // Warps per spine block: up to 4, within 200 KB of shared memory.
 template <int N>
 constexpr int gspine_warps() {
-    constexpr int per = GSmem<N, 1, 1>::WARP * 4;
+    constexpr int per = GChain<N>::STRIDE * 4 * (32 / Grp<N>::GS);
     return per * 4 <= 200 * 1024 ? 4 : (200 * 1024 / per > 0 ? 200 * 1024 / per : 1);
 }
 
@@ -85,20 +103,20 @@ __global__ void __launch_bounds__(NW * 32) gfilter_reduce_kernel(const ModelCons
                                                                  const float* __restrict__ y, int64_t T, GBuf gb,
                                                                  uint32_t* status, Segs<N, M> segs) {
     using SM = GSmem<N, M, NW>;
-    constexpr int FS = Dim<N>::FSLOT;
+    constexpr int FS = Dim<N>::FSLOT, NG = SM::NG;
     extern __shared__ __align__(16) char gsm[];
     ModelConst<N, M>& mc = SM::mc(gsm);
     load_const_all<N, M>(mcg, mc);
     __syncthreads();
     const int tile = blockIdx.x;
-    const int w = threadIdx.x >> 5, r = threadIdx.x & 31;
+    const int w = threadIdx.x / Grp<N>::GS, r = threadIdx.x & (Grp<N>::GS - 1);
     const int64_t nch = (T + CH - 1) / CH;
-    const int64_t c = (int64_t)tile * NW + w;
-    const int64_t left = nch - (int64_t)tile * NW;
-    const int nvalid = left < NW ? (int)left : NW;
+    const int64_t c = (int64_t)tile * NG + w;
+    const int64_t left = nch - (int64_t)tile * NG;
+    const int nvalid = left < NG ? (int)left : NG;
     const bool valid = w < nvalid;
     const int64_t k0 = c * CH;
-    float* wb = SM::warp(gsm, w);
+    float* wb = SM::chain(gsm, w);
     FSlot<N> X[3] = {FSlot<N>{wb}, FSlot<N>{wb + SM::SLOT}, FSlot<N>{wb + 2 * SM::SLOT}};
     Scratch<N> s{wb + 3 * SM::SLOT};
     bool bad = false;
@@ -115,7 +133,7 @@ __global__ void __launch_bounds__(NW * 32) gfilter_reduce_kernel(const ModelCons
             const float b = meas<N, M>(r, *cur.mc, y + k0 * M, wv);
             expand_meas<N, M>(r, *cur.mc, b, wv, X[0]);
         }
-        wsync();
+        gsync<N>();
 #pragma unroll 1
         for (int i = 1; i < CH; ++i) {
             const int64_t k = k0 + i;
@@ -123,7 +141,7 @@ __global__ void __launch_bounds__(NW * 32) gfilter_reduce_kernel(const ModelCons
             cur.forward(segs, k);
             if (cur.first(k)) {
                 reset_first<N, M>(r, *cur.mc, X[a]);
-                wsync();
+                gsync<N>();
             } else {
                 float wv[M];
                 const float b = meas<N, M>(r, *cur.mc, y + k * M, wv);
@@ -131,27 +149,27 @@ __global__ void __launch_bounds__(NW * 32) gfilter_reduce_kernel(const ModelCons
                 a ^= 1;
             }
         }
-        copy_floats(gb.chains + (size_t)c * 2 * FS, X[a].p, FS);
+        copy_floats<N>(gb.chains + (size_t)c * 2 * FS, X[a].p, FS);
     }
     __threadfence_block();
     __syncthreads();
 
     // ---- in-tile combine (warp 0)
     if (w == 0) {
-        const float* T0 = gb.chains + (size_t)tile * NW * 2 * FS;
+        const float* T0 = gb.chains + (size_t)tile * NG * 2 * FS;
         int a = 0;
-        copy_floats(X[0].p, T0, FS);
+        copy_floats<N>(X[0].p, T0, FS);
 #pragma unroll 1
         for (int t = 1; t < nvalid; ++t) {
-            float* cht = gb.chains + ((size_t)tile * NW + t) * 2 * FS;
-            copy_floats(cht + FS, X[a].p, FS);              // E_t = T_0 (x) ... (x) T_{t-1}
-            copy_floats(X[2].p, cht, FS);
+            float* cht = gb.chains + ((size_t)tile * NG + t) * 2 * FS;
+            copy_floats<N>(cht + FS, X[a].p, FS);              // E_t = T_0 (x) ... (x) T_{t-1}
+            copy_floats<N>(X[2].p, cht, FS);
             fcombine<N>(r, X[a], X[2], X[a ^ 1], s, bad);
             a ^= 1;
         }
-        copy_floats(gb.spine0 + (size_t)tile * FS, X[a].p, FS);
+        copy_floats<N>(gb.spine0 + (size_t)tile * FS, X[a].p, FS);
     }
-    if (__any_sync(kFullMask, bad) && r == 0) atomicOr(status, ST_NUMERIC);
+    if (__any_sync(gmask<N>(), bad) && r == 0) atomicOr(status, ST_NUMERIC);
 }
 
 // dst[t] = src[t - s] (x) src[t] for t >= s, else src[t].  src[t - s] covers
@@ -162,26 +180,26 @@ __global__ void __launch_bounds__(NWS * 32) gspine_filter_kernel(const float* __
                                                                  int ntiles, int s, uint32_t* status) {
     using SM = GSpineSmem<N, NWS>;
     constexpr int FS = Dim<N>::FSLOT;
-    constexpr int SLOT = GSmem<N, 1, 1>::SLOT;
+    constexpr int SLOT = GChain<N>::SLOT;
     extern __shared__ __align__(16) char gsm[];
-    const int w = threadIdx.x >> 5, r = threadIdx.x & 31;
-    const int t = blockIdx.x * NWS + w;
+    const int w = threadIdx.x / Grp<N>::GS, r = threadIdx.x & (Grp<N>::GS - 1);
+    const int t = blockIdx.x * SM::NG + w;
     if (t >= ntiles) return;                              // whole warps; no block barrier below
     float* o = dst + (size_t)t * FS;
     if (t < s) {
-        copy_floats_cg(o, src + (size_t)t * FS, FS);
+        copy_floats_cg<N>(o, src + (size_t)t * FS, FS);
         return;
     }
-    float* wb = SM::warp(gsm, w);
+    float* wb = SM::chain(gsm, w);
     FSlot<N> X[3] = {FSlot<N>{wb}, FSlot<N>{wb + SLOT}, FSlot<N>{wb + 2 * SLOT}};
     Scratch<N> sc{wb + 3 * SLOT};
     bool bad = false;
-    copy_floats_cg(X[0].p, src + (size_t)(t - s) * FS, FS);
-    copy_floats_cg(X[1].p, src + (size_t)t * FS, FS);
+    copy_floats_cg<N>(X[0].p, src + (size_t)(t - s) * FS, FS);
+    copy_floats_cg<N>(X[1].p, src + (size_t)t * FS, FS);
     if (t - s < s) fadvance<N>(r, X[0], X[1], X[2], sc, bad);
     else fcombine<N>(r, X[0], X[1], X[2], sc, bad);
-    copy_floats(o, X[2].p, FS);
-    if (__any_sync(kFullMask, bad) && r == 0) atomicOr(status, ST_NUMERIC);
+    copy_floats<N>(o, X[2].p, FS);
+    if (__any_sync(gmask<N>(), bad) && r == 0) atomicOr(status, ST_NUMERIC);
 }
 
 // `pre`: the spine's inclusive prefixes (slot t covers tiles 0..t).
@@ -192,19 +210,19 @@ __global__ void __launch_bounds__(NW * 32) gfilter_apply_kernel(const ModelConst
                                                                 GBuf gb, const float* __restrict__ pre,
                                                                 uint32_t* status, Segs<N, M> segs) {
     using SM = GSmem<N, M, NW>;
-    constexpr int FS = Dim<N>::FSLOT;
+    constexpr int FS = Dim<N>::FSLOT, NG = SM::NG;
     extern __shared__ __align__(16) char gsm[];
     ModelConst<N, M>& mc = SM::mc(gsm);
     load_const_all<N, M>(mcg, mc);
     __syncthreads();
     const int tile = blockIdx.x;
-    const int w = threadIdx.x >> 5, r = threadIdx.x & 31;
+    const int w = threadIdx.x / Grp<N>::GS, r = threadIdx.x & (Grp<N>::GS - 1);
     const int64_t nch = (T + CH - 1) / CH;
-    const int64_t c = (int64_t)tile * NW + w;
+    const int64_t c = (int64_t)tile * NG + w;
     if (c >= nch) return;                                 // whole warps; no block barrier below
     const int64_t k0 = c * CH;
     const float* chE = gb.chains + (size_t)c * 2 * FS + FS;
-    float* wb = SM::warp(gsm, w);
+    float* wb = SM::chain(gsm, w);
     FSlot<N> X[3] = {FSlot<N>{wb}, FSlot<N>{wb + SM::SLOT}, FSlot<N>{wb + 2 * SM::SLOT}};
     Scratch<N> s{wb + 3 * SM::SLOT};
     bool bad = false;
@@ -214,15 +232,15 @@ __global__ void __launch_bounds__(NW * 32) gfilter_apply_kernel(const ModelConst
     if (tile != 0) {
         const float* tex = pre + (size_t)(tile - 1) * FS;
         if (w >= 1) {
-            copy_floats_cg(X[2].p, tex, FS);
-            copy_floats_cg(X[1].p, chE, FS);
+            copy_floats_cg<N>(X[2].p, tex, FS);
+            copy_floats_cg<N>(X[1].p, chE, FS);
             fadvance<N>(r, X[2], X[1], X[0], s, bad);
         } else {
-            copy_floats_cg(X[0].p, tex, FS);
+            copy_floats_cg<N>(X[0].p, tex, FS);
         }
         has = true;
     } else if (w >= 1) {
-        copy_floats_cg(X[0].p, chE, FS);                 // E_w has A = 0 (it starts with the first element)
+        copy_floats_cg<N>(X[0].p, chE, FS);                 // E_w has A = 0 (it starts with the first element)
         has = true;
     }
     cur.seek(segs, &mc, k0, T);
@@ -252,7 +270,7 @@ __global__ void __launch_bounds__(NW * 32) gfilter_apply_kernel(const ModelConst
         }
     }
     bad |= !isfinite(probe);
-    if (__any_sync(kFullMask, bad) && r == 0) atomicOr(status, ST_NUMERIC);
+    if (__any_sync(gmask<N>(), bad) && r == 0) atomicOr(status, ST_NUMERIC);
 }
 
 // ---------------------------------------------------------------- reverse
@@ -264,22 +282,22 @@ __global__ void __launch_bounds__(NW * 32) gsmoother_reduce_kernel(const ModelCo
                                                                    const float* __restrict__ fcov, int64_t T, GBuf gb,
                                                                    uint32_t* status, Segs<N, M> segs) {
     using SM = GSmem<N, M, NW>;
-    constexpr int SS = Dim<N>::SSLOT;
+    constexpr int SS = Dim<N>::SSLOT, NG = SM::NG;
     extern __shared__ __align__(16) char gsm[];
     ModelConst<N, M>& mc = SM::mc(gsm);
     load_const_all<N, M>(mcg, mc);
     __syncthreads();
     const int tile = blockIdx.x;
-    const int w = threadIdx.x >> 5, r = threadIdx.x & 31;
+    const int w = threadIdx.x / Grp<N>::GS, r = threadIdx.x & (Grp<N>::GS - 1);
     const int64_t nch = (T + CH - 1) / CH;
-    const int64_t u = (int64_t)tile * NW + w;            // scan-order chain index
-    const int64_t left = nch - (int64_t)tile * NW;
-    const int nvalid = left < NW ? (int)left : NW;
+    const int64_t u = (int64_t)tile * NG + w;            // scan-order chain index
+    const int64_t left = nch - (int64_t)tile * NG;
+    const int nvalid = left < NG ? (int)left : NG;
     const bool valid = w < nvalid;
     const int64_t cblk = nch - 1 - u;                     // forward block
     const int64_t klo = cblk * CH;
     const int64_t khi = valid ? ((klo + CH < T ? klo + CH : T) - 1) : -1;
-    float* wb = SM::warp(gsm, w);
+    float* wb = SM::chain(gsm, w);
     SSlot<N> X[3] = {SSlot<N>{wb}, SSlot<N>{wb + SM::SLOT}, SSlot<N>{wb + 2 * SM::SLOT}};
     Scratch<N> s{wb + 3 * SM::SLOT};
     bool bad = false;
@@ -295,43 +313,43 @@ __global__ void __launch_bounds__(NW * 32) gsmoother_reduce_kernel(const ModelCo
                 for (int q = 0; q < N; ++q) dst[q] = __ldg(src + q);
                 s.V(5)[r] = __ldg(fmean + k * N + r);
             }
-            wsync();
+            gsync<N>();
         };
         cur.seek(segs, &mc, khi, T);
         int a = 0;
         load_post(khi);
         selem<N, M>(r, *cur.mc, s.S(3), s.V(5), cur.last(khi), X[0], s, bad);
-        copy_floats(gb.elems + (size_t)khi * SS, X[0].p, SS);
+        copy_floats<N>(gb.elems + (size_t)khi * SS, X[0].p, SS);
 #pragma unroll 1
         for (int64_t k = khi - 1; k >= klo; --k) {
             cur.backward(segs, k);
             load_post(k);
             selem<N, M>(r, *cur.mc, s.S(3), s.V(5), cur.last(k), X[2], s, bad);
-            copy_floats(gb.elems + (size_t)k * SS, X[2].p, SS);
+            copy_floats<N>(gb.elems + (size_t)k * SS, X[2].p, SS);
             scombine<N, false>(r, X[2], X[a], X[a ^ 1], s);
             a ^= 1;
         }
-        copy_floats(gb.chains + (size_t)u * 2 * SS, X[a].p, SS);
+        copy_floats<N>(gb.chains + (size_t)u * 2 * SS, X[a].p, SS);
     }
     __threadfence_block();
     __syncthreads();
 
     // ---- in-tile combine (warp 0): E_t = T_{t-1} (x) ... (x) T_0 in time order
     if (w == 0) {
-        const float* T0 = gb.chains + (size_t)tile * NW * 2 * SS;
+        const float* T0 = gb.chains + (size_t)tile * NG * 2 * SS;
         int a = 0;
-        copy_floats(X[0].p, T0, SS);
+        copy_floats<N>(X[0].p, T0, SS);
 #pragma unroll 1
         for (int t = 1; t < nvalid; ++t) {
-            float* cht = gb.chains + ((size_t)tile * NW + t) * 2 * SS;
-            copy_floats(cht + SS, X[a].p, SS);
-            copy_floats(X[2].p, cht, SS);
+            float* cht = gb.chains + ((size_t)tile * NG + t) * 2 * SS;
+            copy_floats<N>(cht + SS, X[a].p, SS);
+            copy_floats<N>(X[2].p, cht, SS);
             scombine<N, false>(r, X[2], X[a], X[a ^ 1], s);
             a ^= 1;
         }
-        copy_floats(gb.spine0 + (size_t)tile * SS, X[a].p, SS);
+        copy_floats<N>(gb.spine0 + (size_t)tile * SS, X[a].p, SS);
     }
-    if (__any_sync(kFullMask, bad) && r == 0) atomicOr(status, ST_NUMERIC);
+    if (__any_sync(gmask<N>(), bad) && r == 0) atomicOr(status, ST_NUMERIC);
 }
 
 // Scan order (tile 0 = latest time): dst[u] = src[u] (x) src[u - s] in time
@@ -343,24 +361,24 @@ __global__ void __launch_bounds__(NWS * 32) gspine_smoother_kernel(const float* 
                                                                    uint32_t* status) {
     using SM = GSpineSmem<N, NWS>;
     constexpr int SS = Dim<N>::SSLOT;
-    constexpr int SLOT = GSmem<N, 1, 1>::SLOT;
+    constexpr int SLOT = GChain<N>::SLOT;
     extern __shared__ __align__(16) char gsm[];
-    const int w = threadIdx.x >> 5, r = threadIdx.x & 31;
-    const int u = blockIdx.x * NWS + w;
+    const int w = threadIdx.x / Grp<N>::GS, r = threadIdx.x & (Grp<N>::GS - 1);
+    const int u = blockIdx.x * SM::NG + w;
     if (u >= ntiles) return;                              // whole warps; no block barrier below
     float* o = dst + (size_t)u * SS;
     if (u < s) {
-        copy_floats_cg(o, src + (size_t)u * SS, SS);
+        copy_floats_cg<N>(o, src + (size_t)u * SS, SS);
         return;
     }
-    float* wb = SM::warp(gsm, w);
+    float* wb = SM::chain(gsm, w);
     SSlot<N> X[3] = {SSlot<N>{wb}, SSlot<N>{wb + SLOT}, SSlot<N>{wb + 2 * SLOT}};
     Scratch<N> sc{wb + 3 * SLOT};
-    copy_floats_cg(X[0].p, src + (size_t)u * SS, SS);
-    copy_floats_cg(X[1].p, src + (size_t)(u - s) * SS, SS);
+    copy_floats_cg<N>(X[0].p, src + (size_t)u * SS, SS);
+    copy_floats_cg<N>(X[1].p, src + (size_t)(u - s) * SS, SS);
     if (u - s < s) scombine<N, true>(r, X[0], X[1], X[2], sc);
     else scombine<N, false>(r, X[0], X[1], X[2], sc);
-    copy_floats(o, X[2].p, SS);
+    copy_floats<N>(o, X[2].p, SS);
     (void)status;
 }
 
@@ -371,18 +389,18 @@ __global__ void __launch_bounds__(NW * 32) gsmoother_apply_kernel(int64_t T, flo
                                                                   float* __restrict__ scov, GBuf gb,
                                                                   const float* __restrict__ pre, uint32_t* status) {
     using SM = GSmem<N, M, NW>;
-    constexpr int SS = Dim<N>::SSLOT;
+    constexpr int SS = Dim<N>::SSLOT, NG = SM::NG;
     extern __shared__ __align__(16) char gsm[];
     const int tile = blockIdx.x;
-    const int w = threadIdx.x >> 5, r = threadIdx.x & 31;
+    const int w = threadIdx.x / Grp<N>::GS, r = threadIdx.x & (Grp<N>::GS - 1);
     const int64_t nch = (T + CH - 1) / CH;
-    const int64_t u = (int64_t)tile * NW + w;
+    const int64_t u = (int64_t)tile * NG + w;
     if (u >= nch) return;                                 // whole warps; no block barrier in this kernel
     const int64_t cblk = nch - 1 - u;
     const int64_t klo = cblk * CH;
     const int64_t khi = (klo + CH < T ? klo + CH : T) - 1;
     const float* chE = gb.chains + (size_t)u * 2 * SS + SS;
-    float* wb = SM::warp(gsm, w);
+    float* wb = SM::chain(gsm, w);
     SSlot<N> X[3] = {SSlot<N>{wb}, SSlot<N>{wb + SM::SLOT}, SSlot<N>{wb + 2 * SM::SLOT}};
     Scratch<N> s{wb + 3 * SM::SLOT};
     bool bad = false;
@@ -391,23 +409,23 @@ __global__ void __launch_bounds__(NW * 32) gsmoother_apply_kernel(int64_t T, flo
     if (tile != 0) {
         const float* tex = pre + (size_t)(tile - 1) * SS;
         if (w >= 1) {
-            copy_floats_cg(X[2].p, tex, SS);
-            copy_floats_cg(X[1].p, chE, SS);
+            copy_floats_cg<N>(X[2].p, tex, SS);
+            copy_floats_cg<N>(X[1].p, chE, SS);
             scombine<N, true>(r, X[1], X[2], X[0], s);
         } else {
-            copy_floats_cg(X[0].p, tex, SS);
+            copy_floats_cg<N>(X[0].p, tex, SS);
         }
         has = true;
     } else if (w >= 1) {
-        copy_floats_cg(X[0].p, chE, SS);                 // E = 0: it ends with the sequence's last element
+        copy_floats_cg<N>(X[0].p, chE, SS);                 // E = 0: it ends with the sequence's last element
         has = true;
     }
     float probe = 0.f;
 #pragma unroll 1
     for (int64_t k = khi; k >= klo; --k) {
-        copy_floats_cg(X[2].p, gb.elems + (size_t)k * SS, SS);
+        copy_floats_cg<N>(X[2].p, gb.elems + (size_t)k * SS, SS);
         if (!has) {
-            copy_floats(X[a].p, X[2].p, SS);
+            copy_floats<N>(X[a].p, X[2].p, SS);
             has = true;
         } else {
             scombine<N, true>(r, X[2], X[a], X[a ^ 1], s);
@@ -424,7 +442,7 @@ __global__ void __launch_bounds__(NW * 32) gsmoother_apply_kernel(int64_t T, flo
         }
     }
     bad |= !isfinite(probe);
-    if (__any_sync(kFullMask, bad) && r == 0) atomicOr(status, ST_NUMERIC);
+    if (__any_sync(gmask<N>(), bad) && r == 0) atomicOr(status, ST_NUMERIC);
 }
 
 }  // namespace grp
