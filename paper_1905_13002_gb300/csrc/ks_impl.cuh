@@ -48,15 +48,25 @@ struct VTable {
                       cudaStream_t);
 };
 
+// The fused end-to-end entry points of one steps-per-thread choice.
+struct ChunkVariant {
+    Layout (*layout)(int64_t T, int B);
+    int (*smooth)(const ks_model*, const float*, int64_t, void*, size_t, float*, float*, float*, float*,
+                  cudaStream_t, void* const*);
+    int (*smooth_batch)(const ks_model_batch*, const float*, int64_t, void*, size_t, float*, float*, float*,
+                        float*, cudaStream_t);
+};
+
 inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 inline int launch_status() {
     return cudaGetLastError() == cudaSuccess ? KS_OK : KS_ECUDA;
 }
 
-template <int N, int M>
+// FCH_ = steps per thread of the block scans (one tile = 128 * FCH_ steps).
+template <int N, int M, int FCH_ = 32>
 struct Impl {
-    static constexpr int FNT = 128, FCH = 32;   // forward scan: threads, steps per thread
+    static constexpr int FNT = 128, FCH = FCH_;   // forward scan: threads, steps per thread
     static constexpr int SNT = 128, SCH = FCH;  // reverse scan (same block grid)
     static constexpr int64_t FTILE = (int64_t)FNT * FCH, STILE = (int64_t)SNT * SCH;
     static constexpr int NCOMP = 3 * N * N + 2 * N;   // scalars of one filtering element
@@ -355,6 +365,59 @@ struct Impl {
     static constexpr VTable vtable() {
         return VTable{N, M, &layout, &build_elements, &filter_scan, &smooth_scan, &smooth, &smooth_batch,
                       &fcomb_batch, &scomb_batch, &agg_bytes, &faggregate, &saggregate};
+    }
+    static constexpr ChunkVariant chunk_variant() { return ChunkVariant{&layout, &smooth, &smooth_batch}; }
+};
+
+// Steps per thread of the fused smooth / smooth_batch scans, picked from
+// {4, 8, 16, 32} by the total number of steps T.  A block scan covers
+// 128 * chunk steps, so short inputs need short chunks to launch enough
+// blocks for the 152 SMs; long inputs keep 32 steps per thread, which cuts
+// the per-block look-back, aggregate and per-thread-prefix work per step.
+// The crossovers are where the measured times of neighbouring chunk lengths
+// cross for nx = 2, 4 and 6 on GB300 (single sequences and segmented
+// batches alike).
+inline int chunk_index(int64_t T) {
+    return T < 96 * 1024 ? 0 : T < 192 * 1024 ? 1 : T < 640 * 1024 ? 2 : 3;
+}
+
+// Per-(nx, ny) table of the four chunk variants; each instantiation file
+// defines it (the 4-, 8- and 16-step variants compile in their own units).
+template <int N, int M>
+struct ChunkTable {
+    static const ChunkVariant* const v[4];
+};
+
+// The registered function table: every entry of the 32-step Impl, except that
+// smooth and smooth_batch go to the chunk variant chosen by T, and the
+// workspace sizes cover every variant (offsets stay the 32-step layout's,
+// which the element-building and scan-only entry points use).
+template <int N, int M>
+struct Tuned {
+    using Base = Impl<N, M, 32>;
+    static Layout layout(int64_t T, int B) {
+        Layout L = Base::layout(T, B);
+        for (int i = 0; i < 4; ++i) {
+            const Layout Li = ChunkTable<N, M>::v[i]->layout(T, B);
+            L.bytes_smooth = std::max(L.bytes_smooth, Li.bytes_smooth);
+            L.bytes_elements = std::max(L.bytes_elements, Li.bytes_elements);
+        }
+        return L;
+    }
+    static int smooth(const ks_model* m, const float* y, int64_t T, void* ws, size_t ws_bytes, float* fm,
+                      float* fc, float* sm, float* sc, cudaStream_t st, void* const* ev) {
+        return ChunkTable<N, M>::v[chunk_index(T)]->smooth(m, y, T, ws, ws_bytes, fm, fc, sm, sc, st, ev);
+    }
+    static int smooth_batch(const ks_model_batch* mb, const float* y, int64_t T, void* ws, size_t ws_bytes,
+                            float* fm, float* fc, float* sm, float* sc, cudaStream_t st) {
+        return ChunkTable<N, M>::v[chunk_index(T)]->smooth_batch(mb, y, T, ws, ws_bytes, fm, fc, sm, sc, st);
+    }
+    static constexpr VTable vtable() {
+        VTable t = Base::vtable();
+        t.layout = &layout;
+        t.smooth = &smooth;
+        t.smooth_batch = &smooth_batch;
+        return t;
     }
 };
 

@@ -17,6 +17,8 @@
 #include "ks_impl.cuh"
 
 namespace ks {
+extern const VTable kImpl32_4_2;
+
 namespace {
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[KS_NOALLOC_SCRATCH_BYTES];
@@ -49,8 +51,7 @@ extern "C" int ks_smooth_noalloc(const ks_model* m, const float* y, int64_t T, f
     if (m->nx != 4 || m->ny != 2) return KS_EUNSUPPORTED;
     if (T < 1 || T > KS_NOALLOC_MAX_T) return KS_EINVAL;
     if (!fmean || !fcov || !smean || !scov) return KS_EINVAL;
-    const VTable* v = find_impl(4, 2);
-    if (!v) return KS_EUNSUPPORTED;
+    const VTable* v = &kImpl32_4_2;   // 32 steps per thread: the smallest scratch layout
     if (v->layout(T, 1).bytes_smooth > (size_t)KS_NOALLOC_SCRATCH_BYTES) return KS_EINVAL;
     void* ws = nullptr;
     int rc = scratch_on_current_device(&ws);

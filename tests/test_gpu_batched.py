@@ -65,6 +65,20 @@ def test_log_uniform_lengths(ks, dim):
     run_and_check(ks, make_batch(dim, lengths, 30 + dim))
 
 
+
+# Batches are dispatched by their total length like single sequences (4, 8,
+# 16 or 32 steps per thread below 96 Ki, 192 Ki, 640 Ki steps, and above):
+# one batch per band, the edge lengths mixed in.
+@pytest.mark.parametrize("dim,B,band", [(2, 30, (98304, 196608)), (2, 90, (196608, 655360)),
+                                        (2, 200, (655360, 1 << 30)), (3, 90, (196608, 655360)),
+                                        (1, 200, (655360, 1 << 30))])
+def test_chunk_variant_batches(ks, dim, B, band):
+    rng = np.random.default_rng(50 + B + dim)
+    lengths = np.concatenate([EDGE, workloads.batch_lengths(B, rng, 256, 16384)])
+    rng.shuffle(lengths)
+    assert band[0] <= lengths.sum() < band[1], lengths.sum()
+    run_and_check(ks, make_batch(dim, lengths, 60 + B + dim))
+
 def test_single_sequence_batch_equals_plain_call(ks):
     seqs = make_batch(2, [20000], 7)
     run_and_check(ks, seqs)

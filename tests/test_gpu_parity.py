@@ -53,6 +53,19 @@ def test_tracking_model_sizes(ks, T):
     check(ks, seq.model, seq.y)
 
 
+
+# The fused smooth picks 4, 8, 16 or 32 steps per thread by T (switching at
+# 96 Ki, 192 Ki and 640 Ki steps): both sides of every switch, each with a
+# ragged last tile, for nx = 4, and one size inside each band for nx = 2, 6.
+@pytest.mark.parametrize("dim,T", [(2, 98303), (2, 98304), (2, 196607), (2, 196608), (2, 655359),
+                                   (2, 655360), (1, 150001), (1, 400003), (3, 150001), (3, 400003),
+                                   (3, 700001)])
+def test_chunk_variants(ks, dim, T):
+    rng = np.random.default_rng(4000 + T + dim)
+    m = workloads.wiener_velocity(dim, dt=0.1, q=1.0, r=0.5)
+    _, y = workloads.simulate(m, T, rng)
+    check(ks, m, y)
+
 def test_single_sequence_T1024(ks):
     seq = workloads.config_single()
     e = check(ks, seq.model, seq.y)
