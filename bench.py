@@ -51,10 +51,12 @@ def parse():
     ap.add_argument("--T", type=int, default=1 << 20)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="long", choices=["long", "batched", "precision", "serving"],
+    ap.add_argument("--workload", default="long", choices=["long", "batched", "precision", "serving", "tv", "hmm"],
                     help="long: one T=2^20 nx=4 sequence per GPU (default); batched: 4096 sequences, "
                          "lengths log-uniform in [256, 16384], nx in {2,4,6}; precision: nx=32 T=65536; "
-                         "serving: Poisson request streams, nx in {4,8}, T log-uniform in [64, 2^18]")
+                         "serving: Poisson request streams, nx in {4,8}, T log-uniform in [64, 2^18]; "
+                         "tv: one T=2^20 nx=4 sequence with a time-varying model (irregular sampling); "
+                         "hmm: one T=2^20 discrete-state sequence, K=8 regimes")
     ap.add_argument("--batch", type=int, default=4096)
     ap.add_argument("--rates", default="100,300,1000,3000,10000", help="serving: request rates (req/s)")
     ap.add_argument("--duration", type=float, default=10.0, help="serving: seconds of arrivals per rate")
@@ -104,6 +106,22 @@ def flops_per_step(N: int, M: int, fused_smoothing: bool = True) -> dict:
         return {"filter": fold + adv + 2 * meas + sel + scomb, "smoother": sel + sadv}
     # warp-per-chain kernels (nx >= 8): the reverse scan folds its own blocks
     return {"filter": fold + adv + 2 * meas, "smoother": 2 * sel + scomb + sadv}
+
+
+def tv_bytes_per_step(nx: int, ny: int) -> dict:
+    """Algorithmic DRAM bytes per step of the time-varying path (FP32, u = d =
+    0 so not read).  Element kernel: reads y_k, F_k, Q_k, H_k, R_k and writes
+    the Lemma 3 element in measurement form (A, C lower, U, b, w).  Forward
+    scan: reads that element and the next step's F, Q (for the fused Lemma 5
+    element), writes the filtered mean + covariance.  Reverse scan: reads
+    those moments and the next step's F, Q, writes the smoothed moments."""
+    s = nx * (nx + 1) // 2
+    model = 4 * (2 * nx * nx + ny * nx + ny * ny)
+    elem = 4 * (nx * nx + s + ny * nx + nx + ny)
+    post = 4 * (nx + nx * nx)
+    trans = 4 * 2 * nx * nx
+    return {"elements": 4 * ny + model + elem, "filter": elem + trans + post,
+            "smoother": post + trans + post}
 
 
 def tensor_flops_per_step(N: int, M: int) -> dict:
@@ -206,6 +224,11 @@ KERNEL_SOURCES = {
                                    "ks_inst_32_8.cu"],
     "tsmoother_reduce+spine+apply": ["ks_ops.cuh", "ks_scan.cuh", "ks_tc.cuh", "ks_tscan.cuh", "ks_timpl.cuh",
                                      "ks_inst_32_8.cu"],
+    "tv:elements": ["ks_ops.cuh", "ks_scan.cuh", "ks_impl.cuh"],
+    "hmm:filter": ["ks_scan.cuh", "ks_hmm.cuh", "ks_hmm.cu"],
+    "hmm:smoother": ["ks_scan.cuh", "ks_hmm.cuh", "ks_hmm.cu"],
+    "tv:filter": ["ks_ops.cuh", "ks_async.cuh", "ks_scan.cuh", "ks_impl.cuh", "ks_inst_4_2.cu"],
+    "tv:smoother": ["ks_ops.cuh", "ks_async.cuh", "ks_scan.cuh", "ks_impl.cuh", "ks_inst_4_2.cu"],
 }
 
 
@@ -278,10 +301,13 @@ def main():
     if args.workload == "serving":
         run_serving(args, rank, world, local)
         return
-    run_single(args, rank, world, local, precision=args.workload == "precision")
+    if args.workload == "hmm":
+        run_hmm(args, rank, world, local)
+        return
+    run_single(args, rank, world, local, mode=args.workload)
 
 
-def run_single(args, rank, world, local, precision):
+def run_single(args, rank, world, local, mode):
     import torch
     import torch.distributed as dist
 
@@ -295,6 +321,7 @@ def run_single(args, rank, world, local, precision):
         _build.build()
     if world > 1:
         dist.barrier()
+    precision, tv = mode == "precision", mode == "tv"
     if precision:
         T = 65536 if args.T == (1 << 20) else args.T
         seq = workloads.config_precision(T=T)
@@ -303,6 +330,11 @@ def run_single(args, rank, world, local, precision):
             _, y = workloads.simulate(seq.model, T, rng)
             seq = workloads.Sequence(seq.model, y)
         wl = "random_stable nx=32 ny=8 F=O diag(U[0.9,0.99]) Q=0.1I H~N(0,1/32) R=0.5I"
+    elif tv:
+        T = args.T
+        seq = workloads.irregular_tracking(T, seed=workloads.SEED_BASE + 6 + rank)
+        wl = ("irregular_tracking_2d nx=4 ny=2 time-varying: dt_k~logU[0.02,0.5] (F_k, Q_k), "
+              "R_k=r_k I r_k~logU[0.25,4], q=1 u=d=0 m0=0 P0=I")
     else:
         T = args.T
         seq = workloads.tracking_sequence(T, seed=workloads.SEED_BASE + 2 + rank)
@@ -310,7 +342,10 @@ def run_single(args, rank, world, local, precision):
     dev = torch.device("cuda", local)
     m = seq.model
     nx, ny = m.nx, m.ny
-    model = ks.Model.create(m.F, m.Q, m.H, m.R, m.m0, m.P0, u=m.u, d=m.d, device=dev)
+    if tv:   # u = d = 0: passed as absent
+        model = ks.Model.create(m.F, m.Q, m.H, m.R, m.m0, m.P0, device=dev)
+    else:
+        model = ks.Model.create(m.F, m.Q, m.H, m.R, m.m0, m.P0, u=m.u, d=m.d, device=dev)
     y = torch.as_tensor(seq.y, dtype=torch.float32, device=dev)
     ws = ks.alloc_workspace(model, T, ks.KS_WS_ELEMENTS)
     fm = torch.empty(T, nx, device=dev)
@@ -351,6 +386,7 @@ def run_single(args, rank, world, local, precision):
 
     tot = [e[0].elapsed_time(e[3]) for e in evs]
     lat = {"p50_ms": float(np.percentile(tot, 50)), "p99_ms": float(np.percentile(tot, 99))}
+    kel = [e[0].elapsed_time(e[1]) for e in evs]
     kf = [e[1].elapsed_time(e[2]) for e in evs]
     ksm = [e[2].elapsed_time(e[3]) for e in evs]
     ms = statistics.mean(tot)
@@ -365,12 +401,17 @@ def run_single(args, rank, world, local, precision):
     sm_h = torch.empty(T, nx, dtype=torch.float32).pin_memory()
     sP_h = torch.empty(T, nx, nx, dtype=torch.float32).pin_memory()
     y_d = torch.empty_like(y)
+    # a time-varying model is part of each call's input: its per-step arrays
+    # are copied in with y
+    model_h = {k: getattr(model, k).cpu().pin_memory() for k in ("F", "Q", "H", "R")} if tv else {}
     e2e_times = []
     for i in range(args.warmup + args.steps):
         flush.zero_()
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record()
+        for k, h in model_h.items():
+            getattr(model, k).copy_(h, non_blocking=True)
         y_d.copy_(y_h, non_blocking=True)
         ks.smooth(model, y_d, ws, smean=sm, scov=sP, keep_filtered=False)
         sm_h.copy_(sm, non_blocking=True)
@@ -383,14 +424,57 @@ def run_single(args, rank, world, local, precision):
     if ks.status(ws) != ks.KS_OK:
         raise SystemExit("device status not OK after the end-to-end steps")
     e2e = {"value": T * world / (e2e_ms / 1e3), "unit": UNIT,
-           "h2d_bytes_per_step": int(y_h.numel() * 4),
+           "h2d_bytes_per_step": int(y_h.numel() * 4 + sum(h.numel() * 4 for h in model_h.values())),
            "d2h_bytes_per_step": int((sm_h.numel() + sP_h.numel()) * 4)}
 
     # ---- roofline of the dominant kernel
     hbm, which = peaks()
+    if tv:
+        roof = tv_roofline(nx, ny, T, hbm, which, {"elements": statistics.mean(kel), "filter": statistics.mean(kf),
+                                                   "smoother": statistics.mean(ksm)})
     bps = bytes_per_step(nx, ny)
     fps = flops_per_step(nx, ny, fused_smoothing=nx <= 6)
     kernels = {"filter": statistics.mean(kf), "smoother": statistics.mean(ksm)}
+    if not tv:
+        roof = scan_roofline(nx, ny, T, hbm, which, kernels, bps, fps)
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": wl, "T": T,
+                      "sequences_per_gpu": 1, "parallelism": f"replicas{world}",
+                      "l2": "flushed between timed steps (256 MiB memset outside the events)"},
+           "clocks": {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+           "gpu_launches": 3 * args.steps, "latency": lat, "e2e": e2e, "roofline": roof}
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_oracle_rate(seq, args.cpu_seconds)
+    print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def tv_roofline(nx, ny, T, hbm, which, kernels):
+    """Time-varying path: every kernel is HBM-side (the element kernel
+    streams the per-step model; the scans stream elements and posteriors)."""
+    bps = tv_bytes_per_step(nx, ny)
+    dom = max(kernels, key=kernels.get)
+    gbs = bps[dom] * T / (kernels[dom] / 1e3) / 1e9
+    names = {"elements": "tv_elements_kernel", "filter": "filter_scan_kernel (materialised elements)",
+             "smoother": "smoother_scan_kernel (time-varying)"}
+    return {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+            "traffic": recorded_traffic("tv:" + dom), "kernel": names[dom], "peak_source": which,
+            "ms_per_launch": kernels[dom], "bytes_per_step": bps,
+            "kernels_ms": {k: round(v, 4) for k, v in kernels.items()},
+            "gbs_by_kernel": {k: round(bps[k] * T / (v / 1e3) / 1e9, 1) for k, v in kernels.items()}}
+
+
+def scan_roofline(nx, ny, T, hbm, which, kernels, bps, fps):
+    """Time-invariant scans: the dominant kernel against the ALU, HBM or
+    tensor roof, whichever its work model reaches first."""
     dom = max(kernels, key=kernels.get)
     dur_s = kernels[dom] / 1e3
     gbs = bps[dom] * T / dur_s / 1e9
@@ -398,7 +482,7 @@ def run_single(args, rank, world, local, precision):
     tfl = fps[dom] * T / dur_s / 1e12
     kname = ({"filter": "filter_scan_kernel", "smoother": "smoother_scan_kernel"} if nx <= 6 else
              {"filter": "tfilter_reduce+spine+apply", "smoother": "tsmoother_reduce+spine+apply"} if nx >= 32 else
-             {"filter": "gfilter_kernel", "smoother": "gsmoother_kernel"})[dom]
+             {"filter": "gfilter_reduce+spine+apply", "smoother": "gsmoother_reduce+spine+apply"})[dom]
     traffic = recorded_traffic(kname)
     if nx >= 32:
         tpeak, tsrc = tf32_peak()
@@ -422,6 +506,132 @@ def run_single(args, rank, world, local, precision):
                      "bytes_per_step": bps[dom], "flops_per_step": fps[dom],
                      "kernels_ms": {k: round(v, 4) for k, v in kernels.items()}})
 
+    return roof
+
+
+# ---------------------------------------------------------------- discrete-state workload
+def hmm_work_per_step(K: int) -> tuple[dict, dict]:
+    """(flops, algorithmic DRAM bytes) per step of the two HMM scans (FP32,
+    FMA = 2).  Forward: the fold of the step element ((f Pi) then the
+    likelihood scaling and row normalisation), its application to the running
+    marginal, the step's Definition 2 element from that marginal and its fold
+    into the thread's smoothing aggregate; reads lik, writes filt and loglik.
+    Reverse: the Definition 2 element and its application; reads filt, writes
+    smooth.  Tile-level combines are not counted."""
+    fold = 2 * K ** 3 + 3 * K * K + 2 * K
+    adv = 2 * K * K + 3 * K
+    sel = 2 * K * K + K
+    smul = 2 * K ** 3
+    flops = {"filter": fold + adv + sel + smul, "smoother": sel + 2 * K * K}
+    nbytes = {"filter": 4 * K + 4 * K + 4, "smoother": 4 * K + 4 * K}
+    return flops, nbytes
+
+
+def run_hmm(args, rank, world, local):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1905_13002_gb300 as ks
+    from paper_1905_13002_gb300 import _build
+
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if local == 0:
+        _build.build()
+    if world > 1:
+        dist.barrier()
+    K = 8
+    T = args.T
+    seq = workloads.hmm_sequence(K, T, seed=workloads.SEED_BASE + 7 + rank)
+    dev = torch.device("cuda", local)
+    model = ks.HmmModel.create(seq.pi, seq.Pi, device=dev)
+    lik = torch.as_tensor(seq.lik, dtype=torch.float32, device=dev)
+    ws = torch.empty(ks.hmm_workspace_bytes(K, T), dtype=torch.uint8, device=dev)
+    ks.lib().ks_workspace_init(ks._p(ws), ws.numel(), ks._stream(None))
+    filt = torch.empty(T, K, device=dev)
+    smooth = torch.empty(T, K, device=dev)
+    ll = torch.empty(T, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step(events=None):
+        ks.hmm_smooth(model, lik, ws, filt=filt, smooth=smooth, loglik=ll, events=events)
+
+    for _ in range(max(args.warmup, 3)):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    if ks.status(ws) != ks.KS_OK:
+        raise SystemExit("device status not OK after warm-up")
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    for i in range(args.steps):
+        flush.zero_()
+        step(evs[i])
+    torch.cuda.synchronize()
+    time.sleep(0.3)
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    if ks.status(ws) != ks.KS_OK:
+        raise SystemExit("device status not OK after the timed steps")
+    tot = [e[0].elapsed_time(e[3]) for e in evs]
+    kf = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
+    ksm = statistics.mean(e[2].elapsed_time(e[3]) for e in evs)
+    ms = statistics.mean(tot)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = T * world / (ms / 1e3)
+
+    # end to end: likelihoods in from pinned host memory, marginals and
+    # log-likelihoods back
+    lik_h = torch.as_tensor(seq.lik, dtype=torch.float32).pin_memory()
+    filt_h = torch.empty(T, K).pin_memory()
+    smooth_h = torch.empty(T, K).pin_memory()
+    ll_h = torch.empty(T).pin_memory()
+    lik_d = torch.empty_like(lik)
+    e2e_times = []
+    for i in range(args.warmup + args.steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        lik_d.copy_(lik_h, non_blocking=True)
+        ks.hmm_smooth(model, lik_d, ws, filt=filt, smooth=smooth, loglik=ll)
+        filt_h.copy_(filt, non_blocking=True)
+        smooth_h.copy_(smooth, non_blocking=True)
+        ll_h.copy_(ll, non_blocking=True)
+        b.record()
+        b.synchronize()
+        if i >= args.warmup:
+            e2e_times.append(a.elapsed_time(b))
+    e2e = {"value": T * world / (statistics.mean(e2e_times) / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": int(lik_h.numel() * 4),
+           "d2h_bytes_per_step": int((filt_h.numel() + smooth_h.numel() + ll_h.numel()) * 4)}
+
+    flops, nbytes = hmm_work_per_step(K)
+    kernels = {"filter": kf, "smoother": ksm}
+    dom = max(kernels, key=kernels.get)
+    dur_s = kernels[dom] / 1e3
+    alu_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    tfl = flops[dom] * T / dur_s / 1e12
+    hbm, which = peaks()
+    gbs = nbytes[dom] * T / dur_s / 1e9
+    roof = ({"bound": "alu", "achieved": tfl, "peak": alu_peak, "unit": "TFLOP/s", "frac": tfl / alu_peak}
+            if tfl / alu_peak >= gbs / hbm else
+            {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm})
+    roof.update({"traffic": recorded_traffic("hmm:" + dom), "kernel": f"hmm_{dom}_kernel<8>",
+                 "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz" if roof["bound"] == "alu" else which,
+                 "ms_per_launch": kernels[dom], "alu_frac": tfl / alu_peak, "hbm_frac": gbs / hbm,
+                 "flops_per_step": flops[dom], "bytes_per_step": nbytes[dom],
+                 "kernels_ms": {k: round(v, 4) for k, v in kernels.items()}})
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -429,13 +639,26 @@ def run_single(args, rank, world, local, precision):
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": wl, "T": T,
-                      "sequences_per_gpu": 1, "parallelism": f"replicas{world}",
+           "config": {"workload": "regime-switching HMM K=8, stay 0.95, y~N(x, 0.6^2), Gaussian likelihood rows",
+                      "T": T, "sequences_per_gpu": 1, "parallelism": f"replicas{world}",
                       "l2": "flushed between timed steps (256 MiB memset outside the events)"},
            "clocks": {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
-           "gpu_launches": 3 * args.steps, "latency": lat, "e2e": e2e, "roofline": roof}
+           "gpu_launches": 3 * args.steps, "latency": {"p50_ms": float(np.percentile(tot, 50)),
+                                                       "p99_ms": float(np.percentile(tot, 99))},
+           "e2e": e2e, "roofline": roof}
     if world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_oracle_rate(seq, args.cpu_seconds)
+        from oracle import hmm as ohmm
+        Ts = min(T, 1 << 16)
+        t0 = time.perf_counter()
+        reps = 0
+        while True:
+            ohmm.forward_backward(seq.pi, seq.Pi, seq.lik[:Ts])
+            reps += 1
+            el = time.perf_counter() - t0
+            if el >= args.cpu_seconds:
+                break
+        out["cpu_baseline"] = {"value": reps * Ts / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": f"{reps} passes over the first {Ts} steps ({el:.1f} s, 1 thread, numpy)"}
     print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()

@@ -66,12 +66,26 @@ extern "C" {
 #define KS_WS_ELEMENTS 1      /* additionally the materialised element arrays of ks_build_elements */
 
 /*
- * Time-invariant linear/Gaussian model of Section IV.  F [nx][nx],
- * u [nx], Q [nx][nx], H [ny][nx], d [ny], R [ny][ny] are DEVICE pointers to
- * FP32 row-major arrays; u and d may be NULL (zero).  m0 [nx] and P0
- * [nx][nx] are DEVICE pointers to FP64 arrays.  Q, R and P0 must be
- * symmetric positive definite (R, P0) / semidefinite with F P F^T + Q
- * definite (Q).  time_varying must be 0.
+ * Linear/Gaussian model of Sections II and IV.
+ *
+ * time_varying = 0 (time-invariant): F [nx][nx], u [nx], Q [nx][nx],
+ * H [ny][nx], d [ny], R [ny][ny] are DEVICE pointers to FP32 row-major
+ * arrays; u and d may be NULL (zero).
+ *
+ * time_varying = 1: every one of them holds one entry per step, step-major:
+ * F [T][nx][nx], u [T][nx], Q [T][nx][nx], H [T][ny][nx], d [T][ny],
+ * R [T][ny][ny] (u, d may be NULL).  With 0-based steps, step k is predicted
+ * from step k-1 with F[k], u[k], Q[k] (F[0], u[0], Q[0] take the prior
+ * N(m0, P0) to step 0) and observed as y[k] = H[k] x_k + d[k] + r_k with
+ * r_k ~ N(0, R[k]): Section II's model with its indices shifted by one.
+ * Time-varying models are accepted by ks_smooth and ks_smooth_traced for
+ * nx in {2, 4, 6} (KS_EUNSUPPORTED elsewhere), and need
+ * ks_workspace_bytes(m, T, KS_WS_SMOOTH) bytes, which for them equals the
+ * KS_WS_ELEMENTS size.
+ *
+ * m0 [nx] and P0 [nx][nx] are DEVICE pointers to FP64 arrays.  Q, R and P0
+ * must be symmetric positive definite (R, P0) / semidefinite with
+ * F P F^T + Q definite (Q).
  */
 typedef struct ks_model {
     int32_t nx;
@@ -123,8 +137,10 @@ const char *ks_strerror(int code);
 
 /*
  * Bytes of workspace needed for sequences of up to T steps of model `m`
- * (only m->nx, m->ny are read; host pointer).  purpose = KS_WS_SMOOTH or
- * KS_WS_ELEMENTS.  Returns 0 for invalid arguments.
+ * (only m->nx, m->ny and m->time_varying are read; host pointer).
+ * purpose = KS_WS_SMOOTH or KS_WS_ELEMENTS.  Returns 0 for invalid
+ * arguments, and for a time-varying model of an (nx, ny) whose smoother
+ * does not take one.
  */
 size_t ks_workspace_bytes(const ks_model *m, int64_t T, int purpose);
 
@@ -222,8 +238,9 @@ int ks_status(void *ws, void *stream);
  * application that owns the device memory budget and does not let plug-ins
  * allocate.  The paper has no counterpart; this is an interface convenience.
  *
- * Same computation and arguments as ks_smooth for nx = 4, ny = 2 (other
- * sizes: KS_EUNSUPPORTED), with T <= KS_NOALLOC_MAX_T (larger T, or NULL
+ * Same computation and arguments as ks_smooth for time-invariant models with
+ * nx = 4, ny = 2 (other sizes, or time-varying models: KS_EUNSUPPORTED), with
+ * T <= KS_NOALLOC_MAX_T (larger T, or NULL
  * fmean / fcov: KS_EINVAL).  The caller still provides every input and
  * output; the scratch lives in a static device array of
  * KS_NOALLOC_SCRATCH_BYTES that every GPU loading this library holds until
@@ -312,6 +329,45 @@ int ks_filter_combine_batch(int nx, int64_t count, const float *left, const floa
                             float *out, void *ws, size_t ws_bytes, void *stream);
 int ks_smoother_combine_batch(int nx, int64_t count, const float *left, const float *right,
                               float *out, void *ws, size_t ws_bytes, void *stream);
+
+/*
+ * Discrete-state (hidden Markov model) filter and smoother: Section III's
+ * general elements and operators (Definitions 1 and 2, Theorems 1 and 2)
+ * with every integral a sum over the K states, the counting-measure case the
+ * paper's Section VI points to.
+ *
+ * Model: x_0 ~ pi [K], p(x_k = j | x_k-1 = i) = Pi[i][j] ([K][K], rows sum
+ * to one), and the measurements only through their likelihoods
+ * lik [T][K], lik[k][j] = p(y_k | x_k = j) >= 0 (any emission model; a row
+ * needs a positive entry).  pi and Pi: device FP32 (ks_hmm holds device
+ * pointers; the struct itself is a host object).  Supported K:
+ * ks_hmm_supported(K) (2, 4 and 8); others return KS_EUNSUPPORTED.
+ *
+ * ks_hmm_smooth writes, device FP32:
+ *   filt   [T][K]  p(x_k | y_1:k)      (required; the smoother reads it back);
+ *   smooth [T][K]  p(x_k | y_1:T)      (NULL: filter only);
+ *   loglik [T]     log p(y_1:k)        (NULL: not written).
+ * The marginal likelihoods come from the filtering scan itself (Theorem 1's
+ * g), carried as logarithms.  ws: ks_hmm_workspace_bytes(K, T) bytes,
+ * 256-byte aligned, initialised once with ks_workspace_init; its status word
+ * is read with ks_status (bit 0: a likelihood row with no positive finite
+ * entry, an impossible observation sequence or a non-finite result; bit 1: a
+ * look-back wait ran out).  Stream-ordered, no host synchronisation.
+ */
+typedef struct ks_hmm {
+    int32_t K;
+    int32_t reserved;
+    const float *pi, *Pi;
+} ks_hmm;
+
+int ks_hmm_supported(int K);
+size_t ks_hmm_workspace_bytes(int K, int64_t T);
+int ks_hmm_smooth(const ks_hmm *h, const float *lik, int64_t T, void *ws, size_t ws_bytes, float *filt,
+                  float *smooth, float *loglik, void *stream);
+/* The same, recording events[0..3] (cudaEvent_t, entries may be NULL) around
+ * the preparation, filter and smoother launches. */
+int ks_hmm_smooth_traced(const ks_hmm *h, const float *lik, int64_t T, void *ws, size_t ws_bytes, float *filt,
+                         float *smooth, float *loglik, void *stream, void *const *events);
 
 #ifdef __cplusplus
 }

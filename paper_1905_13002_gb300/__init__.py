@@ -24,6 +24,7 @@ __all__ = [
     "KsError", "Model", "ModelBatch", "smooth_batch", "workspace_bytes_batch", "lib", "workspace_bytes", "alloc_workspace", "smooth", "build_elements",
     "elements", "filter_scan", "smooth_scan", "status", "filter_combine_batch",
     "smoother_combine_batch", "supported", "KS_WS_SMOOTH", "KS_WS_ELEMENTS",
+    "HmmModel", "hmm_supported", "hmm_workspace_bytes", "hmm_smooth",
 ]
 
 KS_OK, KS_EINVAL, KS_ECUDA, KS_ENUMERIC, KS_ETIMEOUT, KS_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
@@ -53,6 +54,11 @@ class _KsModelBatch(ctypes.Structure):
                 ("F", ctypes.c_void_p), ("u", ctypes.c_void_p), ("Q", ctypes.c_void_p),
                 ("H", ctypes.c_void_p), ("d", ctypes.c_void_p), ("R", ctypes.c_void_p),
                 ("m0", ctypes.c_void_p), ("P0", ctypes.c_void_p), ("offsets", ctypes.c_void_p)]
+
+
+class _KsHmm(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int32), ("reserved", ctypes.c_int32), ("pi", ctypes.c_void_p),
+                ("Pi", ctypes.c_void_p)]
 
 
 class _KsLayout(ctypes.Structure):
@@ -94,6 +100,11 @@ def lib():
             "ks_loglik": ([M, vp, i64, vp, vp, vp, vp, vp, vp], i32),
             "ks_filter_aggregate": ([M, vp, i64, i32, vp, sz, vp, vp], i32),
             "ks_smoother_aggregate": ([M, i64, vp, vp, i32, vp, sz, vp, vp], i32),
+            "ks_hmm_supported": ([i32], i32),
+            "ks_hmm_workspace_bytes": ([i32, i64], sz),
+            "ks_hmm_smooth": ([ctypes.POINTER(_KsHmm), vp, i64, vp, sz, vp, vp, vp, vp], i32),
+            "ks_hmm_smooth_traced": ([ctypes.POINTER(_KsHmm), vp, i64, vp, sz, vp, vp, vp, vp,
+                                      ctypes.POINTER(vp)], i32),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -124,10 +135,13 @@ def _dev(x, dtype, device):
 
 @dataclass
 class Model:
-    """Device-resident time-invariant linear/Gaussian model (Section IV).
+    """Device-resident linear/Gaussian model (Sections II and IV).
 
-    F [nx,nx], u [nx], Q [nx,nx], H [ny,nx], d [ny], R [ny,ny] are FP32;
-    m0 [nx], P0 [nx,nx] are FP64 (the k = 1 element is built in FP64).
+    Time-invariant: F [nx,nx], u [nx], Q [nx,nx], H [ny,nx], d [ny], R [ny,ny]
+    FP32.  Time-varying: the same with a leading step axis, F [T,nx,nx] ...
+    (F[k], u[k], Q[k] predict step k from step k-1, F[0] from the prior;
+    H[k], d[k], R[k] observe step k).  m0 [nx], P0 [nx,nx] are FP64 (the
+    k = 1 element is built in double-float arithmetic).
     """
 
     F: torch.Tensor
@@ -148,15 +162,34 @@ class Model:
                    d=None if d is None else _dev(d, f32, device))
 
     @property
+    def time_varying(self) -> bool:
+        return self.F.dim() == 3
+
+    @property
     def nx(self) -> int:
-        return int(self.F.shape[0])
+        return int(self.F.shape[-1])
 
     @property
     def ny(self) -> int:
-        return int(self.H.shape[0])
+        return int(self.H.shape[-2])
+
+    def check_steps(self, T: int) -> None:
+        """A time-varying model must carry (at least) T contiguous per-step
+        entries of every parameter: the device reads entry k for step k."""
+        if not self.time_varying:
+            return
+        nx, ny = self.nx, self.ny
+        want = {"F": (nx, nx), "Q": (nx, nx), "H": (ny, nx), "R": (ny, ny), "u": (nx,), "d": (ny,)}
+        for name, tail in want.items():
+            t = getattr(self, name)
+            if t is None:
+                continue
+            if t.dim() != len(tail) + 1 or tuple(t.shape[1:]) != tail or t.shape[0] < T or not t.is_contiguous():
+                raise ValueError(f"time-varying {name} must be a contiguous [T >= {T}, {tail}] tensor, "
+                                 f"got {tuple(t.shape)}")
 
     def struct(self) -> _KsModel:
-        return _KsModel(self.nx, self.ny, 0, 0, self.F.data_ptr(),
+        return _KsModel(self.nx, self.ny, int(self.time_varying), 0, self.F.data_ptr(),
                         0 if self.u is None else self.u.data_ptr(), self.Q.data_ptr(),
                         self.H.data_ptr(), 0 if self.d is None else self.d.data_ptr(),
                         self.R.data_ptr(), self.m0.data_ptr(), self.P0.data_ptr())
@@ -201,6 +234,7 @@ def smooth(model: Model, y: torch.Tensor, ws: torch.Tensor | None = None, *, fme
     torch.cuda.Event objects to time the kernels (``ks_smooth_traced``).
     """
     T = int(y.shape[0])
+    model.check_steps(T)
     if filter_only and not keep_filtered:
         raise ValueError("filter_only needs keep_filtered")
     purpose = KS_WS_SMOOTH if keep_filtered else KS_WS_ELEMENTS
@@ -436,3 +470,67 @@ def smooth_batch(batch: ModelBatch, y: torch.Tensor, ws: torch.Tensor | None = N
     _check(lib().ks_smooth_batch(ctypes.byref(mb), _p(y), T, _p(ws), ws.numel(), _p(fmean), _p(fcov),
                                  _p(smean), _p(scov), _stream(stream)), "ks_smooth_batch")
     return fmean, fcov, smean, scov
+
+
+# ---------------------------------------------------------------- discrete-state models
+@dataclass
+class HmmModel:
+    """Device-resident hidden Markov model (``ks_hmm``): prior pi [K] of x_0
+    and row-stochastic transitions Pi [K, K], FP32."""
+
+    pi: torch.Tensor
+    Pi: torch.Tensor
+
+    @classmethod
+    def create(cls, pi, Pi, device="cuda") -> "HmmModel":
+        return cls(pi=_dev(pi, torch.float32, device), Pi=_dev(Pi, torch.float32, device))
+
+    @property
+    def K(self) -> int:
+        return int(self.pi.shape[0])
+
+    def struct(self) -> _KsHmm:
+        return _KsHmm(self.K, 0, self.pi.data_ptr(), self.Pi.data_ptr())
+
+
+def hmm_supported(K: int) -> bool:
+    return bool(lib().ks_hmm_supported(K))
+
+
+def hmm_workspace_bytes(K: int, T: int) -> int:
+    n = lib().ks_hmm_workspace_bytes(K, T)
+    if n == 0:
+        raise KsError(KS_EUNSUPPORTED if not hmm_supported(K) else KS_EINVAL, "ks_hmm_workspace_bytes")
+    return int(n)
+
+
+def hmm_smooth(model: HmmModel, lik: torch.Tensor, ws: torch.Tensor | None = None, *, filt=None, smooth=None,
+               loglik=None, filter_only: bool = False, want_loglik: bool = True, stream=None, events=None):
+    """Discrete-state filter and smoother (``ks_hmm_smooth``) over the
+    likelihoods ``lik`` [T, K]: returns (filt [T, K], smooth [T, K] or None,
+    loglik [T] or None)."""
+    T, K = int(lik.shape[0]), int(lik.shape[1])
+    if K != model.K or not lik.is_contiguous():
+        raise ValueError("lik must be a contiguous [T, K] tensor with the model's K")
+    if ws is None:
+        nbytes = hmm_workspace_bytes(K, T)
+        ws = torch.empty(nbytes, dtype=torch.uint8, device=lik.device)
+        _check(lib().ks_workspace_init(_p(ws), nbytes, _stream(stream)), "ks_workspace_init")
+    filt = _out((T, K), lik, filt)
+    smooth = None if filter_only else _out((T, K), lik, smooth)
+    if want_loglik:
+        loglik = _out((T,), lik, loglik)
+    else:
+        loglik = None
+    h = model.struct()
+    args = (ctypes.byref(h), _p(lik), T, _p(ws), ws.numel(), _p(filt), _p(smooth), _p(loglik), _stream(stream))
+    if events is None:
+        _check(lib().ks_hmm_smooth(*args), "ks_hmm_smooth")
+    else:
+        for e in events:
+            if e is not None and not e.cuda_event:
+                e.record(torch.cuda.current_stream() if stream is None else stream)
+        handles = (ctypes.c_void_p * 4)(*[ctypes.c_void_p(e.cuda_event) if e is not None else None
+                                          for e in events])
+        _check(lib().ks_hmm_smooth_traced(*args, handles), "ks_hmm_smooth_traced")
+    return filt, smooth, loglik, ws

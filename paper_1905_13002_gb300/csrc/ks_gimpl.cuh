@@ -82,7 +82,7 @@ struct GImpl {
         static const bool ok = allow_smem(k, smem);
         if (!ok) return KS_ECUDA;
         uint32_t* z = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + L.off_flags);
-        k<<<B, 128, smem, st>>>(F, u, Q, H, d, R, m0, P0, y, mconst(ws, L), status(ws), z,
+        k<<<B, kPrepThreads, smem, st>>>(F, u, Q, H, d, R, m0, P0, y, mconst(ws, L), status(ws), z,
                                 (int)(L.flags_bytes / 4), off, L.T);
         return launch_status();
     }
@@ -218,7 +218,7 @@ struct GImpl {
 
     static constexpr VTable vtable() {
         return VTable{N, M, &layout, &build_elements, &filter_scan, &smooth_scan, &smooth, &smooth_batch,
-                      &no_comb, &no_comb, &no_agg_bytes, &no_fagg, &no_sagg};
+                      &no_comb, &no_comb, &no_agg_bytes, &no_fagg, &no_sagg, 0};
     }
 };
 

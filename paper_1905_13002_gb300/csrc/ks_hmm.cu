@@ -1,0 +1,149 @@
+// ks_hmm.cu -- C ABI of the discrete-state (HMM) filter and smoother
+// (ks_hmm.cuh): workspace layout, argument checks and launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "../../include/ks.h"
+#include "ks_hmm.cuh"
+#include "ks_impl.cuh"
+
+namespace ks {
+namespace hmm {
+namespace {
+
+struct HLayout {
+    int64_t T = 0;
+    int ntiles = 0;
+    int64_t nblk = 0;
+    size_t off_const = 0, off_flags = 0, flags_bytes = 0;
+    size_t off_fagg = 0, off_fpre = 0, off_sagg = 0, off_spre = 0, off_sblk = 0, bytes = 0;
+};
+
+// K states, CH steps per thread, 128 threads per block.
+template <int K, int CH>
+struct HImpl {
+    static constexpr int NT = 128;
+    static constexpr int64_t TILE = (int64_t)NT * CH;
+
+    static HLayout layout(int64_t T) {
+        HLayout L;
+        L.T = T;
+        L.ntiles = (int)((T + TILE - 1) / TILE);
+        L.nblk = (T + CH - 1) / CH;
+        size_t off = 256;                                   // status word + reserved
+        L.off_const = off;
+        off = align_up(off + sizeof(Const<K>), 256);
+        L.off_flags = off;                                  // [fcounter, scounter, 2 pad][fflags][sflags]
+        L.flags_bytes = 16 + 4 * 2 * (size_t)L.ntiles;
+        off = align_up(off + L.flags_bytes, 256);
+        L.off_fagg = off;
+        off = align_up(off + sizeof(FE<K>) * (size_t)L.ntiles, 256);
+        L.off_fpre = off;
+        off = align_up(off + sizeof(FS<K>) * (size_t)L.ntiles, 256);
+        L.off_sagg = off;
+        off = align_up(off + sizeof(SE<K>) * (size_t)L.ntiles, 256);
+        L.off_spre = off;
+        off = align_up(off + sizeof(SS<K>) * (size_t)L.ntiles, 256);
+        L.off_sblk = off;                                   // one smoothing aggregate per CH steps
+        off = align_up(off + sizeof(SE<K>) * (size_t)L.nblk, 256);
+        L.bytes = off;
+        return L;
+    }
+
+    static ScanState state(void* ws, const HLayout& L, bool forward) {
+        char* b = static_cast<char*>(ws);
+        ScanState s;
+        s.counter = reinterpret_cast<uint32_t*>(b + L.off_flags + (forward ? 0 : 4));
+        s.flags = reinterpret_cast<uint32_t*>(b + L.off_flags + 16 + (forward ? 0 : 4 * (size_t)L.ntiles));
+        s.agg = reinterpret_cast<float*>(b + (forward ? L.off_fagg : L.off_sagg));
+        s.pre = reinterpret_cast<float*>(b + (forward ? L.off_fpre : L.off_spre));
+        s.status = static_cast<uint32_t*>(ws);
+        s.spin_limit = kSpinLimit;
+        return s;
+    }
+
+    static int smooth(const ks_hmm* h, const float* lik, int64_t T, void* ws, size_t ws_bytes, float* filt,
+                      float* smooth, float* loglik, cudaStream_t st, void* const* ev) {
+        const HLayout L = layout(T);
+        if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) != 0 || ws_bytes < L.bytes) return KS_EINVAL;
+        char* b = static_cast<char*>(ws);
+        const Const<K>* cg = reinterpret_cast<const Const<K>*>(b + L.off_const);
+        float* sblk = reinterpret_cast<float*>(b + L.off_sblk);
+        auto rec = [&](int i) {
+            return (ev && ev[i] && cudaEventRecord(static_cast<cudaEvent_t>(ev[i]), st) != cudaSuccess) ? KS_ECUDA
+                                                                                                        : KS_OK;
+        };
+        int rc;
+        if ((rc = rec(0))) return rc;
+        hmm_prep_kernel<K><<<1, 64, 0, st>>>(h->pi, h->Pi, reinterpret_cast<Const<K>*>(b + L.off_const),
+                                             static_cast<uint32_t*>(ws),
+                                             reinterpret_cast<uint32_t*>(b + L.off_flags), (int)(L.flags_bytes / 4));
+        if ((rc = launch_status())) return rc;
+        if ((rc = rec(1))) return rc;
+        hmm_filter_kernel<K, NT, CH><<<L.ntiles, NT, 0, st>>>(cg, lik, T, filt, loglik, state(ws, L, true), sblk);
+        if ((rc = launch_status())) return rc;
+        if ((rc = rec(2))) return rc;
+        if (smooth) {
+            hmm_smoother_kernel<K, NT, CH><<<L.ntiles, NT, 0, st>>>(cg, filt, T, smooth, state(ws, L, false), sblk);
+            if ((rc = launch_status())) return rc;
+        }
+        return rec(3);
+    }
+};
+
+// Steps per thread by length: short inputs take 4 (more blocks for the
+// SMs), long ones 16 (fewer tiles in the look-back per step).
+constexpr int64_t kLongT = 256 * 1024;
+
+template <int K>
+size_t bytes(int64_t T) {
+    return std::max(HImpl<K, 4>::layout(T).bytes, HImpl<K, 16>::layout(T).bytes);
+}
+
+template <int K>
+int run(const ks_hmm* h, const float* lik, int64_t T, void* ws, size_t ws_bytes, float* filt, float* smooth,
+        float* loglik, cudaStream_t st, void* const* ev) {
+    return T < kLongT ? HImpl<K, 4>::smooth(h, lik, T, ws, ws_bytes, filt, smooth, loglik, st, ev)
+                      : HImpl<K, 16>::smooth(h, lik, T, ws, ws_bytes, filt, smooth, loglik, st, ev);
+}
+
+}  // namespace
+}  // namespace hmm
+}  // namespace ks
+
+using namespace ks;
+
+extern "C" {
+
+int ks_hmm_supported(int K) { return (K == 2 || K == 4 || K == 8) ? 1 : 0; }
+
+size_t ks_hmm_workspace_bytes(int K, int64_t T) {
+    if (T < 1 || T > 0x7fffffffLL) return 0;
+    switch (K) {
+        case 2: return hmm::bytes<2>(T);
+        case 4: return hmm::bytes<4>(T);
+        case 8: return hmm::bytes<8>(T);
+        default: return 0;
+    }
+}
+
+int ks_hmm_smooth_traced(const ks_hmm* h, const float* lik, int64_t T, void* ws, size_t ws_bytes, float* filt,
+                         float* smooth, float* loglik, void* stream, void* const* events) {
+    if (!h || !h->pi || !h->Pi) return KS_EINVAL;
+    if (!ks_hmm_supported(h->K)) return KS_EUNSUPPORTED;
+    if (T < 1 || T > 0x7fffffffLL || !lik || !filt) return KS_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    switch (h->K) {
+        case 2: return hmm::run<2>(h, lik, T, ws, ws_bytes, filt, smooth, loglik, st, events);
+        case 4: return hmm::run<4>(h, lik, T, ws, ws_bytes, filt, smooth, loglik, st, events);
+        default: return hmm::run<8>(h, lik, T, ws, ws_bytes, filt, smooth, loglik, st, events);
+    }
+}
+
+int ks_hmm_smooth(const ks_hmm* h, const float* lik, int64_t T, void* ws, size_t ws_bytes, float* filt,
+                  float* smooth, float* loglik, void* stream) {
+    return ks_hmm_smooth_traced(h, lik, T, ws, ws_bytes, filt, smooth, loglik, stream, nullptr);
+}
+
+}  // extern "C"

@@ -46,6 +46,7 @@ struct VTable {
     int (*faggregate)(const ks_model*, const float*, int64_t, int, void*, size_t, float*, cudaStream_t);
     int (*saggregate)(const ks_model*, int64_t, const float*, const float*, int, void*, size_t, float*,
                       cudaStream_t);
+    int time_varying;   // 1 if smooth accepts time-varying models
 };
 
 // The fused end-to-end entry points of one steps-per-thread choice.
@@ -153,7 +154,7 @@ struct Impl {
     // scans' tile counters and flags, which every scan launch needs.
     static int prep(const ks_model* m, const float* y, void* ws, const Layout& L, cudaStream_t st) {
         uint32_t* z = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + L.off_flags);
-        prep_kernel<N, M><<<1, 128, prep_smem(), st>>>(m->F, m->u, m->Q, m->H, m->d, m->R, m->m0, m->P0, y,
+        prep_kernel<N, M><<<1, kPrepThreads, prep_smem(), st>>>(m->F, m->u, m->Q, m->H, m->d, m->R, m->m0, m->P0, y,
                                              mconst(ws, L), status(ws), z, (int)(L.flags_bytes / 4), nullptr,
                                              L.T);
         return launch_status();
@@ -180,34 +181,47 @@ struct Impl {
     static int launch_filter_fused(void* ws, const Layout& L, const float* y, float* fm, float* fc,
                                    Segs<N, M> segs, cudaStream_t st) {
         constexpr int smem = filter_dyn_smem<N, FNT>();
-        auto k = filter_scan_kernel<N, M, FNT, FCH, true, true, SEG>;
+        auto k = filter_scan_kernel<N, M, FNT, FCH, true, true, SEG, false>;
         static const bool ok = allow_smem(k, smem);
         if (!ok) return KS_ECUDA;
         k<<<L.ntf, FNT, smem, st>>>(mconst(ws, L), y, nullptr, L.ld, L.T, fm, fc, fstate(ws, L), sblk(ws, L),
-                                    segs);
+                                    segs, TVArgs{});
+        return launch_status();
+    }
+
+    // Time-varying model: elements from the TVElem records `el`, smoothing
+    // aggregates fused as in the time-invariant scan.
+    static int launch_filter_tv(void* ws, const Layout& L, const float* el, float* fm, float* fc,
+                                const TVArgs& tv, cudaStream_t st) {
+        constexpr int smem = filter_dyn_smem<N, FNT>();
+        auto k = filter_scan_kernel<N, M, FNT, FCH, false, true, false, true>;
+        static const bool ok = allow_smem(k, smem);
+        if (!ok) return KS_ECUDA;
+        k<<<L.ntf, FNT, smem, st>>>(mconst(ws, L), nullptr, el, L.ld, L.T, fm, fc, fstate(ws, L), sblk(ws, L),
+                                    no_segs(), tv);
         return launch_status();
     }
 
     static int launch_filter_soa(void* ws, const Layout& L, const float* el, float* fm, float* fc,
                                  cudaStream_t st) {
         constexpr int smem = filter_dyn_smem<N, FNT>();
-        auto k = filter_scan_kernel<N, M, FNT, FCH, false, false, false>;
+        auto k = filter_scan_kernel<N, M, FNT, FCH, false, false, false, false>;
         static const bool ok = allow_smem(k, smem);
         if (!ok) return KS_ECUDA;
         k<<<L.ntf, FNT, smem, st>>>(mconst(ws, L), nullptr, el, L.ld, L.T, fm, fc, fstate(ws, L), nullptr,
-                                    no_segs());
+                                    no_segs(), TVArgs{});
         return launch_status();
     }
 
-    template <bool FROM_AGG, bool SEG>
+    template <bool FROM_AGG, bool SEG, bool TV = false>
     static int launch_smoother(void* ws, const Layout& L, const float* fm, const float* fc, float* sm,
-                               float* sc, Segs<N, M> segs, cudaStream_t st) {
+                               float* sc, Segs<N, M> segs, cudaStream_t st, TVArgs tv = TVArgs{}) {
         constexpr int smem = smoother_dyn_smem<N, SNT>();
-        auto k = smoother_scan_kernel<N, M, SNT, SCH, FROM_AGG, SEG>;
+        auto k = smoother_scan_kernel<N, M, SNT, SCH, FROM_AGG, SEG, TV>;
         static const bool ok = allow_smem(k, smem);
         if (!ok) return KS_ECUDA;
         k<<<L.nts, SNT, smem, st>>>(mconst(ws, L), fm, fc, L.T, sm, sc, sstate(ws, L),
-                                    FROM_AGG ? sblk(ws, L) : nullptr, segs);
+                                    FROM_AGG ? sblk(ws, L) : nullptr, segs, tv);
         return launch_status();
     }
 
@@ -251,8 +265,49 @@ struct Impl {
         return cudaEventRecord(static_cast<cudaEvent_t>(ev[i]), st) == cudaSuccess ? KS_OK : KS_ECUDA;
     }
 
+    // Time-varying model (m->time_varying = 1): the filtering elements are
+    // materialised in their measurement form (TVElem records) from the
+    // per-step arrays; the forward scan combines them with the rank-ny
+    // operators and folds each thread's Lemma 5 elements, built from the next
+    // step's transition, for the reverse scan.  Needs the KS_WS_ELEMENTS
+    // workspace.
+    static int smooth_tv(const ks_model* m, const float* y, int64_t T, void* ws, size_t ws_bytes, float* fm,
+                         float* fc, float* sm, float* sc, cudaStream_t st, void* const* ev) {
+        if (!m->F || !m->Q || !m->H || !m->R || !m->m0 || !m->P0) return KS_EINVAL;
+        if (m->time_varying != 1) return KS_EUNSUPPORTED;
+        if (T < 1 || T > 0x7fffffffLL) return KS_EINVAL;
+        const Layout L = layout(T);
+        if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) != 0 || ws_bytes < L.bytes_elements) return KS_EINVAL;
+        const bool own = (fm == nullptr) || (fc == nullptr);
+        const bool filter_only = (sm == nullptr) && (sc == nullptr);
+        if (!y || !aligned16(y) || (filter_only && own)) return KS_EINVAL;
+        if (!filter_only && (!sm || !sc || !aligned16(sm) || !aligned16(sc))) return KS_EINVAL;
+        if (own) {
+            fm = reinterpret_cast<float*>(static_cast<char*>(ws) + L.off_fmean);
+            fc = reinterpret_cast<float*>(static_cast<char*>(ws) + L.off_fcov);
+        } else if (!aligned16(fm) || !aligned16(fc)) {
+            return KS_EINVAL;
+        }
+        const TVArgs tv{m->F, m->u, m->Q, m->H, m->d, m->R, m->m0, m->P0};
+        float* el = reinterpret_cast<float*>(static_cast<char*>(ws) + L.off_elems);
+        uint32_t* z = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + L.off_flags);
+        int rc;
+        if ((rc = record(ev, 0, st))) return rc;
+        const int blocks = (int)std::min<int64_t>((T + 255) / 256, 152 * 8);
+        static_assert(TVElem<N, M>::kFloats <= NCOMP, "records fit the elements region");
+        tv_elements_kernel<N, M><<<blocks, 256, 0, st>>>(tv, y, T, el, status(ws), z, (int)(L.flags_bytes / 4));
+        if ((rc = launch_status())) return rc;
+        if ((rc = record(ev, 1, st))) return rc;
+        if ((rc = launch_filter_tv(ws, L, el, fm, fc, tv, st))) return rc;
+        if ((rc = record(ev, 2, st))) return rc;
+        if (!filter_only && (rc = launch_smoother<true, false, true>(ws, L, fm, fc, sm, sc, no_segs(), st, tv)))
+            return rc;
+        return record(ev, 3, st);
+    }
+
     static int smooth(const ks_model* m, const float* y, int64_t T, void* ws, size_t ws_bytes, float* fm,
                       float* fc, float* sm, float* sc, cudaStream_t st, void* const* ev) {
+        if (m && m->time_varying) return smooth_tv(m, y, T, ws, ws_bytes, fm, fc, sm, sc, st, ev);
         const Layout L = layout(T);
         const bool own = (fm == nullptr) || (fc == nullptr);
         const bool filter_only = (sm == nullptr) && (sc == nullptr);
@@ -287,7 +342,7 @@ struct Impl {
         if (!aligned16(y) || !aligned16(fm) || !aligned16(fc) || !aligned16(sm) || !aligned16(sc))
             return KS_EINVAL;
         uint32_t* z = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + L.off_flags);
-        prep_kernel<N, M><<<mb->B, 128, prep_smem(), st>>>(mb->F, mb->u, mb->Q, mb->H, mb->d, mb->R, mb->m0, mb->P0, y,
+        prep_kernel<N, M><<<mb->B, kPrepThreads, prep_smem(), st>>>(mb->F, mb->u, mb->Q, mb->H, mb->d, mb->R, mb->m0, mb->P0, y,
                                                  mconst(ws, L), status(ws), z, (int)(L.flags_bytes / 4),
                                                  mb->offsets, T);
         int rc = launch_status();
@@ -364,7 +419,7 @@ struct Impl {
 
     static constexpr VTable vtable() {
         return VTable{N, M, &layout, &build_elements, &filter_scan, &smooth_scan, &smooth, &smooth_batch,
-                      &fcomb_batch, &scomb_batch, &agg_bytes, &faggregate, &saggregate};
+                      &fcomb_batch, &scomb_batch, &agg_bytes, &faggregate, &saggregate, 1};
     }
     static constexpr ChunkVariant chunk_variant() { return ChunkVariant{&layout, &smooth, &smooth_batch}; }
 };

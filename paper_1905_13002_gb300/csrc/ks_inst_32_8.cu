@@ -36,5 +36,6 @@ extern const VTable kImpl_32_8 = VTable{32,
                                         &GR::no_comb,
                                         &GR::no_agg_bytes,
                                         &GR::no_fagg,
-                                        &GR::no_sagg};
+                                        &GR::no_sagg,
+                                        0};
 }  // namespace ks

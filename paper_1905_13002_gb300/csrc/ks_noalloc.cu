@@ -48,7 +48,7 @@ extern "C" int ks_smooth_noalloc(const ks_model* m, const float* y, int64_t T, f
                                  float* smean, float* scov, int32_t* status_out, void* stream) {
     using namespace ks;
     if (!m) return KS_EINVAL;
-    if (m->nx != 4 || m->ny != 2) return KS_EUNSUPPORTED;
+    if (m->nx != 4 || m->ny != 2 || m->time_varying != 0) return KS_EUNSUPPORTED;
     if (T < 1 || T > KS_NOALLOC_MAX_T) return KS_EINVAL;
     if (!fmean || !fcov || !smean || !scov) return KS_EINVAL;
     const VTable* v = &kImpl32_4_2;   // 32 steps per thread: the smallest scratch layout

@@ -76,7 +76,7 @@ struct ModelConst {
     float K[N * M];         // Q H^T S^{-1}
     float Lsi[M * M];       // L_S^{-1} (lower triangular, row-major)
     float hud[M];           // H u + d
-    float b1[N];            // k = 1 element (FP64-built): b_1
+    float b1[N];            // k = 1 element (double-float-built): b_1
     float C1[sym_size(N)];  //                              C_1
     float pad[4];
 };
@@ -431,8 +431,10 @@ KS_DEV void fadvance(FState<N>& st, const FElem<N>& ej, bool& bad) {
 //   eta_ij = (UL A_i)^T L^{-1} (w_j - U b_i) + eta_i
 //   J_ij   = (UL A_i)^T (UL A_i) + J_i
 // with one M x M Cholesky factorisation instead of an N x N pivoted inverse.
-template <int N, int M>
-KS_DEV FElem<N> fcombine_meas(const FElem<N>& ei, const ModelConst<N, M>& mc, const float (&bj)[N],
+// MC holds the element's A [N*N], C (packed lower) and U [M*N]: a ModelConst
+// (time-invariant model) or one step's element of a time-varying model.
+template <int N, int M, class MC>
+KS_DEV FElem<N> fcombine_meas(const FElem<N>& ei, const MC& mc, const float (&bj)[N],
                               const float (&wj)[M], bool& bad) {
     FElem<N> r;
     float CU[N][M];
@@ -608,8 +610,8 @@ KS_DEV FElem<N> fcombine_meas(const FElem<N>& ei, const ModelConst<N, M>& mc, co
 
 // Prefix (A = 0) combined with a single measurement element (rank-M form):
 //   b' = A_j M^{-1} (xbar + P U^T w_j) + b_j,   C' = A_j (P - CUL CUL^T) A_j^T + C_j.
-template <int N, int M>
-KS_DEV void fadvance_meas(FState<N>& st, const ModelConst<N, M>& mc, const float (&bj)[N],
+template <int N, int M, class MC>
+KS_DEV void fadvance_meas(FState<N>& st, const MC& mc, const float (&bj)[N],
                           const float (&wj)[M], bool& bad) {
     float CU[N][M];
 #pragma unroll
@@ -740,8 +742,8 @@ KS_DEV void meas_element(const ModelConst<N, M>& mc, const float (&y)[M], float 
 }
 
 // The same element expanded to the general form (A, b, C, eta, J).
-template <int N, int M>
-KS_DEV void expand_meas(const ModelConst<N, M>& mc, const float (&b)[N], const float (&w)[M],
+template <int N, int M, class MC>
+KS_DEV void expand_meas(const MC& mc, const float (&b)[N], const float (&w)[M],
                         FElem<N>& e) {
 #pragma unroll
     for (int a = 0; a < N * N; ++a) e.A[a] = mc.A[a];
@@ -766,7 +768,7 @@ KS_DEV void expand_meas(const ModelConst<N, M>& mc, const float (&b)[N], const f
         }
 }
 
-// The k = 1 element of Lemma 3: A_1 = 0, (b_1, C_1) built in FP64, eta_1 = J_1 = 0.
+// The k = 1 element of Lemma 3: A_1 = 0, (b_1, C_1) built in double-float, eta_1 = J_1 = 0.
 template <int N, int M>
 KS_DEV void first_element(const ModelConst<N, M>& mc, FElem<N>& e) {
 #pragma unroll
@@ -781,8 +783,10 @@ KS_DEV void first_element(const ModelConst<N, M>& mc, FElem<N>& e) {
 // Smoothing element for k < n from the filtered (xbar, P):
 //   P- = F P F^T + Q = Lc Lc^T (Cholesky),  E = P F^T (P-)^{-1}  (solved as
 //   E^T = (P-)^{-1} (F P)),  g = xbar - E (F xbar + u),  L = P - E (F P).
-template <int N, int M>
-KS_DEV void smoother_element(const ModelConst<N, M>& mc, const float (&xbar)[N],
+// MC holds F [N*N], u [N] and Q (packed lower): a ModelConst, or one step's
+// transition of a time-varying model.
+template <int N, int M, class MC>
+KS_DEV void smoother_element(const MC& mc, const float (&xbar)[N],
                              const float (&P)[sym_size(N)], SElem<N>& e, bool& bad) {
     float FP[N][N];
 #pragma unroll

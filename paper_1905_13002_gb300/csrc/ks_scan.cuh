@@ -20,6 +20,7 @@
 #pragma once
 
 #include "ks_async.cuh"
+#include "ks_df.cuh"
 #include "ks_ops.cuh"
 
 namespace ks {
@@ -282,25 +283,86 @@ struct Cursor {
     KS_DEV bool last(int64_t k) const { return k == end - 1; }
 };
 
+// ---------------------------------------------------------------- time-varying models
+// Per-step model arrays of one time-varying sequence (device, row-major FP32):
+// F [T][N][N], u [T][N] or null, Q [T][N][N], H [T][M][N], d [T][M] or null,
+// R [T][M][M]; m0 [N], P0 [N][N] FP64.  Step k is predicted from step k - 1
+// with F[k], u[k], Q[k] (F[0] maps the prior N(m0, P0) to step 0) and observed
+// through H[k], d[k], R[k] (the model of Section II with its indices shifted
+// to start at 0).
+struct TVArgs {
+    const float *F, *u, *Q, *H, *d, *R;
+    const double *m0, *P0;
+};
+
+// One step's transition (what the Lemma 5 element of the step before reads).
+template <int N>
+struct Trans {
+    float F[N * N];
+    float u[N];
+    float Q[sym_size(N)];
+};
+
+template <int N>
+KS_DEV void load_trans(const TVArgs& tv, int64_t k, Trans<N>& t) {
+    const float* F = tv.F + k * (N * N);
+    const float* Q = tv.Q + k * (N * N);
+#pragma unroll
+    for (int a = 0; a < N * N; ++a) t.F[a] = __ldg(F + a);
+#pragma unroll
+    for (int a = 0; a < N; ++a) t.u[a] = tv.u ? __ldg(tv.u + k * N + a) : 0.f;
+#pragma unroll
+    for (int a = 0; a < N; ++a)
+#pragma unroll
+        for (int b = 0; b <= a; ++b) t.Q[sidx(a, b)] = 0.5f * (__ldg(Q + a * N + b) + __ldg(Q + b * N + a));
+}
+
+// Lemma 5 element of step k of a time-varying sequence of T steps: the
+// transition into step k + 1 is that step's (F, u, Q).
+template <int N, int M>
+KS_DEV void build_selem_tv(const TVArgs& tv, int64_t k, int64_t T, const float (&xb)[N],
+                           const float (&P)[sym_size(N)], SElem<N>& e, bool& bad) {
+    if (k == T - 1) {   // Lemma 5, k = n: E = 0, g = xbar_n, L = P_n
+#pragma unroll
+        for (int a = 0; a < N * N; ++a) e.E[a] = 0.f;
+#pragma unroll
+        for (int a = 0; a < N; ++a) e.g[a] = xb[a];
+#pragma unroll
+        for (int a = 0; a < sym_size(N); ++a) e.L[a] = P[a];
+    } else {
+        Trans<N> t;
+        load_trans<N>(tv, k + 1, t);
+        smoother_element<N, M>(t, xb, P, e, bad);
+    }
+}
+
 // ---------------------------------------------------------------- prep
 // Model constants, one thread block.  k > 1 quantities in FP32 (Lemma 3 with
 // the Cholesky factor of S); the k = 1 element (Kalman prediction and update
-// from N(m0, P0), Lemma 3) in FP64.  Every matrix product is spread over the
-// block, one output entry per thread, so the FP64 chain is a few products
-// deep.  Block s prepares segment s (batched: the model arrays hold one model
-// per segment and `off` gives the segments' first steps); block 0 also zeroes
-// the scans' tile counters and flags and checks the segment table.
+// from N(m0, P0), Lemma 3) in double-float arithmetic (about 44 bits).  Every
+// matrix product is spread over a warp, one output entry per lane.  Block s
+// prepares segment s (batched: the model arrays hold one model per segment
+// and `off` gives the segments' first steps); block 0 also zeroes the scans'
+// tile counters and flags and checks the segment table.
 template <int N, int M>
 struct PrepSmem {
-    float F[N][N], Q[N][N], H[M][N], R[M][M], u[N], d[M];
+    float F[N][N], Q[N][N], H[M][N], R[M][M], u[N], d[M], y[M];
+    df m0[N], P0[N][N];
+    // warp 0: the FP32 model constants
     float HQ[M][N], HF[M][N], S[M][M], Lsi[M][M], tmp[M][N], K[N][M];
-    double m0[N], P0[N][N], mm[N], FP[N][N], Pm[N][N], HP[M][N], S1[M][M], L1[M][M], t1[M][N], e1[M],
-        z[M];
-    int ok;
+    // warp 1: the k = 1 element in double-float
+    df mm[N], FP[N][N], Pm[N][N], HP[M][N], S1[M][M], L1[M][M], r1[M], t1[M][N], z[M];
+    int ok0, ok1;
 };
 
+constexpr int kPrepThreads = 64;
+
+// One block per model (segment).  After one round of loads, warp 0 builds the
+// FP32 constants of Lemma 3 for k > 1 and warp 1, at the same time, the k = 1
+// element (prediction of N(m0, P0) and update with y_1) in double-float
+// arithmetic (ks_df.cuh); the two chains only meet for the final store.
 template <int N, int M>
-__global__ void __launch_bounds__(128) prep_kernel(const float* __restrict__ F, const float* __restrict__ u,
+__global__ void __launch_bounds__(kPrepThreads) prep_kernel(const float* __restrict__ F, const float* __restrict__ u,
                                                    const float* __restrict__ Q, const float* __restrict__ H,
                                                    const float* __restrict__ d, const float* __restrict__ R,
                                                    const double* __restrict__ m0, const double* __restrict__ P0,
@@ -312,6 +374,7 @@ __global__ void __launch_bounds__(128) prep_kernel(const float* __restrict__ F, 
     ModelConst<N, M>& mc =
         *reinterpret_cast<ModelConst<N, M>*>(prep_dsm + ((sizeof(PrepSmem<N, M>) + 15) / 16) * 16);
     const int t = threadIdx.x, nt = blockDim.x;
+    const int warp = t >> 5, l = t & 31;
     const int sg = blockIdx.x;
     if (sg == 0)
         for (int i = t; i < nzero; i += nt) zero[i] = 0u;
@@ -333,181 +396,212 @@ __global__ void __launch_bounds__(128) prep_kernel(const float* __restrict__ F, 
         y = (a >= 0 && a < b && a < T) ? y + a * M : nullptr;
     }
     out += sg;
-    if (t == 0) p.ok = 1;
-    for (int e = t; e < N * N; e += nt) {
-        const int a = e / N, b = e % N;
-        p.F[a][b] = F[e];
-        p.Q[a][b] = 0.5f * (Q[a * N + b] + Q[b * N + a]);
-        p.P0[a][b] = P0[e];
+    // ---- every input in one round of independent loads
+    constexpr int nF = N * N, nQ = N * N, nP = N * N, nH = M * N, nR = M * M;
+    constexpr int nAll = nF + nQ + nP + nH + nR + N + N + M + M;
+    for (int e = t; e < nAll; e += nt) {
+        int i = e;
+        if (i < nF) { p.F[i / N][i % N] = F[i]; continue; }
+        i -= nF;
+        if (i < nQ) { p.Q[i / N][i % N] = Q[i]; continue; }
+        i -= nQ;
+        if (i < nP) { p.P0[i / N][i % N] = df_make(P0[i]); continue; }
+        i -= nP;
+        if (i < nH) { p.H[i / N][i % N] = H[i]; continue; }
+        i -= nH;
+        if (i < nR) { p.R[i / M][i % M] = R[i]; continue; }
+        i -= nR;
+        if (i < N) { p.u[i] = u ? u[i] : 0.f; continue; }
+        i -= N;
+        if (i < N) { p.m0[i] = df_make(m0[i]); continue; }
+        i -= N;
+        if (i < M) { p.d[i] = d ? d[i] : 0.f; continue; }
+        i -= M;
+        p.y[i] = y ? y[i] : 0.f;
     }
-    for (int e = t; e < M * N; e += nt) p.H[e / N][e % N] = H[e];
-    for (int e = t; e < M * M; e += nt) {
-        const int a = e / M, b = e % M;
-        p.R[a][b] = 0.5f * (R[a * M + b] + R[b * M + a]);
-    }
-    for (int e = t; e < N; e += nt) { p.u[e] = u ? u[e] : 0.f; p.m0[e] = m0[e]; }
-    for (int e = t; e < M; e += nt) p.d[e] = d ? d[e] : 0.f;
+    if (t == 0) { p.ok0 = 1; p.ok1 = 1; }
     __syncthreads();
-    // ---- FP32, k > 1: HQ = H Q, HF = H F, and the FP64 k = 1 prediction
-    for (int e = t; e < M * N; e += nt) {
-        const int q = e / N, a = e % N;
-        float s = 0.f, h = 0.f;
-        for (int c = 0; c < N; ++c) { s = fmaf(p.H[q][c], p.Q[c][a], s); h = fmaf(p.H[q][c], p.F[c][a], h); }
-        p.HQ[q][a] = s;
-        p.HF[q][a] = h;
-    }
-    for (int e = t; e < N * N; e += nt) {          // FP = F P0
-        const int a = e / N, b = e % N;
-        double s = 0.0;
-        for (int c = 0; c < N; ++c) s += (double)p.F[a][c] * p.P0[c][b];
-        p.FP[a][b] = s;
-    }
-    for (int e = t; e < N; e += nt) {              // m- = F m0 + u
-        double s = p.u[e];
-        for (int c = 0; c < N; ++c) s += (double)p.F[e][c] * p.m0[c];
-        p.mm[e] = s;
-    }
-    __syncthreads();
-    for (int e = t; e < M * M; e += nt) {          // S = H Q H^T + R
-        const int q = e / M, r = e % M;
-        float s = p.R[q][r];
-        for (int c = 0; c < N; ++c) s = fmaf(p.HQ[q][c], p.H[r][c], s);
-        p.S[q][r] = s;
-    }
-    for (int e = t; e < N * N; e += nt) {          // P- = F P0 F^T + Q
-        const int a = e / N, b = e % N;
-        double s = 0.5 * ((double)p.Q[a][b] + (double)p.Q[b][a]);
-        for (int c = 0; c < N; ++c) s += p.FP[a][c] * (double)p.F[b][c];
-        p.Pm[a][b] = s;
-    }
-    __syncthreads();
-    if (t == 0) {                                  // Cholesky of S, L_S^{-1}
-        float Ls[M][M];
-        bool ok = true;
-        for (int j = 0; j < M; ++j) {
-            float s = p.S[j][j];
-            for (int l = 0; l < j; ++l) s -= Ls[j][l] * Ls[j][l];
-            ok = ok && (s > 0.f);
-            Ls[j][j] = sqrtf(fmaxf(s, 1e-37f));
-            for (int i = j + 1; i < M; ++i) {
-                float q = p.S[i][j];
-                for (int l = 0; l < j; ++l) q -= Ls[i][l] * Ls[j][l];
-                Ls[i][j] = q / Ls[j][j];
+
+    if (warp == 0) {
+        // ---- FP32 constants for k > 1: S = H Q H^T + R = L_S L_S^T, U = L_S^{-1} H F,
+        // K = Q H^T S^{-1}, A = F - K H F, C = Q - K S K^T (Q, R symmetrised)
+        for (int e = l; e < M * N; e += 32) {
+            const int q = e / N, a = e % N;
+            float s = 0.f, h = 0.f;
+            for (int c = 0; c < N; ++c) {
+                s = fmaf(p.H[q][c], 0.5f * (p.Q[c][a] + p.Q[a][c]), s);
+                h = fmaf(p.H[q][c], p.F[c][a], h);
             }
+            p.HQ[q][a] = s;
+            p.HF[q][a] = h;
         }
-        for (int c = 0; c < M; ++c)
-            for (int i = 0; i < M; ++i) {
-                if (i < c) { p.Lsi[i][c] = 0.f; continue; }
-                float q = (i == c) ? 1.f : 0.f;
-                for (int l = c; l < i; ++l) q -= Ls[i][l] * p.Lsi[l][c];
-                p.Lsi[i][c] = q / Ls[i][i];
+        __syncwarp();
+        for (int e = l; e < M * M; e += 32) {
+            const int q = e / M, r = e % M;
+            float s = 0.5f * (p.R[q][r] + p.R[r][q]);
+            for (int c = 0; c < N; ++c) s = fmaf(p.HQ[q][c], p.H[r][c], s);
+            p.S[q][r] = s;
+        }
+        __syncwarp();
+        if (l == 0) {                              // Cholesky of S, L_S^{-1}
+            float Ls[M][M];
+            bool ok = true;
+            for (int j = 0; j < M; ++j) {
+                float s = p.S[j][j];
+                for (int k = 0; k < j; ++k) s -= Ls[j][k] * Ls[j][k];
+                ok = ok && (s > 0.f);
+                Ls[j][j] = sqrtf(fmaxf(s, 1e-37f));
+                for (int i = j + 1; i < M; ++i) {
+                    float q = p.S[i][j];
+                    for (int k = 0; k < j; ++k) q -= Ls[i][k] * Ls[j][k];
+                    Ls[i][j] = q / Ls[j][j];
+                }
             }
-        if (!ok) p.ok = 0;
-    }
-    for (int e = t; e < M * N; e += nt) {          // HP = H P-
-        const int q = e / N, a = e % N;
-        double s = 0.0;
-        for (int c = 0; c < N; ++c) s += (double)p.H[q][c] * p.Pm[c][a];
-        p.HP[q][a] = s;
-    }
-    __syncthreads();
-    for (int e = t; e < M * N; e += nt) {          // tmp = L_S^{-1} H Q, U = L_S^{-1} H F
-        const int q = e / N, a = e % N;
-        float s = 0.f, v = 0.f;
-        for (int r = 0; r <= q; ++r) { s = fmaf(p.Lsi[q][r], p.HQ[r][a], s); v = fmaf(p.Lsi[q][r], p.HF[r][a], v); }
-        p.tmp[q][a] = s;
-        mc.U[q * N + a] = v;
-    }
-    for (int e = t; e < M * M; e += nt) {          // S1 = H P- H^T + R
-        const int q = e / M, r = e % M;
-        double s = 0.5 * ((double)p.R[q][r] + (double)p.R[r][q]);
-        for (int c = 0; c < N; ++c) s += p.HP[q][c] * (double)p.H[r][c];
-        p.S1[q][r] = s;
-    }
-    for (int e = t; e < M; e += nt) {
-        float s = p.d[e];
-        for (int c = 0; c < N; ++c) s = fmaf(p.H[e][c], p.u[c], s);
-        mc.hud[e] = s;
-        for (int r = 0; r < M; ++r) mc.Lsi[e * M + r] = p.Lsi[e][r];
-    }
-    __syncthreads();
-    for (int e = t; e < N * M; e += nt) {          // K = tmp^T L_S^{-1}
-        const int a = e / M, q = e % M;
-        float s = 0.f;
-        for (int r = q; r < M; ++r) s = fmaf(p.tmp[r][a], p.Lsi[r][q], s);
-        p.K[a][q] = s;
-        mc.K[a * M + q] = s;
-    }
-    if (t == 0 && y != nullptr) {                  // FP64 Cholesky of S1 and the innovation solve
-        bool ok = true;
-        for (int j = 0; j < M; ++j) {
-            double s = p.S1[j][j];
-            for (int l = 0; l < j; ++l) s -= p.L1[j][l] * p.L1[j][l];
-            ok = ok && (s > 0.0);
-            p.L1[j][j] = sqrt(s > 0.0 ? s : 1e-300);
-            for (int i = j + 1; i < M; ++i) {
-                double q = p.S1[i][j];
-                for (int l = 0; l < j; ++l) q -= p.L1[i][l] * p.L1[j][l];
-                p.L1[i][j] = q / p.L1[j][j];
-            }
+            for (int c = 0; c < M; ++c)
+                for (int i = 0; i < M; ++i) {
+                    if (i < c) { p.Lsi[i][c] = 0.f; continue; }
+                    float q = (i == c) ? 1.f : 0.f;
+                    for (int k = c; k < i; ++k) q -= Ls[i][k] * p.Lsi[k][c];
+                    p.Lsi[i][c] = q / Ls[i][i];
+                }
+            if (!ok) p.ok0 = 0;
         }
-        for (int q = 0; q < M; ++q) {
-            double s = (double)y[q] - (double)p.d[q];
-            for (int c = 0; c < N; ++c) s -= (double)p.H[q][c] * p.mm[c];
-            for (int l = 0; l < q; ++l) s -= p.L1[q][l] * p.z[l];
-            p.z[q] = s / p.L1[q][q];
+        __syncwarp();
+        for (int e = l; e < M * N; e += 32) {      // tmp = L_S^{-1} H Q, U = L_S^{-1} H F
+            const int q = e / N, a = e % N;
+            float s = 0.f, v = 0.f;
+            for (int r = 0; r <= q; ++r) { s = fmaf(p.Lsi[q][r], p.HQ[r][a], s); v = fmaf(p.Lsi[q][r], p.HF[r][a], v); }
+            p.tmp[q][a] = s;
+            mc.U[q * N + a] = v;
         }
-        if (!ok) p.ok = 0;
-    }
-    __syncthreads();
-    for (int e = t; e < N * N; e += nt) {          // A = F - K H F ; C = Q - tmp^T tmp ; copies
-        const int a = e / N, b = e % N;
-        float s = p.F[a][b];
-        for (int q = 0; q < M; ++q) s = fmaf(-p.K[a][q], p.HF[q][b], s);
-        mc.A[a * N + b] = s;
-        mc.F[a * N + b] = p.F[a][b];
-        if (b <= a) {
-            float c = p.Q[a][b];
-            for (int q = 0; q < M; ++q) c = fmaf(-p.tmp[q][a], p.tmp[q][b], c);
-            mc.C[sidx(a, b)] = c;
-            mc.Q[sidx(a, b)] = p.Q[a][b];
+        for (int e = l; e < M; e += 32) {
+            float s = p.d[e];
+            for (int c = 0; c < N; ++c) s = fmaf(p.H[e][c], p.u[c], s);
+            mc.hud[e] = s;
+            for (int r = 0; r < M; ++r) mc.Lsi[e * M + r] = p.Lsi[e][r];
         }
-    }
-    for (int e = t; e < N; e += nt) mc.u[e] = p.u[e];
-    if (y != nullptr) {
-        for (int a = t; a < N; a += nt) {          // t1 = L1^{-1} H P- (column a)
-            for (int q = 0; q < M; ++q) {
-                double s = p.HP[q][a];
-                for (int l = 0; l < q; ++l) s -= p.L1[q][l] * p.t1[l][a];
-                p.t1[q][a] = s / p.L1[q][q];
-            }
+        __syncwarp();
+        for (int e = l; e < N * M; e += 32) {      // K = tmp^T L_S^{-1}
+            const int a = e / M, q = e % M;
+            float s = 0.f;
+            for (int r = q; r < M; ++r) s = fmaf(p.tmp[r][a], p.Lsi[r][q], s);
+            p.K[a][q] = s;
+            mc.K[a * M + q] = s;
         }
-        __syncthreads();
-        for (int e = t; e < N * N; e += nt) {      // b1 = m- + t1^T z ; C1 = P- - t1^T t1
+        __syncwarp();
+        for (int e = l; e < N * N; e += 32) {      // A = F - K H F ; C = Q - tmp^T tmp ; copies
             const int a = e / N, b = e % N;
-            if (b == 0) {
-                double s = p.mm[a];
-                for (int q = 0; q < M; ++q) s += p.t1[q][a] * p.z[q];
-                mc.b1[a] = (float)s;
-            }
+            float s = p.F[a][b];
+            for (int q = 0; q < M; ++q) s = fmaf(-p.K[a][q], p.HF[q][b], s);
+            mc.A[a * N + b] = s;
+            mc.F[a * N + b] = p.F[a][b];
             if (b <= a) {
-                double s = 0.5 * (p.Pm[a][b] + p.Pm[b][a]);
-                for (int q = 0; q < M; ++q) s -= p.t1[q][a] * p.t1[q][b];
-                mc.C1[sidx(a, b)] = (float)s;
+                const float qs = 0.5f * (p.Q[a][b] + p.Q[b][a]);
+                float c = qs;
+                for (int q = 0; q < M; ++q) c = fmaf(-p.tmp[q][a], p.tmp[q][b], c);
+                mc.C[sidx(a, b)] = c;
+                mc.Q[sidx(a, b)] = qs;
             }
         }
-    } else {
-        for (int e = t; e < N; e += nt) mc.b1[e] = 0.f;
-        for (int e = t; e < sym_size(N); e += nt) mc.C1[e] = 0.f;
+        for (int e = l; e < N; e += 32) mc.u[e] = p.u[e];
+        if (l < 4) mc.pad[l] = 0.f;
+    } else if (warp == 1) {
+        if (y != nullptr) {
+            // ---- k = 1: m- = F m0 + u, P- = F P0 F^T + Q, S1 = H P- H^T + R = L1 L1^T,
+            // t1 = L1^{-1} H P-, z = L1^{-1} (y - H m- - d), b1 = m- + t1^T z, C1 = P- - t1^T t1
+            for (int e = l; e < N * N; e += 32) {
+                const int a = e / N, b = e % N;
+                df s = df_make(0.f);
+                for (int c = 0; c < N; ++c) s = df_fma(df_make(p.F[a][c]), p.P0[c][b], s);
+                p.FP[a][b] = s;
+            }
+            for (int e = l; e < N; e += 32) {
+                df s = df_make(p.u[e]);
+                for (int c = 0; c < N; ++c) s = df_fma(df_make(p.F[e][c]), p.m0[c], s);
+                p.mm[e] = s;
+            }
+            __syncwarp();
+            for (int e = l; e < N * N; e += 32) {
+                const int a = e / N, b = e % N;
+                if (b > a) continue;
+                df s = df_make(0.5f * (p.Q[a][b] + p.Q[b][a]));
+                for (int c = 0; c < N; ++c) s = df_fma(p.FP[a][c], df_make(p.F[b][c]), s);
+                p.Pm[a][b] = s;
+                p.Pm[b][a] = s;
+            }
+            __syncwarp();
+            for (int e = l; e < M * N; e += 32) {
+                const int q = e / N, a = e % N;
+                df s = df_make(0.f);
+                for (int c = 0; c < N; ++c) s = df_fma(df_make(p.H[q][c]), p.Pm[c][a], s);
+                p.HP[q][a] = s;
+            }
+            __syncwarp();
+            for (int e = l; e < M * M; e += 32) {
+                const int q = e / M, r = e % M;
+                df s = df_make(0.5f * (p.R[q][r] + p.R[r][q]));
+                for (int c = 0; c < N; ++c) s = df_fma(p.HP[q][c], df_make(p.H[r][c]), s);
+                p.S1[q][r] = s;
+            }
+            __syncwarp();
+            if (l == 0) {                          // Cholesky of S1 (reciprocal diagonal), z
+                bool ok = true;
+                for (int j = 0; j < M; ++j) {
+                    df s = p.S1[j][j];
+                    for (int k = 0; k < j; ++k) s = df_sub(s, df_mul(p.L1[j][k], p.L1[j][k]));
+                    ok = ok && (s.hi > 0.f);
+                    const df Ljj = df_sqrt(s.hi > 0.f ? s : df_make(1e-30f));
+                    const df rj = df_recip(Ljj);
+                    p.L1[j][j] = Ljj;
+                    p.r1[j] = rj;
+                    for (int i = j + 1; i < M; ++i) {
+                        df q = p.S1[i][j];
+                        for (int k = 0; k < j; ++k) q = df_sub(q, df_mul(p.L1[i][k], p.L1[j][k]));
+                        p.L1[i][j] = df_mul(q, rj);
+                    }
+                }
+                for (int q = 0; q < M; ++q) {
+                    df s = df_sub(df_make(p.y[q]), df_make(p.d[q]));
+                    for (int c = 0; c < N; ++c) s = df_sub(s, df_mul(df_make(p.H[q][c]), p.mm[c]));
+                    for (int k = 0; k < q; ++k) s = df_sub(s, df_mul(p.L1[q][k], p.z[k]));
+                    p.z[q] = df_mul(s, p.r1[q]);
+                }
+                if (!ok) p.ok1 = 0;
+            }
+            __syncwarp();
+            for (int a = l; a < N; a += 32) {      // t1 column a
+                for (int q = 0; q < M; ++q) {
+                    df s = p.HP[q][a];
+                    for (int k = 0; k < q; ++k) s = df_sub(s, df_mul(p.L1[q][k], p.t1[k][a]));
+                    p.t1[q][a] = df_mul(s, p.r1[q]);
+                }
+            }
+            __syncwarp();
+            for (int e = l; e < N * N; e += 32) {
+                const int a = e / N, b = e % N;
+                if (b == 0) {
+                    df s = p.mm[a];
+                    for (int q = 0; q < M; ++q) s = df_fma(p.t1[q][a], p.z[q], s);
+                    mc.b1[a] = df_float(s);
+                }
+                if (b <= a) {
+                    df s = p.Pm[a][b];
+                    for (int q = 0; q < M; ++q) s = df_sub(s, df_mul(p.t1[q][a], p.t1[q][b]));
+                    mc.C1[sidx(a, b)] = df_float(s);
+                }
+            }
+        } else {
+            for (int e = l; e < N; e += 32) mc.b1[e] = 0.f;
+            for (int e = l; e < sym_size(N); e += 32) mc.C1[e] = 0.f;
+        }
     }
-    if (t < 4) mc.pad[t] = 0.f;
     __syncthreads();
     {
         const float* src = reinterpret_cast<const float*>(&mc);
         float* dst = reinterpret_cast<float*>(out);
         for (int i = t; i < (int)(sizeof(ModelConst<N, M>) / 4); i += nt) dst[i] = src[i];
     }
-    if (t == 0 && !p.ok) atomicOr(status, ST_NUMERIC);
+    if (t == 0 && !(p.ok0 && p.ok1)) atomicOr(status, ST_NUMERIC);
 }
 
 // ---------------------------------------------------------------- Lemma 3 materialised
@@ -547,6 +641,235 @@ __global__ void __launch_bounds__(256) build_elements_kernel(const ModelConst<N,
                 el[(oJ + a * N + b) * ld + k] = e.J[sidx(a, b)];
             }
     }
+}
+
+// ---------------------------------------------------------------- Lemma 3, time-varying
+// Filtering element of a time-varying model in its measurement form: A, b,
+// C and (U, w) with eta = U^T w and J = U^T U (rank ny), so that the scans
+// combine it with the rank-ny operators of a time-invariant model.  Stored
+// per step as one contiguous record of kFloats (a multiple of 4).
+template <int N, int M>
+struct TVElem {
+    static constexpr int kFloats = N * N + sym_size(N) + M * N + N + M;
+    static_assert(kFloats % 4 == 0, "records are moved as float4");
+    float A[N * N];
+    float C[sym_size(N)];
+    float U[M * N];
+    float b[N];
+    float w[M];
+};
+
+template <int N, int M>
+KS_DEV void store_tvelem(float* __restrict__ el, int64_t k, const TVElem<N, M>& e) {
+    static_assert(sizeof(TVElem<N, M>) == 4 * TVElem<N, M>::kFloats, "packed record");
+    const float4* src = reinterpret_cast<const float4*>(&e);
+    float4* dst = reinterpret_cast<float4*>(el + k * TVElem<N, M>::kFloats);
+#pragma unroll
+    for (int i = 0; i < TVElem<N, M>::kFloats / 4; ++i) dst[i] = src[i];
+}
+
+template <int N, int M>
+KS_DEV void load_tvelem(const float* __restrict__ el, int64_t k, TVElem<N, M>& e) {
+    const float4* src = reinterpret_cast<const float4*>(el + k * TVElem<N, M>::kFloats);
+    float4* dst = reinterpret_cast<float4*>(&e);
+#pragma unroll
+    for (int i = 0; i < TVElem<N, M>::kFloats / 4; ++i) dst[i] = __ldg(src + i);
+}
+
+// Step k >= 1 from that step's (F, u, Q) and (H, d, R).  With
+// S = H Q H^T + R = L L^T (Cholesky), U = L^{-1} H F, V = L^{-1} H Q and
+// w = L^{-1} (y - H u - d), Lemma 3's gain is K = Q H^T S^{-1} = V^T L^{-1}, so
+//   A = F - V^T U,  b = u + V^T w,  C = Q - V^T V,  eta = U^T w,  J = U^T U.
+template <int N, int M>
+KS_DEV void tv_element(const TVArgs& tv, const float* __restrict__ y, int64_t k, TVElem<N, M>& e, bool& bad) {
+    float F[N][N], Q[N][N], H[M][N], R[M][M], u[N], d[M], yk[M];
+    const float* Fk = tv.F + k * (N * N);
+    const float* Qk = tv.Q + k * (N * N);
+    const float* Hk = tv.H + k * (M * N);
+    const float* Rk = tv.R + k * (M * M);
+#pragma unroll
+    for (int a = 0; a < N; ++a) {
+#pragma unroll
+        for (int b = 0; b < N; ++b) F[a][b] = __ldg(Fk + a * N + b);
+#pragma unroll
+        for (int b = 0; b <= a; ++b) Q[a][b] = Q[b][a] = 0.5f * (__ldg(Qk + a * N + b) + __ldg(Qk + b * N + a));
+        u[a] = tv.u ? __ldg(tv.u + k * N + a) : 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < M; ++q) {
+#pragma unroll
+        for (int c = 0; c < N; ++c) H[q][c] = __ldg(Hk + q * N + c);
+#pragma unroll
+        for (int r = 0; r <= q; ++r) R[q][r] = 0.5f * (__ldg(Rk + q * M + r) + __ldg(Rk + r * M + q));
+        d[q] = tv.d ? __ldg(tv.d + k * M + q) : 0.f;
+        yk[q] = __ldg(y + k * M + q);
+    }
+    float HF[M][N], HQ[M][N], r0[M];
+#pragma unroll
+    for (int q = 0; q < M; ++q) {
+        float hu = d[q];
+#pragma unroll
+        for (int a = 0; a < N; ++a) {
+            float f = 0.f, g = 0.f;
+#pragma unroll
+            for (int c = 0; c < N; ++c) { f = fmaf(H[q][c], F[c][a], f); g = fmaf(H[q][c], Q[c][a], g); }
+            HF[q][a] = f;
+            HQ[q][a] = g;
+            hu = fmaf(H[q][a], u[a], hu);
+        }
+        r0[q] = yk[q] - hu;
+    }
+    float L[M][M], rd[M];
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+        float s = R[j][j];
+#pragma unroll
+        for (int c = 0; c < N; ++c) s = fmaf(HQ[j][c], H[j][c], s);
+#pragma unroll
+        for (int l = 0; l < j; ++l) s = fmaf(-L[j][l], L[j][l], s);
+        bad |= !(s > 0.f);
+        const float r = rsqrtf(fmaxf(s, 1e-37f));
+        L[j][j] = s * r;
+        rd[j] = r;
+#pragma unroll
+        for (int i = j + 1; i < M; ++i) {
+            float t = R[i][j];
+#pragma unroll
+            for (int c = 0; c < N; ++c) t = fmaf(HQ[i][c], H[j][c], t);
+#pragma unroll
+            for (int l = 0; l < j; ++l) t = fmaf(-L[i][l], L[j][l], t);
+            L[i][j] = t * r;
+        }
+    }
+    float V[M][N];   // forward substitution with L
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+        float t = r0[i];
+#pragma unroll
+        for (int l = 0; l < i; ++l) t = fmaf(-L[i][l], e.w[l], t);
+        e.w[i] = t * rd[i];
+#pragma unroll
+        for (int a = 0; a < N; ++a) {
+            float x = HF[i][a], v = HQ[i][a];
+#pragma unroll
+            for (int l = 0; l < i; ++l) { x = fmaf(-L[i][l], e.U[l * N + a], x); v = fmaf(-L[i][l], V[l][a], v); }
+            e.U[i * N + a] = x * rd[i];
+            V[i][a] = v * rd[i];
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < N; ++a) {
+        float bb = u[a];
+#pragma unroll
+        for (int q = 0; q < M; ++q) bb = fmaf(V[q][a], e.w[q], bb);
+        e.b[a] = bb;
+#pragma unroll
+        for (int b = 0; b < N; ++b) {
+            float x = F[a][b];
+#pragma unroll
+            for (int q = 0; q < M; ++q) x = fmaf(-V[q][a], e.U[q * N + b], x);
+            e.A[a * N + b] = x;
+        }
+#pragma unroll
+        for (int b = 0; b <= a; ++b) {
+            float c = Q[a][b];
+#pragma unroll
+            for (int q = 0; q < M; ++q) c = fmaf(-V[q][a], V[q][b], c);
+            e.C[sidx(a, b)] = c;
+        }
+    }
+}
+
+// Step 0 of a time-varying model (Lemma 3, k = 1) in FP64: the prior N(m0, P0)
+// is predicted with (F[0], u[0], Q[0]) and updated with y[0]; A = 0 and
+// U = w = 0, i.e. eta = J = 0 (the element does not depend on the state
+// before it).
+template <int N, int M>
+__device__ __noinline__ void tv_first_element(const TVArgs& tv, const float* __restrict__ y, TVElem<N, M>& e,
+                                              bool& bad) {
+    double Pm[N][N], mm[N], HP[M][N], S[M][M], L[M][M], t1[M][N], z[M];
+    for (int a = 0; a < N; ++a) {
+        double s = tv.u ? (double)tv.u[a] : 0.0;
+        for (int c = 0; c < N; ++c) s += (double)tv.F[a * N + c] * tv.m0[c];
+        mm[a] = s;
+    }
+    for (int a = 0; a < N; ++a)
+        for (int b = 0; b <= a; ++b) {           // P- = F P0 F^T + Q (lower, mirrored)
+            double s = 0.5 * ((double)tv.Q[a * N + b] + (double)tv.Q[b * N + a]);
+            for (int c = 0; c < N; ++c) {
+                double fp = 0.0;                 // (F P0)[a][c]
+                for (int l = 0; l < N; ++l) fp += (double)tv.F[a * N + l] * tv.P0[l * N + c];
+                s += fp * (double)tv.F[b * N + c];
+            }
+            Pm[a][b] = Pm[b][a] = s;
+        }
+    for (int q = 0; q < M; ++q)
+        for (int a = 0; a < N; ++a) {
+            double s = 0.0;
+            for (int c = 0; c < N; ++c) s += (double)tv.H[q * N + c] * Pm[c][a];
+            HP[q][a] = s;
+        }
+    for (int q = 0; q < M; ++q)
+        for (int r = 0; r <= q; ++r) {
+            double s = 0.5 * ((double)tv.R[q * M + r] + (double)tv.R[r * M + q]);
+            for (int c = 0; c < N; ++c) s += HP[q][c] * (double)tv.H[r * N + c];
+            S[q][r] = s;
+        }
+    for (int j = 0; j < M; ++j) {               // Cholesky S = L L^T
+        double s = S[j][j];
+        for (int l = 0; l < j; ++l) s -= L[j][l] * L[j][l];
+        bad |= !(s > 0.0);
+        L[j][j] = sqrt(s > 0.0 ? s : 1e-300);
+        for (int i = j + 1; i < M; ++i) {
+            double t = S[i][j];
+            for (int l = 0; l < j; ++l) t -= L[i][l] * L[j][l];
+            L[i][j] = t / L[j][j];
+        }
+    }
+    for (int q = 0; q < M; ++q) {               // z = L^{-1} (y - H m- - d), t1 = L^{-1} H P-
+        double s = (double)y[q] - (tv.d ? (double)tv.d[q] : 0.0);
+        for (int c = 0; c < N; ++c) s -= (double)tv.H[q * N + c] * mm[c];
+        for (int l = 0; l < q; ++l) s -= L[q][l] * z[l];
+        z[q] = s / L[q][q];
+        for (int a = 0; a < N; ++a) {
+            double t = HP[q][a];
+            for (int l = 0; l < q; ++l) t -= L[q][l] * t1[l][a];
+            t1[q][a] = t / L[q][q];
+        }
+    }
+    for (int a = 0; a < N; ++a) {               // b = m- + t1^T z, C = P- - t1^T t1
+        double s = mm[a];
+        for (int q = 0; q < M; ++q) s += t1[q][a] * z[q];
+        e.b[a] = (float)s;
+        for (int b = 0; b < N; ++b) e.A[a * N + b] = 0.f;
+        for (int b = 0; b <= a; ++b) {
+            double c = Pm[a][b];
+            for (int q = 0; q < M; ++q) c -= t1[q][a] * t1[q][b];
+            e.C[sidx(a, b)] = (float)c;
+        }
+    }
+    for (int a = 0; a < M * N; ++a) e.U[a] = 0.f;
+    for (int q = 0; q < M; ++q) e.w[q] = 0.f;
+}
+
+// Filtering elements of a time-varying model, one TVElem record per step
+// (el must be 16-byte aligned).  Block 0 also clears the scans' counters and
+// flags.
+template <int N, int M>
+__global__ void __launch_bounds__(256) tv_elements_kernel(TVArgs tv, const float* __restrict__ y, int64_t T,
+                                                          float* __restrict__ el, uint32_t* __restrict__ status,
+                                                          uint32_t* __restrict__ zero, int nzero) {
+    if (blockIdx.x == 0)
+        for (int i = threadIdx.x; i < nzero; i += blockDim.x) zero[i] = 0u;
+    bool bad = false;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < T;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        TVElem<N, M> e;
+        if (k == 0) tv_first_element<N, M>(tv, y, e, bad);
+        else tv_element<N, M>(tv, y, k, e, bad);
+        store_tvelem<N, M>(el, k, e);
+    }
+    if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicOr(status, ST_NUMERIC);
 }
 
 // ---------------------------------------------------------------- staging
@@ -816,8 +1139,8 @@ struct BlockScan {
 };
 
 // Lemma 5 element from a filtered mean and covariance (k = n when `last`).
-template <int N, int M>
-KS_DEV void build_selem_from(const ModelConst<N, M>& mc, const float (&xb)[N], const float (&P)[sym_size(N)],
+template <int N, int M, class MC>
+KS_DEV void build_selem_from(const MC& mc, const float (&xb)[N], const float (&P)[sym_size(N)],
                              bool last, SElem<N>& e, bool& bad) {
     if (last) {  // Lemma 5, k = n: E = 0, g = xbar_n, L = P_n
 #pragma unroll
@@ -836,14 +1159,18 @@ KS_DEV void build_selem_from(const ModelConst<N, M>& mc, const float (&xb)[N], c
 // from the posterior it has just produced and folds the thread's block of
 // them (Lemma 6, associativity lets the fold run forward), writing one
 // smoothing block aggregate per thread to `sagg` for the reverse scan.
-template <int N, int M, int NT, int CH, bool FROM_Y, bool SAGG, bool SEG>
+// With TV the elements are a time-varying model's TVElem records (`el`) and
+// the fused smoothing elements use the next step's transition from `tv`.
+template <int N, int M, int NT, int CH, bool FROM_Y, bool SAGG, bool SEG, bool TV>
 __global__ void __launch_bounds__(NT) filter_scan_kernel(const ModelConst<N, M>* __restrict__ mcg,
                                                          const float* __restrict__ y,
                                                          const float* __restrict__ el, int64_t ld,
                                                          int64_t T, float* __restrict__ fmean,
                                                          float* __restrict__ fcov, ScanState ss,
-                                                         float* __restrict__ sagg, Segs<N, M> segs) {
+                                                         float* __restrict__ sagg, Segs<N, M> segs,
+                                                         TVArgs tv) {
     static_assert(FROM_Y || !SEG, "segmented scans build their elements from y");
+    static_assert(!TV || (!FROM_Y && !SEG), "time-varying elements come materialised");
     using BS = BlockScan<FilterOp<N>, NT>;
     using SG = Stage<N>;
     constexpr int64_t TILE = (int64_t)NT * CH;
@@ -895,6 +1222,17 @@ __global__ void __launch_bounds__(NT) filter_scan_kernel(const ModelConst<N, M>*
                 acc = fcombine_meas<N, M>(acc, *cur.mc, b, w, bad);
             }
         }
+    } else if constexpr (TV) {
+        TVElem<N, M> te;
+        load_tvelem<N, M>(el, k0, te);
+        expand_meas<N, M>(te, te.b, te.w, acc);
+#pragma unroll 1
+        for (int i = 1; i < CH; ++i) {
+            const int64_t k = k0 + i;
+            if (k >= T) break;
+            load_tvelem<N, M>(el, k, te);
+            acc = fcombine_meas<N, M>(acc, te, te.b, te.w, bad);
+        }
     } else {
         acc = load_soa<N>(el, ld, k0);
 #pragma unroll 1
@@ -937,6 +1275,18 @@ __global__ void __launch_bounds__(NT) filter_scan_kernel(const ModelConst<N, M>*
                     meas_element<N, M>(*cur.mc, yk, b, w);
                     fadvance_meas<N, M>(st, *cur.mc, b, w, bad);
                 }
+            } else if constexpr (TV) {
+                TVElem<N, M> te;
+                load_tvelem<N, M>(el, k, te);
+                if (!has) {   // step 0: A = 0, U = w = 0
+#pragma unroll
+                    for (int a = 0; a < N; ++a) st.b[a] = te.b[a];
+#pragma unroll
+                    for (int a = 0; a < sym_size(N); ++a) st.C[a] = te.C[a];
+                    has = true;
+                } else {
+                    fadvance_meas<N, M>(st, te, te.b, te.w, bad);
+                }
             } else {
                 const FElem<N> e = load_soa<N>(el, ld, k);
                 if (!has) {
@@ -949,7 +1299,8 @@ __global__ void __launch_bounds__(NT) filter_scan_kernel(const ModelConst<N, M>*
             probe += finite_probe<N>(st.b, st.C);
             if constexpr (SAGG) {
                 SElem<N> e;
-                build_selem_from<N, M>(*cur.mc, st.b, st.C, cur.last(k), e, bad);
+                if constexpr (TV) build_selem_tv<N, M>(tv, k, T, st.b, st.C, e, bad);
+                else build_selem_from<N, M>(*cur.mc, st.b, st.C, cur.last(k), e, bad);
                 sacc = (i == 0) ? e : scombine<N>(sacc, e);
             }
             if constexpr (SG::kOn) {
@@ -1024,13 +1375,17 @@ struct RevReader {
 // scan's grid); the reverse scan visits them last block first.  With FROM_AGG
 // each thread's block aggregate comes from the forward scan (`sagg`);
 // otherwise it is folded here from the filtered moments.
-template <int N, int M, int NT, int CH, bool FROM_AGG, bool SEG>
+// With TV the elements come from a time-varying model's per-step transitions
+// (`tv`) instead of the constant model.
+template <int N, int M, int NT, int CH, bool FROM_AGG, bool SEG, bool TV>
 __global__ void __launch_bounds__(NT) smoother_scan_kernel(const ModelConst<N, M>* __restrict__ mcg,
                                                            const float* __restrict__ fmean,
                                                            const float* __restrict__ fcov, int64_t T,
                                                            float* __restrict__ smean,
                                                            float* __restrict__ scov, ScanState ss,
-                                                           const float* __restrict__ sagg, Segs<N, M> segs) {
+                                                           const float* __restrict__ sagg, Segs<N, M> segs,
+                                                           TVArgs tv) {
+    static_assert(!TV || !SEG, "time-varying models run unsegmented");
     using BS = BlockScan<SmootherOp<N>, NT>;
     using SG = Stage<N>;
     using RR = RevReader<N>;
@@ -1083,7 +1438,8 @@ __global__ void __launch_bounds__(NT) smoother_scan_kernel(const ModelConst<N, M
                     stage_read<N>(rd.buf(g), s, xb, P);
                     cur.backward(segs, lo + s);
                     SElem<N> e;
-                    build_selem_from<N, M>(*cur.mc, xb, P, cur.last(lo + s), e, bad);
+                    if constexpr (TV) build_selem_tv<N, M>(tv, lo + s, T, xb, P, e, bad);
+                    else build_selem_from<N, M>(*cur.mc, xb, P, cur.last(lo + s), e, bad);
                     acc = first ? e : scombine<N>(e, acc);
                     first = false;
                 }
@@ -1097,7 +1453,8 @@ __global__ void __launch_bounds__(NT) smoother_scan_kernel(const ModelConst<N, M
                 load_posterior<N>(fmean, fcov, k, xb, P);
                 cur.backward(segs, k);
                 SElem<N> e;
-                build_selem_from<N, M>(*cur.mc, xb, P, cur.last(k), e, bad);
+                if constexpr (TV) build_selem_tv<N, M>(tv, k, T, xb, P, e, bad);
+                else build_selem_from<N, M>(*cur.mc, xb, P, cur.last(k), e, bad);
                 acc = (i == 0) ? e : scombine<N>(e, acc);
             }
         }
@@ -1128,7 +1485,8 @@ __global__ void __launch_bounds__(NT) smoother_scan_kernel(const ModelConst<N, M
                     stage_read<N>(b, s, xb, P);
                     cur.backward(segs, lo + s);
                     SElem<N> e;
-                    build_selem_from<N, M>(*cur.mc, xb, P, cur.last(lo + s), e, bad);
+                    if constexpr (TV) build_selem_tv<N, M>(tv, lo + s, T, xb, P, e, bad);
+                    else build_selem_from<N, M>(*cur.mc, xb, P, cur.last(lo + s), e, bad);
                     if (!has) { st = SmootherOp<N>::state_of(e); has = true; }   // only k = T-1
                     else sadvance<N>(e, st);
                     stage_write<N>(b, s, st.g, st.L);     // the slot's input is already in registers
@@ -1149,7 +1507,8 @@ __global__ void __launch_bounds__(NT) smoother_scan_kernel(const ModelConst<N, M
                 load_posterior<N>(fmean, fcov, k, xb, P);
                 cur.backward(segs, k);
                 SElem<N> e;
-                build_selem_from<N, M>(*cur.mc, xb, P, cur.last(k), e, bad);
+                if constexpr (TV) build_selem_tv<N, M>(tv, k, T, xb, P, e, bad);
+                else build_selem_from<N, M>(*cur.mc, xb, P, cur.last(k), e, bad);
                 if (!has) { st = SmootherOp<N>::state_of(e); has = true; }
                 else sadvance<N>(e, st);
                 store_posterior<N>(smean, scov, k, st.g, st.L);

@@ -65,8 +65,17 @@ def test_argument_errors_need_no_device(ks):
     # T out of range and null / misaligned pointers are rejected before any CUDA call
     assert L.ks_smooth(ctypes.byref(m), None, 10, None, 0, None, None, None, None, None) == ks.KS_EINVAL
     assert L.ks_smooth(ctypes.byref(m), 16, 0, 256, 1 << 20, None, None, 16, 16, None) == ks.KS_EINVAL
+    # time-varying models: an unknown mode, a size without time-varying
+    # support, and a misaligned y are all rejected before any launch
+    tv2 = ks._KsModel(4, 2, 2, 0, 1, 0, 1, 1, 0, 1, 1, 1)
+    assert L.ks_smooth(ctypes.byref(tv2), 16, 10, 256, 1 << 30, None, None, 16, 16, None) == ks.KS_EUNSUPPORTED
+    tv8 = ks._KsModel(8, 4, 1, 0, 1, 0, 1, 1, 0, 1, 1, 1)
+    assert L.ks_smooth(ctypes.byref(tv8), 16, 10, 256, 1 << 30, None, None, 16, 16, None) == ks.KS_EUNSUPPORTED
+    assert L.ks_workspace_bytes(ctypes.byref(tv8), 10, ks.KS_WS_SMOOTH) == 0
     tv = ks._KsModel(4, 2, 1, 0, 1, 0, 1, 1, 0, 1, 1, 1)
-    assert L.ks_smooth(ctypes.byref(tv), 16, 10, 256, 1 << 30, None, None, 16, 16, None) == ks.KS_EUNSUPPORTED
+    assert L.ks_smooth(ctypes.byref(tv), 4, 10, 256, 1 << 30, None, None, 16, 16, None) == ks.KS_EINVAL
+    assert L.ks_workspace_bytes(ctypes.byref(tv), 10, ks.KS_WS_SMOOTH) == \
+        L.ks_workspace_bytes(ctypes.byref(tv), 10, ks.KS_WS_ELEMENTS) > 0
     other = ks._KsModel(5, 3, 0, 0, 1, 0, 1, 1, 0, 1, 1, 1)
     assert L.ks_smooth(ctypes.byref(other), 16, 10, 256, 1 << 30, None, None, 16, 16, None) == ks.KS_EUNSUPPORTED
     assert L.ks_filter_combine_batch(4, 10, None, None, None, 256, 256, None) == ks.KS_EINVAL

@@ -86,6 +86,32 @@ def test_paper_experiment_model(ks):
     check(ks, m, y)
 
 
+
+@pytest.mark.parametrize("p0", [1e-4, 1e6])
+def test_extreme_prior_first_element(ks, p0):
+    """The k = 1 element (prediction and update of N(m0, P0)) is built in
+    double-float arithmetic: with a near-exact or a diffuse prior (P- ~ 1e6
+    against R = 0.5) its update P- - K S K^T keeps FP32 accuracy.  T = 1, so
+    the output is that element alone."""
+    rng = np.random.default_rng(79)
+    m = workloads.wiener_velocity(2, dt=0.1, q=1.0, r=0.5, m0=np.array([30.0, -20.0, 1.0, 2.0]),
+                                  P0=p0 * np.eye(4))
+    _, y = workloads.simulate(m, 1, rng)
+    check(ks, m, y)
+
+
+@pytest.mark.parametrize("p0", [1e-4, 25.0])
+def test_prior_scales(ks, p0):
+    """A near-exact and a broad prior over a long sequence (m0 far from the
+    data).  A very diffuse one (P0 ~ 1e6 I) is outside the FP32 scan's
+    reach: Lemma 4's I + C_i J_j then has entries ~1e8."""
+    rng = np.random.default_rng(80)
+    m = workloads.wiener_velocity(2, dt=0.1, q=1.0, r=0.5, m0=np.array([30.0, -20.0, 1.0, 2.0]),
+                                  P0=p0 * np.eye(4))
+    _, y = workloads.simulate(m, 2000, rng)
+    check(ks, m, y)
+
+
 def test_random_model_with_offsets(ks):
     """A dense random stable model with non-zero u and d."""
     rng = np.random.default_rng(78)

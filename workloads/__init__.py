@@ -9,7 +9,8 @@ Models follow the linear/Gaussian state-space form of Section IV,
     x_k = F x_{k-1} + u + q_{k-1},  q ~ N(0, Q)
     y_k = H x_k + d + r_k,          r ~ N(0, R),   x_0 ~ N(m0, P0),
 
-with the time-invariant parameters of every workload used here.
+with time-invariant parameters, except the time-varying workloads at the end
+(one parameter set per step, Section II's F_{k-1}, Q_{k-1}, H_k, R_k).
 
 Precision convention: F, u, Q, H, d, R and y are rounded to FP32 once (the
 GPU computes in FP32) and kept as float64 arrays holding those FP32 values, so
@@ -47,11 +48,15 @@ class Model:
 
     @property
     def nx(self) -> int:
-        return self.F.shape[0]
+        return self.F.shape[-1]
 
     @property
     def ny(self) -> int:
-        return self.H.shape[0]
+        return self.H.shape[-2]
+
+    @property
+    def time_varying(self) -> bool:
+        return self.F.ndim == 3
 
     def f32(self) -> dict:
         """The FP32 arrays the GPU path reads (m0, P0 stay FP64)."""
@@ -271,3 +276,134 @@ def serving_measurements(models: dict, T: int, seed: int = SEED_BASE + 5) -> dic
             _, y = simulate(m, T, rng)
             out[nx].append(np.ascontiguousarray(y.astype(np.float32)))
     return out
+
+
+# ---------------------------------------------------------------- time-varying workloads
+def _wiener_blocks(dts: np.ndarray, dim: int, q: float):
+    """Per-step Wiener-velocity F_k, Q_k for sampling intervals dts [T]."""
+    T = dts.shape[0]
+    nx = 2 * dim
+    I = np.eye(dim)
+    F = np.zeros((T, nx, nx))
+    F[:, :dim, :dim] = I
+    F[:, dim:, dim:] = I
+    F[:, :dim, dim:] = dts[:, None, None] * I
+    Q = np.zeros((T, nx, nx))
+    Q[:, :dim, :dim] = q * (dts ** 3 / 3)[:, None, None] * I
+    Q[:, :dim, dim:] = q * (dts ** 2 / 2)[:, None, None] * I
+    Q[:, dim:, :dim] = q * (dts ** 2 / 2)[:, None, None] * I
+    Q[:, dim:, dim:] = q * dts[:, None, None] * I
+    return F, Q
+
+
+def irregular_tracking(T: int, seed: int, dim: int = 2, q: float = 1.0, dt_lo: float = 0.02,
+                       dt_hi: float = 0.5, r_lo: float = 0.25, r_hi: float = 4.0) -> Sequence:
+    """Time-varying workload: the Wiener-velocity model of Section V observed
+    at irregular times.  The interval before step k is dt_k ~ log-uniform
+    [dt_lo, dt_hi] (F_k, Q_k follow from it) and the sensor noise of step k is
+    R_k = r_k I with r_k ~ log-uniform [r_lo, r_hi]; H = [I 0], u = d = 0,
+    m0 = 0, P0 = I.  The states are drawn exactly (per axis, the velocity is a
+    cumulative sum of its noise and the position integrates it), so T = 2^20
+    takes well under a second."""
+    rng = np.random.default_rng(np.random.PCG64(seed))
+    nx = 2 * dim
+    dts = np.exp(rng.uniform(math.log(dt_lo), math.log(dt_hi), size=T))
+    rs = np.exp(rng.uniform(math.log(r_lo), math.log(r_hi), size=T))
+    F, Q = _wiener_blocks(dts, dim, q)
+    H = np.broadcast_to(np.hstack([np.eye(dim), np.zeros((dim, dim))]), (T, dim, nx)).copy()
+    R = rs[:, None, None] * np.eye(dim)[None]
+    model = Model(F=_f32(F), u=np.zeros((T, nx)), Q=_f32(Q), H=_f32(H), d=np.zeros((T, dim)), R=_f32(R),
+                  m0=np.zeros(nx), P0=np.eye(nx), name=f"irregular_tracking_{dim}d")
+    # exact simulation with the FP32-rounded parameters: per axis the step
+    # noise (w_p, w_v) ~ N(0, q [[dt^3/3, dt^2/2], [dt^2/2, dt]])
+    Fd, Qd = model.F, model.Q
+    x0 = rng.standard_normal(nx)
+    a = Qd[:, 0, 0]
+    c = Qd[:, 0, dim]
+    b = Qd[:, dim, dim]
+    l11 = np.sqrt(a)
+    l21 = c / l11
+    l22 = np.sqrt(np.maximum(b - l21 * l21, 0.0))
+    z = rng.standard_normal((T, 2, dim))
+    wp = l11[:, None] * z[:, 0]
+    wv = l21[:, None] * z[:, 0] + l22[:, None] * z[:, 1]
+    v = x0[dim:][None, :] + np.cumsum(wv, axis=0)                 # v_k
+    vprev = np.vstack([x0[dim:][None, :], v[:-1]])
+    p = x0[:dim][None, :] + np.cumsum(Fd[:, 0, dim][:, None] * vprev + wp, axis=0)
+    X = np.hstack([p, v])
+    Y = p + np.sqrt(model.R[:, 0, 0])[:, None] * rng.standard_normal((T, dim))
+    return Sequence(model, _f32(Y), np.vstack([x0[None, :], X]))
+
+
+def random_time_varying(nx: int, ny: int, T: int, rng: np.random.Generator, q: float = 0.1,
+                        r: float = 0.5) -> Sequence:
+    """Dense time-varying model: per step F_k = O_k diag(U[0.9, 0.99]) with
+    O_k Haar-orthogonal, Q_k = q (I + G G^T / nx), H_k ~ N(0, 1/nx),
+    R_k = r (I + G' G'^T / ny), u_k ~ N(0, 0.1), d_k ~ N(0, 0.1); m0 ~ N(0, 1),
+    P0 = 2 I.  The states are simulated step by step (small T only)."""
+    G = rng.standard_normal((T, nx, nx))
+    O, Rq = np.linalg.qr(G)
+    O = O * np.sign(np.diagonal(Rq, axis1=1, axis2=2))[:, None, :]
+    F = O * rng.uniform(0.9, 0.99, size=(T, 1, nx))
+    A = rng.standard_normal((T, nx, nx))
+    Q = q * (np.eye(nx)[None] + A @ A.transpose(0, 2, 1) / nx)
+    H = rng.standard_normal((T, ny, nx)) / math.sqrt(nx)
+    B = rng.standard_normal((T, ny, ny))
+    R = r * (np.eye(ny)[None] + B @ B.transpose(0, 2, 1) / ny)
+    u = 0.3 * rng.standard_normal((T, nx))
+    d = 0.3 * rng.standard_normal((T, ny))
+    model = Model(F=_f32(F), u=_f32(u), Q=_f32(Q), H=_f32(H), d=_f32(d), R=_f32(R),
+                  m0=rng.standard_normal(nx), P0=2.0 * np.eye(nx), name=f"random_time_varying_{nx}x{ny}")
+    x = model.m0 + _chol_psd(model.P0) @ rng.standard_normal(nx)
+    X = np.empty((T, nx))
+    Y = np.empty((T, ny))
+    for k in range(T):
+        x = model.F[k] @ x + model.u[k] + _chol_psd(model.Q[k]) @ rng.standard_normal(nx)
+        X[k] = x
+        Y[k] = model.H[k] @ x + model.d[k] + _chol_psd(model.R[k]) @ rng.standard_normal(ny)
+    return Sequence(model, _f32(Y), np.vstack([model.m0[None, :], X]))
+
+
+# ---------------------------------------------------------------- discrete-state workloads
+@dataclass
+class HmmSequence:
+    pi: np.ndarray     # [K] prior of x_0
+    Pi: np.ndarray     # [K, K] row-stochastic transitions
+    lik: np.ndarray    # [T, K] p(y_k | x_k = j), FP32-representable
+    x: np.ndarray = field(default=None, repr=False)   # true states [T]
+
+    @property
+    def T(self) -> int:
+        return self.lik.shape[0]
+
+    @property
+    def K(self) -> int:
+        return self.pi.shape[0]
+
+
+def hmm_sequence(K: int, T: int, seed: int, stay: float = 0.95, sigma: float = 0.6) -> HmmSequence:
+    """Regime-switching workload: K states, each kept with probability `stay`
+    per step and otherwise left for another drawn from a Dirichlet(1) row;
+    the measurement is y_k ~ N(x_k, sigma^2) (state j has mean j), given to
+    the filter as its Gaussian likelihood row lik[k, j] = N(y_k; j, sigma^2).
+    pi uniform.  Pi and lik are rounded to FP32 (the rows of Pi renormalised
+    in FP64 first)."""
+    rng = np.random.default_rng(np.random.PCG64(seed))
+    off = rng.dirichlet(np.ones(K - 1), size=K) if K > 1 else np.zeros((1, 0))
+    Pi = np.zeros((K, K))
+    for i in range(K):
+        Pi[i, i] = stay if K > 1 else 1.0
+        Pi[i, [j for j in range(K) if j != i]] = (1.0 - stay) * off[i]
+    Pi = _f32(Pi / Pi.sum(axis=1, keepdims=True))
+    pi = _f32(np.full(K, 1.0 / K))
+    x = np.empty(T, dtype=np.int64)
+    u = rng.random(T + 1)
+    cum = np.cumsum(Pi, axis=1)
+    s = int(np.searchsorted(np.cumsum(pi), u[0] * np.cumsum(pi)[-1]))
+    for k in range(T):
+        s = int(min(np.searchsorted(cum[s], u[k + 1] * cum[s, -1]), K - 1))
+        x[k] = s
+    y = x + sigma * rng.standard_normal(T)
+    mu = np.arange(K, dtype=np.float64)
+    lik = np.exp(-0.5 * ((y[:, None] - mu[None, :]) / sigma) ** 2) / (sigma * math.sqrt(2 * math.pi))
+    return HmmSequence(pi, Pi, _f32(lik), x)
