@@ -78,6 +78,7 @@ extern "C" {
  * from step k-1 with F[k], u[k], Q[k] (F[0], u[0], Q[0] take the prior
  * N(m0, P0) to step 0) and observed as y[k] = H[k] x_k + d[k] + r_k with
  * r_k ~ N(0, R[k]): Section II's model with its indices shifted by one.
+ * Each of these arrays must start on a 16-byte boundary (KS_EINVAL otherwise).
  * Time-varying models are accepted by ks_smooth and ks_smooth_traced for
  * nx in {2, 4, 6} (KS_EUNSUPPORTED elsewhere), and need
  * ks_workspace_bytes(m, T, KS_WS_SMOOTH) bytes, which for them equals the

@@ -33,31 +33,60 @@
 namespace ks {
 namespace hmm {
 
+// Each element and state is padded to an odd number of floats, so that the
+// block scan's per-thread shared-memory copies (one element per thread,
+// thread-contiguous) fall in distinct banks.
 template <int K>
 struct FE {
     float f[K * K];
     float lg[K];
+    float pad[(K * K + K) % 2 == 0 ? 1 : 0];
 };
 template <int K>
 struct FS {
     float p[K];
     float L;
+    float pad[(K + 1) % 2 == 0 ? 1 : 0];
 };
 template <int K>
 struct SE {
     float a[K * K];
+    float pad[(K * K) % 2 == 0 ? 1 : 0];
 };
 template <int K>
 struct SS {
     float s[K];
+    float pad[K % 2 == 0 ? 1 : 0];
 };
 
-// Model constants: the transition matrix and the prior predicted to step 1.
+// Model constants: the transition matrix, its transpose and the prior
+// predicted to step 1 (16-byte aligned: rows are read as float4).
 template <int K>
-struct Const {
+struct alignas(16) Const {
     float Pi[K * K];
+    float PiT[K * K];
     float q1[K];   // p(x_1) = (pi Pi)
+    float pad[(4 - K % 4) % 4];
 };
+
+// Row r of a K x K shared-memory matrix into registers (float4 when K % 4 == 0).
+template <int K>
+KS_DEV void load_row(const float* __restrict__ M, int r, float (&v)[K]) {
+    if constexpr (K % 4 == 0) {
+        const float4* p = reinterpret_cast<const float4*>(M + r * K);
+#pragma unroll
+        for (int i = 0; i < K / 4; ++i) {
+            const float4 q = p[i];
+            v[4 * i] = q.x;
+            v[4 * i + 1] = q.y;
+            v[4 * i + 2] = q.z;
+            v[4 * i + 3] = q.w;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < K; ++i) v[i] = M[r * K + i];
+    }
+}
 
 template <int K>
 KS_DEV void set_identity(FE<K>& e) {
@@ -80,13 +109,16 @@ KS_DEV void set_identity(SE<K>& e) {
 // Likelihood row of step k scaled to a maximum of 1; returns log of the
 // maximum (a row with no positive finite maximum is flagged).
 template <int K>
-KS_DEV float load_lik(const float* __restrict__ lik, int64_t k, float (&l)[K], bool& bad) {
+KS_DEV void load_raw(const float* __restrict__ src, int64_t k, float (&v)[K]) {
+#pragma unroll
+    for (int x = 0; x < K; ++x) v[x] = __ldg(src + k * K + x);
+}
+
+template <int K>
+KS_DEV float scale_lik(float (&l)[K], bool& bad) {
     float m = 0.f;
 #pragma unroll
-    for (int x = 0; x < K; ++x) {
-        l[x] = __ldg(lik + k * K + x);
-        m = fmaxf(m, l[x]);
-    }
+    for (int x = 0; x < K; ++x) m = fmaxf(m, l[x]);
     bad |= !(m > 0.f) || !(m <= 3.0e38f);
     const float r = 1.f / m;
 #pragma unroll
@@ -94,19 +126,24 @@ KS_DEV float load_lik(const float* __restrict__ lik, int64_t k, float (&l)[K], b
     return __logf(m);
 }
 
+template <int K>
+KS_DEV float load_lik(const float* __restrict__ lik, int64_t k, float (&l)[K], bool& bad) {
+    load_raw<K>(lik, k, l);
+    return scale_lik<K>(l, bad);
+}
+
 // Definition 1, a_i (x) a_j for general elements (i earlier).  With
 // w(y) = exp(lg_j(y) - max lg_j):
 //   d(z) = sum_y f_i(y | z) w(y),  f_ij(x | z) = sum_y f_i(y | z) w(y) f_j(x | y) / d(z),
 //   lg_ij(z) = lg_i(z) + max lg_j + log d(z).
 template <int K>
-KS_DEV FE<K> fcombine(const FE<K>& ei, const FE<K>& ej, bool& bad) {
+KS_DEV FE<K> fcombine(FE<K> ei, const FE<K>& ej, bool& bad) {   // ei is overwritten row by row
     float mx = ej.lg[0];
 #pragma unroll
     for (int y = 1; y < K; ++y) mx = fmaxf(mx, ej.lg[y]);
     float w[K];
 #pragma unroll
     for (int y = 0; y < K; ++y) w[y] = __expf(ej.lg[y] - mx);
-    FE<K> r;
 #pragma unroll
     for (int z = 0; z < K; ++z) {
         float fw[K], d = 0.f;
@@ -122,11 +159,11 @@ KS_DEV FE<K> fcombine(const FE<K>& ei, const FE<K>& ej, bool& bad) {
             float s = 0.f;
 #pragma unroll
             for (int y = 0; y < K; ++y) s = fmaf(fw[y], ej.f[y * K + x], s);
-            r.f[z * K + x] = s * rd;
+            ei.f[z * K + x] = s * rd;
         }
-        r.lg[z] = ei.lg[z] + mx + __logf(d);
+        ei.lg[z] += mx + __logf(d);
     }
-    return r;
+    return ei;
 }
 
 // Prefix state (identical rows p, constant L) (x) general element.
@@ -160,23 +197,32 @@ KS_DEV void fadvance(FS<K>& st, const FE<K>& e, bool& bad) {
 // of its scale (see the header).  Pi is read from shared memory.
 template <int K>
 KS_DEV void ffold_step(FE<K>& acc, const float* __restrict__ Pi, const float (&l)[K], float lm, bool& bad) {
+    float row[K][K];   // row[z][x] accumulates (f Pi)[z][x], one Pi row at a time
+#pragma unroll
+    for (int z = 0; z < K; ++z)
+#pragma unroll
+        for (int x = 0; x < K; ++x) row[z][x] = 0.f;
+#pragma unroll
+    for (int y = 0; y < K; ++y) {
+        float pr[K];
+        load_row<K>(Pi, y, pr);
+#pragma unroll
+        for (int z = 0; z < K; ++z)
+#pragma unroll
+            for (int x = 0; x < K; ++x) row[z][x] = fmaf(acc.f[z * K + y], pr[x], row[z][x]);
+    }
 #pragma unroll
     for (int z = 0; z < K; ++z) {
-        float row[K];
-#pragma unroll
-        for (int x = 0; x < K; ++x) {
-            float s = 0.f;
-#pragma unroll
-            for (int y = 0; y < K; ++y) s = fmaf(acc.f[z * K + y], Pi[y * K + x], s);
-            row[x] = s * l[x];
-        }
         float r = 0.f;
 #pragma unroll
-        for (int x = 0; x < K; ++x) r += row[x];
+        for (int x = 0; x < K; ++x) {
+            row[z][x] *= l[x];
+            r += row[z][x];
+        }
         bad |= !(r > 0.f);
         const float rr = 1.f / r;
 #pragma unroll
-        for (int x = 0; x < K; ++x) acc.f[z * K + x] = row[x] * rr;
+        for (int x = 0; x < K; ++x) acc.f[z * K + x] = row[z][x] * rr;
         acc.lg[z] += lm + __logf(r);
     }
 }
@@ -222,11 +268,17 @@ KS_DEV void fadvance_step(FS<K>& st, const float* __restrict__ Pi, const float (
                           bool& bad) {
     float v[K], c = 0.f;
 #pragma unroll
-    for (int x = 0; x < K; ++x) {
-        float s = 0.f;
+    for (int x = 0; x < K; ++x) v[x] = 0.f;
 #pragma unroll
-        for (int y = 0; y < K; ++y) s = fmaf(st.p[y], Pi[y * K + x], s);
-        v[x] = s * l[x];
+    for (int y = 0; y < K; ++y) {
+        float pr[K];
+        load_row<K>(Pi, y, pr);
+#pragma unroll
+        for (int x = 0; x < K; ++x) v[x] = fmaf(st.p[y], pr[x], v[x]);
+    }
+#pragma unroll
+    for (int x = 0; x < K; ++x) {
+        v[x] *= l[x];
         c += v[x];
     }
     bad |= !(c > 0.f);
@@ -243,13 +295,14 @@ KS_DEV void fadvance_step(FS<K>& st, const float* __restrict__ Pi, const float (
 // Smoothing element of step k from its filtered marginal p (k < n):
 // a(x | z) = p(x) Pi[x][z] / sum_x' p(x') Pi[x'][z].
 template <int K>
-KS_DEV void selem(SE<K>& e, const float* __restrict__ Pi, const float (&p)[K], bool& bad) {
+KS_DEV void selem(SE<K>& e, const float* __restrict__ PiT, const float (&p)[K], bool& bad) {
 #pragma unroll
     for (int z = 0; z < K; ++z) {
-        float d = 0.f;
+        float pc[K], d = 0.f;
+        load_row<K>(PiT, z, pc);   // column z of Pi
 #pragma unroll
         for (int x = 0; x < K; ++x) {
-            e.a[z * K + x] = p[x] * Pi[x * K + z];
+            e.a[z * K + x] = p[x] * pc[x];
             d += e.a[z * K + x];
         }
         bad |= !(d > 0.f);
@@ -271,18 +324,21 @@ KS_DEV void selem_last(SE<K>& e, const float (&p)[K]) {
 // Definition 2 in matrix form: (a_i (x) a_j)[z][x] = sum_y a_j[z][y] a_i[y][x]
 // (i earlier), i.e. the product a_j a_i.
 template <int K>
-KS_DEV SE<K> smatmul(const SE<K>& l, const SE<K>& r) {   // l r
-    SE<K> o;
+KS_DEV SE<K> smatmul(SE<K> l, const SE<K>& r) {   // l r, l overwritten row by row
 #pragma unroll
-    for (int z = 0; z < K; ++z)
+    for (int z = 0; z < K; ++z) {
+        float o[K];
 #pragma unroll
         for (int x = 0; x < K; ++x) {
             float s = 0.f;
 #pragma unroll
             for (int y = 0; y < K; ++y) s = fmaf(l.a[z * K + y], r.a[y * K + x], s);
-            o.a[z * K + x] = s;
+            o[x] = s;
         }
-    return o;
+#pragma unroll
+        for (int x = 0; x < K; ++x) l.a[z * K + x] = o[x];
+    }
+    return l;
 }
 
 template <int K>
@@ -351,7 +407,9 @@ __global__ void __launch_bounds__(64) hmm_prep_kernel(const float* __restrict__ 
         const float v = Pi[e];
         bad |= !(v >= 0.f) || !(v <= 3.0e38f);
         out->Pi[e] = v;
+        out->PiT[(e % K) * K + e / K] = v;
     }
+    for (int e = t; e < (4 - K % 4) % 4; e += blockDim.x) out->pad[e] = 0.f;
     for (int x = t; x < K; x += blockDim.x) {
         float s = 0.f;
         for (int y = 0; y < K; ++y) s = fmaf(pi[y], Pi[y * K + x], s);
@@ -378,7 +436,7 @@ __global__ void __launch_bounds__(NT) hmm_filter_kernel(const Const<K>* __restri
                                                         ScanState ss, float* __restrict__ sagg) {
     using BS = BlockScan<FilterOp<K>, NT>;
     constexpr int64_t TILE = (int64_t)NT * CH;
-    __shared__ Const<K> mc;
+    __shared__ __align__(16) Const<K> mc;
     __shared__ typename BS::Smem bsm;
     __shared__ int s_tile;
     const int tid = threadIdx.x;
@@ -409,11 +467,16 @@ __global__ void __launch_bounds__(NT) hmm_filter_kernel(const Const<K>* __restri
         } else {
             step_element<K>(acc, mc.Pi, l, lm, bad);
         }
+        // the next step's likelihood row is loaded while the current one folds
+        float ln[K];
+        const int last = (int)((k0 + CH <= T ? k0 + CH : T) - k0);
+        if (1 < last) load_raw<K>(lik, k0 + 1, ln);
 #pragma unroll 1
-        for (int i = 1; i < CH; ++i) {
-            const int64_t k = k0 + i;
-            if (k >= T) break;
-            const float lmk = load_lik<K>(lik, k, l, bad);
+        for (int i = 1; i < last; ++i) {
+#pragma unroll
+            for (int x = 0; x < K; ++x) l[x] = ln[x];
+            if (i + 1 < last) load_raw<K>(lik, k0 + i + 1, ln);
+            const float lmk = scale_lik<K>(l, bad);
             ffold_step<K>(acc, mc.Pi, l, lmk, bad);
         }
     }
@@ -427,12 +490,17 @@ __global__ void __launch_bounds__(NT) hmm_filter_kernel(const Const<K>* __restri
     if (valid) {
         SE<K> sacc;
         float comp = 0.f, probe = 0.f;
+        const int last = (int)((k0 + CH <= T ? k0 + CH : T) - k0);
+        float ln[K];
+        load_raw<K>(lik, k0, ln);
 #pragma unroll 1
-        for (int i = 0; i < CH; ++i) {
+        for (int i = 0; i < last; ++i) {
             const int64_t k = k0 + i;
-            if (k >= T) break;
             float l[K];
-            const float lm = load_lik<K>(lik, k, l, bad);
+#pragma unroll
+            for (int x = 0; x < K; ++x) l[x] = ln[x];
+            if (i + 1 < last) load_raw<K>(lik, k + 1, ln);
+            const float lm = scale_lik<K>(l, bad);
             if (!has) {   // only step 1
                 first_state<K>(st, mc.q1, l, lm, bad);
                 has = true;
@@ -448,10 +516,10 @@ __global__ void __launch_bounds__(NT) hmm_filter_kernel(const Const<K>* __restri
             probe += st.L;
             SE<K> e;
             if (k == T - 1) selem_last<K>(e, st.p);
-            else selem<K>(e, mc.Pi, st.p, bad);
+            else selem<K>(e, mc.PiT, st.p, bad);
             sacc = (i == 0) ? e : smatmul<K>(e, sacc);   // a_k0 (x) ... (x) a_k = a_k ... a_k0
         }
-        store_plain(sagg + (k0 / CH) * (int64_t)K * K, sacc);
+        store_plain(sagg + (k0 / CH) * (int64_t)(sizeof(SE<K>) / 4), sacc);
         bad |= !isfinite(probe);
     }
     if (__any_sync(kFull, bad) && (tid & 31) == 0) atomicOr(ss.status, ST_NUMERIC);
@@ -466,7 +534,7 @@ __global__ void __launch_bounds__(NT) hmm_smoother_kernel(const Const<K>* __rest
                                                           float* __restrict__ smooth, ScanState ss,
                                                           const float* __restrict__ sagg) {
     using BS = BlockScan<SmootherOp<K>, NT>;
-    __shared__ Const<K> mc;
+    __shared__ __align__(16) Const<K> mc;
     __shared__ typename BS::Smem bsm;
     __shared__ int s_tile;
     const int tid = threadIdx.x;
@@ -482,7 +550,7 @@ __global__ void __launch_bounds__(NT) hmm_smoother_kernel(const Const<K>* __rest
     bool bad = false;
 
     SE<K> acc;
-    if (valid) acc = load_cg<SE<K>>(sagg + c * (int64_t)K * K);
+    if (valid) acc = load_cg<SE<K>>(sagg + c * (int64_t)(sizeof(SE<K>) / 4));
     else set_identity<K>(acc);
 
     SS<K> st;
@@ -491,14 +559,17 @@ __global__ void __launch_bounds__(NT) hmm_smoother_kernel(const Const<K>* __rest
 
     if (valid) {
         float probe = 0.f;
+        float pn[K];
+        load_raw<K>(filt, khi, pn);
 #pragma unroll 1
         for (int64_t k = khi; k >= klo; --k) {
             float p[K];
 #pragma unroll
-            for (int x = 0; x < K; ++x) p[x] = __ldg(filt + k * K + x);
+            for (int x = 0; x < K; ++x) p[x] = pn[x];
+            if (k > klo) load_raw<K>(filt, k - 1, pn);
             SE<K> e;
             if (k == T - 1) selem_last<K>(e, p);
-            else selem<K>(e, mc.Pi, p, bad);
+            else selem<K>(e, mc.PiT, p, bad);
             if (!has) { st = SmootherOp<K>::state_of(e); has = true; }   // only k = T - 1
             else SmootherOp<K>::advance(st, e, bad);
 #pragma unroll

@@ -275,6 +275,9 @@ struct Impl {
                          float* fc, float* sm, float* sc, cudaStream_t st, void* const* ev) {
         if (!m->F || !m->Q || !m->H || !m->R || !m->m0 || !m->P0) return KS_EINVAL;
         if (m->time_varying != 1) return KS_EUNSUPPORTED;
+        if (!aligned16(m->F) || !aligned16(m->Q) || !aligned16(m->H) || !aligned16(m->R) ||
+            (m->u && !aligned16(m->u)) || (m->d && !aligned16(m->d)))
+            return KS_EINVAL;   // per-step rows are read with vector loads
         if (T < 1 || T > 0x7fffffffLL) return KS_EINVAL;
         const Layout L = layout(T);
         if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) != 0 || ws_bytes < L.bytes_elements) return KS_EINVAL;

@@ -284,9 +284,9 @@ struct Cursor {
 };
 
 // ---------------------------------------------------------------- time-varying models
-// Per-step model arrays of one time-varying sequence (device, row-major FP32):
-// F [T][N][N], u [T][N] or null, Q [T][N][N], H [T][M][N], d [T][M] or null,
-// R [T][M][M]; m0 [N], P0 [N][N] FP64.  Step k is predicted from step k - 1
+// Per-step model arrays of one time-varying sequence (device, row-major FP32,
+// each 16-byte aligned): F [T][N][N], u [T][N] or null, Q [T][N][N],
+// H [T][M][N], d [T][M] or null, R [T][M][M]; m0 [N], P0 [N][N] FP64.  Step k is predicted from step k - 1
 // with F[k], u[k], Q[k] (F[0] maps the prior N(m0, P0) to step 0) and observed
 // through H[k], d[k], R[k] (the model of Section II with its indices shifted
 // to start at 0).
@@ -294,6 +294,34 @@ struct TVArgs {
     const float *F, *u, *Q, *H, *d, *R;
     const double *m0, *P0;
 };
+
+// COUNT consecutive floats of step k of a step-major array whose base is
+// 16-byte aligned: float4 loads when a step's block is a multiple of 16
+// bytes, float2 when of 8, scalar otherwise.
+template <int COUNT>
+KS_DEV void load_step(const float* __restrict__ base, int64_t k, float* __restrict__ dst) {
+    const float* p = base + k * COUNT;
+    if constexpr (COUNT % 4 == 0) {
+#pragma unroll
+        for (int i = 0; i < COUNT / 4; ++i) {
+            const float4 q = __ldg(reinterpret_cast<const float4*>(p) + i);
+            dst[4 * i] = q.x;
+            dst[4 * i + 1] = q.y;
+            dst[4 * i + 2] = q.z;
+            dst[4 * i + 3] = q.w;
+        }
+    } else if constexpr (COUNT % 2 == 0) {
+#pragma unroll
+        for (int i = 0; i < COUNT / 2; ++i) {
+            const float2 q = __ldg(reinterpret_cast<const float2*>(p) + i);
+            dst[2 * i] = q.x;
+            dst[2 * i + 1] = q.y;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < COUNT; ++i) dst[i] = __ldg(p + i);
+    }
+}
 
 // One step's transition (what the Lemma 5 element of the step before reads).
 template <int N>
@@ -305,16 +333,18 @@ struct Trans {
 
 template <int N>
 KS_DEV void load_trans(const TVArgs& tv, int64_t k, Trans<N>& t) {
-    const float* F = tv.F + k * (N * N);
-    const float* Q = tv.Q + k * (N * N);
+    float Q[N * N];
+    load_step<N * N>(tv.F, k, t.F);
+    load_step<N * N>(tv.Q, k, Q);
+    if (tv.u) load_step<N>(tv.u, k, t.u);
+    else {
 #pragma unroll
-    for (int a = 0; a < N * N; ++a) t.F[a] = __ldg(F + a);
-#pragma unroll
-    for (int a = 0; a < N; ++a) t.u[a] = tv.u ? __ldg(tv.u + k * N + a) : 0.f;
+        for (int a = 0; a < N; ++a) t.u[a] = 0.f;
+    }
 #pragma unroll
     for (int a = 0; a < N; ++a)
 #pragma unroll
-        for (int b = 0; b <= a; ++b) t.Q[sidx(a, b)] = 0.5f * (__ldg(Q + a * N + b) + __ldg(Q + b * N + a));
+        for (int b = 0; b <= a; ++b) t.Q[sidx(a, b)] = 0.5f * (Q[a * N + b] + Q[b * N + a]);
 }
 
 // Lemma 5 element of step k of a time-varying sequence of T steps: the
@@ -683,26 +713,31 @@ KS_DEV void load_tvelem(const float* __restrict__ el, int64_t k, TVElem<N, M>& e
 template <int N, int M>
 KS_DEV void tv_element(const TVArgs& tv, const float* __restrict__ y, int64_t k, TVElem<N, M>& e, bool& bad) {
     float F[N][N], Q[N][N], H[M][N], R[M][M], u[N], d[M], yk[M];
-    const float* Fk = tv.F + k * (N * N);
-    const float* Qk = tv.Q + k * (N * N);
-    const float* Hk = tv.H + k * (M * N);
-    const float* Rk = tv.R + k * (M * M);
+    {
+        float Qr[N * N], Rr[M * M];
+        load_step<N * N>(tv.F, k, &F[0][0]);
+        load_step<N * N>(tv.Q, k, Qr);
+        load_step<M * N>(tv.H, k, &H[0][0]);
+        load_step<M * M>(tv.R, k, Rr);
+        load_step<M>(y, k, yk);
+        if (tv.u) load_step<N>(tv.u, k, u);
+        else {
 #pragma unroll
-    for (int a = 0; a < N; ++a) {
+            for (int a = 0; a < N; ++a) u[a] = 0.f;
+        }
+        if (tv.d) load_step<M>(tv.d, k, d);
+        else {
 #pragma unroll
-        for (int b = 0; b < N; ++b) F[a][b] = __ldg(Fk + a * N + b);
+            for (int q = 0; q < M; ++q) d[q] = 0.f;
+        }
 #pragma unroll
-        for (int b = 0; b <= a; ++b) Q[a][b] = Q[b][a] = 0.5f * (__ldg(Qk + a * N + b) + __ldg(Qk + b * N + a));
-        u[a] = tv.u ? __ldg(tv.u + k * N + a) : 0.f;
-    }
+        for (int a = 0; a < N; ++a)
 #pragma unroll
-    for (int q = 0; q < M; ++q) {
+            for (int b = 0; b <= a; ++b) Q[a][b] = Q[b][a] = 0.5f * (Qr[a * N + b] + Qr[b * N + a]);
 #pragma unroll
-        for (int c = 0; c < N; ++c) H[q][c] = __ldg(Hk + q * N + c);
+        for (int q = 0; q < M; ++q)
 #pragma unroll
-        for (int r = 0; r <= q; ++r) R[q][r] = 0.5f * (__ldg(Rk + q * M + r) + __ldg(Rk + r * M + q));
-        d[q] = tv.d ? __ldg(tv.d + k * M + q) : 0.f;
-        yk[q] = __ldg(y + k * M + q);
+            for (int r = 0; r <= q; ++r) R[q][r] = 0.5f * (Rr[q * M + r] + Rr[r * M + q]);
     }
     float HF[M][N], HQ[M][N], r0[M];
 #pragma unroll
