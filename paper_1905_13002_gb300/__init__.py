@@ -141,7 +141,7 @@ class Model:
     FP32.  Time-varying: the same with a leading step axis, F [T,nx,nx] ...
     (F[k], u[k], Q[k] predict step k from step k-1, F[0] from the prior;
     H[k], d[k], R[k] observe step k).  m0 [nx], P0 [nx,nx] are FP64 (the
-    k = 1 element is built in double-float arithmetic).
+    k = 1 element is built in FP64).
     """
 
     F: torch.Tensor

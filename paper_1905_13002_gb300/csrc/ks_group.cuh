@@ -574,7 +574,7 @@ KS_DEV void expand_meas(int r, const ModelConst<N, M>& mc, float b, const float 
     gsync<N>();
 }
 
-// The k = 1 element: A_1 = 0, b_1, C_1 (built in double-float), eta_1 = 0, J_1 = 0.
+// The k = 1 element: A_1 = 0, b_1, C_1 (built in FP64), eta_1 = 0, J_1 = 0.
 template <int N, int M>
 KS_DEV void first_elem(int r, const ModelConst<N, M>& mc, FSlot<N> o) {
     if (r < N) {

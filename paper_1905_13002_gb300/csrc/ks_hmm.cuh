@@ -323,20 +323,26 @@ KS_DEV void selem_last(SE<K>& e, const float (&p)[K]) {
 
 // Definition 2 in matrix form: (a_i (x) a_j)[z][x] = sum_y a_j[z][y] a_i[y][x]
 // (i earlier), i.e. the product a_j a_i.
+// The rows of a product of row-stochastic matrices sum to one in exact
+// arithmetic; each row is rescaled to that sum, so that the rounding of the
+// total probability does not build up along the look-back's chain of tile
+// prefixes (one product per tile).
 template <int K>
 KS_DEV SE<K> smatmul(SE<K> l, const SE<K>& r) {   // l r, l overwritten row by row
 #pragma unroll
     for (int z = 0; z < K; ++z) {
-        float o[K];
+        float o[K], t = 0.f;
 #pragma unroll
         for (int x = 0; x < K; ++x) {
             float s = 0.f;
 #pragma unroll
             for (int y = 0; y < K; ++y) s = fmaf(l.a[z * K + y], r.a[y * K + x], s);
             o[x] = s;
+            t += s;
         }
+        const float rt = 1.f / t;
 #pragma unroll
-        for (int x = 0; x < K; ++x) l.a[z * K + x] = o[x];
+        for (int x = 0; x < K; ++x) l.a[z * K + x] = o[x] * rt;
     }
     return l;
 }
@@ -369,17 +375,19 @@ struct SmootherOp {
     using Elem = SE<K>;
     using State = SS<K>;
     KS_DEV static Elem combine(const Elem& a, const Elem& b, bool&) { return smatmul<K>(a, b); }
-    KS_DEV static void advance(State& s, const Elem& e, bool&) {   // s <- s e.a
-        float o[K];
+    KS_DEV static void advance(State& s, const Elem& e, bool&) {   // s <- s e.a, rescaled to sum 1
+        float o[K], t = 0.f;
 #pragma unroll
         for (int x = 0; x < K; ++x) {
-            float t = 0.f;
+            float v = 0.f;
 #pragma unroll
-            for (int z = 0; z < K; ++z) t = fmaf(s.s[z], e.a[z * K + x], t);
-            o[x] = t;
+            for (int z = 0; z < K; ++z) v = fmaf(s.s[z], e.a[z * K + x], v);
+            o[x] = v;
+            t += v;
         }
+        const float rt = 1.f / t;
 #pragma unroll
-        for (int x = 0; x < K; ++x) s.s[x] = o[x];
+        for (int x = 0; x < K; ++x) s.s[x] = o[x] * rt;
     }
     KS_DEV static void identity(Elem& e) { set_identity<K>(e); }
     KS_DEV static void zero_state(State& s) {

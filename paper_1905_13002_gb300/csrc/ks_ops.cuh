@@ -76,7 +76,7 @@ struct ModelConst {
     float K[N * M];         // Q H^T S^{-1}
     float Lsi[M * M];       // L_S^{-1} (lower triangular, row-major)
     float hud[M];           // H u + d
-    float b1[N];            // k = 1 element (double-float-built): b_1
+    float b1[N];            // k = 1 element (FP64-built): b_1
     float C1[sym_size(N)];  //                              C_1
     float pad[4];
 };
@@ -768,7 +768,7 @@ KS_DEV void expand_meas(const MC& mc, const float (&b)[N], const float (&w)[M],
         }
 }
 
-// The k = 1 element of Lemma 3: A_1 = 0, (b_1, C_1) built in double-float, eta_1 = J_1 = 0.
+// The k = 1 element of Lemma 3: A_1 = 0, (b_1, C_1) built in FP64, eta_1 = J_1 = 0.
 template <int N, int M>
 KS_DEV void first_element(const ModelConst<N, M>& mc, FElem<N>& e) {
 #pragma unroll

@@ -20,7 +20,6 @@
 #pragma once
 
 #include "ks_async.cuh"
-#include "ks_df.cuh"
 #include "ks_ops.cuh"
 
 namespace ks {
@@ -369,19 +368,19 @@ KS_DEV void build_selem_tv(const TVArgs& tv, int64_t k, int64_t T, const float (
 // ---------------------------------------------------------------- prep
 // Model constants, one thread block.  k > 1 quantities in FP32 (Lemma 3 with
 // the Cholesky factor of S); the k = 1 element (Kalman prediction and update
-// from N(m0, P0), Lemma 3) in double-float arithmetic (about 44 bits).  Every
-// matrix product is spread over a warp, one output entry per lane.  Block s
+// from N(m0, P0), Lemma 3) in FP64.  Every matrix product is spread over a
+// warp, one output entry per lane.  Block s
 // prepares segment s (batched: the model arrays hold one model per segment
 // and `off` gives the segments' first steps); block 0 also zeroes the scans'
 // tile counters and flags and checks the segment table.
 template <int N, int M>
 struct PrepSmem {
     float F[N][N], Q[N][N], H[M][N], R[M][M], u[N], d[M], y[M];
-    df m0[N], P0[N][N];
+    double m0[N], P0[N][N];
     // warp 0: the FP32 model constants
     float HQ[M][N], HF[M][N], S[M][M], Lsi[M][M], tmp[M][N], K[N][M];
-    // warp 1: the k = 1 element in double-float
-    df mm[N], FP[N][N], Pm[N][N], HP[M][N], S1[M][M], L1[M][M], r1[M], t1[M][N], z[M];
+    // warp 1: the k = 1 element in FP64
+    double mm[N], FP[N][N], Pm[N][N], HP[M][N], S1[M][M], L1[M][M], r1[M], t1[M][N], z[M];
     int ok0, ok1;
 };
 
@@ -389,8 +388,8 @@ constexpr int kPrepThreads = 64;
 
 // One block per model (segment).  After one round of loads, warp 0 builds the
 // FP32 constants of Lemma 3 for k > 1 and warp 1, at the same time, the k = 1
-// element (prediction of N(m0, P0) and update with y_1) in double-float
-// arithmetic (ks_df.cuh); the two chains only meet for the final store.
+// element (prediction of N(m0, P0) and update with y_1) in FP64; the two
+// chains only meet for the final store.
 template <int N, int M>
 __global__ void __launch_bounds__(kPrepThreads) prep_kernel(const float* __restrict__ F, const float* __restrict__ u,
                                                    const float* __restrict__ Q, const float* __restrict__ H,
@@ -435,7 +434,7 @@ __global__ void __launch_bounds__(kPrepThreads) prep_kernel(const float* __restr
         i -= nF;
         if (i < nQ) { p.Q[i / N][i % N] = Q[i]; continue; }
         i -= nQ;
-        if (i < nP) { p.P0[i / N][i % N] = df_make(P0[i]); continue; }
+        if (i < nP) { p.P0[i / N][i % N] = P0[i]; continue; }
         i -= nP;
         if (i < nH) { p.H[i / N][i % N] = H[i]; continue; }
         i -= nH;
@@ -443,7 +442,7 @@ __global__ void __launch_bounds__(kPrepThreads) prep_kernel(const float* __restr
         i -= nR;
         if (i < N) { p.u[i] = u ? u[i] : 0.f; continue; }
         i -= N;
-        if (i < N) { p.m0[i] = df_make(m0[i]); continue; }
+        if (i < N) { p.m0[i] = m0[i]; continue; }
         i -= N;
         if (i < M) { p.d[i] = d ? d[i] : 0.f; continue; }
         i -= M;
@@ -537,87 +536,88 @@ __global__ void __launch_bounds__(kPrepThreads) prep_kernel(const float* __restr
         if (l < 4) mc.pad[l] = 0.f;
     } else if (warp == 1) {
         if (y != nullptr) {
-            // ---- k = 1: m- = F m0 + u, P- = F P0 F^T + Q, S1 = H P- H^T + R = L1 L1^T,
-            // t1 = L1^{-1} H P-, z = L1^{-1} (y - H m- - d), b1 = m- + t1^T z, C1 = P- - t1^T t1
+            // ---- k = 1 in FP64: m- = F m0 + u, P- = F P0 F^T + Q, S1 = H P- H^T + R = L1 L1^T,
+            // t1 = L1^{-1} H P-, z = L1^{-1} (y - H m- - d), b1 = m- + t1^T z, C1 = P- - t1^T t1.
+            // Each product is spread over the warp's lanes; the triangular solves use the
+            // reciprocal square roots of the Cholesky pivots, so the chain has no division.
             for (int e = l; e < N * N; e += 32) {
                 const int a = e / N, b = e % N;
-                df s = df_make(0.f);
-                for (int c = 0; c < N; ++c) s = df_fma(df_make(p.F[a][c]), p.P0[c][b], s);
+                double s = 0.0;
+                for (int c = 0; c < N; ++c) s = fma((double)p.F[a][c], p.P0[c][b], s);
                 p.FP[a][b] = s;
             }
             for (int e = l; e < N; e += 32) {
-                df s = df_make(p.u[e]);
-                for (int c = 0; c < N; ++c) s = df_fma(df_make(p.F[e][c]), p.m0[c], s);
+                double s = p.u[e];
+                for (int c = 0; c < N; ++c) s = fma((double)p.F[e][c], p.m0[c], s);
                 p.mm[e] = s;
             }
             __syncwarp();
             for (int e = l; e < N * N; e += 32) {
                 const int a = e / N, b = e % N;
                 if (b > a) continue;
-                df s = df_make(0.5f * (p.Q[a][b] + p.Q[b][a]));
-                for (int c = 0; c < N; ++c) s = df_fma(p.FP[a][c], df_make(p.F[b][c]), s);
+                double s = 0.5 * ((double)p.Q[a][b] + (double)p.Q[b][a]);
+                for (int c = 0; c < N; ++c) s = fma(p.FP[a][c], (double)p.F[b][c], s);
                 p.Pm[a][b] = s;
                 p.Pm[b][a] = s;
             }
             __syncwarp();
             for (int e = l; e < M * N; e += 32) {
                 const int q = e / N, a = e % N;
-                df s = df_make(0.f);
-                for (int c = 0; c < N; ++c) s = df_fma(df_make(p.H[q][c]), p.Pm[c][a], s);
+                double s = 0.0;
+                for (int c = 0; c < N; ++c) s = fma((double)p.H[q][c], p.Pm[c][a], s);
                 p.HP[q][a] = s;
             }
             __syncwarp();
             for (int e = l; e < M * M; e += 32) {
                 const int q = e / M, r = e % M;
-                df s = df_make(0.5f * (p.R[q][r] + p.R[r][q]));
-                for (int c = 0; c < N; ++c) s = df_fma(p.HP[q][c], df_make(p.H[r][c]), s);
+                double s = 0.5 * ((double)p.R[q][r] + (double)p.R[r][q]);
+                for (int c = 0; c < N; ++c) s = fma(p.HP[q][c], (double)p.H[r][c], s);
                 p.S1[q][r] = s;
             }
             __syncwarp();
-            if (l == 0) {                          // Cholesky of S1 (reciprocal diagonal), z
+            if (l == 0) {                          // Cholesky of S1 (reciprocal pivots), z
                 bool ok = true;
                 for (int j = 0; j < M; ++j) {
-                    df s = p.S1[j][j];
-                    for (int k = 0; k < j; ++k) s = df_sub(s, df_mul(p.L1[j][k], p.L1[j][k]));
-                    ok = ok && (s.hi > 0.f);
-                    const df Ljj = df_sqrt(s.hi > 0.f ? s : df_make(1e-30f));
-                    const df rj = df_recip(Ljj);
-                    p.L1[j][j] = Ljj;
+                    double s = p.S1[j][j];
+                    for (int k = 0; k < j; ++k) s = fma(-p.L1[j][k], p.L1[j][k], s);
+                    ok = ok && (s > 0.0);
+                    const double rj = rsqrt(s > 0.0 ? s : 1e-300);
+                    p.L1[j][j] = s * rj;
                     p.r1[j] = rj;
                     for (int i = j + 1; i < M; ++i) {
-                        df q = p.S1[i][j];
-                        for (int k = 0; k < j; ++k) q = df_sub(q, df_mul(p.L1[i][k], p.L1[j][k]));
-                        p.L1[i][j] = df_mul(q, rj);
+                        double q = p.S1[i][j];
+                        for (int k = 0; k < j; ++k) q = fma(-p.L1[i][k], p.L1[j][k], q);
+                        p.L1[i][j] = q * rj;
                     }
                 }
                 for (int q = 0; q < M; ++q) {
-                    df s = df_sub(df_make(p.y[q]), df_make(p.d[q]));
-                    for (int c = 0; c < N; ++c) s = df_sub(s, df_mul(df_make(p.H[q][c]), p.mm[c]));
-                    for (int k = 0; k < q; ++k) s = df_sub(s, df_mul(p.L1[q][k], p.z[k]));
-                    p.z[q] = df_mul(s, p.r1[q]);
+                    double s = (double)p.y[q] - (double)p.d[q];
+                    for (int c = 0; c < N; ++c) s = fma(-(double)p.H[q][c], p.mm[c], s);
+                    for (int k = 0; k < q; ++k) s = fma(-p.L1[q][k], p.z[k], s);
+                    p.z[q] = s * p.r1[q];
                 }
                 if (!ok) p.ok1 = 0;
             }
             __syncwarp();
             for (int a = l; a < N; a += 32) {      // t1 column a
                 for (int q = 0; q < M; ++q) {
-                    df s = p.HP[q][a];
-                    for (int k = 0; k < q; ++k) s = df_sub(s, df_mul(p.L1[q][k], p.t1[k][a]));
-                    p.t1[q][a] = df_mul(s, p.r1[q]);
+                    double s = p.HP[q][a];
+                    for (int k = 0; k < q; ++k) s = fma(-p.L1[q][k], p.t1[k][a], s);
+                    p.t1[q][a] = s * p.r1[q];
                 }
             }
             __syncwarp();
             for (int e = l; e < N * N; e += 32) {
                 const int a = e / N, b = e % N;
                 if (b == 0) {
-                    df s = p.mm[a];
-                    for (int q = 0; q < M; ++q) s = df_fma(p.t1[q][a], p.z[q], s);
-                    mc.b1[a] = df_float(s);
+                    double s = p.mm[a];
+                    for (int q = 0; q < M; ++q) s = fma(p.t1[q][a], p.z[q], s);
+                    mc.b1[a] = (float)s;
                 }
                 if (b <= a) {
-                    df s = p.Pm[a][b];
-                    for (int q = 0; q < M; ++q) s = df_sub(s, df_mul(p.t1[q][a], p.t1[q][b]));
-                    mc.C1[sidx(a, b)] = df_float(s);
+                    double s = p.Pm[a][b];
+                    for (int q = 0; q < M; ++q) s = fma(-p.t1[q][a], p.t1[q][b], s);
+                    mc.C1[sidx(a, b)] = (float)s;
                 }
             }
         } else {

@@ -647,7 +647,7 @@ KS_DEV void expand_meas(const FConst<N, M>& c, float b, const float (&w)[M], con
     __syncwarp();
 }
 
-// The k = 1 element (built in double-float by the model preparation): A_1 = 0,
+// The k = 1 element (built in FP64 by the model preparation): A_1 = 0,
 // (b_1, C_1), eta_1 = 0, J_1 = 0.  A or J may be null (prefix state only).
 template <int N, int M>
 KS_DEV void first_elem(const ModelConst<N, M>& g, const FConst<N, M>& c, const FE& o) {

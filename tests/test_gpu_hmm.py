@@ -44,15 +44,17 @@ def check(ks, seq):
     return ef, es, el
 
 
-# K = 8: sizes span one thread's steps (4 or 16), a 512- or 2048-step tile,
-# many tiles with ragged tails, and both steps-per-thread choices (the switch
-# is at 256 Ki steps).
-@pytest.mark.parametrize("T", [1, 2, 3, 33, 511, 512, 513, 2049, 65537, 262143, 262144, 300001])
+# K = 8: sizes span one thread's steps (4, 16 or 32), a 512-, 2048- or
+# 4096-step tile, many tiles with ragged tails, and all three steps-per-thread
+# choices (switching at 256 Ki and 768 Ki steps).
+@pytest.mark.parametrize("T", [1, 2, 3, 33, 511, 512, 513, 2049, 65537, 262143, 262144, 300001, 786431,
+                               786432, 800001])
 def test_regime_switching_k8(ks, T):
     check(ks, workloads.hmm_sequence(8, T, seed=8000 + T))
 
 
-@pytest.mark.parametrize("K,T", [(2, 1), (2, 5000), (2, 300001), (4, 7), (4, 40000), (4, 270001)])
+@pytest.mark.parametrize("K,T", [(2, 1), (2, 5000), (2, 300001), (2, 800001), (4, 7), (4, 40000), (4, 270001),
+                                 (4, 790001)])
 def test_other_state_counts(ks, K, T):
     check(ks, workloads.hmm_sequence(K, T, seed=8100 + T + K))
 

@@ -90,9 +90,9 @@ def test_paper_experiment_model(ks):
 @pytest.mark.parametrize("p0", [1e-4, 1e6])
 def test_extreme_prior_first_element(ks, p0):
     """The k = 1 element (prediction and update of N(m0, P0)) is built in
-    double-float arithmetic: with a near-exact or a diffuse prior (P- ~ 1e6
-    against R = 0.5) its update P- - K S K^T keeps FP32 accuracy.  T = 1, so
-    the output is that element alone."""
+    FP64: with a near-exact or a diffuse prior (P- ~ 1e6 against R = 0.5) its
+    update P- - K S K^T keeps FP32 accuracy.  T = 1, so the output is that
+    element alone."""
     rng = np.random.default_rng(79)
     m = workloads.wiener_velocity(2, dt=0.1, q=1.0, r=0.5, m0=np.array([30.0, -20.0, 1.0, 2.0]),
                                   P0=p0 * np.eye(4))
