@@ -80,9 +80,9 @@ extern "C" {
  * r_k ~ N(0, R[k]): Section II's model with its indices shifted by one.
  * Each of these arrays must start on a 16-byte boundary (KS_EINVAL otherwise).
  * Time-varying models are accepted by ks_smooth and ks_smooth_traced for
- * nx in {2, 4, 6} (KS_EUNSUPPORTED elsewhere), and need
- * ks_workspace_bytes(m, T, KS_WS_SMOOTH) bytes, which for them equals the
- * KS_WS_ELEMENTS size.
+ * nx in {2, 4, 6, 8} (KS_EUNSUPPORTED elsewhere), and need
+ * ks_workspace_bytes(m, T, KS_WS_SMOOTH) bytes (the same as KS_WS_ELEMENTS
+ * for them: per-step elements or model constants live in the workspace).
  *
  * m0 [nx] and P0 [nx][nx] are DEVICE pointers to FP64 arrays.  Q, R and P0
  * must be symmetric positive definite (R, P0) / semidefinite with

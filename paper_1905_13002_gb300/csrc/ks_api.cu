@@ -62,9 +62,9 @@ size_t ks_workspace_bytes(const ks_model* m, int64_t T, int purpose) {
     const VTable* v = nullptr;
     if (check_nx_ny(m, &v) || T < 1 || T > 0x7fffffffLL) return 0;
     const Layout L = v->layout(T, 1);
-    if (m->time_varying) {   // time-varying smoothing materialises its filtering elements
-        if (m->time_varying != 1 || !v->time_varying) return 0;
-        return (purpose == KS_WS_SMOOTH || purpose == KS_WS_ELEMENTS) ? L.bytes_elements : 0;
+    if (m->time_varying) {   // time-varying smoothing keeps per-step elements or constants
+        if (m->time_varying != 1 || !v->tv_bytes) return 0;
+        return (purpose == KS_WS_SMOOTH || purpose == KS_WS_ELEMENTS) ? v->tv_bytes(T) : 0;
     }
     if (purpose == KS_WS_SMOOTH) return L.bytes_smooth;
     if (purpose == KS_WS_ELEMENTS) return L.bytes_elements;

@@ -88,7 +88,7 @@ struct GImpl {
     }
 
     // Per scan: a reduce launch, log2(tiles) spine launches, an apply launch.
-    template <bool SEG>
+    template <bool SEG, bool TV = false>
     static int scans(void* ws, const Layout& L, const float* y, float* fm, float* fc, float* sm, float* sc,
                      Segs<N, M> segs, cudaStream_t st, void* const* ev, bool filter, bool smoother) {
         grp::GBuf fb, sb;
@@ -100,9 +100,9 @@ struct GImpl {
         uint32_t* stat = status(ws);
         int rc;
         if (filter) {
-            auto kr = grp::gfilter_reduce_kernel<N, M, NW, CH, SEG>;
+            auto kr = grp::gfilter_reduce_kernel<N, M, NW, CH, SEG, TV>;
             auto ks = grp::gspine_filter_kernel<N, SW>;
-            auto ka = grp::gfilter_apply_kernel<N, M, NW, CH, SEG>;
+            auto ka = grp::gfilter_apply_kernel<N, M, NW, CH, SEG, TV>;
             static const bool ok = allow_smem(kr, smem) && allow_smem(ks, ssmem) && allow_smem(ka, smem);
             if (!ok) return KS_ECUDA;
             kr<<<L.ntf, NW * 32, smem, st>>>(mconst(ws, L), y, L.T, fb, stat, segs);
@@ -121,7 +121,7 @@ struct GImpl {
         }
         if (ev && ev[2] && cudaEventRecord(static_cast<cudaEvent_t>(ev[2]), st) != cudaSuccess) return KS_ECUDA;
         if (smoother) {
-            auto kr = grp::gsmoother_reduce_kernel<N, M, NW, CH, SEG>;
+            auto kr = grp::gsmoother_reduce_kernel<N, M, NW, CH, SEG, TV>;
             auto ks = grp::gspine_smoother_kernel<N, SW>;
             auto ka = grp::gsmoother_apply_kernel<N, M, NW, CH>;
             static const bool ok = allow_smem(kr, smem) && allow_smem(ks, ssmem) && allow_smem(ka, smem);
@@ -170,8 +170,59 @@ struct GImpl {
                             Segs<N, M>{nullptr, nullptr, 1}, st, nullptr, false, true);
     }
 
+    // Time-varying model: per-step constants (prep_kernel for step 0 with its
+    // FP64 k = 1 element, tv_const_kernel for the rest) after the elements
+    // region, read by the scans through a per-step Cursor.
+    static size_t tv_offset(int64_t T) { return align_up(layout(T).bytes_elements, 256); }
+    static size_t tv_bytes(int64_t T) { return tv_offset(T) + sizeof(ModelConst<N, M>) * (size_t)T; }
+
+    static int smooth_tv(const ks_model* m, const float* y, int64_t T, void* ws, size_t ws_bytes, float* fm,
+                         float* fc, float* sm, float* sc, cudaStream_t st, void* const* ev) {
+        if (!m->F || !m->Q || !m->H || !m->R || !m->m0 || !m->P0) return KS_EINVAL;
+        if (m->time_varying != 1) return KS_EUNSUPPORTED;
+        if (T < 1 || T > 0x7fffffffLL) return KS_EINVAL;
+        if (!aligned16(m->F) || !aligned16(m->Q) || !aligned16(m->H) || !aligned16(m->R) ||
+            (m->u && !aligned16(m->u)) || (m->d && !aligned16(m->d)))
+            return KS_EINVAL;
+        const Layout L = layout(T);
+        if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) != 0 || ws_bytes < tv_bytes(T)) return KS_EINVAL;
+        const bool own = (fm == nullptr) || (fc == nullptr);
+        const bool filter_only = (sm == nullptr) && (sc == nullptr);
+        if (!y || (filter_only && own) || (!filter_only && (!sm || !sc))) return KS_EINVAL;
+        if (own) {
+            fm = reinterpret_cast<float*>(static_cast<char*>(ws) + L.off_fmean);
+            fc = reinterpret_cast<float*>(static_cast<char*>(ws) + L.off_fcov);
+        }
+        auto* tvc = reinterpret_cast<ModelConst<N, M>*>(static_cast<char*>(ws) + tv_offset(T));
+        const TVArgs tv{m->F, m->u, m->Q, m->H, m->d, m->R, m->m0, m->P0};
+        int rc;
+        if (ev && ev[0] && cudaEventRecord(static_cast<cudaEvent_t>(ev[0]), st) != cudaSuccess) return KS_ECUDA;
+        {
+            const int smem = (int)prep_smem();
+            auto k = prep_kernel<N, M>;
+            static const bool ok = allow_smem(k, smem);
+            if (!ok) return KS_ECUDA;
+            uint32_t* z = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + L.off_flags);
+            k<<<1, kPrepThreads, smem, st>>>(m->F, m->u, m->Q, m->H, m->d, m->R, m->m0, m->P0, y, tvc, status(ws), z,
+                                             (int)(L.flags_bytes / 4), nullptr, T);
+            if ((rc = launch_status())) return rc;
+        }
+        if (T > 1) {
+            const int blocks = (int)std::min<int64_t>((T + 127) / 128, 152 * 8);
+            tv_const_kernel<N, M><<<blocks, 128, 0, st>>>(tv, T, tvc, status(ws));
+            if ((rc = launch_status())) return rc;
+        }
+        if (ev && ev[1] && cudaEventRecord(static_cast<cudaEvent_t>(ev[1]), st) != cudaSuccess) return KS_ECUDA;
+        if ((rc = scans<false, true>(ws, L, y, fm, fc, sm, sc, Segs<N, M>{tvc, nullptr, 1}, st, ev, true,
+                                     !filter_only)))
+            return rc;
+        if (ev && ev[3] && cudaEventRecord(static_cast<cudaEvent_t>(ev[3]), st) != cudaSuccess) return KS_ECUDA;
+        return KS_OK;
+    }
+
     static int smooth(const ks_model* m, const float* y, int64_t T, void* ws, size_t ws_bytes, float* fm,
                       float* fc, float* sm, float* sc, cudaStream_t st, void* const* ev) {
+        if (m && m->time_varying) return smooth_tv(m, y, T, ws, ws_bytes, fm, fc, sm, sc, st, ev);
         const Layout L = layout(T);
         const bool own = (fm == nullptr) || (fc == nullptr);
         const bool filter_only = (sm == nullptr) && (sc == nullptr);
@@ -218,7 +269,7 @@ struct GImpl {
 
     static constexpr VTable vtable() {
         return VTable{N, M, &layout, &build_elements, &filter_scan, &smooth_scan, &smooth, &smooth_batch,
-                      &no_comb, &no_comb, &no_agg_bytes, &no_fagg, &no_sagg, 0};
+                      &no_comb, &no_comb, &no_agg_bytes, &no_fagg, &no_sagg, &tv_bytes};
     }
 };
 

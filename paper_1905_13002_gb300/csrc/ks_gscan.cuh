@@ -98,7 +98,7 @@ constexpr int gspine_warps() {
 }
 
 // ---------------------------------------------------------------- forward
-template <int N, int M, int NW, int CH, bool SEG>
+template <int N, int M, int NW, int CH, bool SEG, bool TV = false>
 __global__ void __launch_bounds__(NW * 32) gfilter_reduce_kernel(const ModelConst<N, M>* __restrict__ mcg,
                                                                  const float* __restrict__ y, int64_t T, GBuf gb,
                                                                  uint32_t* status, Segs<N, M> segs) {
@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(NW * 32) gfilter_reduce_kernel(const ModelCons
     FSlot<N> X[3] = {FSlot<N>{wb}, FSlot<N>{wb + SM::SLOT}, FSlot<N>{wb + 2 * SM::SLOT}};
     Scratch<N> s{wb + 3 * SM::SLOT};
     bool bad = false;
-    Cursor<N, M, SEG> cur;
+    Cursor<N, M, SEG, TV> cur;
 
     // ---- chain fold
     if (valid) {
@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(NWS * 32) gspine_filter_kernel(const float* __
 }
 
 // `pre`: the spine's inclusive prefixes (slot t covers tiles 0..t).
-template <int N, int M, int NW, int CH, bool SEG>
+template <int N, int M, int NW, int CH, bool SEG, bool TV = false>
 __global__ void __launch_bounds__(NW * 32) gfilter_apply_kernel(const ModelConst<N, M>* __restrict__ mcg,
                                                                 const float* __restrict__ y, int64_t T,
                                                                 float* __restrict__ fmean, float* __restrict__ fcov,
@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(NW * 32) gfilter_apply_kernel(const ModelConst
     FSlot<N> X[3] = {FSlot<N>{wb}, FSlot<N>{wb + SM::SLOT}, FSlot<N>{wb + 2 * SM::SLOT}};
     Scratch<N> s{wb + 3 * SM::SLOT};
     bool bad = false;
-    Cursor<N, M, SEG> cur;
+    Cursor<N, M, SEG, TV> cur;
     int a = 0;
     bool has = false;
     if (tile != 0) {
@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(NW * 32) gfilter_apply_kernel(const ModelConst
 // ---------------------------------------------------------------- reverse
 // Chains are the forward blocks of CH steps, visited last first; in time
 // order the operator takes the earlier step on the left (Lemma 6).
-template <int N, int M, int NW, int CH, bool SEG>
+template <int N, int M, int NW, int CH, bool SEG, bool TV = false>
 __global__ void __launch_bounds__(NW * 32) gsmoother_reduce_kernel(const ModelConst<N, M>* __restrict__ mcg,
                                                                    const float* __restrict__ fmean,
                                                                    const float* __restrict__ fcov, int64_t T, GBuf gb,
@@ -301,7 +301,7 @@ __global__ void __launch_bounds__(NW * 32) gsmoother_reduce_kernel(const ModelCo
     SSlot<N> X[3] = {SSlot<N>{wb}, SSlot<N>{wb + SM::SLOT}, SSlot<N>{wb + 2 * SM::SLOT}};
     Scratch<N> s{wb + 3 * SM::SLOT};
     bool bad = false;
-    Cursor<N, M, SEG> cur;
+    Cursor<N, M, SEG, TV> cur;
 
     // ---- chain fold: a_{klo} (x) ... (x) a_{khi}, from the latest step back
     if (valid) {
@@ -318,13 +318,13 @@ __global__ void __launch_bounds__(NW * 32) gsmoother_reduce_kernel(const ModelCo
         cur.seek(segs, &mc, khi, T);
         int a = 0;
         load_post(khi);
-        selem<N, M>(r, *cur.mc, s.S(3), s.V(5), cur.last(khi), X[0], s, bad);
+        selem<N, M>(r, *cur.trans(khi), s.S(3), s.V(5), cur.last(khi), X[0], s, bad);
         copy_floats<N>(gb.elems + (size_t)khi * SS, X[0].p, SS);
 #pragma unroll 1
         for (int64_t k = khi - 1; k >= klo; --k) {
             cur.backward(segs, k);
             load_post(k);
-            selem<N, M>(r, *cur.mc, s.S(3), s.V(5), cur.last(k), X[2], s, bad);
+            selem<N, M>(r, *cur.trans(k), s.S(3), s.V(5), cur.last(k), X[2], s, bad);
             copy_floats<N>(gb.elems + (size_t)k * SS, X[2].p, SS);
             scombine<N, false>(r, X[2], X[a], X[a ^ 1], s);
             a ^= 1;

@@ -46,7 +46,7 @@ struct VTable {
     int (*faggregate)(const ks_model*, const float*, int64_t, int, void*, size_t, float*, cudaStream_t);
     int (*saggregate)(const ks_model*, int64_t, const float*, const float*, int, void*, size_t, float*,
                       cudaStream_t);
-    int time_varying;   // 1 if smooth accepts time-varying models
+    size_t (*tv_bytes)(int64_t T);   // workspace of a time-varying smooth (null: not supported)
 };
 
 // The fused end-to-end entry points of one steps-per-thread choice.
@@ -265,6 +265,8 @@ struct Impl {
         return cudaEventRecord(static_cast<cudaEvent_t>(ev[i]), st) == cudaSuccess ? KS_OK : KS_ECUDA;
     }
 
+    static size_t tv_bytes(int64_t T) { return layout(T).bytes_elements; }
+
     // Time-varying model (m->time_varying = 1): the filtering elements are
     // materialised in their measurement form (TVElem records) from the
     // per-step arrays; the forward scan combines them with the rank-ny
@@ -422,7 +424,7 @@ struct Impl {
 
     static constexpr VTable vtable() {
         return VTable{N, M, &layout, &build_elements, &filter_scan, &smooth_scan, &smooth, &smooth_batch,
-                      &fcomb_batch, &scomb_batch, &agg_bytes, &faggregate, &saggregate, 1};
+                      &fcomb_batch, &scomb_batch, &agg_bytes, &faggregate, &saggregate, &tv_bytes};
     }
     static constexpr ChunkVariant chunk_variant() { return ChunkVariant{&layout, &smooth, &smooth_batch}; }
 };
@@ -470,9 +472,11 @@ struct Tuned {
                             float* fm, float* fc, float* sm, float* sc, cudaStream_t st) {
         return ChunkTable<N, M>::v[chunk_index(T)]->smooth_batch(mb, y, T, ws, ws_bytes, fm, fc, sm, sc, st);
     }
+    static size_t tv_bytes(int64_t T) { return layout(T, 1).bytes_elements; }
     static constexpr VTable vtable() {
         VTable t = Base::vtable();
         t.layout = &layout;
+        t.tv_bytes = &tv_bytes;
         t.smooth = &smooth;
         t.smooth_batch = &smooth_batch;
         return t;

@@ -37,5 +37,5 @@ extern const VTable kImpl_32_8 = VTable{32,
                                         &GR::no_agg_bytes,
                                         &GR::no_fagg,
                                         &GR::no_sagg,
-                                        0};
+                                        nullptr};
 }  // namespace ks

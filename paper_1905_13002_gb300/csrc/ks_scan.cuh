@@ -231,14 +231,25 @@ struct Segs {
     int B;
 };
 
-template <int N, int M, bool SEG>
+// With TV the constants are per step (g.mcg[k] for step k of one sequence of
+// g.mcg's length): the step's filtering element reads g.mcg[k], and its
+// Lemma 5 element the next step's transition, g.mcg[k + 1] (trans(k)).
+template <int N, int M, bool SEG, bool TV = false>
 struct Cursor {
+    static_assert(!(SEG && TV), "a time-varying model is one sequence");
     const ModelConst<N, M>* mc;
+    const ModelConst<N, M>* base;
     int64_t start, end;
     int s;
 
     KS_DEV void seek(const Segs<N, M>& g, const ModelConst<N, M>* single, int64_t k, int64_t T) {
-        if constexpr (!SEG) {
+        if constexpr (TV) {
+            base = g.mcg;
+            mc = base + k;
+            start = 0;
+            end = T;
+            s = 0;
+        } else if constexpr (!SEG) {
             mc = single;
             start = 0;
             end = T;
@@ -259,7 +270,9 @@ struct Cursor {
     // The loops stop at the table's ends, so an inconsistent table (reported
     // by the preparation kernel) cannot take a cursor out of bounds.
     KS_DEV void forward(const Segs<N, M>& g, int64_t k) {
-        if constexpr (SEG) {
+        if constexpr (TV) {
+            mc = base + k;
+        } else if constexpr (SEG) {
             while (k >= end && s < g.B - 1) {
                 ++s;
                 start = end;
@@ -269,7 +282,9 @@ struct Cursor {
         }
     }
     KS_DEV void backward(const Segs<N, M>& g, int64_t k) {
-        if constexpr (SEG) {
+        if constexpr (TV) {
+            mc = base + k;
+        } else if constexpr (SEG) {
             while (k < start && s > 0) {
                 --s;
                 end = start;
@@ -280,6 +295,11 @@ struct Cursor {
     }
     KS_DEV bool first(int64_t k) const { return k == start; }
     KS_DEV bool last(int64_t k) const { return k == end - 1; }
+    // Constants holding the transition that Lemma 5 reads at step k.
+    KS_DEV const ModelConst<N, M>* trans(int64_t k) const {
+        if constexpr (TV) return (k + 1 < end) ? base + k + 1 : mc;
+        else return mc;
+    }
 };
 
 // ---------------------------------------------------------------- time-varying models
@@ -903,6 +923,108 @@ __global__ void __launch_bounds__(256) tv_elements_kernel(TVArgs tv, const float
         if (k == 0) tv_first_element<N, M>(tv, y, e, bad);
         else tv_element<N, M>(tv, y, k, e, bad);
         store_tvelem<N, M>(el, k, e);
+    }
+    if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicOr(status, ST_NUMERIC);
+}
+
+// Per-step model constants of a time-varying model (steps 1..T-1; step 0,
+// with its k = 1 element, comes from prep_kernel): the FP32 part of
+// prep_kernel evaluated per step by one thread, for the kernels that read
+// their model through a Cursor (one warp per chain).
+template <int N, int M>
+__global__ void __launch_bounds__(128) tv_const_kernel(TVArgs tv, int64_t T, ModelConst<N, M>* __restrict__ out,
+                                                       uint32_t* __restrict__ status) {
+    bool bad = false;
+    for (int64_t k = 1 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < T;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        ModelConst<N, M>& mc = out[k];
+        float F[N * N], Q[N * N], H[M * N], R[M * M], u[N], d[M];
+        load_step<N * N>(tv.F, k, F);
+        load_step<N * N>(tv.Q, k, Q);
+        load_step<M * N>(tv.H, k, H);
+        load_step<M * M>(tv.R, k, R);
+        if (tv.u) load_step<N>(tv.u, k, u);
+        else {
+#pragma unroll
+            for (int a = 0; a < N; ++a) u[a] = 0.f;
+        }
+        if (tv.d) load_step<M>(tv.d, k, d);
+        else {
+#pragma unroll
+            for (int q = 0; q < M; ++q) d[q] = 0.f;
+        }
+        float HQ[M][N], HF[M][N];
+        for (int q = 0; q < M; ++q)
+            for (int a = 0; a < N; ++a) {
+                float sq = 0.f, sf = 0.f;
+                for (int c = 0; c < N; ++c) {
+                    sq = fmaf(H[q * N + c], 0.5f * (Q[c * N + a] + Q[a * N + c]), sq);
+                    sf = fmaf(H[q * N + c], F[c * N + a], sf);
+                }
+                HQ[q][a] = sq;
+                HF[q][a] = sf;
+            }
+        float Ls[M][M], Lsi[M][M];
+        for (int j = 0; j < M; ++j) {
+            float sj = 0.5f * (R[j * M + j] + R[j * M + j]);
+            for (int c = 0; c < N; ++c) sj = fmaf(HQ[j][c], H[j * N + c], sj);
+            for (int l = 0; l < j; ++l) sj = fmaf(-Ls[j][l], Ls[j][l], sj);
+            bad |= !(sj > 0.f);
+            const float rj = rsqrtf(fmaxf(sj, 1e-37f));
+            Ls[j][j] = sj * rj;
+            for (int i = j + 1; i < M; ++i) {
+                float t = 0.5f * (R[i * M + j] + R[j * M + i]);
+                for (int c = 0; c < N; ++c) t = fmaf(HQ[i][c], H[j * N + c], t);
+                for (int l = 0; l < j; ++l) t = fmaf(-Ls[i][l], Ls[j][l], t);
+                Ls[i][j] = t * rj;
+            }
+        }
+        for (int c = 0; c < M; ++c)                // L_S^{-1}, column by column
+            for (int i = 0; i < M; ++i) {
+                if (i < c) { Lsi[i][c] = 0.f; continue; }
+                float t = (i == c) ? 1.f : 0.f;
+                for (int l = c; l < i; ++l) t = fmaf(-Ls[i][l], Lsi[l][c], t);
+                Lsi[i][c] = t / Ls[i][i];
+            }
+        float tmp[M][N];
+        for (int q = 0; q < M; ++q)
+            for (int a = 0; a < N; ++a) {
+                float st = 0.f, sv = 0.f;
+                for (int r = 0; r <= q; ++r) { st = fmaf(Lsi[q][r], HQ[r][a], st); sv = fmaf(Lsi[q][r], HF[r][a], sv); }
+                tmp[q][a] = st;
+                mc.U[q * N + a] = sv;
+            }
+        for (int q = 0; q < M; ++q) {
+            float hu = d[q];
+            for (int c = 0; c < N; ++c) hu = fmaf(H[q * N + c], u[c], hu);
+            mc.hud[q] = hu;
+            for (int r = 0; r < M; ++r) mc.Lsi[q * M + r] = Lsi[q][r];
+        }
+        for (int a = 0; a < N; ++a)
+            for (int q = 0; q < M; ++q) {
+                float sk = 0.f;
+                for (int r = q; r < M; ++r) sk = fmaf(tmp[r][a], Lsi[r][q], sk);
+                mc.K[a * M + q] = sk;
+            }
+        for (int a = 0; a < N; ++a) {
+            for (int b = 0; b < N; ++b) {
+                float sa = F[a * N + b];
+                for (int q = 0; q < M; ++q) sa = fmaf(-mc.K[a * M + q], HF[q][b], sa);
+                mc.A[a * N + b] = sa;
+                mc.F[a * N + b] = F[a * N + b];
+            }
+            for (int b = 0; b <= a; ++b) {
+                const float qs = 0.5f * (Q[a * N + b] + Q[b * N + a]);
+                float c = qs;
+                for (int q = 0; q < M; ++q) c = fmaf(-tmp[q][a], tmp[q][b], c);
+                mc.C[sidx(a, b)] = c;
+                mc.Q[sidx(a, b)] = qs;
+            }
+            mc.u[a] = u[a];
+            mc.b1[a] = 0.f;
+        }
+        for (int a = 0; a < sym_size(N); ++a) mc.C1[a] = 0.f;
+        for (int a = 0; a < 4; ++a) mc.pad[a] = 0.f;
     }
     if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicOr(status, ST_NUMERIC);
 }

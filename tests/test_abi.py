@@ -69,9 +69,12 @@ def test_argument_errors_need_no_device(ks):
     # support, and a misaligned y are all rejected before any launch
     tv2 = ks._KsModel(4, 2, 2, 0, 1, 0, 1, 1, 0, 1, 1, 1)
     assert L.ks_smooth(ctypes.byref(tv2), 16, 10, 256, 1 << 30, None, None, 16, 16, None) == ks.KS_EUNSUPPORTED
-    tv8 = ks._KsModel(8, 4, 1, 0, 1, 0, 1, 1, 0, 1, 1, 1)
-    assert L.ks_smooth(ctypes.byref(tv8), 16, 10, 256, 1 << 30, None, None, 16, 16, None) == ks.KS_EUNSUPPORTED
-    assert L.ks_workspace_bytes(ctypes.byref(tv8), 10, ks.KS_WS_SMOOTH) == 0
+    tv32 = ks._KsModel(32, 8, 1, 0, 1, 0, 1, 1, 0, 1, 1, 1)
+    assert L.ks_smooth(ctypes.byref(tv32), 16, 10, 256, 1 << 30, None, None, 16, 16, None) == ks.KS_EUNSUPPORTED
+    assert L.ks_workspace_bytes(ctypes.byref(tv32), 10, ks.KS_WS_SMOOTH) == 0
+    tv8 = ks._KsModel(8, 4, 1, 0, 1, 0, 1, 1, 0, 1, 1, 1)   # misaligned F: rejected before any launch
+    assert L.ks_smooth(ctypes.byref(tv8), 16, 10, 256, 1 << 30, None, None, 16, 16, None) == ks.KS_EINVAL
+    assert L.ks_workspace_bytes(ctypes.byref(tv8), 10, ks.KS_WS_SMOOTH) > 0
     tv = ks._KsModel(4, 2, 1, 0, 1, 0, 1, 1, 0, 1, 1, 1)
     assert L.ks_smooth(ctypes.byref(tv), 4, 10, 256, 1 << 30, None, None, 16, 16, None) == ks.KS_EINVAL
     assert L.ks_workspace_bytes(ctypes.byref(tv), 10, ks.KS_WS_SMOOTH) == \

@@ -51,12 +51,14 @@ def test_irregular_tracking_sizes(ks, T):
     check(ks, workloads.irregular_tracking(T, seed=7000 + T))
 
 
-@pytest.mark.parametrize("dim,T", [(1, 1), (1, 3000), (1, 150001), (3, 2), (3, 2500), (3, 150001)])
+@pytest.mark.parametrize("dim,T", [(1, 1), (1, 3000), (1, 150001), (3, 2), (3, 2500), (3, 150001),
+                                   (4, 2), (4, 63), (4, 64), (4, 65), (4, 5000), (4, 40001)])
 def test_irregular_tracking_other_state_sizes(ks, dim, T):
     check(ks, workloads.irregular_tracking(T, seed=7100 + T + dim, dim=dim))
 
 
-@pytest.mark.parametrize("nx,ny,T", [(2, 1, 700), (4, 2, 1), (4, 2, 900), (6, 3, 700)])
+@pytest.mark.parametrize("nx,ny,T", [(2, 1, 700), (4, 2, 1), (4, 2, 900), (6, 3, 700), (8, 4, 1), (8, 4, 65),
+                                     (8, 4, 700)])
 def test_random_time_varying_dense(ks, nx, ny, T):
     """Dense per-step F_k, Q_k, H_k, R_k with non-zero u_k, d_k."""
     check(ks, workloads.random_time_varying(nx, ny, T, np.random.default_rng(7200 + T + nx)))
@@ -103,8 +105,8 @@ def test_too_few_steps_rejected_before_launch(ks):
 
 
 def test_entry_points_without_time_varying_support(ks):
-    """Entry points other than ks_smooth reject time-varying models, and so do
-    the nx = 8 and nx = 32 smoothers; the workspace query returns 0 there."""
+    """Entry points other than ks_smooth reject time-varying models, and so
+    does the nx = 32 smoother; the workspace query returns 0 there."""
     seq = workloads.irregular_tracking(64, seed=7600)
     model = gpu_model(ks, seq.model)
     y = torch.as_tensor(seq.y, dtype=torch.float32, device="cuda")
@@ -117,7 +119,7 @@ def test_entry_points_without_time_varying_support(ks):
     fP = torch.empty(64, 4, 4, device="cuda")
     assert L.ks_smooth_scan(ctypes.byref(m), 64, ks._p(fm), ks._p(fP), ks._p(ws), ws.numel(), ks._p(fm),
                             ks._p(fP), st) == ks.KS_EUNSUPPORTED
-    big = ks._KsModel(8, 4, 1, 0, m.F, 0, m.Q, m.H, 0, m.R, m.m0, m.P0)
+    big = ks._KsModel(32, 8, 1, 0, m.F, 0, m.Q, m.H, 0, m.R, m.m0, m.P0)
     assert L.ks_workspace_bytes(ctypes.byref(big), 64, ks.KS_WS_SMOOTH) == 0
     assert L.ks_smooth(ctypes.byref(big), ks._p(y), 64, ks._p(ws), ws.numel(), None, None, ks._p(fm), ks._p(fP),
                        st) == ks.KS_EUNSUPPORTED
