@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--batch", type=int, default=4096)
     ap.add_argument("--rates", default="100,300,1000,3000,10000", help="serving: request rates (req/s)")
     ap.add_argument("--duration", type=float, default=10.0, help="serving: seconds of arrivals per rate")
-    ap.add_argument("--streams", type=int, default=2, help="serving: launches in flight")
+    ap.add_argument("--streams", type=int, default=3, help="serving: launches in flight")
     ap.add_argument("--budget-gb", type=float, default=80.0, help="serving: device-memory admission budget")
     return ap.parse_args()
 

@@ -59,7 +59,7 @@ extern "C" {
 #define KS_ECUDA (-2)         /* a CUDA launch or copy failed */
 #define KS_ENUMERIC (-3)      /* device: non-finite value or failed factorisation */
 #define KS_ETIMEOUT (-4)      /* device: bounded look-back wait ran out */
-#define KS_EUNSUPPORTED (-5)  /* (nx, ny) not compiled into this library */
+#define KS_EUNSUPPORTED (-5)  /* size not compiled in, or a model form the entry point does not take */
 
 /* Workspace purposes for ks_workspace_bytes(). */
 #define KS_WS_SMOOTH 0        /* ks_smooth / ks_filter_scan / ks_smooth_scan scratch */

@@ -53,7 +53,7 @@ const char* ks_strerror(int code) {
         case KS_ECUDA: return "CUDA launch or copy failed";
         case KS_ENUMERIC: return "non-finite value or failed factorisation on the device";
         case KS_ETIMEOUT: return "look-back wait on the device ran out";
-        case KS_EUNSUPPORTED: return "(nx, ny) not compiled into this library, or time-varying model";
+        case KS_EUNSUPPORTED: return "size not compiled into this library, or a model form this entry point does not take";
         default: return "unknown status code";
     }
 }

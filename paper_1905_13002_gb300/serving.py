@@ -87,7 +87,7 @@ class Server:
     seconds on ``clock`` relative to the start of ``run``.
     """
 
-    def __init__(self, launcher, budget_bytes: int, streams: int = 2, max_batch_steps: int = 1 << 24,
+    def __init__(self, launcher, budget_bytes: int, streams: int = 3, max_batch_steps: int = 1 << 24,
                  max_batch_requests: int = 1024, bytes_fn=request_bytes, clock=time.perf_counter):
         if streams < 1:
             raise ValueError("streams must be >= 1")
@@ -231,7 +231,7 @@ class GpuLauncher:
     its previous launch completed.
     """
 
-    def __init__(self, model_sets: dict, streams: int = 2, device="cuda"):
+    def __init__(self, model_sets: dict, streams: int = 3, device="cuda"):
         self.sets = model_sets
         self.device = torch.device(device)
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(streams)]

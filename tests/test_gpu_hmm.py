@@ -104,3 +104,10 @@ def test_unsupported_state_count(ks):
     assert ks.lib().ks_hmm_workspace_bytes(3, 10) == 0
     assert ks.lib().ks_hmm_smooth(ctypes.byref(h), ks._p(lik), 10, None, 0, ks._p(out), None, None,
                                   ks._stream(None)) == ks.KS_EUNSUPPORTED
+
+
+def test_bench_workload_full_size(ks):
+    """The discrete-state bench workload at its full size (K = 8, T = 2^20),
+    every step against the oracle."""
+    e = check(ks, workloads.hmm_sequence(8, 1 << 20, seed=workloads.SEED_BASE + 7))
+    print("HMM K=8 T=2^20 errors (filt, smooth, loglik)", e)

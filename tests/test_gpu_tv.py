@@ -124,3 +124,11 @@ def test_entry_points_without_time_varying_support(ks):
     assert L.ks_smooth(ctypes.byref(big), ks._p(y), 64, ks._p(ws), ws.numel(), None, None, ks._p(fm), ks._p(fP),
                        st) == ks.KS_EUNSUPPORTED
     torch.cuda.synchronize()
+
+
+def test_bench_workload_full_size(ks):
+    """The time-varying bench workload at its full size (T = 2^20, the launch
+    configuration bench.py times), every step against the oracle."""
+    import workloads as w
+    e = check(ks, w.irregular_tracking(1 << 20, seed=w.SEED_BASE + 6))
+    print("time-varying T=2^20 errors", e)
