@@ -770,6 +770,46 @@ def run_batched(args, rank, world, local):
         ms = float(t.item())
     value = total * world / (ms / 1e3)
 
+    # end to end through the public API: each group's measurements in from
+    # pinned host memory, its smoothed means and covariances back
+    for g in groups:
+        nx = g["nx"]
+        g["y_h"] = g["y"].cpu().pin_memory()
+        g["sm_h"] = torch.empty(g["T"], nx).pin_memory()
+        g["sP_h"] = torch.empty(g["T"], nx, nx).pin_memory()
+        g["y_d"] = torch.empty_like(g["y"])
+
+    def e2e_step():
+        main = torch.cuda.current_stream()
+        for g in groups:
+            g["stream"].wait_stream(main)
+            with torch.cuda.stream(g["stream"]):
+                fm, fP, sm, sP = g["outs"]
+                g["y_d"].copy_(g["y_h"], non_blocking=True)
+                ks.smooth_batch(g["batch"], g["y_d"], g["ws"], fmean=fm, fcov=fP, smean=sm, scov=sP)
+                g["sm_h"].copy_(sm, non_blocking=True)
+                g["sP_h"].copy_(sP, non_blocking=True)
+        for g in groups:
+            main.wait_stream(g["stream"])
+
+    e2e_times = []
+    for i in range(args.warmup + args.steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        e2e_step()
+        b.record()
+        b.synchronize()
+        if i >= args.warmup:
+            e2e_times.append(a.elapsed_time(b))
+    for g in groups:
+        if ks.status(g["ws"]) != ks.KS_OK:
+            raise SystemExit(f"device status not OK after the end-to-end steps (nx={g['nx']})")
+    e2e = {"value": total * world / (statistics.mean(e2e_times) / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": int(sum(g["y_h"].numel() * 4 for g in groups)),
+           "d2h_bytes_per_step": int(sum((g["sm_h"].numel() + g["sP_h"].numel()) * 4 for g in groups))}
+
     # the plain single-sequence scan, one call per sequence, same GPU
     plain = []
     for q in seqs:
@@ -835,7 +875,7 @@ def run_batched(args, rank, world, local):
            "latency": {"p50_ms": float(np.percentile(times, 50)), "p99_ms": float(np.percentile(times, 99))},
            "plain_scan": {"value": total / (pms / 1e3), "unit": UNIT, "ms_per_pass": pms,
                           "how": "ks_smooth once per sequence, sequentially on one stream"},
-           "roofline": roof}
+           "e2e": e2e, "roofline": roof}
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_oracle_batched(seqs, args.cpu_seconds)
     print(json.dumps(out))
