@@ -21,6 +21,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -58,6 +59,7 @@ def parse():
                          "tv: one T=2^20 nx=4 sequence with a time-varying model (irregular sampling); "
                          "hmm: one T=2^20 discrete-state sequence, K=8 regimes")
     ap.add_argument("--batch", type=int, default=4096)
+    ap.add_argument("--hmm-k", type=int, default=8, choices=[2, 4, 8, 32], help="hmm: number of states")
     ap.add_argument("--rates", default="100,300,1000,3000,10000", help="serving: request rates (req/s)")
     ap.add_argument("--duration", type=float, default=10.0, help="serving: seconds of arrivals per rate")
     ap.add_argument("--streams", type=int, default=3, help="serving: launches in flight")
@@ -541,7 +543,7 @@ def run_hmm(args, rank, world, local):
         _build.build()
     if world > 1:
         dist.barrier()
-    K = 8
+    K = args.hmm_k
     T = args.T
     seq = workloads.hmm_sequence(K, T, seed=workloads.SEED_BASE + 7 + rank)
     dev = torch.device("cuda", local)
@@ -617,6 +619,11 @@ def run_hmm(args, rank, world, local):
            "d2h_bytes_per_step": int((filt_h.numel() + smooth_h.numel() + ll_h.numel()) * 4)}
 
     flops, nbytes = hmm_work_per_step(K)
+    if K <= 8:
+        launches_per_step = 3
+    else:   # prep, then per scan a reduce, ceil(log2(tiles)) spine levels and an apply (256-step tiles)
+        tiles = -(-T // 256)
+        launches_per_step = 1 + 2 * (2 + max(0, math.ceil(math.log2(tiles))))
     kernels = {"filter": kf, "smoother": ksm}
     dom = max(kernels, key=kernels.get)
     dur_s = kernels[dom] / 1e3
@@ -627,7 +634,8 @@ def run_hmm(args, rank, world, local):
     roof = ({"bound": "alu", "achieved": tfl, "peak": alu_peak, "unit": "TFLOP/s", "frac": tfl / alu_peak}
             if tfl / alu_peak >= gbs / hbm else
             {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm})
-    roof.update({"traffic": recorded_traffic("hmm:" + dom), "kernel": f"hmm_{dom}_kernel<8>",
+    roof.update({"traffic": recorded_traffic("hmm:" + dom) if K == 8 else None,
+                 "kernel": f"hmm_{dom}_kernel<{K}>" if K <= 8 else f"hmmw {dom} reduce+spine+apply (K=32)",
                  "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz" if roof["bound"] == "alu" else which,
                  "ms_per_launch": kernels[dom], "alu_frac": tfl / alu_peak, "hbm_frac": gbs / hbm,
                  "flops_per_step": flops[dom], "bytes_per_step": nbytes[dom],
@@ -639,11 +647,11 @@ def run_hmm(args, rank, world, local):
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": "regime-switching HMM K=8, stay 0.95, y~N(x, 0.6^2), Gaussian likelihood rows",
+           "config": {"workload": f"regime-switching HMM K={K}, stay 0.95, y~N(x, 0.6^2), Gaussian likelihood rows",
                       "T": T, "sequences_per_gpu": 1, "parallelism": f"replicas{world}",
                       "l2": "flushed between timed steps (256 MiB memset outside the events)"},
            "clocks": {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
-           "gpu_launches": 3 * args.steps, "latency": {"p50_ms": float(np.percentile(tot, 50)),
+           "gpu_launches": launches_per_step * args.steps, "latency": {"p50_ms": float(np.percentile(tot, 50)),
                                                        "p99_ms": float(np.percentile(tot, 99))},
            "e2e": e2e, "roofline": roof}
     if world == 1 and not args.no_cpu_baseline:

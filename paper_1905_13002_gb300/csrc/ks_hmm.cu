@@ -6,6 +6,7 @@
 
 #include "../../include/ks.h"
 #include "ks_hmm.cuh"
+#include "ks_hmmw.cuh"
 #include "ks_impl.cuh"
 
 namespace ks {
@@ -111,6 +112,101 @@ int run(const ks_hmm* h, const float* lik, int64_t T, void* ws, size_t ws_bytes,
     return HImpl<K, 32>::smooth(h, lik, T, ws, ws_bytes, filt, smooth, loglik, st, ev);
 }
 
+// K = 32: one warp per chain of CH steps, NW chains per tile (ks_hmmw.cuh).
+struct WImpl {
+    static constexpr int NW = 4, CH = 64, NWS = 4;
+    struct WLayout {
+        int64_t nch = 0;
+        int ntiles = 0;
+        size_t off_const = 0, off_fexcl = 0, off_fsp0 = 0, off_fsp1 = 0, off_schain = 0, off_sexcl = 0,
+               off_ssp0 = 0, off_ssp1 = 0, bytes = 0;
+    };
+    static WLayout layout(int64_t T) {
+        using namespace hmmw;
+        WLayout L;
+        L.nch = (T + CH - 1) / CH;
+        L.ntiles = (int)((L.nch + NW - 1) / NW);
+        size_t off = 256;
+        L.off_const = off;
+        off = align_up(off + sizeof(hmmw::Const), 256);
+        L.off_fexcl = off;
+        off = align_up(off + 4 * (size_t)FREC * L.nch, 256);
+        L.off_fsp0 = off;
+        off = align_up(off + 4 * (size_t)FREC * L.ntiles, 256);
+        L.off_fsp1 = off;
+        off = align_up(off + 4 * (size_t)FREC * L.ntiles, 256);
+        L.off_schain = off;
+        off = align_up(off + 4 * (size_t)SREC * L.nch, 256);
+        L.off_sexcl = off;
+        off = align_up(off + 4 * (size_t)SREC * L.nch, 256);
+        L.off_ssp0 = off;
+        off = align_up(off + 4 * (size_t)SREC * L.ntiles, 256);
+        L.off_ssp1 = off;
+        off = align_up(off + 4 * (size_t)SREC * L.ntiles, 256);
+        L.bytes = off;
+        return L;
+    }
+
+    static int smooth(const ks_hmm* h, const float* lik, int64_t T, void* ws, size_t ws_bytes, float* filt,
+                      float* smooth, float* loglik, cudaStream_t st, void* const* ev) {
+        using namespace hmmw;
+        const WLayout L = layout(T);
+        if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) != 0 || ws_bytes < L.bytes) return KS_EINVAL;
+        if (!aligned16(lik)) return KS_EINVAL;   // likelihood rows are read as float4
+        char* b = static_cast<char*>(ws);
+        uint32_t* stat = static_cast<uint32_t*>(ws);
+        hmmw::Const* cg = reinterpret_cast<hmmw::Const*>(b + L.off_const);
+        hmmw::Bufs bf;
+        bf.fexcl = reinterpret_cast<float*>(b + L.off_fexcl);
+        bf.fspine0 = reinterpret_cast<float*>(b + L.off_fsp0);
+        bf.fspine1 = reinterpret_cast<float*>(b + L.off_fsp1);
+        bf.schain = reinterpret_cast<float*>(b + L.off_schain);
+        bf.sexcl = reinterpret_cast<float*>(b + L.off_sexcl);
+        bf.sspine0 = reinterpret_cast<float*>(b + L.off_ssp0);
+        bf.sspine1 = reinterpret_cast<float*>(b + L.off_ssp1);
+        auto rec = [&](int i) {
+            return (ev && ev[i] && cudaEventRecord(static_cast<cudaEvent_t>(ev[i]), st) != cudaSuccess) ? KS_ECUDA
+                                                                                                        : KS_OK;
+        };
+        const int sgrid = (L.ntiles + NWS - 1) / NWS;
+        int rc;
+        if ((rc = rec(0))) return rc;
+        hmmw::prep_kernel<<<1, 64, 0, st>>>(h->pi, h->Pi, cg, stat);
+        if ((rc = launch_status())) return rc;
+        if ((rc = rec(1))) return rc;
+        filter_reduce_kernel<NW, CH><<<L.ntiles, NW * 32, 0, st>>>(cg, lik, T, bf, stat);
+        if ((rc = launch_status())) return rc;
+        const float* src = bf.fspine0;
+        float* dst = bf.fspine1;
+        for (int s = 1; s < L.ntiles; s <<= 1) {
+            spine_kernel<true, NWS><<<sgrid, NWS * 32, 0, st>>>(src, dst, L.ntiles, s, stat);
+            if ((rc = launch_status())) return rc;
+            float* t = const_cast<float*>(src);
+            src = dst;
+            dst = t;
+        }
+        filter_apply_kernel<NW, CH><<<L.ntiles, NW * 32, 0, st>>>(cg, lik, T, filt, loglik, bf, src, stat);
+        if ((rc = launch_status())) return rc;
+        if ((rc = rec(2))) return rc;
+        if (smooth) {
+            smoother_reduce_kernel<NW><<<L.ntiles, NW * 32, 0, st>>>(L.nch, bf, stat);
+            if ((rc = launch_status())) return rc;
+            const float* ssrc = bf.sspine0;
+            float* sdst = bf.sspine1;
+            for (int s = 1; s < L.ntiles; s <<= 1) {
+                spine_kernel<false, NWS><<<sgrid, NWS * 32, 0, st>>>(ssrc, sdst, L.ntiles, s, stat);
+                if ((rc = launch_status())) return rc;
+                float* t = const_cast<float*>(ssrc);
+                ssrc = sdst;
+                sdst = t;
+            }
+            smoother_apply_kernel<NW, CH><<<L.ntiles, NW * 32, 0, st>>>(cg, filt, T, smooth, bf, ssrc, stat);
+            if ((rc = launch_status())) return rc;
+        }
+        return rec(3);
+    }
+};
+
 }  // namespace
 }  // namespace hmm
 }  // namespace ks
@@ -119,7 +215,7 @@ using namespace ks;
 
 extern "C" {
 
-int ks_hmm_supported(int K) { return (K == 2 || K == 4 || K == 8) ? 1 : 0; }
+int ks_hmm_supported(int K) { return (K == 2 || K == 4 || K == 8 || K == 32) ? 1 : 0; }
 
 size_t ks_hmm_workspace_bytes(int K, int64_t T) {
     if (T < 1 || T > 0x7fffffffLL) return 0;
@@ -127,6 +223,7 @@ size_t ks_hmm_workspace_bytes(int K, int64_t T) {
         case 2: return hmm::bytes<2>(T);
         case 4: return hmm::bytes<4>(T);
         case 8: return hmm::bytes<8>(T);
+        case 32: return hmm::WImpl::layout(T).bytes;
         default: return 0;
     }
 }
@@ -140,7 +237,8 @@ int ks_hmm_smooth_traced(const ks_hmm* h, const float* lik, int64_t T, void* ws,
     switch (h->K) {
         case 2: return hmm::run<2>(h, lik, T, ws, ws_bytes, filt, smooth, loglik, st, events);
         case 4: return hmm::run<4>(h, lik, T, ws, ws_bytes, filt, smooth, loglik, st, events);
-        default: return hmm::run<8>(h, lik, T, ws, ws_bytes, filt, smooth, loglik, st, events);
+        case 8: return hmm::run<8>(h, lik, T, ws, ws_bytes, filt, smooth, loglik, st, events);
+        default: return hmm::WImpl::smooth(h, lik, T, ws, ws_bytes, filt, smooth, loglik, st, events);
     }
 }
 

@@ -59,6 +59,23 @@ def test_other_state_counts(ks, K, T):
     check(ks, workloads.hmm_sequence(K, T, seed=8100 + T + K))
 
 
+# K = 32 runs one warp per chain of 64 steps, 4 chains per tile, with
+# reduce / spine / apply launches: sizes span one chain, one tile (256 steps),
+# ragged tails and many spine levels.
+@pytest.mark.parametrize("T", [1, 2, 63, 64, 65, 255, 256, 257, 5000, 70001])
+def test_k32(ks, T):
+    check(ks, workloads.hmm_sequence(32, T, seed=8500 + T))
+
+
+def test_k32_filter_only(ks):
+    seq = workloads.hmm_sequence(32, 9000, seed=8600)
+    filt, smooth, ll, st = run(ks, seq, filter_only=True)
+    assert st == ks.KS_OK and smooth is None
+    rf, _, rll = ohmm.forward_backward(seq.pi, seq.Pi, seq.lik)
+    assert np.abs(filt.cpu().numpy() - rf).max() < TOL_P
+    assert (np.abs(ll.cpu().numpy() - rll) / np.maximum(1.0, np.abs(rll))).max() < TOL_LL
+
+
 @pytest.mark.parametrize("stay", [0.999, 0.9999])
 def test_nearly_static_chain(ks, stay):
     """Long runs in one state with weak evidence per step (sigma = 1.5).  A
@@ -100,7 +117,7 @@ def test_unsupported_state_count(ks):
     h = ks._KsHmm(3, 0, pi.data_ptr(), Pi.data_ptr())
     lik = torch.ones(10, 3, device="cuda")
     out = torch.empty(10, 3, device="cuda")
-    assert not ks.hmm_supported(3)
+    assert not ks.hmm_supported(3) and ks.hmm_supported(32)
     assert ks.lib().ks_hmm_workspace_bytes(3, 10) == 0
     assert ks.lib().ks_hmm_smooth(ctypes.byref(h), ks._p(lik), 10, None, 0, ks._p(out), None, None,
                                   ks._stream(None)) == ks.KS_EUNSUPPORTED
