@@ -59,7 +59,7 @@ def parse():
                          "tv: one T=2^20 nx=4 sequence with a time-varying model (irregular sampling); "
                          "hmm: one T=2^20 discrete-state sequence, K=8 regimes")
     ap.add_argument("--batch", type=int, default=4096)
-    ap.add_argument("--hmm-k", type=int, default=8, choices=[2, 4, 8, 32], help="hmm: number of states")
+    ap.add_argument("--hmm-k", type=int, default=8, choices=[2, 4, 8, 16, 32], help="hmm: number of states")
     ap.add_argument("--rates", default="100,300,1000,3000,10000", help="serving: request rates (req/s)")
     ap.add_argument("--duration", type=float, default=10.0, help="serving: seconds of arrivals per rate")
     ap.add_argument("--streams", type=int, default=3, help="serving: launches in flight")
@@ -217,15 +217,13 @@ def cpu_oracle_rate(seq, seconds: float) -> dict:
             "sample": f"{reps} full passes over the T={seq.T} sequence ({el:.1f} s, 1 thread)"}
 
 
-# The sources each recorded kernel is built from (its traffic record is
+# The sources that define each recorded kernel's code (its traffic record is
 # dropped when any of them changes).
 KERNEL_SOURCES = {
     "filter_scan_kernel": ["ks_ops.cuh", "ks_async.cuh", "ks_scan.cuh", "ks_impl.cuh", "ks_inst_4_2.cu"],
     "smoother_scan_kernel": ["ks_ops.cuh", "ks_async.cuh", "ks_scan.cuh", "ks_impl.cuh", "ks_inst_4_2.cu"],
-    "tfilter_reduce+spine+apply": ["ks_ops.cuh", "ks_scan.cuh", "ks_tc.cuh", "ks_tscan.cuh", "ks_timpl.cuh",
-                                   "ks_inst_32_8.cu"],
-    "tsmoother_reduce+spine+apply": ["ks_ops.cuh", "ks_scan.cuh", "ks_tc.cuh", "ks_tscan.cuh", "ks_timpl.cuh",
-                                     "ks_inst_32_8.cu"],
+    "tfilter_reduce+spine+apply": ["ks_tc.cuh", "ks_tscan.cuh"],
+    "tsmoother_reduce+spine+apply": ["ks_tc.cuh", "ks_tscan.cuh"],
     "tv:elements": ["ks_ops.cuh", "ks_scan.cuh", "ks_impl.cuh"],
     "hmm:filter": ["ks_scan.cuh", "ks_hmm.cuh", "ks_hmm.cu"],
     "hmm:smoother": ["ks_scan.cuh", "ks_hmm.cuh", "ks_hmm.cu"],
@@ -621,8 +619,8 @@ def run_hmm(args, rank, world, local):
     flops, nbytes = hmm_work_per_step(K)
     if K <= 8:
         launches_per_step = 3
-    else:   # prep, then per scan a reduce, ceil(log2(tiles)) spine levels and an apply (256-step tiles)
-        tiles = -(-T // 256)
+    else:   # prep, then per scan a reduce, ceil(log2(tiles)) spine levels and an apply
+        tiles = -(-T // (64 * 128 // K))    # 64 steps per chain, 128 / K chains per tile
         launches_per_step = 1 + 2 * (2 + max(0, math.ceil(math.log2(tiles))))
     kernels = {"filter": kf, "smoother": ksm}
     dom = max(kernels, key=kernels.get)
@@ -635,7 +633,7 @@ def run_hmm(args, rank, world, local):
             if tfl / alu_peak >= gbs / hbm else
             {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm})
     roof.update({"traffic": recorded_traffic("hmm:" + dom) if K == 8 else None,
-                 "kernel": f"hmm_{dom}_kernel<{K}>" if K <= 8 else f"hmmw {dom} reduce+spine+apply (K=32)",
+                 "kernel": f"hmm_{dom}_kernel<{K}>" if K <= 8 else f"hmmw {dom} reduce+spine+apply (K={K})",
                  "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz" if roof["bound"] == "alu" else which,
                  "ms_per_launch": kernels[dom], "alu_frac": tfl / alu_peak, "hbm_frac": gbs / hbm,
                  "flops_per_step": flops[dom], "bytes_per_step": nbytes[dom],

@@ -342,8 +342,8 @@ int ks_smoother_combine_batch(int nx, int64_t count, const float *left, const fl
  * lik [T][K], lik[k][j] = p(y_k | x_k = j) >= 0 (any emission model; a row
  * needs a positive entry).  pi and Pi: device FP32 (ks_hmm holds device
  * pointers; the struct itself is a host object).  Supported K:
- * ks_hmm_supported(K) (2, 4, 8 and 32); others return KS_EUNSUPPORTED.  At
- * K = 32 lik must be 16-byte aligned (KS_EINVAL otherwise).
+ * ks_hmm_supported(K) (2, 4, 8, 16 and 32); others return KS_EUNSUPPORTED.
+ * At K = 16 and 32 lik must be 16-byte aligned (KS_EINVAL otherwise).
  *
  * ks_hmm_smooth writes, device FP32:
  *   filt   [T][K]  p(x_k | y_1:k)      (required; the smoother reads it back);

@@ -112,9 +112,12 @@ int run(const ks_hmm* h, const float* lik, int64_t T, void* ws, size_t ws_bytes,
     return HImpl<K, 32>::smooth(h, lik, T, ws, ws_bytes, filt, smooth, loglik, st, ev);
 }
 
-// K = 32: one warp per chain of CH steps, NW chains per tile (ks_hmmw.cuh).
+// K = 16, 32: one K-lane group per chain of CH steps, NG chains per tile
+// (ks_hmmw.cuh).
+template <int K>
 struct WImpl {
     static constexpr int NW = 4, CH = 64, NWS = 4;
+    static constexpr int NG = NW * 32 / K;
     struct WLayout {
         int64_t nch = 0;
         int ntiles = 0;
@@ -122,27 +125,27 @@ struct WImpl {
                off_ssp0 = 0, off_ssp1 = 0, bytes = 0;
     };
     static WLayout layout(int64_t T) {
-        using namespace hmmw;
+        using D = hmmw::Dims<K>;
         WLayout L;
         L.nch = (T + CH - 1) / CH;
-        L.ntiles = (int)((L.nch + NW - 1) / NW);
+        L.ntiles = (int)((L.nch + NG - 1) / NG);
         size_t off = 256;
         L.off_const = off;
-        off = align_up(off + sizeof(hmmw::Const), 256);
+        off = align_up(off + sizeof(hmmw::Const<K>), 256);
         L.off_fexcl = off;
-        off = align_up(off + 4 * (size_t)FREC * L.nch, 256);
+        off = align_up(off + 4 * (size_t)D::FREC * L.nch, 256);
         L.off_fsp0 = off;
-        off = align_up(off + 4 * (size_t)FREC * L.ntiles, 256);
+        off = align_up(off + 4 * (size_t)D::FREC * L.ntiles, 256);
         L.off_fsp1 = off;
-        off = align_up(off + 4 * (size_t)FREC * L.ntiles, 256);
+        off = align_up(off + 4 * (size_t)D::FREC * L.ntiles, 256);
         L.off_schain = off;
-        off = align_up(off + 4 * (size_t)SREC * L.nch, 256);
+        off = align_up(off + 4 * (size_t)D::SREC * L.nch, 256);
         L.off_sexcl = off;
-        off = align_up(off + 4 * (size_t)SREC * L.nch, 256);
+        off = align_up(off + 4 * (size_t)D::SREC * L.nch, 256);
         L.off_ssp0 = off;
-        off = align_up(off + 4 * (size_t)SREC * L.ntiles, 256);
+        off = align_up(off + 4 * (size_t)D::SREC * L.ntiles, 256);
         L.off_ssp1 = off;
-        off = align_up(off + 4 * (size_t)SREC * L.ntiles, 256);
+        off = align_up(off + 4 * (size_t)D::SREC * L.ntiles, 256);
         L.bytes = off;
         return L;
     }
@@ -151,11 +154,12 @@ struct WImpl {
                       float* smooth, float* loglik, cudaStream_t st, void* const* ev) {
         using namespace hmmw;
         const WLayout L = layout(T);
+        const int sgrid_tiles = NWS * 32 / K;   // tiles per spine block
         if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) != 0 || ws_bytes < L.bytes) return KS_EINVAL;
         if (!aligned16(lik)) return KS_EINVAL;   // likelihood rows are read as float4
         char* b = static_cast<char*>(ws);
         uint32_t* stat = static_cast<uint32_t*>(ws);
-        hmmw::Const* cg = reinterpret_cast<hmmw::Const*>(b + L.off_const);
+        hmmw::Const<K>* cg = reinterpret_cast<hmmw::Const<K>*>(b + L.off_const);
         hmmw::Bufs bf;
         bf.fexcl = reinterpret_cast<float*>(b + L.off_fexcl);
         bf.fspine0 = reinterpret_cast<float*>(b + L.off_fsp0);
@@ -168,39 +172,39 @@ struct WImpl {
             return (ev && ev[i] && cudaEventRecord(static_cast<cudaEvent_t>(ev[i]), st) != cudaSuccess) ? KS_ECUDA
                                                                                                         : KS_OK;
         };
-        const int sgrid = (L.ntiles + NWS - 1) / NWS;
+        const int sgrid = (L.ntiles + sgrid_tiles - 1) / sgrid_tiles;
         int rc;
         if ((rc = rec(0))) return rc;
-        hmmw::prep_kernel<<<1, 64, 0, st>>>(h->pi, h->Pi, cg, stat);
+        hmmw::prep_kernel<K><<<1, 64, 0, st>>>(h->pi, h->Pi, cg, stat);
         if ((rc = launch_status())) return rc;
         if ((rc = rec(1))) return rc;
-        filter_reduce_kernel<NW, CH><<<L.ntiles, NW * 32, 0, st>>>(cg, lik, T, bf, stat);
+        filter_reduce_kernel<K, NW, CH><<<L.ntiles, NW * 32, 0, st>>>(cg, lik, T, bf, stat);
         if ((rc = launch_status())) return rc;
         const float* src = bf.fspine0;
         float* dst = bf.fspine1;
         for (int s = 1; s < L.ntiles; s <<= 1) {
-            spine_kernel<true, NWS><<<sgrid, NWS * 32, 0, st>>>(src, dst, L.ntiles, s, stat);
+            spine_kernel<true, K, NWS><<<sgrid, NWS * 32, 0, st>>>(src, dst, L.ntiles, s, stat);
             if ((rc = launch_status())) return rc;
             float* t = const_cast<float*>(src);
             src = dst;
             dst = t;
         }
-        filter_apply_kernel<NW, CH><<<L.ntiles, NW * 32, 0, st>>>(cg, lik, T, filt, loglik, bf, src, stat);
+        filter_apply_kernel<K, NW, CH><<<L.ntiles, NW * 32, 0, st>>>(cg, lik, T, filt, loglik, bf, src, stat);
         if ((rc = launch_status())) return rc;
         if ((rc = rec(2))) return rc;
         if (smooth) {
-            smoother_reduce_kernel<NW><<<L.ntiles, NW * 32, 0, st>>>(L.nch, bf, stat);
+            smoother_reduce_kernel<K, NW><<<L.ntiles, NW * 32, 0, st>>>(L.nch, bf, stat);
             if ((rc = launch_status())) return rc;
             const float* ssrc = bf.sspine0;
             float* sdst = bf.sspine1;
             for (int s = 1; s < L.ntiles; s <<= 1) {
-                spine_kernel<false, NWS><<<sgrid, NWS * 32, 0, st>>>(ssrc, sdst, L.ntiles, s, stat);
+                spine_kernel<false, K, NWS><<<sgrid, NWS * 32, 0, st>>>(ssrc, sdst, L.ntiles, s, stat);
                 if ((rc = launch_status())) return rc;
                 float* t = const_cast<float*>(ssrc);
                 ssrc = sdst;
                 sdst = t;
             }
-            smoother_apply_kernel<NW, CH><<<L.ntiles, NW * 32, 0, st>>>(cg, filt, T, smooth, bf, ssrc, stat);
+            smoother_apply_kernel<K, NW, CH><<<L.ntiles, NW * 32, 0, st>>>(cg, filt, T, smooth, bf, ssrc, stat);
             if ((rc = launch_status())) return rc;
         }
         return rec(3);
@@ -215,7 +219,7 @@ using namespace ks;
 
 extern "C" {
 
-int ks_hmm_supported(int K) { return (K == 2 || K == 4 || K == 8 || K == 32) ? 1 : 0; }
+int ks_hmm_supported(int K) { return (K == 2 || K == 4 || K == 8 || K == 16 || K == 32) ? 1 : 0; }
 
 size_t ks_hmm_workspace_bytes(int K, int64_t T) {
     if (T < 1 || T > 0x7fffffffLL) return 0;
@@ -223,7 +227,8 @@ size_t ks_hmm_workspace_bytes(int K, int64_t T) {
         case 2: return hmm::bytes<2>(T);
         case 4: return hmm::bytes<4>(T);
         case 8: return hmm::bytes<8>(T);
-        case 32: return hmm::WImpl::layout(T).bytes;
+        case 16: return hmm::WImpl<16>::layout(T).bytes;
+        case 32: return hmm::WImpl<32>::layout(T).bytes;
         default: return 0;
     }
 }
@@ -238,7 +243,8 @@ int ks_hmm_smooth_traced(const ks_hmm* h, const float* lik, int64_t T, void* ws,
         case 2: return hmm::run<2>(h, lik, T, ws, ws_bytes, filt, smooth, loglik, st, events);
         case 4: return hmm::run<4>(h, lik, T, ws, ws_bytes, filt, smooth, loglik, st, events);
         case 8: return hmm::run<8>(h, lik, T, ws, ws_bytes, filt, smooth, loglik, st, events);
-        default: return hmm::WImpl::smooth(h, lik, T, ws, ws_bytes, filt, smooth, loglik, st, events);
+        case 16: return hmm::WImpl<16>::smooth(h, lik, T, ws, ws_bytes, filt, smooth, loglik, st, events);
+        default: return hmm::WImpl<32>::smooth(h, lik, T, ws, ws_bytes, filt, smooth, loglik, st, events);
     }
 }
 

@@ -59,12 +59,17 @@ def test_other_state_counts(ks, K, T):
     check(ks, workloads.hmm_sequence(K, T, seed=8100 + T + K))
 
 
-# K = 32 runs one warp per chain of 64 steps, 4 chains per tile, with
-# reduce / spine / apply launches: sizes span one chain, one tile (256 steps),
-# ragged tails and many spine levels.
+# K = 16 and 32 run one K-lane group per chain of 64 steps (8 or 4 chains
+# per tile) with reduce / spine / apply launches: sizes span one chain, one
+# tile (512 or 256 steps), ragged tails and many spine levels.
 @pytest.mark.parametrize("T", [1, 2, 63, 64, 65, 255, 256, 257, 5000, 70001])
 def test_k32(ks, T):
     check(ks, workloads.hmm_sequence(32, T, seed=8500 + T))
+
+
+@pytest.mark.parametrize("T", [1, 2, 64, 65, 511, 512, 513, 5000, 70001])
+def test_k16(ks, T):
+    check(ks, workloads.hmm_sequence(16, T, seed=8700 + T))
 
 
 def test_k32_filter_only(ks):
@@ -117,7 +122,7 @@ def test_unsupported_state_count(ks):
     h = ks._KsHmm(3, 0, pi.data_ptr(), Pi.data_ptr())
     lik = torch.ones(10, 3, device="cuda")
     out = torch.empty(10, 3, device="cuda")
-    assert not ks.hmm_supported(3) and ks.hmm_supported(32)
+    assert not ks.hmm_supported(3) and ks.hmm_supported(16) and ks.hmm_supported(32)
     assert ks.lib().ks_hmm_workspace_bytes(3, 10) == 0
     assert ks.lib().ks_hmm_smooth(ctypes.byref(h), ks._p(lik), 10, None, 0, ks._p(out), None, None,
                                   ks._stream(None)) == ks.KS_EUNSUPPORTED
