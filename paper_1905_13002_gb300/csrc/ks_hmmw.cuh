@@ -16,8 +16,9 @@
 //    smoothing aggregate;
 //  * reverse reduce / spine / apply over those aggregates in reversed order,
 //    the apply walking each chain backwards from its suffix.
-// Likelihood rows are scaled to a maximum of 1 and g is kept as log g
-// (R20); products of row-stochastic matrices are rescaled to unit row sums.
+// Likelihood rows are scaled to a maximum of 1 and g is kept as log g, so
+// that p(y_1:k) survives long prefixes in FP32; products of row-stochastic
+// matrices are rescaled to unit row sums.
 #pragma once
 
 #include "ks_scan.cuh"
