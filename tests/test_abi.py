@@ -95,3 +95,28 @@ def test_product_path_has_no_oracle_dependency():
                     text = fh.read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "kf_rts" not in text and "libks_oracle" not in text, f
+
+
+def test_hmm_host_queries_and_argument_errors(ks):
+    """The discrete-state entry points: supported sizes, workspace sizes, and
+    argument errors returned before any device work."""
+    L = ks.lib()
+    for K in (2, 4, 8, 16, 32):
+        assert L.ks_hmm_supported(K) == 1
+        assert L.ks_hmm_workspace_bytes(K, 1000) > 0
+    for K in (0, 3, 64):
+        assert L.ks_hmm_supported(K) == 0
+        assert L.ks_hmm_workspace_bytes(K, 1000) == 0
+    assert L.ks_hmm_workspace_bytes(8, 0) == 0
+    # bigger T, bigger workspace
+    assert L.ks_hmm_workspace_bytes(32, 1 << 20) > L.ks_hmm_workspace_bytes(32, 1 << 10)
+    h3 = ks._KsHmm(3, 0, 16, 16)
+    assert L.ks_hmm_smooth(ctypes.byref(h3), 16, 10, 256, 1 << 20, 16, None, None, None) == ks.KS_EUNSUPPORTED
+    h8 = ks._KsHmm(8, 0, 16, 16)
+    assert L.ks_hmm_smooth(ctypes.byref(h8), None, 10, 256, 1 << 20, 16, None, None, None) == ks.KS_EINVAL
+    assert L.ks_hmm_smooth(ctypes.byref(h8), 16, 0, 256, 1 << 20, 16, None, None, None) == ks.KS_EINVAL
+    assert L.ks_hmm_smooth(ctypes.byref(h8), 16, 10, 256, 16, 16, None, None, None) == ks.KS_EINVAL   # workspace
+    h32 = ks._KsHmm(32, 0, 16, 16)   # misaligned likelihood rows
+    assert L.ks_hmm_smooth(ctypes.byref(h32), 4, 10, 256, 1 << 30, 16, None, None, None) == ks.KS_EINVAL
+    hnull = ks._KsHmm(8, 0, 0, 16)
+    assert L.ks_hmm_smooth(ctypes.byref(hnull), 16, 10, 256, 1 << 20, 16, None, None, None) == ks.KS_EINVAL
