@@ -95,18 +95,26 @@ KS_DEV void st_release(uint32_t* p, uint32_t v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+KS_DEV uint32_t ld_relaxed(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
 // Poll a flag until it is non-zero, at most `limit` times with a growing
-// sleep; returns 0 if it never became non-zero.
+// sleep; returns 0 if it never became non-zero.  Polls are relaxed loads; the
+// value that ends the wait is read once more with acquire semantics, which
+// orders the caller's later loads after it.
 KS_DEV uint32_t wait_flag(const uint32_t* p, uint32_t limit) {
-    uint32_t v = ld_acquire(p);
+    uint32_t v = ld_relaxed(p);
     uint32_t ns = 32;
     for (uint32_t it = 0; v == 0u; ++it) {
         if (it >= limit) return 0u;
         __nanosleep(ns);
         if (ns < 1024) ns <<= 1;
-        v = ld_acquire(p);
+        v = ld_relaxed(p);
     }
-    return v;
+    return ld_acquire(p);
 }
 
 // ---------------------------------------------------------------- vector I/O
@@ -382,6 +390,33 @@ KS_DEV void build_selem_tv(const TVArgs& tv, int64_t k, int64_t T, const float (
         Trans<N> t;
         load_trans<N>(tv, k + 1, t);
         smoother_element<N, M>(t, xb, P, e, bad);
+    }
+}
+
+// Lemma 5 element of step k with no branch around its arithmetic, so that
+// two calls can be interleaved: the element is always built from the step's
+// transition (a time-varying model's k + 1, or k itself when k = n, whose
+// result is discarded) and the k = n case (E = 0, g = xbar_n, L = P_n) then
+// replaces it.
+template <int N, int M, bool TV>
+KS_DEV void build_selem_flat(const ModelConst<N, M>* mc, const TVArgs& tv, int64_t k, int64_t T, bool last,
+                             const float (&xb)[N], const float (&P)[sym_size(N)], SElem<N>& e, bool& bad) {
+    bool b = false;
+    if constexpr (TV) {
+        Trans<N> t;
+        load_trans<N>(tv, last ? k : k + 1, t);
+        smoother_element<N, M>(t, xb, P, e, b);
+    } else {
+        smoother_element<N, M>(*mc, xb, P, e, b);
+    }
+    bad |= b && !last;
+    if (last) {
+#pragma unroll
+        for (int a = 0; a < N * N; ++a) e.E[a] = 0.f;
+#pragma unroll
+        for (int a = 0; a < N; ++a) e.g[a] = xb[a];
+#pragma unroll
+        for (int a = 0; a < sym_size(N); ++a) e.L[a] = P[a];
     }
 }
 
@@ -1352,18 +1387,26 @@ __global__ void __launch_bounds__(NT) filter_scan_kernel(const ModelConst<N, M>*
         set_identity<N>(acc);
     } else if constexpr (FROM_Y) {
         cur.seek(segs, &mc, k0, T);
+        // y of the next step is loaded one step ahead, so that its latency
+        // overlaps the current step's combine
+        float yn[M];
+        load_meas<M>(y, k0, yn);
         if (cur.first(k0)) {
             first_element<N, M>(*cur.mc, acc);
         } else {
-            float yk[M], b[N], w[M];
-            load_meas<M>(y, k0, yk);
-            meas_element<N, M>(*cur.mc, yk, b, w);
+            float b[N], w[M];
+            meas_element<N, M>(*cur.mc, yn, b, w);
             expand_meas<N, M>(*cur.mc, b, w, acc);
         }
+        if (k0 + 1 < T) load_meas<M>(y, k0 + 1, yn);
 #pragma unroll 1
         for (int i = 1; i < CH; ++i) {
             const int64_t k = k0 + i;
             if (k >= T) break;
+            float yk[M];
+#pragma unroll
+            for (int a = 0; a < M; ++a) yk[a] = yn[a];
+            if (i + 1 < CH && k + 1 < T) load_meas<M>(y, k + 1, yn);
             cur.forward(segs, k);
             if (cur.first(k)) {   // acc (x) a_1 = (0, b_1, C_1, eta_acc, J_acc) since A_1 = 0, eta_1 = J_1 = 0
 #pragma unroll
@@ -1373,8 +1416,7 @@ __global__ void __launch_bounds__(NT) filter_scan_kernel(const ModelConst<N, M>*
 #pragma unroll
                 for (int a = 0; a < sym_size(N); ++a) acc.C[a] = cur.mc->C1[a];
             } else {
-                float yk[M], b[N], w[M];
-                load_meas<M>(y, k, yk);
+                float b[N], w[M];
                 meas_element<N, M>(*cur.mc, yk, b, w);
                 acc = fcombine_meas<N, M>(acc, *cur.mc, b, w, bad);
             }
@@ -1413,12 +1455,20 @@ __global__ void __launch_bounds__(NT) filter_scan_kernel(const ModelConst<N, M>*
         bool pending = false;
         float probe = 0.f;
         SElem<N> sacc;
-        if constexpr (FROM_Y) cur.seek(segs, &mc, k0, T);
+        float yn[M];
+        if constexpr (FROM_Y) {
+            cur.seek(segs, &mc, k0, T);
+            load_meas<M>(y, k0, yn);
+        }
 #pragma unroll 1
         for (int i = 0; i < CH; ++i) {
             const int64_t k = k0 + i;
             if (k >= T) break;
             if constexpr (FROM_Y) {
+                float yk[M];
+#pragma unroll
+                for (int a = 0; a < M; ++a) yk[a] = yn[a];
+                if (i + 1 < CH && k + 1 < T) load_meas<M>(y, k + 1, yn);   // one step ahead
                 cur.forward(segs, k);
                 if (cur.first(k)) {  // posterior (x) a_1 = (b_1, C_1): A_1 = 0
 #pragma unroll
@@ -1427,8 +1477,7 @@ __global__ void __launch_bounds__(NT) filter_scan_kernel(const ModelConst<N, M>*
                     for (int a = 0; a < sym_size(N); ++a) st.C[a] = cur.mc->C1[a];
                     has = true;
                 } else {
-                    float yk[M], b[N], w[M];
-                    load_meas<M>(y, k, yk);
+                    float b[N], w[M];
                     meas_element<N, M>(*cur.mc, yk, b, w);
                     fadvance_meas<N, M>(st, *cur.mc, b, w, bad);
                 }
@@ -1528,6 +1577,12 @@ struct RevReader {
     }
 };
 
+// With staged reads the reverse scan's shared memory allows two blocks per SM,
+// so up to 255 registers per thread cost no occupancy and the paired element
+// builds of phase 3 keep theirs; otherwise the compiler's default applies (0).
+template <int N>
+constexpr int kRevMinBlocks = Stage<N>::kOn ? 2 : 0;
+
 // Blocks of CH steps start at multiples of CH from step 0 (the forward
 // scan's grid); the reverse scan visits them last block first.  With FROM_AGG
 // each thread's block aggregate comes from the forward scan (`sagg`);
@@ -1535,7 +1590,7 @@ struct RevReader {
 // With TV the elements come from a time-varying model's per-step transitions
 // (`tv`) instead of the constant model.
 template <int N, int M, int NT, int CH, bool FROM_AGG, bool SEG, bool TV>
-__global__ void __launch_bounds__(NT) smoother_scan_kernel(const ModelConst<N, M>* __restrict__ mcg,
+__global__ void __launch_bounds__(NT, kRevMinBlocks<N>) smoother_scan_kernel(const ModelConst<N, M>* __restrict__ mcg,
                                                            const float* __restrict__ fmean,
                                                            const float* __restrict__ fcov, int64_t T,
                                                            float* __restrict__ smean,
@@ -1636,24 +1691,61 @@ __global__ void __launch_bounds__(NT) smoother_scan_kernel(const ModelConst<N, M
                 const int gc = rd.gcount(g);
                 const int64_t lo = rd.glo(g);
                 char* b = rd.buf(g);
+                int s = gc - 1;
+                // The next group's moments go into the buffer that the store
+                // of the previous group reads; that store was issued a whole
+                // group ago, so the refill waits for it after this group's
+                // first steps rather than right after issuing a store.
+                bool refill = (g >= 1) && (g + 1 < rd.ngroups);
+                // Two steps at a time: a step's Lemma 5 element depends only on
+                // its filtered moments, not on the running smoothed state, so
+                // the two element builds run side by side and only the two
+                // applications form the chain.
 #pragma unroll 1
-                for (int s = gc - 1; s >= 0; --s) {
-                    float xb[N], P[sym_size(N)];
-                    stage_read<N>(b, s, xb, P);
-                    cur.backward(segs, lo + s);
-                    SElem<N> e;
-                    if constexpr (TV) build_selem_tv<N, M>(tv, lo + s, T, xb, P, e, bad);
-                    else build_selem_from<N, M>(*cur.mc, xb, P, cur.last(lo + s), e, bad);
-                    if (!has) { st = SmootherOp<N>::state_of(e); has = true; }   // only k = T-1
-                    else sadvance<N>(e, st);
+                for (; s >= 1; s -= 2) {
+                    float xa[N], Pa[sym_size(N)], xc[N], Pc[sym_size(N)];
+                    stage_read<N>(b, s, xa, Pa);     // later step
+                    stage_read<N>(b, s - 1, xc, Pc);
+                    const int64_t ka = lo + s, kc = ka - 1;
+                    cur.backward(segs, ka);
+                    const ModelConst<N, M>* ma = cur.mc;
+                    const bool la = TV ? (ka == T - 1) : cur.last(ka);
+                    cur.backward(segs, kc);
+                    const ModelConst<N, M>* mcc = cur.mc;
+                    const bool lc = TV ? (kc == T - 1) : cur.last(kc);
+                    SElem<N> ea, ec;
+                    build_selem_flat<N, M, TV>(ma, tv, ka, T, la, xa, Pa, ea, bad);
+                    build_selem_flat<N, M, TV>(mcc, tv, kc, T, lc, xc, Pc, ec, bad);
+                    if (!has) { st = SmootherOp<N>::state_of(ea); has = true; }   // only k = T-1
+                    else sadvance<N>(ea, st);
                     stage_write<N>(b, s, st.g, st.L);     // the slot's input is already in registers
                     probe += finite_probe<N>(st.g, st.L);
+                    sadvance<N>(ec, st);                  // a segment's last step has E = 0
+                    stage_write<N>(b, s - 1, st.g, st.L);
+                    probe += finite_probe<N>(st.g, st.L);
+                    if (refill) {
+                        bulk_wait_read_all();
+                        rd.fetch(fmean, fcov, g + 1);
+                        refill = false;
+                    }
+                }
+                if (s == 0) {
+                    float xb[N], P[sym_size(N)];
+                    stage_read<N>(b, 0, xb, P);
+                    cur.backward(segs, lo);
+                    SElem<N> e;
+                    if constexpr (TV) build_selem_tv<N, M>(tv, lo, T, xb, P, e, bad);
+                    else build_selem_from<N, M>(*cur.mc, xb, P, cur.last(lo), e, bad);
+                    if (!has) { st = SmootherOp<N>::state_of(e); has = true; }
+                    else sadvance<N>(e, st);
+                    stage_write<N>(b, 0, st.g, st.L);
+                    probe += finite_probe<N>(st.g, st.L);
+                }
+                if (refill) {
+                    bulk_wait_read_all();
+                    rd.fetch(fmean, fcov, g + 1);
                 }
                 stage_flush<N>(b, smean, scov, lo, gc);
-                if (g + 2 < rd.ngroups) {
-                    bulk_wait_read_all();
-                    rd.fetch(fmean, fcov, g + 2);
-                }
             }
             bulk_wait_all();
         } else {
