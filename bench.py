@@ -241,16 +241,17 @@ def source_hash(kernel: str) -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel: str):
+def recorded_traffic(kernel: str, T: int):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources; else None."""
+    on the current kernel sources and holds the figure for this sequence
+    length (another T runs another chunk variant); else None."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         d = json.load(f)
     e = d.get(kernel)
-    if not e or e.get("source_hash") != source_hash(kernel):
+    if not e or e.get("source_hash") != source_hash(kernel) or e.get("T") != T:
         return None
     return e.get("dram_bytes_per_launch_full")
 
@@ -466,7 +467,7 @@ def tv_roofline(nx, ny, T, hbm, which, kernels):
     names = {"elements": "tv_elements_kernel", "filter": "filter_scan_kernel (materialised elements)",
              "smoother": "smoother_scan_kernel (time-varying)"}
     return {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
-            "traffic": recorded_traffic("tv:" + dom), "kernel": names[dom], "peak_source": which,
+            "traffic": recorded_traffic("tv:" + dom, T), "kernel": names[dom], "peak_source": which,
             "ms_per_launch": kernels[dom], "bytes_per_step": bps,
             "kernels_ms": {k: round(v, 4) for k, v in kernels.items()},
             "gbs_by_kernel": {k: round(bps[k] * T / (v / 1e3) / 1e9, 1) for k, v in kernels.items()}}
@@ -483,7 +484,7 @@ def scan_roofline(nx, ny, T, hbm, which, kernels, bps, fps):
     kname = ({"filter": "filter_scan_kernel", "smoother": "smoother_scan_kernel"} if nx <= 6 else
              {"filter": "tfilter_reduce+spine+apply", "smoother": "tsmoother_reduce+spine+apply"} if nx >= 32 else
              {"filter": "gfilter_reduce+spine+apply", "smoother": "gsmoother_reduce+spine+apply"})[dom]
-    traffic = recorded_traffic(kname)
+    traffic = recorded_traffic(kname, T)
     if nx >= 32:
         tpeak, tsrc = tf32_peak()
         tfs = tensor_flops_per_step(nx, ny)[dom]
@@ -632,7 +633,7 @@ def run_hmm(args, rank, world, local):
     roof = ({"bound": "alu", "achieved": tfl, "peak": alu_peak, "unit": "TFLOP/s", "frac": tfl / alu_peak}
             if tfl / alu_peak >= gbs / hbm else
             {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm})
-    roof.update({"traffic": recorded_traffic("hmm:" + dom) if K == 8 else None,
+    roof.update({"traffic": recorded_traffic("hmm:" + dom, T) if K == 8 else None,
                  "kernel": f"hmm_{dom}_kernel<{K}>" if K <= 8 else f"hmmw {dom} reduce+spine+apply (K={K})",
                  "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz" if roof["bound"] == "alu" else which,
                  "ms_per_launch": kernels[dom], "alu_frac": tfl / alu_peak, "hbm_frac": gbs / hbm,

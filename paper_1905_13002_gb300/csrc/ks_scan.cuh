@@ -95,26 +95,18 @@ KS_DEV void st_release(uint32_t* p, uint32_t v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-KS_DEV uint32_t ld_relaxed(const uint32_t* p) {
-    uint32_t v;
-    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
 // Poll a flag until it is non-zero, at most `limit` times with a growing
-// sleep; returns 0 if it never became non-zero.  Polls are relaxed loads; the
-// value that ends the wait is read once more with acquire semantics, which
-// orders the caller's later loads after it.
+// sleep; returns 0 if it never became non-zero.
 KS_DEV uint32_t wait_flag(const uint32_t* p, uint32_t limit) {
-    uint32_t v = ld_relaxed(p);
+    uint32_t v = ld_acquire(p);
     uint32_t ns = 32;
     for (uint32_t it = 0; v == 0u; ++it) {
         if (it >= limit) return 0u;
         __nanosleep(ns);
         if (ns < 1024) ns <<= 1;
-        v = ld_relaxed(p);
+        v = ld_acquire(p);
     }
-    return ld_acquire(p);
+    return v;
 }
 
 // ---------------------------------------------------------------- vector I/O
