@@ -1447,6 +1447,11 @@ __global__ void __launch_bounds__(NT) filter_scan_kernel(const ModelConst<N, M>*
         bool pending = false;
         float probe = 0.f;
         SElem<N> sacc;
+        // Single sequence: step k's Lemma 5 element is built in the next
+        // iteration, beside the advance to step k + 1, which does not depend on
+        // it (two independent chains in one loop body).
+        constexpr bool LAG = FROM_Y && SAGG && !SEG && !TV;
+        int nsteps = 0;
         float yn[M];
         if constexpr (FROM_Y) {
             cur.seek(segs, &mc, k0, T);
@@ -1456,6 +1461,7 @@ __global__ void __launch_bounds__(NT) filter_scan_kernel(const ModelConst<N, M>*
         for (int i = 0; i < CH; ++i) {
             const int64_t k = k0 + i;
             if (k >= T) break;
+            const FState<N> prev = st;    // posterior of step k - 1 (i >= 1)
             if constexpr (FROM_Y) {
                 float yk[M];
 #pragma unroll
@@ -1495,7 +1501,14 @@ __global__ void __launch_bounds__(NT) filter_scan_kernel(const ModelConst<N, M>*
                 }
             }
             probe += finite_probe<N>(st.b, st.C);
-            if constexpr (SAGG) {
+            ++nsteps;
+            if constexpr (LAG) {
+                if (i >= 1) {   // step k - 1 < T - 1: never the last step
+                    SElem<N> e;
+                    smoother_element<N, M>(*cur.mc, prev.b, prev.C, e, bad);
+                    sacc = (i == 1) ? e : scombine<N>(sacc, e);
+                }
+            } else if constexpr (SAGG) {
                 SElem<N> e;
                 if constexpr (TV) build_selem_tv<N, M>(tv, k, T, st.b, st.C, e, bad);
                 else build_selem_from<N, M>(*cur.mc, st.b, st.C, cur.last(k), e, bad);
@@ -1514,6 +1527,12 @@ __global__ void __launch_bounds__(NT) filter_scan_kernel(const ModelConst<N, M>*
             } else {
                 store_posterior<N>(fmean, fcov, k, st.b, st.C);
             }
+        }
+        if constexpr (LAG) {   // the block's last step
+            const int64_t kl = k0 + nsteps - 1;
+            SElem<N> e;
+            build_selem_from<N, M>(*cur.mc, st.b, st.C, kl == T - 1, e, bad);
+            sacc = (nsteps == 1) ? e : scombine<N>(sacc, e);
         }
         if constexpr (SG::kOn) {
             if (pending) bulk_wait_all();
