@@ -1447,10 +1447,12 @@ __global__ void __launch_bounds__(NT) filter_scan_kernel(const ModelConst<N, M>*
         bool pending = false;
         float probe = 0.f;
         SElem<N> sacc;
-        // Single sequence: step k's Lemma 5 element is built in the next
-        // iteration, beside the advance to step k + 1, which does not depend on
-        // it (two independent chains in one loop body).
-        constexpr bool LAG = FROM_Y && SAGG && !SEG && !TV;
+        // Single sequence, 32 steps per thread: step k's Lemma 5 element is
+        // built in the next iteration, beside the advance to step k + 1, which
+        // does not depend on it (two independent chains in one loop body).
+        // With 4 steps per thread the element left over after the loop costs
+        // more than the overlap gains.
+        constexpr bool LAG = FROM_Y && SAGG && !SEG && !TV && CH >= 32;
         int nsteps = 0;
         float yn[M];
         if constexpr (FROM_Y) {
