@@ -1,0 +1,38 @@
+"""Host-side pieces of bench.py that shape its JSON line: the work models
+behind the roofline fields and the gating of the recorded ncu traffic."""
+import json
+
+import bench
+
+
+def test_flop_model_nx4():
+    """Per-step flops of the fused nx = 4, ny = 2 scans (the roofline's
+    algorithmic work): forward 2230 (fold + advance + two measurement
+    elements + Lemma 5 element + fused Lemma 6 fold), reverse 744."""
+    f = bench.flops_per_step(4, 2)
+    assert f == {"filter": 2230, "smoother": 744}
+    # without the fused smoothing fold the reverse scan builds its elements twice
+    g = bench.flops_per_step(4, 2, fused_smoothing=False)
+    assert g["filter"] < f["filter"] and g["smoother"] > f["smoother"]
+
+
+def test_time_varying_bytes_nx4():
+    """Algorithmic bytes per step of the time-varying path at nx = 4, ny = 2
+    (u = d = 0): element kernel 344, forward scan 368, reverse scan 288."""
+    assert bench.tv_bytes_per_step(4, 2) == {"elements": 344, "filter": 368, "smoother": 288}
+
+
+def test_recorded_traffic_only_for_its_length_and_sources(tmp_path, monkeypatch):
+    """The ncu traffic goes into the bench line only for the sequence length it
+    was captured at and while the kernel's sources hash as recorded."""
+    key = "filter_scan_kernel"
+    rec = {key: {"source_hash": bench.source_hash(key), "T": 1 << 20, "dram_bytes_per_launch_full": 123.0}}
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "source_hash", lambda k: rec[key]["source_hash"] if k == key else "x")
+    assert bench.recorded_traffic(key, 1 << 20) == 123.0
+    assert bench.recorded_traffic(key, 1024) is None
+    assert bench.recorded_traffic("smoother_scan_kernel", 1 << 20) is None
+    monkeypatch.setattr(bench, "source_hash", lambda k: "changed")
+    assert bench.recorded_traffic(key, 1 << 20) is None
