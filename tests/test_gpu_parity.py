@@ -57,9 +57,12 @@ def test_tracking_model_sizes(ks, T):
 # The fused smooth picks 4, 8, 16 or 32 steps per thread by T (switching at
 # 96 Ki, 192 Ki and 640 Ki steps): both sides of every switch, each with a
 # ragged last tile, for nx = 4, and one size inside each band for nx = 2, 6.
+# At 32 steps per thread a single sequence builds each step's Lemma 5 element
+# one iteration late, and the reverse scan applies its elements in pairs from
+# groups of 4: last blocks of 1 and 19 steps (groups of 4, 4, 4, 4, 3) cover both tails.
 @pytest.mark.parametrize("dim,T", [(2, 98303), (2, 98304), (2, 196607), (2, 196608), (2, 655359),
-                                   (2, 655360), (1, 150001), (1, 400003), (3, 150001), (3, 400003),
-                                   (3, 700001)])
+                                   (2, 655360), (2, 655361), (2, 700019), (1, 150001), (1, 400003),
+                                   (1, 655361), (3, 150001), (3, 400003), (3, 700001)])
 def test_chunk_variants(ks, dim, T):
     rng = np.random.default_rng(4000 + T + dim)
     m = workloads.wiener_velocity(dim, dt=0.1, q=1.0, r=0.5)
