@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--T", type=int, default=1 << 20)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="default workload: leave out the batched measurement beside the headline")
     ap.add_argument("--workload", default="long", choices=["long", "batched", "precision", "serving", "tv", "hmm"],
                     help="long: one T=2^20 nx=4 sequence per GPU (default); batched: 4096 sequences, "
                          "lengths log-uniform in [256, 16384], nx in {2,4,6}; precision: nx=32 T=65536; "
@@ -229,6 +231,8 @@ KERNEL_SOURCES = {
     "hmm:smoother": ["ks_scan.cuh", "ks_hmm.cuh", "ks_hmm.cu"],
     "tv:filter": ["ks_ops.cuh", "ks_async.cuh", "ks_scan.cuh", "ks_impl.cuh", "ks_inst_4_2.cu"],
     "tv:smoother": ["ks_ops.cuh", "ks_async.cuh", "ks_scan.cuh", "ks_impl.cuh", "ks_inst_4_2.cu"],
+    "mixed_filter_kernel": ["ks_ops.cuh", "ks_async.cuh", "ks_scan.cuh", "ks_impl.cuh", "ks_mixed.cuh",
+                            "ks_mixed32.cu"],
 }
 
 
@@ -397,36 +401,60 @@ def run_single(args, rank, world, local, mode):
         ms = float(t.item())
     value = T * world / (ms / 1e3)
 
-    # ---- end to end through the public API with host buffers
+    # ---- end to end through the public API with host buffers: every step
+    # copies its measurements in from pinned host memory, runs ks_smooth and
+    # reads its smoothed means and covariances back.  Consecutive steps
+    # alternate between two streams (each with its own device buffers and
+    # workspace), so one step's copies overlap the next step's kernels: the
+    # figure is K steps over the wall time of all K.
     y_h = torch.as_tensor(seq.y, dtype=torch.float32).pin_memory()
-    sm_h = torch.empty(T, nx, dtype=torch.float32).pin_memory()
-    sP_h = torch.empty(T, nx, nx, dtype=torch.float32).pin_memory()
-    y_d = torch.empty_like(y)
     # a time-varying model is part of each call's input: its per-step arrays
     # are copied in with y
     model_h = {k: getattr(model, k).cpu().pin_memory() for k in ("F", "Q", "H", "R")} if tv else {}
-    e2e_times = []
-    for i in range(args.warmup + args.steps):
-        flush.zero_()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record()
-        for k, h in model_h.items():
-            getattr(model, k).copy_(h, non_blocking=True)
-        y_d.copy_(y_h, non_blocking=True)
-        ks.smooth(model, y_d, ws, smean=sm, scov=sP, keep_filtered=False)
-        sm_h.copy_(sm, non_blocking=True)
-        sP_h.copy_(sP, non_blocking=True)
-        b.record()
-        b.synchronize()
-        if i >= args.warmup:
-            e2e_times.append(a.elapsed_time(b))
-    e2e_ms = statistics.mean(e2e_times)
-    if ks.status(ws) != ks.KS_OK:
-        raise SystemExit("device status not OK after the end-to-end steps")
+    lanes = []
+    for j in range(2):
+        mj = model if j == 0 else (ks.Model.create(m.F, m.Q, m.H, m.R, m.m0, m.P0, device=dev) if tv else model)
+        lanes.append({"stream": torch.cuda.Stream(device=dev), "model": mj, "y": torch.empty_like(y),
+                      "ws": ws if j == 0 else ks.alloc_workspace(model, T, ks.KS_WS_ELEMENTS),
+                      "sm": sm if j == 0 else torch.empty(T, nx, device=dev),
+                      "sP": sP if j == 0 else torch.empty(T, nx, nx, device=dev),
+                      "sm_h": torch.empty(T, nx, dtype=torch.float32).pin_memory(),
+                      "sP_h": torch.empty(T, nx, nx, dtype=torch.float32).pin_memory()})
+
+    def e2e_call(L):
+        with torch.cuda.stream(L["stream"]):
+            for k, h in model_h.items():
+                getattr(L["model"], k).copy_(h, non_blocking=True)
+            L["y"].copy_(y_h, non_blocking=True)
+            ks.smooth(L["model"], L["y"], L["ws"], smean=L["sm"], scov=L["sP"], keep_filtered=False)
+            L["sm_h"].copy_(L["sm"], non_blocking=True)
+            L["sP_h"].copy_(L["sP"], non_blocking=True)
+
+    main_s = torch.cuda.current_stream()
+    for i in range(args.warmup):
+        e2e_call(lanes[i % 2])
+    torch.cuda.synchronize()
+    flush.zero_()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(main_s)
+    for L in lanes:
+        L["stream"].wait_stream(main_s)
+    for i in range(args.steps):
+        e2e_call(lanes[i % 2])
+    for L in lanes:
+        main_s.wait_stream(L["stream"])
+    b.record(main_s)
+    b.synchronize()
+    e2e_ms = a.elapsed_time(b) / args.steps
+    for L in lanes:
+        if ks.status(L["ws"]) != ks.KS_OK:
+            raise SystemExit("device status not OK after the end-to-end steps")
     e2e = {"value": T * world / (e2e_ms / 1e3), "unit": UNIT,
            "h2d_bytes_per_step": int(y_h.numel() * 4 + sum(h.numel() * 4 for h in model_h.values())),
-           "d2h_bytes_per_step": int((sm_h.numel() + sP_h.numel()) * 4)}
+           "d2h_bytes_per_step": int((lanes[0]["sm_h"].numel() + lanes[0]["sP_h"].numel()) * 4),
+           "how": "consecutive calls alternate between 2 streams (copies of one overlap the kernels of the next)"}
+    del lanes
 
     # ---- roofline of the dominant kernel
     hbm, which = peaks()
@@ -439,6 +467,14 @@ def run_single(args, rank, world, local, mode):
     if not tv:
         roof = scan_roofline(nx, ny, T, hbm, which, kernels, bps, fps)
 
+    # the batched workload beside it (the metric's "batched FP32 scan vs plain
+    # scan"): one mixed-size launch per scan, and the plain per-sequence scan
+    batched = None
+    if mode == "long" and not args.no_batched:
+        del fm, fP, sm, sP, ws, flush
+        batched = measure_batched(args, rank, world, dev, full=False)
+        batched["roofline"]["traffic"] = recorded_traffic("mixed_filter_kernel", batched["config"]["total_steps"])
+        batched.pop("_seqs", None)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -453,6 +489,8 @@ def run_single(args, rank, world, local, mode):
            "gpu_launches": 3 * args.steps, "latency": lat, "e2e": e2e, "roofline": roof}
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_oracle_rate(seq, args.cpu_seconds)
+    if batched is not None:
+        out["batched"] = batched
     print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()
@@ -696,128 +734,92 @@ def cpu_oracle_batched(seqs, seconds: float) -> dict:
             "sample": f"first {done} of {len(seqs)} sequences ({done_steps} steps, {el:.1f} s, {cores} threads)"}
 
 
-def run_batched(args, rank, world, local):
+def measure_batched(args, rank, world, dev, full: bool) -> dict:
+    """The batched workload (4096 sequences, log-uniform lengths, nx in {2, 4,
+    6}) through ks_smooth_batched: one preparation, one forward and one
+    reverse launch over all three state sizes, captured in a CUDA graph.
+    Returns the JSON fields of the measurement; `full` adds the end-to-end
+    figure and the per-size comparison (three ks_smooth_batch calls on three
+    streams), which the default benchmark line leaves out."""
     import torch
     import torch.distributed as dist
 
     import paper_1905_13002_gb300 as ks
-    from paper_1905_13002_gb300 import _build
 
-    if world > 1:
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    if local == 0:
-        _build.build()
-    if world > 1:
-        dist.barrier()
     seqs = workloads.config_batched(B=args.batch, seed=workloads.SEED_BASE + 3 + rank)
     total = sum(q.T for q in seqs)
     groups = []
-    for nx in sorted({q.model.nx for q in seqs}):
+    for nx in (6, 4, 2):
         g = [q for q in seqs if q.model.nx == nx]
+        if not g:
+            continue
         batch = ks.ModelBatch.create([q.model for q in g], [q.T for q in g], device=dev)
         y = torch.as_tensor(np.concatenate([q.y for q in g]), dtype=torch.float32, device=dev)
         T = int(y.shape[0])
-        ws = torch.zeros(ks.workspace_bytes_batch(batch.nx, batch.ny, batch.B, T), dtype=torch.uint8,
-                         device=dev)
-        outs = [torch.empty(T, nx, device=dev), torch.empty(T, nx, nx, device=dev),
-                torch.empty(T, nx, device=dev), torch.empty(T, nx, nx, device=dev)]
-        groups.append({"nx": nx, "B": batch.B, "T": T, "batch": batch, "y": y, "ws": ws, "outs": outs,
-                       "stream": torch.cuda.Stream(device=dev)})
+        outs = (torch.empty(T, nx, device=dev), torch.empty(T, nx, nx, device=dev),
+                torch.empty(T, nx, device=dev), torch.empty(T, nx, nx, device=dev))
+        groups.append({"nx": nx, "B": batch.B, "T": T, "batch": batch, "y": y, "outs": outs})
+    sizes = [(g["nx"], g["nx"] // 2, g["B"], g["T"]) for g in groups]
+    ws = torch.zeros(ks.workspace_bytes_batched(sizes), dtype=torch.uint8, device=dev)
+    pairs = [(g["batch"], g["y"]) for g in groups]
+    outs = [g["outs"] for g in groups]
+
     def step():
-        main = torch.cuda.current_stream()      # the capture stream while a graph is recorded
-        for g in groups:
-            g["stream"].wait_stream(main)
-            with torch.cuda.stream(g["stream"]):
-                fm, fP, sm, sP = g["outs"]
-                ks.smooth_batch(g["batch"], g["y"], g["ws"], fmean=fm, fcov=fP, smean=sm, scov=sP)
-        for g in groups:
-            main.wait_stream(g["stream"])
+        ks.smooth_batched(pairs, ws, outs=outs)
 
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize()
-    for g in groups:
-        if ks.status(g["ws"]) != ks.KS_OK:
-            raise SystemExit(f"device status not OK (nx={g['nx']})")
+    if ks.status(ws) != ks.KS_OK:
+        raise SystemExit("batched: device status not OK after warm-up")
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph):
         step()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    for _ in range(2):
-        graph.replay()
-    torch.cuda.synchronize()
-    clocks = ClockSampler(local)
+
+    def timed(fn, n):
+        out = []
+        for _ in range(n):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            b.synchronize()
+            out.append(a.elapsed_time(b))
+        return out
+
+    timed(graph.replay, 2)
+    clocks = ClockSampler(dev.index or 0)
     if world > 1:
         dist.barrier()
     clocks.start()
     time.sleep(0.3)
-    times = []
-    for _ in range(args.steps):
-        flush.zero_()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record()
-        graph.replay()
-        b.record()
-        b.synchronize()
-        times.append(a.elapsed_time(b))
+    times = timed(graph.replay, args.steps)
     time.sleep(0.3)
     clk = clocks.stop()
     if world > 1:
         dist.barrier()
-    for g in groups:
-        if ks.status(g["ws"]) != ks.KS_OK:
-            raise SystemExit(f"device status not OK after timing (nx={g['nx']})")
+    if ks.status(ws) != ks.KS_OK:
+        raise SystemExit("batched: device status not OK after timing")
     ms = statistics.mean(times)
     if world > 1:
         t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    value = total * world / (ms / 1e3)
+    res = {"value": total * world / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+           "latency": {"p50_ms": float(np.percentile(times, 50)), "p99_ms": float(np.percentile(times, 99))},
+           "clocks": {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+           "gpu_launches": 3 * args.steps,
+           "config": {"workload": "batched: log-uniform T in [256,16384], nx in {2,4,6} Wiener-velocity, "
+                                  "q~U[0.5,2], R=rI r~U[0.1,1]", "sequences": len(seqs), "total_steps": total,
+                      "groups": [{"nx": g["nx"], "B": g["B"], "T": g["T"]} for g in groups],
+                      "launch": "ks_smooth_batched: prep + one forward + one reverse launch over all sizes "
+                                "(CUDA graph)",
+                      "l2": "flushed between timed steps (256 MiB memset outside the events)"}}
 
-    # end to end through the public API: each group's measurements in from
-    # pinned host memory, its smoothed means and covariances back
-    for g in groups:
-        nx = g["nx"]
-        g["y_h"] = g["y"].cpu().pin_memory()
-        g["sm_h"] = torch.empty(g["T"], nx).pin_memory()
-        g["sP_h"] = torch.empty(g["T"], nx, nx).pin_memory()
-        g["y_d"] = torch.empty_like(g["y"])
-
-    def e2e_step():
-        main = torch.cuda.current_stream()
-        for g in groups:
-            g["stream"].wait_stream(main)
-            with torch.cuda.stream(g["stream"]):
-                fm, fP, sm, sP = g["outs"]
-                g["y_d"].copy_(g["y_h"], non_blocking=True)
-                ks.smooth_batch(g["batch"], g["y_d"], g["ws"], fmean=fm, fcov=fP, smean=sm, scov=sP)
-                g["sm_h"].copy_(sm, non_blocking=True)
-                g["sP_h"].copy_(sP, non_blocking=True)
-        for g in groups:
-            main.wait_stream(g["stream"])
-
-    e2e_times = []
-    for i in range(args.warmup + args.steps):
-        flush.zero_()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record()
-        e2e_step()
-        b.record()
-        b.synchronize()
-        if i >= args.warmup:
-            e2e_times.append(a.elapsed_time(b))
-    for g in groups:
-        if ks.status(g["ws"]) != ks.KS_OK:
-            raise SystemExit(f"device status not OK after the end-to-end steps (nx={g['nx']})")
-    e2e = {"value": total * world / (statistics.mean(e2e_times) / 1e3), "unit": UNIT,
-           "h2d_bytes_per_step": int(sum(g["y_h"].numel() * 4 for g in groups)),
-           "d2h_bytes_per_step": int(sum((g["sm_h"].numel() + g["sP_h"].numel()) * 4 for g in groups))}
-
-    # the plain single-sequence scan, one call per sequence, same GPU
+    # the plain single-sequence scan, one ks_smooth call per sequence, same GPU
     plain = []
     for q in seqs:
         m = q.model
@@ -834,22 +836,14 @@ def run_batched(args, rank, world, local):
 
     plain_pass()
     torch.cuda.synchronize()
-    ptimes = []
-    for _ in range(3):
-        flush.zero_()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record()
-        plain_pass()
-        b.record()
-        b.synchronize()
-        ptimes.append(a.elapsed_time(b))
-    pms = statistics.median(ptimes)
+    pms = statistics.median(timed(plain_pass, 3))
+    res["plain_scan"] = {"value": total / (pms / 1e3), "unit": UNIT, "ms_per_pass": pms,
+                         "how": "ks_smooth once per sequence, sequentially on one stream"}
+    del plain
 
-    # roofline over the whole graph step: algorithmic bytes and flops of all groups
+    # roofline over the whole step: algorithmic bytes and flops of all groups
     hbm, which = peaks()
-    nbytes = 0
-    nflops = 0
+    nbytes = nflops = 0
     for g in groups:
         bps = bytes_per_step(g["nx"], g["nx"] // 2)
         fps = flops_per_step(g["nx"], g["nx"] // 2)
@@ -863,26 +857,91 @@ def run_batched(args, rank, world, local):
         roof = {"bound": "alu", "achieved": tfl, "peak": alu_peak, "unit": "TFLOP/s", "frac": tfl / alu_peak}
     else:
         roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm}
-    roof.update({"traffic": None, "kernel": "whole graph step (3 groups x (prep + 2 scans))",
-                 "hbm_frac": gbs / hbm, "alu_frac": tfl / alu_peak})
+    roof.update({"traffic": None, "kernel": "whole step (mixed prep + forward + reverse launches)",
+                 "hbm_frac": gbs / hbm, "alu_frac": tfl / alu_peak,
+                 "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz" if roof["bound"] == "alu" else which})
+    res["roofline"] = roof
+    if not full:
+        return res
+
+    # the same groups as three per-size segmented calls on three streams (the
+    # form before the mixed-size launch), for comparison
+    per = []
+    for g in groups:
+        wsg = torch.zeros(ks.workspace_bytes_batch(g["nx"], g["nx"] // 2, g["B"], g["T"]), dtype=torch.uint8,
+                          device=dev)
+        per.append((g, wsg, torch.cuda.Stream(device=dev)))
+
+    def per_size():
+        main = torch.cuda.current_stream()
+        for g, wsg, s in per:
+            s.wait_stream(main)
+            with torch.cuda.stream(s):
+                fm, fP, sm, sP = g["outs"]
+                ks.smooth_batch(g["batch"], g["y"], wsg, fmean=fm, fcov=fP, smean=sm, scov=sP)
+        for _, _, s in per:
+            main.wait_stream(s)
+
+    for _ in range(3):
+        per_size()
+    g2 = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g2):
+        per_size()
+    per_ms = statistics.mean(timed(g2.replay, args.steps))
+    res["per_size_calls"] = {"value": total / (per_ms / 1e3), "unit": UNIT, "ms_per_step": per_ms,
+                             "how": "3 ks_smooth_batch calls (one per nx) on 3 streams, one CUDA graph"}
+
+    # end to end through the public API: each group's measurements in from
+    # pinned host memory, its smoothed means and covariances back
+    hosts = []
+    for g in groups:
+        nx = g["nx"]
+        hosts.append((g["y"].cpu().pin_memory(), torch.empty(g["T"], nx).pin_memory(),
+                      torch.empty(g["T"], nx, nx).pin_memory(), torch.empty_like(g["y"])))
+    e2e_pairs = [(g["batch"], h[3]) for g, h in zip(groups, hosts)]
+
+    def e2e_step():
+        for h in hosts:
+            h[3].copy_(h[0], non_blocking=True)
+        ks.smooth_batched(e2e_pairs, ws, outs=outs)
+        for g, h in zip(groups, hosts):
+            h[1].copy_(g["outs"][2], non_blocking=True)
+            h[2].copy_(g["outs"][3], non_blocking=True)
+
+    e2e_times = timed(e2e_step, args.warmup + args.steps)[args.warmup:]
+    if ks.status(ws) != ks.KS_OK:
+        raise SystemExit("batched: device status not OK after the end-to-end steps")
+    res["e2e"] = {"value": total * world / (statistics.mean(e2e_times) / 1e3), "unit": UNIT,
+                  "h2d_bytes_per_step": int(sum(h[0].numel() * 4 for h in hosts)),
+                  "d2h_bytes_per_step": int(sum((h[1].numel() + h[2].numel()) * 4 for h in hosts))}
+    res["_seqs"] = seqs
+    return res
+
+
+def run_batched(args, rank, world, local):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1905_13002_gb300 import _build
+
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if local == 0:
+        _build.build()
+    if world > 1:
+        dist.barrier()
+    res = measure_batched(args, rank, world, dev, full=True)
+    seqs = res.pop("_seqs")
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return
-    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": "batched: log-uniform T in [256,16384], nx in {2,4,6} Wiener-velocity, "
-                                  "q~U[0.5,2], R=rI r~U[0.1,1]", "sequences": len(seqs), "total_steps": total,
-                      "groups": [{"nx": g["nx"], "B": g["B"], "T": g["T"]} for g in groups],
-                      "launch": "one CUDA graph: 3 segmented ks_smooth_batch calls on 3 streams",
-                      "l2": "flushed between timed steps (256 MiB memset outside the events)"},
-           "clocks": {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
-           "gpu_launches": 9 * args.steps,
-           "latency": {"p50_ms": float(np.percentile(times, 50)), "p99_ms": float(np.percentile(times, 99))},
-           "plain_scan": {"value": total / (pms / 1e3), "unit": UNIT, "ms_per_pass": pms,
-                          "how": "ks_smooth once per sequence, sequentially on one stream"},
-           "e2e": e2e, "roofline": roof}
+    out = {"metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic"}
+    out.update({k: v for k, v in res.items() if k not in ("value", "unit", "ms_per_step")})
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_oracle_batched(seqs, args.cpu_seconds)
     print(json.dumps(out))

@@ -24,7 +24,8 @@
  * - Memory: every pointer argument documented "device" must point to memory
  *   the current CUDA device can read/write (cudaMalloc, torch CUDA tensors).
  *   The caller owns every buffer; the library allocates no device memory and
- *   keeps no global state between calls.  Scratch lives in the caller's
+ *   keeps no state between calls, apart from the block-length table of
+ *   ks_set_chunk_rules (host memory).  Scratch lives in the caller's
  *   workspace `ws` (opaque, size from ks_workspace_bytes, 256-byte aligned).
  * - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *   stream).  Calls are stream-ordered and asynchronous, make no host
@@ -35,7 +36,9 @@
  *   ks_supported(); others return KS_EUNSUPPORTED.
  * - nx = 32: the operators' dense products run on the tensor cores (3xTF32,
  *   FP32 accumulate) and the inverses of Lemmas 4 and 5 get one FP64-residual
- *   refinement step when their estimated condition number exceeds 1e3.
+ *   refinement step when their estimated condition number exceeds 1e3.  At
+ *   every nx the general Lemma 4 operator (cross-block combines) refines its
+ *   (I + C_i J_j)^{-1} the same way (ks_refinements counts them).
  *   ks_smooth and ks_smooth_scan then want fmean, fcov, smean and scov
  *   16-byte aligned (KS_EINVAL otherwise).
  * - Errors: every call returns KS_OK (0) or a negative code.  Argument and
@@ -216,6 +219,60 @@ int ks_smooth_batch(const ks_model_batch *mb, const float *y, int64_t total_T, v
                     float *fmean, float *fcov, float *smean, float *scov, void *stream);
 
 /*
+ * Block length of the fused scans (Section III-C: each thread folds a block
+ * of l consecutive steps; a tile is 128 threads).  The nx <= 6 entry points
+ * ks_smooth, ks_smooth_traced, ks_smooth_batch and ks_smooth_batched are
+ * compiled for l in {4, 8, 16, 32} and pick one per call from the call's
+ * total number of steps T.  The built-in choice is 4 below 96 Ki steps, 8
+ * below 192 Ki, 16 below 640 Ki and 32 above.  ks_set_chunk_rules replaces it
+ * for one state size (nx = 2, 4 or 6; nx = 0: ks_smooth_batched) by `count`
+ * rules with strictly increasing T_below: a call uses the steps of the first
+ * rule whose T_below exceeds its T, else the last rule's.  count = 0 restores
+ * the built-in choice.  steps must be 4, 8, 16 or 32 and count <= 16
+ * (KS_EINVAL otherwise).  The table is process state of the library (host
+ * memory, guarded by a mutex); results do not depend on it, only speed.  The
+ * project's tuner measures the table on the device (package module tune.py).
+ * ks_chunk_steps returns the steps per thread a call of T steps would use
+ * (0 for an nx without a table).
+ */
+typedef struct ks_chunk_rule {
+    int64_t T_below;
+    int32_t steps;
+    int32_t reserved;
+} ks_chunk_rule;
+int ks_set_chunk_rules(int nx, int count, const ks_chunk_rule *rules);
+int ks_chunk_steps(int nx, int64_t T);
+
+/*
+ * Batched end to end over sequences of different state sizes, in one/*
+ * Batched end to end over sequences of different state sizes, in one
+ * preparation, one forward-scan and one reverse-scan launch.  The sequences
+ * come in G groups (1 <= G <= 3), one per state size, with distinct
+ * (nx, ny) among (2, 1), (4, 2) and (6, 3) (others: KS_EUNSUPPORTED).  A
+ * group is a segmented batch exactly as for ks_smooth_batch: its models
+ * (ks_model_batch: nx, ny, B >= 1 sequences, per-sequence parameters and the
+ * offsets table, device), its total_T steps (= offsets[B]) and its own
+ * concatenated arrays y [total_T][ny], fmean, smean [total_T][nx], fcov,
+ * scov [total_T][nx][nx] (device, FP32, 16-byte aligned; all required).
+ * Each scan launch takes (group, tile) work items from one queue, the
+ * largest state size first, and runs the code specialised for the item's
+ * size; no combine crosses a sequence start (Lemma 3's A_1 = 0, Lemma 5's
+ * E_n = 0) or a group.  ws: ks_workspace_bytes_batched(G, groups) bytes
+ * (reads nx, ny, B and total_T), 256-byte aligned, initialised once with
+ * ks_workspace_init.  Device-side errors (an inconsistent offsets table:
+ * KS_EINVAL) are reported by ks_status.
+ */
+typedef struct ks_batch_group {
+    ks_model_batch models;
+    int64_t total_T;
+    const float *y;
+    float *fmean, *fcov, *smean, *scov;
+} ks_batch_group;
+size_t ks_workspace_bytes_batched(int G, const ks_batch_group *groups);
+int ks_smooth_batched(int G, const ks_batch_group *groups, void *ws, size_t ws_bytes, void *stream);
+
+/*
+ * ks_smooth with per-kernel timing:/*
  * ks_smooth with per-kernel timing: `events` points to 4 cudaEvent_t handles
  * (passed as void*; any may be NULL) that are recorded on `stream` before the
  * model preparation, before the forward scan kernel, between the two scans
@@ -233,6 +290,39 @@ int ks_smooth_traced(const ks_model *m, const float *y, int64_t T, void *ws, siz
 int ks_status(void *ws, void *stream);
 
 /*
+ * Testing aid for the bounded look-back waits of the block scans (Section
+ * III-C's block-level elements, chained across thread blocks).  Writes two
+ * settings into the workspace header (stream-ordered); they persist until
+ * changed or until ks_workspace_init:
+ *   wait_polls  polls a look-back wait makes before it gives up, records
+ *               KS_ETIMEOUT for ks_status and goes on with an empty prefix
+ *               (0: the default, about one second);
+ *   first_tile  1 makes the forward scan of ks_smooth / ks_smooth_batch at
+ *               nx <= 6 number its tiles from 1, so that tile 0 is never
+ *               published and tile 1's wait must run out; 0 restores the
+ *               normal numbering; other values: KS_EINVAL.
+ * Results computed with first_tile = 1 are not meaningful; the call exists so
+ * that a test can check, in bounded time, that a wait which runs out is
+ * reported and leaves the device usable.  ws: device, >= 256 bytes, 256-byte
+ * aligned.
+ */
+int ks_workspace_set_waits(void *ws, size_t ws_bytes, uint32_t wait_polls, uint32_t first_tile, void *stream);
+
+/*
+ * Refinement counter of the workspace (Lemma 4's (I + C_i J_j)^{-1}, and at
+ * nx = 32 also Lemma 5's (F P F^T + Q)^{-1}): every inverse whose condition
+ * estimate (1-norm, or infinity-norm in the lane-group kernels of nx = 8 and
+ * of nx = 32 batches) exceeds 1e3 gets one refinement step with its residual
+ * formed in FP64, and each warp or lane group in which that happened adds one
+ * to a counter kept beside the status word.  Synchronises `stream`, writes
+ * the count accumulated since the workspace was initialised or last read to
+ * *count (host) and clears it.  ws: device.  A diagnostic: the results do not
+ * depend on reading it.
+ */
+int ks_refinements(void *ws, void *stream, uint32_t *count);
+
+/*
+ * ks_smooth without a workspace, for callers that cannot allocate device/*
  * ks_smooth without a workspace, for callers that cannot allocate device
  * memory: for example a real-time loop that must not take cudaMalloc's
  * implicit device synchronisation or risk its failure once running, or a host
@@ -241,14 +331,16 @@ int ks_status(void *ws, void *stream);
  *
  * Same computation and arguments as ks_smooth for time-invariant models with
  * nx = 4, ny = 2 (other sizes, or time-varying models: KS_EUNSUPPORTED), with
- * T <= KS_NOALLOC_MAX_T (larger T, or NULL
- * fmean / fcov: KS_EINVAL).  The caller still provides every input and
- * output; the scratch lives in a static device array of
- * KS_NOALLOC_SCRATCH_BYTES that every GPU loading this library holds until
- * the process exits.  The function itself allocates nothing.
- *  - The first call on each device looks up that array's device address (with
- *    the device current) and caches it; make that first call before any stream
- *    capture.
+ * T <= KS_NOALLOC_MAX_T.  KS_EINVAL for a larger T, for NULL fmean or fcov,
+ * or for exactly one of smean and scov NULL; both NULL runs the filter only,
+ * as in ks_smooth.  The caller still provides every input and output; the
+ * scratch lives in a static device array of KS_NOALLOC_SCRATCH_BYTES that
+ * every GPU loading this library holds until the process exits.  The
+ * function itself allocates nothing.
+ *  - Every call looks up that array's device address on the current device
+ *    (a host-side query, so the address stays right after a cudaDeviceReset).
+ *    The first call on a device also loads the library's device code there;
+ *    make that first call before any stream capture.
  *  - All calls on a device share the one array: calls that overlap on the GPU
  *    (different streams or threads without ordering) race and give wrong
  *    results.  Each call clears the state it needs, so sequential calls are

@@ -21,8 +21,9 @@ from dataclasses import dataclass
 import torch
 
 __all__ = [
-    "KsError", "Model", "ModelBatch", "smooth_batch", "workspace_bytes_batch", "lib", "workspace_bytes", "alloc_workspace", "smooth", "build_elements",
-    "elements", "filter_scan", "smooth_scan", "status", "filter_combine_batch",
+    "KsError", "Model", "ModelBatch", "smooth_batch", "workspace_bytes_batch", "smooth_batched",
+    "workspace_bytes_batched", "lib", "workspace_bytes", "alloc_workspace", "smooth", "build_elements",
+    "elements", "filter_scan", "smooth_scan", "status", "refinements", "filter_combine_batch",
     "smoother_combine_batch", "supported", "KS_WS_SMOOTH", "KS_WS_ELEMENTS",
     "HmmModel", "hmm_supported", "hmm_workspace_bytes", "hmm_smooth",
 ]
@@ -54,6 +55,16 @@ class _KsModelBatch(ctypes.Structure):
                 ("F", ctypes.c_void_p), ("u", ctypes.c_void_p), ("Q", ctypes.c_void_p),
                 ("H", ctypes.c_void_p), ("d", ctypes.c_void_p), ("R", ctypes.c_void_p),
                 ("m0", ctypes.c_void_p), ("P0", ctypes.c_void_p), ("offsets", ctypes.c_void_p)]
+
+
+class _KsBatchGroup(ctypes.Structure):
+    _fields_ = [("models", _KsModelBatch), ("total_T", ctypes.c_int64), ("y", ctypes.c_void_p),
+                ("fmean", ctypes.c_void_p), ("fcov", ctypes.c_void_p), ("smean", ctypes.c_void_p),
+                ("scov", ctypes.c_void_p)]
+
+
+class _KsChunkRule(ctypes.Structure):
+    _fields_ = [("T_below", ctypes.c_int64), ("steps", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class _KsHmm(ctypes.Structure):
@@ -92,8 +103,14 @@ def lib():
             "ks_smooth": ([M, vp, i64, vp, sz, vp, vp, vp, vp, vp], i32),
             "ks_smooth_traced": ([M, vp, i64, vp, sz, vp, vp, vp, vp, vp, ctypes.POINTER(vp)], i32),
             "ks_status": ([vp, vp], i32),
+            "ks_refinements": ([vp, vp, ctypes.POINTER(ctypes.c_uint32)], i32),
+            "ks_workspace_set_waits": ([vp, sz, ctypes.c_uint32, ctypes.c_uint32, vp], i32),
             "ks_workspace_bytes_batch": ([i32, i32, i32, i64], sz),
             "ks_smooth_batch": ([ctypes.POINTER(_KsModelBatch), vp, i64, vp, sz, vp, vp, vp, vp, vp], i32),
+            "ks_workspace_bytes_batched": ([i32, ctypes.POINTER(_KsBatchGroup)], sz),
+            "ks_set_chunk_rules": ([i32, i32, ctypes.POINTER(_KsChunkRule)], i32),
+            "ks_chunk_steps": ([i32, i64], i32),
+            "ks_smooth_batched": ([i32, ctypes.POINTER(_KsBatchGroup), vp, sz, vp], i32),
             "ks_filter_combine_batch": ([i32, i64, vp, vp, vp, vp, sz, vp], i32),
             "ks_smoother_combine_batch": ([i32, i64, vp, vp, vp, vp, sz, vp], i32),
             "ks_workspace_bytes_aggregate": ([M, i64], sz),
@@ -111,7 +128,23 @@ def lib():
             fn.argtypes = args
             fn.restype = res
         _lib = L
+        from . import tune
+        tune.load_default()
     return _lib
+
+
+def set_chunk_rules(nx: int, rules) -> None:
+    """Block-length table of one state size (``ks_set_chunk_rules``): rules
+    are (T_below, steps) pairs; an empty list restores the built-in table."""
+    arr = (_KsChunkRule * max(len(rules), 1))()
+    for i, (tb, steps) in enumerate(rules):
+        arr[i].T_below, arr[i].steps = int(tb), int(steps)
+    _check(lib().ks_set_chunk_rules(nx, len(rules), arr), "ks_set_chunk_rules")
+
+
+def chunk_steps(nx: int, T: int) -> int:
+    """Steps per thread a call of T steps of state size nx uses (0: mixed batches)."""
+    return int(lib().ks_chunk_steps(nx, T))
 
 
 def _check(rc: int, what: str):
@@ -369,6 +402,22 @@ def status(ws: torch.Tensor, stream=None) -> int:
     return int(lib().ks_status(_p(ws), _stream(stream)))
 
 
+def set_waits(ws: torch.Tensor, wait_polls: int = 0, first_tile: int = 0, stream=None) -> None:
+    """Testing aid (``ks_workspace_set_waits``): the look-back wait limit in
+    polls (0: default) and the forward scan's first tile number (1 leaves
+    tile 0 unpublished, so a wait must run out)."""
+    _check(lib().ks_workspace_set_waits(_p(ws), ws.numel(), wait_polls, first_tile, _stream(stream)),
+           "ks_workspace_set_waits")
+
+
+def refinements(ws: torch.Tensor, stream=None) -> int:
+    """Synchronise, read and clear the workspace's count of warps (or lane
+    groups) that refined an ill-conditioned inverse (``ks_refinements``)."""
+    n = ctypes.c_uint32(0)
+    _check(lib().ks_refinements(_p(ws), _stream(stream), ctypes.byref(n)), "ks_refinements")
+    return int(n.value)
+
+
 def _combine(fn, name, nx, left, right, ws, stream):
     count = int(left.shape[0])
     out = torch.empty_like(left)
@@ -470,6 +519,50 @@ def smooth_batch(batch: ModelBatch, y: torch.Tensor, ws: torch.Tensor | None = N
     _check(lib().ks_smooth_batch(ctypes.byref(mb), _p(y), T, _p(ws), ws.numel(), _p(fmean), _p(fcov),
                                  _p(smean), _p(scov), _stream(stream)), "ks_smooth_batch")
     return fmean, fcov, smean, scov
+
+
+def _groups_struct(groups):
+    arr = (_KsBatchGroup * len(groups))()
+    for i, (batch, y, outs) in enumerate(groups):
+        arr[i].models = batch.struct()
+        arr[i].total_T = int(y.shape[0])
+        arr[i].y = y.data_ptr()
+        arr[i].fmean, arr[i].fcov, arr[i].smean, arr[i].scov = (o.data_ptr() for o in outs)
+    return arr
+
+
+def workspace_bytes_batched(sizes) -> int:
+    """Workspace of ``ks_smooth_batched`` for groups given as (nx, ny, B,
+    total_T) tuples."""
+    arr = (_KsBatchGroup * len(sizes))()
+    for i, (nx, ny, B, T) in enumerate(sizes):
+        arr[i].models.nx, arr[i].models.ny, arr[i].models.B = nx, ny, B
+        arr[i].total_T = T
+    n = lib().ks_workspace_bytes_batched(len(sizes), arr)
+    if n == 0:
+        raise KsError(KS_EINVAL, "ks_workspace_bytes_batched")
+    return int(n)
+
+
+def smooth_batched(groups, ws: torch.Tensor | None = None, *, outs=None, stream=None):
+    """Mixed-size batch (``ks_smooth_batched``): ``groups`` is a list of
+    (ModelBatch, y) pairs, one per state size (nx in {2, 4, 6}, distinct), each
+    y [total_T_g, ny_g] the group's sequences concatenated.  One preparation,
+    one forward and one reverse launch for all groups.  Returns, per group,
+    (fmean, fcov, smean, scov); ``outs`` may give them preallocated."""
+    if outs is None:
+        outs = []
+        for batch, y in groups:
+            T, n = int(y.shape[0]), batch.nx
+            outs.append((_out((T, n), y, None), _out((T, n, n), y, None), _out((T, n), y, None),
+                         _out((T, n, n), y, None)))
+    if ws is None:
+        nbytes = workspace_bytes_batched([(b.nx, b.ny, b.B, int(y.shape[0])) for b, y in groups])
+        ws = torch.empty(nbytes, dtype=torch.uint8, device=groups[0][1].device)
+        _check(lib().ks_workspace_init(_p(ws), nbytes, _stream(stream)), "ks_workspace_init")
+    arr = _groups_struct([(b, y, o) for (b, y), o in zip(groups, outs)])
+    _check(lib().ks_smooth_batched(len(groups), arr, _p(ws), ws.numel(), _stream(stream)), "ks_smooth_batched")
+    return outs
 
 
 # ---------------------------------------------------------------- discrete-state models

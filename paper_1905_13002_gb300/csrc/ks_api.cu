@@ -2,8 +2,11 @@
 // compiled (nx, ny) instantiations, workspace queries and status handling.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "../../include/ks.h"
 #include "ks_impl.cuh"
+#include "ks_mixed.cuh"
 
 namespace ks {
 
@@ -27,6 +30,65 @@ static const VTable* find_nx(int nx) {
     return nullptr;
 }
 
+// ---- steps-per-thread rules (ks_set_chunk_rules); slot 0: mixed-size
+// batches, 1..3: nx = 2, 4, 6.  Host state of the process, guarded by a mutex.
+namespace {
+constexpr int kMaxRules = 16;
+struct RuleSet {
+    int count = 0;   // 0: built-in table
+    int64_t below[kMaxRules];
+    int index[kMaxRules];
+};
+std::mutex g_rules_mutex;
+RuleSet g_rules[4];
+
+int rule_slot(int nx) { return nx == 0 ? 0 : nx == 2 ? 1 : nx == 4 ? 2 : nx == 6 ? 3 : -1; }
+int steps_index(int steps) { return steps == 4 ? 0 : steps == 8 ? 1 : steps == 16 ? 2 : steps == 32 ? 3 : -1; }
+}  // namespace
+
+int chunk_index_for(int nx, int64_t T) {
+    const int sl = rule_slot(nx);
+    if (sl >= 0) {
+        std::lock_guard<std::mutex> lock(g_rules_mutex);
+        const RuleSet& r = g_rules[sl];
+        for (int i = 0; i < r.count; ++i)
+            if (T < r.below[i]) return r.index[i];
+        if (r.count > 0) return r.index[r.count - 1];
+    }
+    return builtin_chunk_index(T);
+}
+
+extern const MixedVariant kMixed4, kMixed8, kMixed16, kMixed32;
+static const MixedVariant* const kMixed[4] = {&kMixed4, &kMixed8, &kMixed16, &kMixed32};
+
+// Slots (nx = 6, 4, 2) of a mixed batch's groups; KS_OK or an error code.
+static int mixed_slots(int G, const ks_batch_group* gs, bool check_data, int (&slot)[3], int64_t* total) {
+    slot[0] = slot[1] = slot[2] = -1;
+    if (G < 1 || G > 3 || !gs) return KS_EINVAL;
+    int64_t sum = 0;
+    for (int i = 0; i < G; ++i) {
+        const ks_batch_group& g = gs[i];
+        const ks_model_batch& mb = g.models;
+        const int s = (mb.nx == 6 && mb.ny == 3) ? 0 : (mb.nx == 4 && mb.ny == 2) ? 1
+                    : (mb.nx == 2 && mb.ny == 1) ? 2 : -1;
+        if (mb.nx < 1 || mb.ny < 1) return KS_EINVAL;
+        if (s < 0) return KS_EUNSUPPORTED;
+        if (slot[s] >= 0) return KS_EINVAL;   // two groups of one size
+        if (mb.B < 1 || g.total_T < mb.B || g.total_T > 0x7fffffffLL) return KS_EINVAL;
+        if (check_data) {
+            if (!mb.F || !mb.Q || !mb.H || !mb.R || !mb.m0 || !mb.P0 || !mb.offsets) return KS_EINVAL;
+            const void* p[5] = {g.y, g.fmean, g.fcov, g.smean, g.scov};
+            for (const void* q : p)
+                if (!q || (reinterpret_cast<uintptr_t>(q) & 15u) != 0) return KS_EINVAL;
+        }
+        slot[s] = i;
+        sum += g.total_T;
+    }
+    if (sum > 0x7fffffffLL) return KS_EINVAL;
+    *total = sum;
+    return KS_OK;
+}
+
 static int check_nx_ny(const ks_model* m, const VTable** out) {
     if (!m) return KS_EINVAL;
     if (m->nx < 1 || m->ny < 1) return KS_EINVAL;
@@ -34,6 +96,12 @@ static int check_nx_ny(const ks_model* m, const VTable** out) {
     if (!v) return KS_EUNSUPPORTED;
     *out = v;
     return KS_OK;
+}
+
+// Look-back settings in the workspace header (ks_workspace_set_waits).
+__global__ void set_header_kernel(uint32_t* hdr, uint32_t wait_polls, uint32_t first_tile) {
+    hdr[HDR_WAIT] = wait_polls;
+    hdr[HDR_FIRST_TILE] = first_tile;
 }
 
 }  // namespace ks
@@ -170,6 +238,46 @@ int ks_smooth_batch(const ks_model_batch* mb, const float* y, int64_t total_T, v
                            static_cast<cudaStream_t>(stream));
 }
 
+size_t ks_workspace_bytes_batched(int G, const ks_batch_group* groups) {
+    int slot[3];
+    int64_t total = 0;
+    if (mixed_slots(G, groups, false, slot, &total) != KS_OK) return 0;
+    size_t need = 0, base[3];
+    for (const MixedVariant* v : kMixed) need = std::max(need, v->regions(groups, slot, base));
+    return need;
+}
+
+int ks_smooth_batched(int G, const ks_batch_group* groups, void* ws, size_t ws_bytes, void* stream) {
+    int slot[3];
+    int64_t total = 0;
+    int rc = mixed_slots(G, groups, true, slot, &total);
+    if (rc) return rc;
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) != 0) return KS_EINVAL;
+    return kMixed[chunk_index_for(0, total)]->run(groups, slot, ws, ws_bytes, static_cast<cudaStream_t>(stream));
+}
+
+int ks_set_chunk_rules(int nx, int count, const ks_chunk_rule* rules) {
+    const int sl = rule_slot(nx);
+    if (sl < 0 || count < 0 || count > kMaxRules || (count > 0 && !rules)) return KS_EINVAL;
+    RuleSet r;
+    r.count = count;
+    for (int i = 0; i < count; ++i) {
+        const int ix = steps_index(rules[i].steps);
+        if (ix < 0 || rules[i].T_below < 1 || (i > 0 && rules[i].T_below <= rules[i - 1].T_below)) return KS_EINVAL;
+        r.below[i] = rules[i].T_below;
+        r.index[i] = ix;
+    }
+    std::lock_guard<std::mutex> lock(g_rules_mutex);
+    g_rules[sl] = r;
+    return KS_OK;
+}
+
+int ks_chunk_steps(int nx, int64_t T) {
+    if (rule_slot(nx) < 0 || T < 1) return 0;
+    static const int kSteps[4] = {4, 8, 16, 32};
+    return kSteps[chunk_index_for(nx, T)];
+}
+
 int ks_status(void* ws, void* stream) {
     if (!ws) return KS_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -181,6 +289,27 @@ int ks_status(void* ws, void* stream) {
     if (h & ST_BADARG) return KS_EINVAL;
     if (h & ST_TIMEOUT) return KS_ETIMEOUT;
     if (h & ST_NUMERIC) return KS_ENUMERIC;
+    return KS_OK;
+}
+
+int ks_workspace_set_waits(void* ws, size_t ws_bytes, uint32_t wait_polls, uint32_t first_tile, void* stream) {
+    if (!ws || ws_bytes < 256 || (reinterpret_cast<uintptr_t>(ws) & 255u) != 0 || first_tile > 1u)
+        return KS_EINVAL;
+    set_header_kernel<<<1, 1, 0, static_cast<cudaStream_t>(stream)>>>(static_cast<uint32_t*>(ws), wait_polls,
+                                                                       first_tile);
+    return launch_status();
+}
+
+int ks_refinements(void* ws, void* stream, uint32_t* count) {
+    if (!ws || !count) return KS_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uint32_t* ctr = static_cast<uint32_t*>(ws) + 1;
+    uint32_t h = 0;
+    if (cudaMemcpyAsync(&h, ctr, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess) return KS_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return KS_ECUDA;
+    if (cudaMemsetAsync(ctr, 0, sizeof(h), s) != cudaSuccess) return KS_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return KS_ECUDA;
+    *count = h;
     return KS_OK;
 }
 

@@ -242,6 +242,74 @@ KS_DEV bool gj_inverse(int r, float (&m)[N], float* pr, float* out) {
     return ok;
 }
 
+// Maximum of v over the lane group.
+template <int N>
+KS_DEV float gmax(float v) {
+#pragma unroll
+    for (int off = Grp<N>::GS / 2; off > 0; off >>= 1) v = fmaxf(v, __shfl_xor_sync(gmask<N>(), v, off));
+    return v;
+}
+
+// Lemma 4's M^{-1} for M = I + C J, from row r of M on lane r (`m`,
+// destroyed): gj_inverse (rows of the result in `out`), then, when the
+// infinity-norm condition estimate ||M||_inf ||M^{-1}||_inf exceeds
+// kRefineCond, one refinement step: lane r forms row r of M and of the
+// residual R = I - M X in FP64 from the FP32 rows of C and J (full, pitch NP)
+// and all rows of X = out, parks R in the scratch matrix `Rs`, and replaces
+// its row of X by the row of X + X R.  Returns FL_BAD on a failed pivot,
+// FL_REFINED when the refinement ran, else 0.
+template <int N>
+KS_DEV Flags ginverse_cj(int r, float (&m)[N], const float* C, const float* J, float* pr, float* out,
+                         float* Rs) {
+    constexpr int NP = Dim<N>::NP;
+    const bool act = r < N;
+    float rs = 0.f;
+#pragma unroll
+    for (int c = 0; c < N; ++c) rs += fabsf(m[c]);
+    const float nm = gmax<N>(act ? rs : 0.f);
+    if (!gj_inverse<N>(r, m, pr, out)) return FL_BAD;
+    float xs = 0.f;
+    if (act) {
+#pragma unroll
+        for (int c = 0; c < N; ++c) xs += fabsf(out[r * NP + c]);
+    }
+    const float cond = nm * gmax<N>(xs);
+    if (!(cond > kRefineCond) || !(cond < 3.0e38f)) return 0u;   // uniform over the group
+    if (act) {
+        double md[N];
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            double t = (c == r) ? 1.0 : 0.0;
+#pragma unroll Unroll<N>::K
+            for (int k = 0; k < N; ++k) t = fma((double)C[r * NP + k], (double)J[k * NP + c], t);
+            md[c] = t;
+        }
+        float rr[N];
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            double t = (c == r) ? 1.0 : 0.0;
+#pragma unroll Unroll<N>::K
+            for (int k = 0; k < N; ++k) t = fma(-md[k], (double)out[k * NP + c], t);
+            rr[c] = (float)t;
+        }
+        store_row<N>(Rs, r, rr);
+    }
+    gsync<N>();
+    if (act) {
+        float xn[N];
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            float t = out[r * NP + c];
+#pragma unroll Unroll<N>::K
+            for (int k = 0; k < N; ++k) t = fmaf(out[r * NP + k], Rs[k * NP + c], t);
+            xn[c] = t;
+        }
+        store_row<N>(out, r, xn);   // other lanes read only their own row of out here
+    }
+    gsync<N>();
+    return FL_REFINED;
+}
+
 // (X + X^T)/2 of a matrix with rows in `tmp`, written row r to `dst`.
 template <int N>
 KS_DEV void symmetrise_into(int r, const float* tmp, float* dst) {
@@ -270,7 +338,7 @@ struct Scratch {
 // Scratch: S0 Mi, S1 T1 = (Mi^T J_j) A_i, S2 X C_i then C_o, S3 J_o, S4 X = A_j Mi,
 // S5 Mi^T J_j;  V0 t, V1 v, V2 Mi^T v, V6-V7 pivots.
 template <int N>
-KS_DEV void fcombine(int r, FSlot<N> i, FSlot<N> j, FSlot<N> o, Scratch<N> s, bool& bad) {
+KS_DEV void fcombine(int r, FSlot<N> i, FSlot<N> j, FSlot<N> o, Scratch<N> s, Flags& bad) {
     const bool act = r < N;
     const int rr = act ? r : 0;
     float m[N];
@@ -281,7 +349,7 @@ KS_DEV void fcombine(int r, FSlot<N> i, FSlot<N> j, FSlot<N> o, Scratch<N> s, bo
         s.V(0)[r] = i.b()[r] + dot<N>(rowp<N>(i.C(), r), j.eta());   // t = b_i + C_i eta_j
         s.V(1)[r] = j.eta()[r] - dot<N>(rowp<N>(j.J(), r), i.b());   // v = eta_j - J_j b_i
     }
-    bad |= !gj_inverse<N>(r, m, s.V(6), s.S(0));                     // Mi rows in S0
+    bad |= ginverse_cj<N>(r, m, i.C(), j.J(), s.V(6), s.S(0), s.S(4));   // Mi rows in S0
     {
         float x[N], v[N];
         row_mul<N>(rowp<N>(j.A(), rr), s.S(0), x);                   // X = A_j Mi
@@ -333,7 +401,7 @@ KS_DEV void fcombine(int r, FSlot<N> i, FSlot<N> j, FSlot<N> o, Scratch<N> s, bo
 // o = (b, C) (x) j for a prefix state (A = 0); only b and C of o are formed:
 //   b_o = A_j Mi (b + C eta_j) + b_j,  C_o = A_j Mi C A_j^T + C_j.
 template <int N>
-KS_DEV void fadvance(int r, FSlot<N> st, FSlot<N> j, FSlot<N> o, Scratch<N> s, bool& bad) {
+KS_DEV void fadvance(int r, FSlot<N> st, FSlot<N> j, FSlot<N> o, Scratch<N> s, Flags& bad) {
     const bool act = r < N;
     const int rr = act ? r : 0;
     float m[N];
@@ -341,7 +409,7 @@ KS_DEV void fadvance(int r, FSlot<N> st, FSlot<N> j, FSlot<N> o, Scratch<N> s, b
 #pragma unroll
     for (int c = 0; c < N; ++c) m[c] += (act && c == r) ? 1.f : 0.f;
     if (act) s.V(0)[r] = st.b()[r] + dot<N>(rowp<N>(st.C(), r), j.eta());
-    bad |= !gj_inverse<N>(r, m, s.V(6), s.S(0));
+    bad |= ginverse_cj<N>(r, m, st.C(), j.J(), s.V(6), s.S(0), s.S(4));
     {
         float x[N];
         row_mul<N>(rowp<N>(j.A(), rr), s.S(0), x);
@@ -380,7 +448,7 @@ KS_DEV void fadvance(int r, FSlot<N> st, FSlot<N> j, FSlot<N> o, Scratch<N> s, b
 // Scratch: S0 CU then C_o, S1 [CUL | UL^T], S2 W, S3 VA^T, S4 X, S5 Y;  V0 b_i, V1 t.
 template <int N, int M, bool PREFIX>
 KS_DEV void fcombine_meas(int r, FSlot<N> i, const ModelConst<N, M>& mc, float bj, const float (&w)[M],
-                          FSlot<N> o, Scratch<N> s, bool& bad) {
+                          FSlot<N> o, Scratch<N> s, Flags& bad) {
     constexpr int NP = Dim<N>::NP;
     const bool act = r < N;
     const int rr = act ? r : 0;
@@ -622,7 +690,7 @@ KS_DEV void first_state(int r, const ModelConst<N, M>& mc, FSlot<N> st) {
 // Scratch: S0 (P-)^{-1}, S1 FP, S2 L, S4 rows of P-;  V0 F xbar + u, V6-V7 pivots.
 template <int N, int M>
 KS_DEV void selem(int r, const ModelConst<N, M>& mc, const float* P, const float* xb, bool last, SSlot<N> o,
-                  Scratch<N> s, bool& bad) {
+                  Scratch<N> s, Flags& bad) {
     constexpr int NP = Dim<N>::NP;
     const bool act = r < N;
     const int rr = act ? r : 0;

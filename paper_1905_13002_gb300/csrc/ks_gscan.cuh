@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(NW * 32) gfilter_reduce_kernel(const ModelCons
     float* wb = SM::chain(gsm, w);
     FSlot<N> X[3] = {FSlot<N>{wb}, FSlot<N>{wb + SM::SLOT}, FSlot<N>{wb + 2 * SM::SLOT}};
     Scratch<N> s{wb + 3 * SM::SLOT};
-    bool bad = false;
+    Flags bad = 0u;
     Cursor<N, M, SEG, TV> cur;
 
     // ---- chain fold
@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(NW * 32) gfilter_reduce_kernel(const ModelCons
         }
         copy_floats<N>(gb.spine0 + (size_t)tile * FS, X[a].p, FS);
     }
-    if (__any_sync(gmask<N>(), bad) && r == 0) atomicOr(status, ST_NUMERIC);
+    report_flags(status, bad, gmask<N>(), r == 0);
 }
 
 // dst[t] = src[t - s] (x) src[t] for t >= s, else src[t].  src[t - s] covers
@@ -193,13 +193,13 @@ __global__ void __launch_bounds__(NWS * 32) gspine_filter_kernel(const float* __
     float* wb = SM::chain(gsm, w);
     FSlot<N> X[3] = {FSlot<N>{wb}, FSlot<N>{wb + SLOT}, FSlot<N>{wb + 2 * SLOT}};
     Scratch<N> sc{wb + 3 * SLOT};
-    bool bad = false;
+    Flags bad = 0u;
     copy_floats_cg<N>(X[0].p, src + (size_t)(t - s) * FS, FS);
     copy_floats_cg<N>(X[1].p, src + (size_t)t * FS, FS);
     if (t - s < s) fadvance<N>(r, X[0], X[1], X[2], sc, bad);
     else fcombine<N>(r, X[0], X[1], X[2], sc, bad);
     copy_floats<N>(o, X[2].p, FS);
-    if (__any_sync(gmask<N>(), bad) && r == 0) atomicOr(status, ST_NUMERIC);
+    report_flags(status, bad, gmask<N>(), r == 0);
 }
 
 // `pre`: the spine's inclusive prefixes (slot t covers tiles 0..t).
@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(NW * 32) gfilter_apply_kernel(const ModelConst
     float* wb = SM::chain(gsm, w);
     FSlot<N> X[3] = {FSlot<N>{wb}, FSlot<N>{wb + SM::SLOT}, FSlot<N>{wb + 2 * SM::SLOT}};
     Scratch<N> s{wb + 3 * SM::SLOT};
-    bool bad = false;
+    Flags bad = 0u;
     Cursor<N, M, SEG, TV> cur;
     int a = 0;
     bool has = false;
@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(NW * 32) gfilter_apply_kernel(const ModelConst
         }
     }
     bad |= !isfinite(probe);
-    if (__any_sync(gmask<N>(), bad) && r == 0) atomicOr(status, ST_NUMERIC);
+    report_flags(status, bad, gmask<N>(), r == 0);
 }
 
 // ---------------------------------------------------------------- reverse
@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(NW * 32) gsmoother_reduce_kernel(const ModelCo
     float* wb = SM::chain(gsm, w);
     SSlot<N> X[3] = {SSlot<N>{wb}, SSlot<N>{wb + SM::SLOT}, SSlot<N>{wb + 2 * SM::SLOT}};
     Scratch<N> s{wb + 3 * SM::SLOT};
-    bool bad = false;
+    Flags bad = 0u;
     Cursor<N, M, SEG, TV> cur;
 
     // ---- chain fold: a_{klo} (x) ... (x) a_{khi}, from the latest step back
@@ -349,7 +349,7 @@ __global__ void __launch_bounds__(NW * 32) gsmoother_reduce_kernel(const ModelCo
         }
         copy_floats<N>(gb.spine0 + (size_t)tile * SS, X[a].p, SS);
     }
-    if (__any_sync(gmask<N>(), bad) && r == 0) atomicOr(status, ST_NUMERIC);
+    report_flags(status, bad, gmask<N>(), r == 0);
 }
 
 // Scan order (tile 0 = latest time): dst[u] = src[u] (x) src[u - s] in time
@@ -403,7 +403,7 @@ __global__ void __launch_bounds__(NW * 32) gsmoother_apply_kernel(int64_t T, flo
     float* wb = SM::chain(gsm, w);
     SSlot<N> X[3] = {SSlot<N>{wb}, SSlot<N>{wb + SM::SLOT}, SSlot<N>{wb + 2 * SM::SLOT}};
     Scratch<N> s{wb + 3 * SM::SLOT};
-    bool bad = false;
+    Flags bad = 0u;
     int a = 0;
     bool has = false;
     if (tile != 0) {
@@ -442,7 +442,7 @@ __global__ void __launch_bounds__(NW * 32) gsmoother_apply_kernel(int64_t T, flo
         }
     }
     bad |= !isfinite(probe);
-    if (__any_sync(gmask<N>(), bad) && r == 0) atomicOr(status, ST_NUMERIC);
+    report_flags(status, bad, gmask<N>(), r == 0);
 }
 
 }  // namespace grp

@@ -115,7 +115,7 @@ KS_DEV void load_raw(const float* __restrict__ src, int64_t k, float (&v)[K]) {
 }
 
 template <int K>
-KS_DEV float scale_lik(float (&l)[K], bool& bad) {
+KS_DEV float scale_lik(float (&l)[K], Flags& bad) {
     float m = 0.f;
 #pragma unroll
     for (int x = 0; x < K; ++x) m = fmaxf(m, l[x]);
@@ -127,7 +127,7 @@ KS_DEV float scale_lik(float (&l)[K], bool& bad) {
 }
 
 template <int K>
-KS_DEV float load_lik(const float* __restrict__ lik, int64_t k, float (&l)[K], bool& bad) {
+KS_DEV float load_lik(const float* __restrict__ lik, int64_t k, float (&l)[K], Flags& bad) {
     load_raw<K>(lik, k, l);
     return scale_lik<K>(l, bad);
 }
@@ -137,7 +137,7 @@ KS_DEV float load_lik(const float* __restrict__ lik, int64_t k, float (&l)[K], b
 //   d(z) = sum_y f_i(y | z) w(y),  f_ij(x | z) = sum_y f_i(y | z) w(y) f_j(x | y) / d(z),
 //   lg_ij(z) = lg_i(z) + max lg_j + log d(z).
 template <int K>
-KS_DEV FE<K> fcombine(FE<K> ei, const FE<K>& ej, bool& bad) {   // ei is overwritten row by row
+KS_DEV FE<K> fcombine(FE<K> ei, const FE<K>& ej, Flags& bad) {   // ei is overwritten row by row
     float mx = ej.lg[0];
 #pragma unroll
     for (int y = 1; y < K; ++y) mx = fmaxf(mx, ej.lg[y]);
@@ -168,7 +168,7 @@ KS_DEV FE<K> fcombine(FE<K> ei, const FE<K>& ej, bool& bad) {   // ei is overwri
 
 // Prefix state (identical rows p, constant L) (x) general element.
 template <int K>
-KS_DEV void fadvance(FS<K>& st, const FE<K>& e, bool& bad) {
+KS_DEV void fadvance(FS<K>& st, const FE<K>& e, Flags& bad) {
     float mx = e.lg[0];
 #pragma unroll
     for (int y = 1; y < K; ++y) mx = fmaxf(mx, e.lg[y]);
@@ -196,7 +196,7 @@ KS_DEV void fadvance(FS<K>& st, const FE<K>& e, bool& bad) {
 // Aggregate (x) step element, with l the scaled likelihood row and lm the log
 // of its scale (see the header).  Pi is read from shared memory.
 template <int K>
-KS_DEV void ffold_step(FE<K>& acc, const float* __restrict__ Pi, const float (&l)[K], float lm, bool& bad) {
+KS_DEV void ffold_step(FE<K>& acc, const float* __restrict__ Pi, const float (&l)[K], float lm, Flags& bad) {
     float row[K][K];   // row[z][x] accumulates (f Pi)[z][x], one Pi row at a time
 #pragma unroll
     for (int z = 0; z < K; ++z)
@@ -229,7 +229,7 @@ KS_DEV void ffold_step(FE<K>& acc, const float* __restrict__ Pi, const float (&l
 
 // The step element itself (fold of the identity).
 template <int K>
-KS_DEV void step_element(FE<K>& e, const float* __restrict__ Pi, const float (&l)[K], float lm, bool& bad) {
+KS_DEV void step_element(FE<K>& e, const float* __restrict__ Pi, const float (&l)[K], float lm, Flags& bad) {
 #pragma unroll
     for (int z = 0; z < K; ++z) {
         float r = 0.f;
@@ -248,7 +248,7 @@ KS_DEV void step_element(FE<K>& e, const float* __restrict__ Pi, const float (&l
 
 // Step 1's element as a prefix state: p(x_1 | y_1) and log p(y_1).
 template <int K>
-KS_DEV void first_state(FS<K>& st, const float (&q1)[K], const float (&l)[K], float lm, bool& bad) {
+KS_DEV void first_state(FS<K>& st, const float (&q1)[K], const float (&l)[K], float lm, Flags& bad) {
     float c = 0.f;
 #pragma unroll
     for (int x = 0; x < K; ++x) {
@@ -265,7 +265,7 @@ KS_DEV void first_state(FS<K>& st, const float (&q1)[K], const float (&l)[K], fl
 // Prefix state (x) step element: p' = (p Pi) . l / c, L' = L + log c + lm.
 template <int K>
 KS_DEV void fadvance_step(FS<K>& st, const float* __restrict__ Pi, const float (&l)[K], float lm, float& comp,
-                          bool& bad) {
+                          Flags& bad) {
     float v[K], c = 0.f;
 #pragma unroll
     for (int x = 0; x < K; ++x) v[x] = 0.f;
@@ -295,7 +295,7 @@ KS_DEV void fadvance_step(FS<K>& st, const float* __restrict__ Pi, const float (
 // Smoothing element of step k from its filtered marginal p (k < n):
 // a(x | z) = p(x) Pi[x][z] / sum_x' p(x') Pi[x'][z].
 template <int K>
-KS_DEV void selem(SE<K>& e, const float* __restrict__ PiT, const float (&p)[K], bool& bad) {
+KS_DEV void selem(SE<K>& e, const float* __restrict__ PiT, const float (&p)[K], Flags& bad) {
 #pragma unroll
     for (int z = 0; z < K; ++z) {
         float pc[K], d = 0.f;
@@ -351,8 +351,8 @@ template <int K>
 struct FilterOp {
     using Elem = FE<K>;
     using State = FS<K>;
-    KS_DEV static Elem combine(const Elem& a, const Elem& b, bool& bad) { return fcombine<K>(a, b, bad); }
-    KS_DEV static void advance(State& s, const Elem& e, bool& bad) { fadvance<K>(s, e, bad); }
+    KS_DEV static Elem combine(const Elem& a, const Elem& b, Flags& bad) { return fcombine<K>(a, b, bad); }
+    KS_DEV static void advance(State& s, const Elem& e, Flags& bad) { fadvance<K>(s, e, bad); }
     KS_DEV static void identity(Elem& e) { set_identity<K>(e); }
     KS_DEV static void zero_state(State& s) {
 #pragma unroll
@@ -374,8 +374,8 @@ template <int K>
 struct SmootherOp {
     using Elem = SE<K>;
     using State = SS<K>;
-    KS_DEV static Elem combine(const Elem& a, const Elem& b, bool&) { return smatmul<K>(a, b); }
-    KS_DEV static void advance(State& s, const Elem& e, bool&) {   // s <- s e.a, rescaled to sum 1
+    KS_DEV static Elem combine(const Elem& a, const Elem& b, Flags&) { return smatmul<K>(a, b); }
+    KS_DEV static void advance(State& s, const Elem& e, Flags&) {   // s <- s e.a, rescaled to sum 1
         float o[K], t = 0.f;
 #pragma unroll
         for (int x = 0; x < K; ++x) {
@@ -410,7 +410,7 @@ __global__ void __launch_bounds__(64) hmm_prep_kernel(const float* __restrict__ 
                                                       uint32_t* __restrict__ zero, int nzero) {
     const int t = threadIdx.x;
     for (int i = t; i < nzero; i += blockDim.x) zero[i] = 0u;
-    bool bad = false;
+    Flags bad = 0u;
     for (int e = t; e < K * K; e += blockDim.x) {
         const float v = Pi[e];
         bad |= !(v >= 0.f) || !(v <= 3.0e38f);
@@ -424,7 +424,7 @@ __global__ void __launch_bounds__(64) hmm_prep_kernel(const float* __restrict__ 
         bad |= !(s >= 0.f) || !(s <= 3.0e38f);
         out->q1[x] = s;
     }
-    if (__any_sync(kFull, bad) && (t & 31) == 0) atomicOr(status, ST_NUMERIC);
+    report_flags(status, bad, kFull, (t & 31) == 0);
 }
 
 template <int K>
@@ -452,9 +452,10 @@ __global__ void __launch_bounds__(NT) hmm_filter_kernel(const Const<K>* __restri
     if (tid == 0) s_tile = (int)atomicAdd(ss.counter, 1u);
     __syncthreads();
     const int tile = s_tile;
+    if (tile >= (int)gridDim.x) return;   // a tile number past the grid (only when the counter was offset)
     const int64_t k0 = tile * TILE + (int64_t)tid * CH;
     const bool valid = k0 < T;
-    bool bad = false;
+    Flags bad = 0u;
 
     // ---- phase 1: fold this thread's steps
     FE<K> acc;
@@ -530,7 +531,7 @@ __global__ void __launch_bounds__(NT) hmm_filter_kernel(const Const<K>* __restri
         store_plain(sagg + (k0 / CH) * (int64_t)(sizeof(SE<K>) / 4), sacc);
         bad |= !isfinite(probe);
     }
-    if (__any_sync(kFull, bad) && (tid & 31) == 0) atomicOr(ss.status, ST_NUMERIC);
+    report_flags(ss.status, bad, kFull, (tid & 31) == 0);
 }
 
 // Reverse scan over the forward scan's per-thread smoothing aggregates; each
@@ -550,12 +551,13 @@ __global__ void __launch_bounds__(NT) hmm_smoother_kernel(const Const<K>* __rest
     if (tid == 0) s_tile = (int)atomicAdd(ss.counter, 1u);
     __syncthreads();
     const int tile = s_tile;
+    if (tile >= (int)gridDim.x) return;   // a tile number past the grid (only when the counter was offset)
     const int64_t nblk = (T + CH - 1) / CH;
     const int64_t c = nblk - 1 - ((int64_t)tile * NT + tid);   // forward block index
     const bool valid = c >= 0;
     const int64_t klo = c * CH;
     const int64_t khi = valid ? ((klo + CH < T ? klo + CH : T) - 1) : -1;
-    bool bad = false;
+    Flags bad = 0u;
 
     SE<K> acc;
     if (valid) acc = load_cg<SE<K>>(sagg + c * (int64_t)(sizeof(SE<K>) / 4));
@@ -588,7 +590,7 @@ __global__ void __launch_bounds__(NT) hmm_smoother_kernel(const Const<K>* __rest
         }
         bad |= !isfinite(probe);
     }
-    if (__any_sync(kFull, bad) && (tid & 31) == 0) atomicOr(ss.status, ST_NUMERIC);
+    report_flags(ss.status, bad, kFull, (tid & 31) == 0);
 }
 
 }  // namespace hmm

@@ -156,7 +156,7 @@ KS_DEV void smem_row(const float* __restrict__ M, int y, float (&v)[K]) {
 // Likelihood row of step k, the same for every lane, scaled to a maximum of
 // 1; returns the log of the maximum.
 template <int K>
-KS_DEV float lik_row(const float* __restrict__ lik, int64_t k, float (&l)[K], bool& bad) {
+KS_DEV float lik_row(const float* __restrict__ lik, int64_t k, float (&l)[K], Flags& bad) {
     const float4* p = reinterpret_cast<const float4*>(lik + k * K);
     float m = 0.f;
 #pragma unroll
@@ -178,7 +178,7 @@ KS_DEV float lik_row(const float* __restrict__ lik, int64_t k, float (&l)[K], bo
 
 // Row z of the step element: Pi[z][x] l(x) normalised, lg = lm + log(row sum).
 template <int K>
-KS_DEV void step_row(FRow<K>& r, const float* __restrict__ Pi, const float (&l)[K], float lm, bool& bad) {
+KS_DEV void step_row(FRow<K>& r, const float* __restrict__ Pi, const float (&l)[K], float lm, Flags& bad) {
     const int z = glane<K>();
     float s = 0.f;
     smem_row<K>(Pi, z, r.f);
@@ -196,7 +196,7 @@ KS_DEV void step_row(FRow<K>& r, const float* __restrict__ Pi, const float (&l)[
 
 // The k = 1 element: every row p(x_1 | y_1), lg = log p(y_1).
 template <int K>
-KS_DEV void first_row(FRow<K>& r, const float* __restrict__ q1, const float (&l)[K], float lm, bool& bad) {
+KS_DEV void first_row(FRow<K>& r, const float* __restrict__ q1, const float (&l)[K], float lm, Flags& bad) {
     float s = 0.f;
 #pragma unroll
     for (int x = 0; x < K; ++x) {
@@ -212,7 +212,7 @@ KS_DEV void first_row(FRow<K>& r, const float* __restrict__ q1, const float (&l)
 
 // Fold of a step element into row z: (f Pi)[z] . l, normalised.
 template <int K>
-KS_DEV void fold_row(FRow<K>& r, const float* __restrict__ Pi, const float (&l)[K], float lm, bool& bad) {
+KS_DEV void fold_row(FRow<K>& r, const float* __restrict__ Pi, const float (&l)[K], float lm, Flags& bad) {
     float o[K];
 #pragma unroll
     for (int x = 0; x < K; ++x) o[x] = 0.f;
@@ -238,7 +238,7 @@ KS_DEV void fold_row(FRow<K>& r, const float* __restrict__ Pi, const float (&l)[
 
 // Definition 1, (row z of a_i, in registers) (x) a_j (in shared memory).
 template <int K>
-KS_DEV void combine_row(FRow<K>& r, const float* __restrict__ ej, bool& bad) {
+KS_DEV void combine_row(FRow<K>& r, const float* __restrict__ ej, Flags& bad) {
     float mx = ej[K * Dims<K>::Q];
 #pragma unroll
     for (int y = 1; y < K; ++y) mx = fmaxf(mx, ej[K * Dims<K>::Q + y]);
@@ -310,7 +310,7 @@ KS_DEV float row0_vec(const float (&a)[K]) {
 // Filtering state (lane x: p(x)) (x) step: p'(x) = (p Pi)(x) l(x) / c.
 template <int K>
 KS_DEV void advance_step(float& p, float& L, float& comp, const float* __restrict__ Pi, float lx, float lm,
-                         bool& bad) {
+                         Flags& bad) {
     const int x = glane<K>();
     float o = 0.f;
 #pragma unroll
@@ -328,7 +328,7 @@ KS_DEV void advance_step(float& p, float& L, float& comp, const float* __restric
 // Row z of the step's Definition 2 element from its filtered marginal
 // (lane x: p(x)): a(x | z) = p(x) Pi[x][z] / sum_x' p(x') Pi[x'][z].
 template <int K>
-KS_DEV void selem_row(float (&a)[K], float p, const float* __restrict__ PiT, bool& bad) {
+KS_DEV void selem_row(float (&a)[K], float p, const float* __restrict__ PiT, Flags& bad) {
     const int z = glane<K>();
     float d = 0.f;
 #pragma unroll
@@ -352,7 +352,7 @@ KS_DEV void selem_last_row(float (&a)[K], float p) {
 // from p (lane x: p(x)):  s'(x) = p(x) sum_z (s(z) / d(z)) Pi[x][z],
 // d(z) = sum_x p(x) Pi[x][z]; rescaled to sum 1.
 template <int K>
-KS_DEV void sadvance_step(float& s, float p, const float* __restrict__ PiT, bool& bad) {
+KS_DEV void sadvance_step(float& s, float p, const float* __restrict__ PiT, Flags& bad) {
     const int lane = glane<K>();
     float d = 0.f;   // lane z: d(z)
 #pragma unroll
@@ -401,7 +401,7 @@ __global__ void __launch_bounds__(NW * 32) filter_reduce_kernel(const Const<K>* 
     const int64_t c = (int64_t)blockIdx.x * NG + w;
     const int64_t left = nch - (int64_t)blockIdx.x * NG;
     const int nvalid = left < NG ? (int)left : NG;
-    bool bad = false;
+    Flags bad = 0u;
     if (w < nvalid) {
         const int64_t k0 = c * CH, k1 = (k0 + CH < T) ? k0 + CH : T;
         FRow<K> r;
@@ -428,7 +428,7 @@ __global__ void __launch_bounds__(NW * 32) filter_reduce_kernel(const Const<K>* 
         }
         store_frow(b.fspine0 + (int64_t)blockIdx.x * Dims<K>::FREC, acc);
     }
-    if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicOr(status, ST_NUMERIC);
+    report_flags(status, bad, kFull, (threadIdx.x & 31) == 0);
 }
 
 // Kogge-Stone level s over tile aggregates: dst[t] = src[t - s] (x) src[t].
@@ -442,7 +442,7 @@ __global__ void __launch_bounds__(NW * 32) spine_kernel(const float* __restrict_
     constexpr int REC = FILTER ? Dims<K>::FREC : Dims<K>::SREC;
     const int w = threadIdx.x / K;
     const int t = blockIdx.x * NG + w;
-    bool bad = false;
+    Flags bad = 0u;
     if (t < ntiles) {
         if (t >= s) {
             if constexpr (FILTER) {
@@ -468,7 +468,7 @@ __global__ void __launch_bounds__(NW * 32) spine_kernel(const float* __restrict_
             for (int i = glane<K>(); i < REC / 4; i += K) q[i] = __ldcg(p + i);
         }
     }
-    if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicOr(status, ST_NUMERIC);
+    report_flags(status, bad, kFull, (threadIdx.x & 31) == 0);
 }
 
 // Forward apply: filt [T][K], loglik [T] (may be null), chain smoothing
@@ -486,7 +486,7 @@ __global__ void __launch_bounds__(NW * 32) filter_apply_kernel(const Const<K>* _
     const int w = threadIdx.x / K, lane = glane<K>();
     const int64_t nch = (T + CH - 1) / CH;
     const int64_t c = (int64_t)blockIdx.x * NG + w;
-    bool bad = false;
+    Flags bad = 0u;
     if (c < nch) {
         const int64_t k0 = c * CH, k1 = (k0 + CH < T) ? k0 + CH : T;
         // incoming prefix: tile prefix (x) the chain's exclusive in-tile prefix
@@ -550,7 +550,7 @@ __global__ void __launch_bounds__(NW * 32) filter_apply_kernel(const Const<K>* _
         store_srow(b.schain + c * Dims<K>::SREC, a);
         bad |= !isfinite(p) || !isfinite(L);
     }
-    if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicOr(status, ST_NUMERIC);
+    report_flags(status, bad, kFull, (threadIdx.x & 31) == 0);
 }
 
 // Reverse reduce: scan position j = tile * NG + w covers chain nch - 1 - j.
@@ -593,7 +593,7 @@ __global__ void __launch_bounds__(NW * 32) smoother_apply_kernel(const Const<K>*
     const int w = threadIdx.x / K, lane = glane<K>();
     const int64_t nch = (T + CH - 1) / CH;
     const int64_t j = (int64_t)blockIdx.x * NG + w;   // scan position
-    bool bad = false;
+    Flags bad = 0u;
     if (j < nch) {
         const int64_t c = nch - 1 - j;
         const int64_t k0 = c * CH, k1 = (k0 + CH < T) ? k0 + CH : T;
@@ -629,14 +629,14 @@ __global__ void __launch_bounds__(NW * 32) smoother_apply_kernel(const Const<K>*
         }
         bad |= !isfinite(s);
     }
-    if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicOr(status, ST_NUMERIC);
+    report_flags(status, bad, kFull, (threadIdx.x & 31) == 0);
 }
 
 template <int K>
 __global__ void __launch_bounds__(64) prep_kernel(const float* __restrict__ pi, const float* __restrict__ Pi,
                                                   Const<K>* __restrict__ out, uint32_t* __restrict__ status) {
     const int t = threadIdx.x;
-    bool bad = false;
+    Flags bad = 0u;
     for (int e = t; e < K * K; e += blockDim.x) {
         const float v = Pi[e];
         bad |= !(v >= 0.f) || !(v <= 3.0e38f);
@@ -648,7 +648,7 @@ __global__ void __launch_bounds__(64) prep_kernel(const float* __restrict__ pi, 
         bad |= !(s >= 0.f) || !(s <= 3.0e38f);
         out->q1[x] = s;
     }
-    if (__any_sync(kFull, bad) && (t & 31) == 0) atomicOr(status, ST_NUMERIC);
+    report_flags(status, bad, kFull, (t & 31) == 0);
 }
 
 }  // namespace hmmw

@@ -84,8 +84,8 @@ struct Impl {
         size_t off = 256;                                   // status word + reserved
         L.off_const = off;                                  // one ModelConst per segment
         off = align_up(off + sizeof(ModelConst<N, M>) * (size_t)B, 256);
-        L.off_flags = off;                                  // [fcounter, scounter, 2 pad][fflags][sflags]
-        L.flags_bytes = 16 + 4 * (size_t)(L.ntf + L.nts);
+        L.off_flags = off;   // [fcounter, scounter, retry counter, pad][fflags][sflags][retry fflags]
+        L.flags_bytes = 16 + 4 * (size_t)(2 * L.ntf + L.nts);
         off = align_up(off + L.flags_bytes, 256);
         L.off_fagg = off;
         off = align_up(off + sizeof(FElem<N>) * (size_t)L.ntf, 256);
@@ -124,6 +124,14 @@ struct Impl {
         s.spin_limit = kSpinLimit;
         return s;
     }
+    // The forward scan's retry with refinement: its own counter and flags.
+    static ScanState fstate_retry(void* ws, const Layout& L) {
+        ScanState s = fstate(ws, L);
+        char* b = static_cast<char*>(ws);
+        s.counter = reinterpret_cast<uint32_t*>(b + L.off_flags + 8);
+        s.flags = reinterpret_cast<uint32_t*>(b + L.off_flags + 16 + 4 * (size_t)(L.ntf + L.nts));
+        return s;
+    }
     static ScanState sstate(void* ws, const Layout& L) {
         char* b = static_cast<char*>(ws);
         ScanState s;
@@ -156,7 +164,7 @@ struct Impl {
         uint32_t* z = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + L.off_flags);
         prep_kernel<N, M><<<1, kPrepThreads, prep_smem(), st>>>(m->F, m->u, m->Q, m->H, m->d, m->R, m->m0, m->P0, y,
                                              mconst(ws, L), status(ws), z, (int)(L.flags_bytes / 4), nullptr,
-                                             L.T);
+                                             L.T, status(ws) + HDR_FIRST_TILE);
         return launch_status();
     }
 
@@ -181,11 +189,16 @@ struct Impl {
     static int launch_filter_fused(void* ws, const Layout& L, const float* y, float* fm, float* fc,
                                    Segs<N, M> segs, cudaStream_t st) {
         constexpr int smem = filter_dyn_smem<N, FNT>();
-        auto k = filter_scan_kernel<N, M, FNT, FCH, true, true, SEG, false>;
-        static const bool ok = allow_smem(k, smem);
+        auto k = filter_scan_kernel<N, M, FNT, FCH, true, true, SEG, false, REF_DETECT, false>;
+        auto kr = filter_scan_kernel<N, M, FNT, FCH, true, true, SEG, false, REF_FP64, true>;
+        static const bool ok = allow_smem(k, smem) && allow_smem(kr, smem);
         if (!ok) return KS_ECUDA;
         k<<<L.ntf, FNT, smem, st>>>(mconst(ws, L), y, nullptr, L.ld, L.T, fm, fc, fstate(ws, L), sblk(ws, L),
                                     segs, TVArgs{});
+        int rc = launch_status();
+        if (rc) return rc;
+        kr<<<L.ntf, FNT, smem, st>>>(mconst(ws, L), y, nullptr, L.ld, L.T, fm, fc, fstate_retry(ws, L),
+                                     sblk(ws, L), segs, TVArgs{});
         return launch_status();
     }
 
@@ -194,11 +207,16 @@ struct Impl {
     static int launch_filter_tv(void* ws, const Layout& L, const float* el, float* fm, float* fc,
                                 const TVArgs& tv, cudaStream_t st) {
         constexpr int smem = filter_dyn_smem<N, FNT>();
-        auto k = filter_scan_kernel<N, M, FNT, FCH, false, true, false, true>;
-        static const bool ok = allow_smem(k, smem);
+        auto k = filter_scan_kernel<N, M, FNT, FCH, false, true, false, true, REF_DETECT, false>;
+        auto kr = filter_scan_kernel<N, M, FNT, FCH, false, true, false, true, REF_FP64, true>;
+        static const bool ok = allow_smem(k, smem) && allow_smem(kr, smem);
         if (!ok) return KS_ECUDA;
         k<<<L.ntf, FNT, smem, st>>>(mconst(ws, L), nullptr, el, L.ld, L.T, fm, fc, fstate(ws, L), sblk(ws, L),
                                     no_segs(), tv);
+        int rc = launch_status();
+        if (rc) return rc;
+        kr<<<L.ntf, FNT, smem, st>>>(mconst(ws, L), nullptr, el, L.ld, L.T, fm, fc, fstate_retry(ws, L),
+                                     sblk(ws, L), no_segs(), tv);
         return launch_status();
     }
 
@@ -349,7 +367,7 @@ struct Impl {
         uint32_t* z = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + L.off_flags);
         prep_kernel<N, M><<<mb->B, kPrepThreads, prep_smem(), st>>>(mb->F, mb->u, mb->Q, mb->H, mb->d, mb->R, mb->m0, mb->P0, y,
                                                  mconst(ws, L), status(ws), z, (int)(L.flags_bytes / 4),
-                                                 mb->offsets, T);
+                                                 mb->offsets, T, status(ws) + HDR_FIRST_TILE);
         int rc = launch_status();
         if (rc) return rc;
         const Segs<N, M> segs{mconst(ws, L), mb->offsets, mb->B};
@@ -434,12 +452,18 @@ struct Impl {
 // 128 * chunk steps, so short inputs need short chunks to launch enough
 // blocks for the 152 SMs; long inputs keep 32 steps per thread, which cuts
 // the per-block look-back, aggregate and per-thread-prefix work per step.
-// The crossovers are where the measured times of neighbouring chunk lengths
-// cross for nx = 2, 4 and 6 on GB300 (single sequences and segmented
-// batches alike).
-inline int chunk_index(int64_t T) {
+// The built-in crossovers are where the measured times of neighbouring chunk
+// lengths cross for nx = 2, 4 and 6 on GB300 (single sequences and
+// segmented batches alike); ks_set_chunk_rules replaces them per state size
+// with a table measured by the tuner.
+inline int builtin_chunk_index(int64_t T) {
     return T < 96 * 1024 ? 0 : T < 192 * 1024 ? 1 : T < 640 * 1024 ? 2 : 3;
 }
+
+// Chunk index (0..3 for 4, 8, 16, 32 steps per thread) of a call over T steps
+// of state size nx (2, 4 or 6; 0: mixed-size batches), from the table set by
+// ks_set_chunk_rules, else the built-in one (ks_api.cu).
+int chunk_index_for(int nx, int64_t T);
 
 // Per-(nx, ny) table of the four chunk variants; each instantiation file
 // defines it (the 4-, 8- and 16-step variants compile in their own units).
@@ -466,11 +490,11 @@ struct Tuned {
     }
     static int smooth(const ks_model* m, const float* y, int64_t T, void* ws, size_t ws_bytes, float* fm,
                       float* fc, float* sm, float* sc, cudaStream_t st, void* const* ev) {
-        return ChunkTable<N, M>::v[chunk_index(T)]->smooth(m, y, T, ws, ws_bytes, fm, fc, sm, sc, st, ev);
+        return ChunkTable<N, M>::v[chunk_index_for(N, T)]->smooth(m, y, T, ws, ws_bytes, fm, fc, sm, sc, st, ev);
     }
     static int smooth_batch(const ks_model_batch* mb, const float* y, int64_t T, void* ws, size_t ws_bytes,
                             float* fm, float* fc, float* sm, float* sc, cudaStream_t st) {
-        return ChunkTable<N, M>::v[chunk_index(T)]->smooth_batch(mb, y, T, ws, ws_bytes, fm, fc, sm, sc, st);
+        return ChunkTable<N, M>::v[chunk_index_for(N, T)]->smooth_batch(mb, y, T, ws, ws_bytes, fm, fc, sm, sc, st);
     }
     static size_t tv_bytes(int64_t T) { return layout(T, 1).bytes_elements; }
     static constexpr VTable vtable() {

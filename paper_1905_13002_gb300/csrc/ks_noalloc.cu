@@ -3,15 +3,15 @@
 // callers that cannot allocate device memory.
 //
 // The array below is a host-side stand-in in host code: its device address is
-// fetched with cudaGetSymbolAddress once per device (with that device
-// current) and cached; that set-up happens on the first call on each device.
+// fetched with cudaGetSymbolAddress, with the calling device current, at the
+// start of every call (a host-side query; the first call on a device also
+// loads the module there).  Asking on every call instead of caching keeps the
+// address valid after a cudaDeviceReset, which gives the array a new address.
 // Every call on a device shares the array; calls that overlap on the GPU race
 // on it.  The status word is cleared at the start of each call and the scan
 // state is cleared by the model-preparation kernel, so a call never depends
 // on what an earlier call left behind.
 #include <cuda_runtime.h>
-
-#include <mutex>
 
 #include "../../include/ks.h"
 #include "ks_impl.cuh"
@@ -23,21 +23,11 @@ namespace {
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[KS_NOALLOC_SCRATCH_BYTES];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mutex;
-void* g_scratch_addr[kMaxDevices];
-
-// Device address of the scratch array on the current device (set up once).
+// Device address of the scratch array on the current device.
 int scratch_on_current_device(void** out) {
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return KS_ECUDA;
-    std::lock_guard<std::mutex> lock(g_mutex);
-    if (g_scratch_addr[dev] == nullptr) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) return KS_ECUDA;
-        g_scratch_addr[dev] = p;
-    }
-    *out = g_scratch_addr[dev];
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) return KS_ECUDA;
+    *out = p;
     return KS_OK;
 }
 
@@ -50,7 +40,8 @@ extern "C" int ks_smooth_noalloc(const ks_model* m, const float* y, int64_t T, f
     if (!m) return KS_EINVAL;
     if (m->nx != 4 || m->ny != 2 || m->time_varying != 0) return KS_EUNSUPPORTED;
     if (T < 1 || T > KS_NOALLOC_MAX_T) return KS_EINVAL;
-    if (!fmean || !fcov || !smean || !scov) return KS_EINVAL;
+    if (!fmean || !fcov) return KS_EINVAL;
+    if ((smean == nullptr) != (scov == nullptr)) return KS_EINVAL;   // both NULL: filtering only
     const VTable* v = &kImpl32_4_2;   // 32 steps per thread: the smallest scratch layout
     if (v->layout(T, 1).bytes_smooth > (size_t)KS_NOALLOC_SCRATCH_BYTES) return KS_EINVAL;
     void* ws = nullptr;

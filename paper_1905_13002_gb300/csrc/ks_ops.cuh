@@ -22,6 +22,46 @@ __host__ __device__ constexpr int sidx(int i, int j) {
 // Device status bits (combined with atomicOr into the workspace status word).
 enum : uint32_t { ST_NUMERIC = 1u, ST_TIMEOUT = 2u, ST_BADARG = 4u };
 
+// Per-thread diagnostic bits carried through the operators:
+//   FL_BAD      a non-finite value or a failed factorisation (reported as ST_NUMERIC);
+//   FL_REFINED  an inverse got the FP64-residual refinement step because its
+//               condition estimate exceeded kRefineCond;
+//   FL_NEED     an inverse's condition estimate exceeded kRefineCond in code
+//               that does not refine (the call then repeats the scan with
+//               refinement, see the scan kernels).
+using Flags = uint32_t;
+enum : uint32_t { FL_BAD = 1u, FL_REFINED = 2u, FL_NEED = 4u };
+
+// How the general Lemma 4 operator takes (I + C_i J_j)^{-1}: plain FP32
+// Gauss-Jordan; the same with the condition estimate (FL_NEED when it
+// exceeds kRefineCond); or with the estimate and the FP64 refinement.
+enum : int { REF_NONE = 0, REF_DETECT = 1, REF_FP64 = 2 };
+
+// Condition number (1-norm or infinity-norm estimate) above which an FP32
+// inverse gets one refinement step with its residual formed in FP64.
+constexpr float kRefineCond = 1.0e3f;
+
+// Workspace header words (the first 256 bytes of every workspace, zeroed by
+// ks_workspace_init): [0] status bits, [1] refinement counter, [2] look-back
+// wait limit in polls (0: the scan's default), [3] the forward scans' first
+// tile number (0; 1 only when a test leaves tile 0 unclaimed to make the
+// look-back waits run out), [4] set when a scan without refinement met an
+// ill-conditioned inverse (cleared by the preparation kernel).
+enum : int { HDR_STATUS = 0, HDR_REFINED = 1, HDR_WAIT = 2, HDR_FIRST_TILE = 3, HDR_NEED = 4 };
+
+// End-of-kernel report of one warp or lane group (`mask`), by its `leader`
+// lane: a numeric failure sets ST_NUMERIC in the status word, a group in
+// which any lane refined an inverse adds one to the refinement counter, and
+// one that met an ill-conditioned inverse without refining it sets HDR_NEED.
+KS_DEV void report_flags(uint32_t* status, Flags f, unsigned mask, bool leader) {
+    const bool b = __any_sync(mask, (f & FL_BAD) != 0u);
+    const bool r = __any_sync(mask, (f & FL_REFINED) != 0u);
+    const bool n = __any_sync(mask, (f & FL_NEED) != 0u);
+    if (leader && b) atomicOr(status + HDR_STATUS, ST_NUMERIC);
+    if (leader && r) atomicAdd(status + HDR_REFINED, 1u);
+    if (leader && n) atomicOr(status + HDR_NEED, 1u);
+}
+
 // ---------------------------------------------------------------- elements
 // Filtering element of Lemma 3: f(x|z) = N(x; A z + b, C), g(z) ∝ N_I(z; eta, J).
 template <int N>
@@ -158,6 +198,79 @@ KS_DEV bool inverse_pp(float (&Mx)[N][N], float (&X)[N][N]) {
     return ok;
 }
 
+// Column-sum (1-) norm of an N x N register matrix.
+template <int N>
+KS_DEV float norm1(const float (&X)[N][N]) {
+    float m = 0.f;
+#pragma unroll
+    for (int c = 0; c < N; ++c) {
+        float s = 0.f;
+#pragma unroll
+        for (int r = 0; r < N; ++r) s += fabsf(X[r][c]);
+        m = fmaxf(m, s);
+    }
+    return m;
+}
+
+// One refinement step of X ~ M^{-1} for M = I + C J (C, J packed lower
+// triangles, Lemma 4's I + C_i J_j), with the residual formed in FP64 from
+// the FP32 inputs: row a of R = I - X M is e_a - x_a - (x_a C) J (x_a = row a
+// of X), and X <- X + R X.
+template <int N>
+KS_DEV void refine_inverse_pp(const float (&C)[sym_size(N)], const float (&J)[sym_size(N)], float (&X)[N][N]) {
+    float Xn[N][N];
+#pragma unroll
+    for (int a = 0; a < N; ++a) {
+        double v[N];
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            double t = 0.0;
+#pragma unroll
+            for (int k = 0; k < N; ++k) t = fma((double)X[a][k], (double)C[sidx(k, c)], t);
+            v[c] = t;
+        }
+        float r[N];
+#pragma unroll
+        for (int b = 0; b < N; ++b) {
+            double t = (a == b ? 1.0 : 0.0) - (double)X[a][b];
+#pragma unroll
+            for (int c = 0; c < N; ++c) t = fma(-v[c], (double)J[sidx(c, b)], t);
+            r[b] = (float)t;
+        }
+#pragma unroll
+        for (int b = 0; b < N; ++b) {
+            float t = X[a][b];
+#pragma unroll
+            for (int k = 0; k < N; ++k) t = fmaf(r[k], X[k][b], t);
+            Xn[a][b] = t;
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < N; ++a)
+#pragma unroll
+        for (int b = 0; b < N; ++b) X[a][b] = Xn[a][b];
+}
+
+// Mi = (I + C J)^{-1} from Mx = I + C J (destroyed): FP32 Gauss-Jordan with
+// partial pivoting, then one FP64-residual refinement step when the 1-norm
+// condition estimate ||M||_1 ||Mi||_1 exceeds kRefineCond.  Returns FL_BAD on
+// a failed pivot, FL_REFINED when the refinement ran, else 0.
+template <int N, int REF = REF_FP64>
+KS_DEV Flags inverse_cj(const float (&C)[sym_size(N)], const float (&J)[sym_size(N)], float (&Mx)[N][N],
+                        float (&Mi)[N][N]) {
+    if constexpr (REF == REF_NONE) return inverse_pp<N>(Mx, Mi) ? 0u : FL_BAD;
+    const float nm = norm1<N>(Mx);
+    if (!inverse_pp<N>(Mx, Mi)) return FL_BAD;
+    const float cond = nm * norm1<N>(Mi);
+    if (!(cond > kRefineCond) || !(cond < 3.0e38f)) return 0u;
+    if constexpr (REF == REF_DETECT) {
+        return FL_NEED;
+    } else {
+        refine_inverse_pp<N>(C, J, Mi);
+        return FL_REFINED;
+    }
+}
+
 // Cholesky G = L L^T of an M x M SPD matrix given as packed lower triangle;
 // returns L^{-1} (lower, dense row-major).  G here is I + U C U^T >= I, so no
 // pivoting is needed.  Returns false for a non-positive pivot.
@@ -209,8 +322,8 @@ KS_DEV bool chol_inv_lower(const float (&G)[sym_size(M)], float (&Li)[M][M]) {
 //   C_ij   = A_j (Mi C_i) A_j^T + C_j          (Mi C_i symmetric)
 //   eta_ij = A_i^T Mi^T (eta_j - J_j b_i) + eta_i
 //   J_ij   = A_i^T (Mi^T J_j) A_i + J_i       (Mi^T J_j symmetric)
-template <int N>
-KS_DEV FElem<N> fcombine(const FElem<N>& ei, const FElem<N>& ej, bool& bad) {
+template <int N, int REF = REF_FP64>
+KS_DEV FElem<N> fcombine(const FElem<N>& ei, const FElem<N>& ej, Flags& bad) {
     FElem<N> r;
     float Mx[N][N], Mi[N][N];
 #pragma unroll
@@ -222,7 +335,7 @@ KS_DEV FElem<N> fcombine(const FElem<N>& ei, const FElem<N>& ej, bool& bad) {
             for (int c = 0; c < N; ++c) s = fmaf(ei.C[sidx(a, c)], ej.J[sidx(c, b)], s);
             Mx[a][b] = s;
         }
-    bad |= !inverse_pp<N>(Mx, Mi);
+    bad |= inverse_cj<N, REF>(ei.C, ej.J, Mx, Mi);
     // X = A_j Mi
     float X[N][N];
 #pragma unroll
@@ -354,8 +467,8 @@ KS_DEV FElem<N> fcombine(const FElem<N>& ei, const FElem<N>& ej, bool& bad) {
 // which only b and C are needed:
 //   M = I + P J_j,  b' = A_j M^{-1} (xbar + P eta_j) + b_j,
 //   C' = A_j (M^{-1} P) A_j^T + C_j.
-template <int N>
-KS_DEV void fadvance(FState<N>& st, const FElem<N>& ej, bool& bad) {
+template <int N, int REF = REF_FP64>
+KS_DEV void fadvance(FState<N>& st, const FElem<N>& ej, Flags& bad) {
     float Mx[N][N], Mi[N][N];
 #pragma unroll
     for (int a = 0; a < N; ++a)
@@ -366,7 +479,7 @@ KS_DEV void fadvance(FState<N>& st, const FElem<N>& ej, bool& bad) {
             for (int c = 0; c < N; ++c) s = fmaf(st.C[sidx(a, c)], ej.J[sidx(c, b)], s);
             Mx[a][b] = s;
         }
-    bad |= !inverse_pp<N>(Mx, Mi);
+    bad |= inverse_cj<N, REF>(st.C, ej.J, Mx, Mi);
     float t[N], mt[N];
 #pragma unroll
     for (int a = 0; a < N; ++a) {
@@ -435,7 +548,7 @@ KS_DEV void fadvance(FState<N>& st, const FElem<N>& ej, bool& bad) {
 // (time-invariant model) or one step's element of a time-varying model.
 template <int N, int M, class MC>
 KS_DEV FElem<N> fcombine_meas(const FElem<N>& ei, const MC& mc, const float (&bj)[N],
-                              const float (&wj)[M], bool& bad) {
+                              const float (&wj)[M], Flags& bad) {
     FElem<N> r;
     float CU[N][M];
 #pragma unroll
@@ -612,7 +725,7 @@ KS_DEV FElem<N> fcombine_meas(const FElem<N>& ei, const MC& mc, const float (&bj
 //   b' = A_j M^{-1} (xbar + P U^T w_j) + b_j,   C' = A_j (P - CUL CUL^T) A_j^T + C_j.
 template <int N, int M, class MC>
 KS_DEV void fadvance_meas(FState<N>& st, const MC& mc, const float (&bj)[N],
-                          const float (&wj)[M], bool& bad) {
+                          const float (&wj)[M], Flags& bad) {
     float CU[N][M];
 #pragma unroll
     for (int a = 0; a < N; ++a)
@@ -785,9 +898,9 @@ KS_DEV void first_element(const ModelConst<N, M>& mc, FElem<N>& e) {
 //   E^T = (P-)^{-1} (F P)),  g = xbar - E (F xbar + u),  L = P - E (F P).
 // MC holds F [N*N], u [N] and Q (packed lower): a ModelConst, or one step's
 // transition of a time-varying model.
-template <int N, int M, class MC>
+template <int N, int M, class MC, class FL>
 KS_DEV void smoother_element(const MC& mc, const float (&xbar)[N],
-                             const float (&P)[sym_size(N)], SElem<N>& e, bool& bad) {
+                             const float (&P)[sym_size(N)], SElem<N>& e, FL& bad) {
     float FP[N][N];
 #pragma unroll
     for (int a = 0; a < N; ++a)

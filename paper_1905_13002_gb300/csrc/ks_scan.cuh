@@ -33,9 +33,14 @@ struct ScanState {
     uint32_t* flags;     // per-tile flags (zeroed before launch)
     float* agg;          // per-tile aggregates
     float* pre;          // per-tile inclusive prefixes
-    uint32_t* status;    // device status word
+    uint32_t* status;    // device status word (workspace header, see below)
     uint32_t spin_limit; // look-back polls before giving up (~1 s)
 };
+
+KS_DEV uint32_t wait_limit(const ScanState& ss) {
+    const uint32_t o = ss.status[HDR_WAIT];
+    return o != 0u ? o : ss.spin_limit;
+}
 
 template <class T>
 KS_DEV T shfl_up_t(const T& x, int d) {
@@ -370,7 +375,7 @@ KS_DEV void load_trans(const TVArgs& tv, int64_t k, Trans<N>& t) {
 // transition into step k + 1 is that step's (F, u, Q).
 template <int N, int M>
 KS_DEV void build_selem_tv(const TVArgs& tv, int64_t k, int64_t T, const float (&xb)[N],
-                           const float (&P)[sym_size(N)], SElem<N>& e, bool& bad) {
+                           const float (&P)[sym_size(N)], SElem<N>& e, Flags& bad) {
     if (k == T - 1) {   // Lemma 5, k = n: E = 0, g = xbar_n, L = P_n
 #pragma unroll
         for (int a = 0; a < N * N; ++a) e.E[a] = 0.f;
@@ -392,7 +397,7 @@ KS_DEV void build_selem_tv(const TVArgs& tv, int64_t k, int64_t T, const float (
 // replaces it.
 template <int N, int M, bool TV>
 KS_DEV void build_selem_flat(const ModelConst<N, M>* mc, const TVArgs& tv, int64_t k, int64_t T, bool last,
-                             const float (&xb)[N], const float (&P)[sym_size(N)], SElem<N>& e, bool& bad) {
+                             const float (&xb)[N], const float (&P)[sym_size(N)], SElem<N>& e, Flags& bad) {
     bool b = false;
     if constexpr (TV) {
         Trans<N> t;
@@ -401,7 +406,7 @@ KS_DEV void build_selem_flat(const ModelConst<N, M>* mc, const TVArgs& tv, int64
     } else {
         smoother_element<N, M>(*mc, xb, P, e, b);
     }
-    bad |= b && !last;
+    bad |= (b && !last) ? FL_BAD : 0u;
     if (last) {
 #pragma unroll
         for (int a = 0; a < N * N; ++a) e.E[a] = 0.f;
@@ -437,26 +442,27 @@ constexpr int kPrepThreads = 64;
 // FP32 constants of Lemma 3 for k > 1 and warp 1, at the same time, the k = 1
 // element (prediction of N(m0, P0) and update with y_1) in FP64; the two
 // chains only meet for the final store.
+// Body of the preparation of segment sg of nseg (one thread block); dyn:
+// its dynamic shared memory (PrepSmem and a ModelConst).
 template <int N, int M>
-__global__ void __launch_bounds__(kPrepThreads) prep_kernel(const float* __restrict__ F, const float* __restrict__ u,
-                                                   const float* __restrict__ Q, const float* __restrict__ H,
-                                                   const float* __restrict__ d, const float* __restrict__ R,
-                                                   const double* __restrict__ m0, const double* __restrict__ P0,
-                                                   const float* __restrict__ y, ModelConst<N, M>* __restrict__ out,
-                                                   uint32_t* __restrict__ status, uint32_t* __restrict__ zero,
-                                                   int nzero, const int64_t* __restrict__ off, int64_t T) {
-    extern __shared__ __align__(16) char prep_dsm[];
+KS_DEV void prep_body(char* prep_dsm, int sg, int nseg, const float* __restrict__ F, const float* __restrict__ u,
+                      const float* __restrict__ Q, const float* __restrict__ H, const float* __restrict__ d,
+                      const float* __restrict__ R, const double* __restrict__ m0, const double* __restrict__ P0,
+                      const float* __restrict__ y, ModelConst<N, M>* __restrict__ out, uint32_t* __restrict__ status,
+                      uint32_t* __restrict__ zero, int nzero, const int64_t* __restrict__ off, int64_t T,
+                      const uint32_t* __restrict__ first_tile) {
     PrepSmem<N, M>& p = *reinterpret_cast<PrepSmem<N, M>*>(prep_dsm);
     ModelConst<N, M>& mc =
         *reinterpret_cast<ModelConst<N, M>*>(prep_dsm + ((sizeof(PrepSmem<N, M>) + 15) / 16) * 16);
     const int t = threadIdx.x, nt = blockDim.x;
     const int warp = t >> 5, l = t & 31;
-    const int sg = blockIdx.x;
-    if (sg == 0)
-        for (int i = t; i < nzero; i += nt) zero[i] = 0u;
+    if (sg == 0) {   // zero[0] is the forward tile counter of the nx <= 6 scans (first_tile: its start)
+        for (int i = t; i < nzero; i += nt) zero[i] = (i == 0 && first_tile != nullptr) ? *first_tile : 0u;
+        if (t == 0) status[HDR_NEED] = 0u;
+    }
     if (off != nullptr && t == 0) {
         const int64_t a = off[sg], b = off[sg + 1];
-        const bool okseg = (a < b) && (sg != 0 || a == 0) && (sg != (int)gridDim.x - 1 || b == T);
+        const bool okseg = (a < b) && (sg != 0 || a == 0) && (sg != nseg - 1 || b == T);
         if (!okseg) atomicOr(status, ST_BADARG);
     }
     F += (size_t)sg * N * N;
@@ -681,6 +687,28 @@ __global__ void __launch_bounds__(kPrepThreads) prep_kernel(const float* __restr
     if (t == 0 && !(p.ok0 && p.ok1)) atomicOr(status, ST_NUMERIC);
 }
 
+// Dynamic shared memory of prep_body.
+template <int N, int M>
+constexpr size_t prep_dyn_smem() {
+    return ((sizeof(PrepSmem<N, M>) + 15) / 16) * 16 + sizeof(ModelConst<N, M>) + 16;
+}
+
+// One block per model (segment); block 0 also zeroes the scans' counters and
+// flags (`zero`), the first one from *first_tile when given.
+template <int N, int M>
+__global__ void __launch_bounds__(kPrepThreads) prep_kernel(const float* __restrict__ F, const float* __restrict__ u,
+                                                   const float* __restrict__ Q, const float* __restrict__ H,
+                                                   const float* __restrict__ d, const float* __restrict__ R,
+                                                   const double* __restrict__ m0, const double* __restrict__ P0,
+                                                   const float* __restrict__ y, ModelConst<N, M>* __restrict__ out,
+                                                   uint32_t* __restrict__ status, uint32_t* __restrict__ zero,
+                                                   int nzero, const int64_t* __restrict__ off, int64_t T,
+                                                   const uint32_t* __restrict__ first_tile = nullptr) {
+    extern __shared__ __align__(16) char prep_dsm[];
+    prep_body<N, M>(prep_dsm, (int)blockIdx.x, (int)gridDim.x, F, u, Q, H, d, R, m0, P0, y, out, status, zero, nzero,
+                    off, T, first_tile);
+}
+
 // ---------------------------------------------------------------- Lemma 3 materialised
 // Element k written component-major: component c of element k at el[c*ld + k],
 // A [N*N], b [N], C [N*N], eta [N], J [N*N] (full, symmetric).
@@ -758,7 +786,7 @@ KS_DEV void load_tvelem(const float* __restrict__ el, int64_t k, TVElem<N, M>& e
 // w = L^{-1} (y - H u - d), Lemma 3's gain is K = Q H^T S^{-1} = V^T L^{-1}, so
 //   A = F - V^T U,  b = u + V^T w,  C = Q - V^T V,  eta = U^T w,  J = U^T U.
 template <int N, int M>
-KS_DEV void tv_element(const TVArgs& tv, const float* __restrict__ y, int64_t k, TVElem<N, M>& e, bool& bad) {
+KS_DEV void tv_element(const TVArgs& tv, const float* __restrict__ y, int64_t k, TVElem<N, M>& e, Flags& bad) {
     float F[N][N], Q[N][N], H[M][N], R[M][M], u[N], d[M], yk[M];
     {
         float Qr[N * N], Rr[M * M];
@@ -868,7 +896,7 @@ KS_DEV void tv_element(const TVArgs& tv, const float* __restrict__ y, int64_t k,
 // before it).
 template <int N, int M>
 __device__ __noinline__ void tv_first_element(const TVArgs& tv, const float* __restrict__ y, TVElem<N, M>& e,
-                                              bool& bad) {
+                                              Flags& bad) {
     double Pm[N][N], mm[N], HP[M][N], S[M][M], L[M][M], t1[M][N], z[M];
     for (int a = 0; a < N; ++a) {
         double s = tv.u ? (double)tv.u[a] : 0.0;
@@ -941,9 +969,11 @@ template <int N, int M>
 __global__ void __launch_bounds__(256) tv_elements_kernel(TVArgs tv, const float* __restrict__ y, int64_t T,
                                                           float* __restrict__ el, uint32_t* __restrict__ status,
                                                           uint32_t* __restrict__ zero, int nzero) {
-    if (blockIdx.x == 0)
+    if (blockIdx.x == 0) {
         for (int i = threadIdx.x; i < nzero; i += blockDim.x) zero[i] = 0u;
-    bool bad = false;
+        if (threadIdx.x == 0) status[HDR_NEED] = 0u;
+    }
+    Flags bad = 0u;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < T;
          k += (int64_t)gridDim.x * blockDim.x) {
         TVElem<N, M> e;
@@ -951,7 +981,7 @@ __global__ void __launch_bounds__(256) tv_elements_kernel(TVArgs tv, const float
         else tv_element<N, M>(tv, y, k, e, bad);
         store_tvelem<N, M>(el, k, e);
     }
-    if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicOr(status, ST_NUMERIC);
+    report_flags(status, bad, kFull, (threadIdx.x & 31) == 0);
 }
 
 // Per-step model constants of a time-varying model (steps 1..T-1; step 0,
@@ -961,7 +991,7 @@ __global__ void __launch_bounds__(256) tv_elements_kernel(TVArgs tv, const float
 template <int N, int M>
 __global__ void __launch_bounds__(128) tv_const_kernel(TVArgs tv, int64_t T, ModelConst<N, M>* __restrict__ out,
                                                        uint32_t* __restrict__ status) {
-    bool bad = false;
+    Flags bad = 0u;
     for (int64_t k = 1 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < T;
          k += (int64_t)gridDim.x * blockDim.x) {
         ModelConst<N, M>& mc = out[k];
@@ -1053,7 +1083,7 @@ __global__ void __launch_bounds__(128) tv_const_kernel(TVArgs tv, int64_t T, Mod
         for (int a = 0; a < sym_size(N); ++a) mc.C1[a] = 0.f;
         for (int a = 0; a < 4; ++a) mc.pad[a] = 0.f;
     }
-    if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicOr(status, ST_NUMERIC);
+    report_flags(status, bad, kFull, (threadIdx.x & 31) == 0);
 }
 
 // ---------------------------------------------------------------- staging
@@ -1140,7 +1170,7 @@ KS_DEV void stage_fetch(char* buf, const float* mean, const float* cov, int64_t 
 //   Op::combine(x, y)   x (x) y for general elements, x earlier in scan order
 //   Op::advance(st, e)  prefix-form state (x) general element
 template <class Op>
-KS_DEV typename Op::State lookback_warp(const ScanState& ss, int tile, int lane, bool& bad, bool& timeout) {
+KS_DEV typename Op::State lookback_warp(const ScanState& ss, int tile, int lane, Flags& bad, bool& timeout) {
     using E = typename Op::Elem;
     using S = typename Op::State;
     constexpr int AF = sizeof(E) / 4, PF = sizeof(S) / 4;
@@ -1148,10 +1178,11 @@ KS_DEV typename Op::State lookback_warp(const ScanState& ss, int tile, int lane,
     E run;
     bool have_run = false;
     int base = tile - 1;
+    const uint32_t limit = wait_limit(ss);
     while (true) {
         const int j = base - lane;
         uint32_t f = 0u;
-        if (j >= 0) f = wait_flag(ss.flags + j, ss.spin_limit);
+        if (j >= 0) f = wait_flag(ss.flags + j, limit);
         const bool lost = (j >= 0) && (f == 0u);
         if (__any_sync(kFull, lost)) {
             timeout = true;
@@ -1184,12 +1215,12 @@ KS_DEV typename Op::State lookback_warp(const ScanState& ss, int tile, int lane,
     }
 }
 
-template <int N>
+template <int N, int REF = REF_FP64>
 struct FilterOp {
     using Elem = FElem<N>;
     using State = FState<N>;
-    KS_DEV static Elem combine(const Elem& a, const Elem& b, bool& bad) { return fcombine<N>(a, b, bad); }
-    KS_DEV static void advance(State& s, const Elem& e, bool& bad) { fadvance<N>(s, e, bad); }
+    KS_DEV static Elem combine(const Elem& a, const Elem& b, Flags& bad) { return fcombine<N, REF>(a, b, bad); }
+    KS_DEV static void advance(State& s, const Elem& e, Flags& bad) { fadvance<N, REF>(s, e, bad); }
     KS_DEV static void identity(Elem& e) { set_identity<N>(e); }
     KS_DEV static void zero_state(State& s) {
 #pragma unroll
@@ -1212,8 +1243,8 @@ template <int N>
 struct SmootherOp {
     using Elem = SElem<N>;
     using State = SState<N>;
-    KS_DEV static Elem combine(const Elem& a, const Elem& b, bool&) { return scombine<N>(b, a); }
-    KS_DEV static void advance(State& s, const Elem& e, bool&) { sadvance<N>(e, s); }
+    KS_DEV static Elem combine(const Elem& a, const Elem& b, Flags&) { return scombine<N>(b, a); }
+    KS_DEV static void advance(State& s, const Elem& e, Flags&) { sadvance<N>(e, s); }
     KS_DEV static void identity(Elem& e) { set_identity<N>(e); }
     KS_DEV static void zero_state(State& s) {
 #pragma unroll
@@ -1236,22 +1267,27 @@ struct SmootherOp {
 // aggregate and the look-back.  On return every thread of a valid block has
 // `st` = the prefix entering its block and `has` = whether there is one (only
 // the very first block of the sequence has none).
-template <class Op, int NT>
+template <class E, class S, int NT>
+struct BlockScanSmem {
+    E wtot[NT / 32];
+    E wincl[NT / 32];
+    E lexcl[NT];     // per-thread in-warp exclusive prefix, parked across the look-back
+    E tagg;
+    S texcl;
+    int has;
+};
+
+// LOp: the operator of the look-back (the same operator; a variant may differ
+// in how it takes its inverses).
+template <class Op, int NT, class LOp = Op>
 struct BlockScan {
     static constexpr int NW = NT / 32;
     using E = typename Op::Elem;
     using S = typename Op::State;
-    struct Smem {
-        E wtot[NW];
-        E wincl[NW];
-        E lexcl[NT];     // per-thread in-warp exclusive prefix, parked across the look-back
-        E tagg;
-        S texcl;
-        int has;
-    };
+    using Smem = BlockScanSmem<E, S, NT>;
 
     KS_DEV static void run(Smem& sm, const ScanState& ss, int tile, const E& acc, S& st, bool& has,
-                           bool& bad) {
+                           Flags& bad) {
         const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
         constexpr int AF = sizeof(E) / 4, PF = sizeof(S) / 4;
         E incl = acc;
@@ -1292,10 +1328,10 @@ struct BlockScan {
                     store_plain(ss.agg + (int64_t)tile * AF, sm.tagg);
                     st_release(ss.flags + tile, kFlagAgg);
                 }
-                ex = lookback_warp<Op>(ss, tile, lane, bad, timeout);
+                ex = lookback_warp<LOp>(ss, tile, lane, bad, timeout);
                 if (lane == 0) {
                     S inc = ex;
-                    Op::advance(inc, sm.tagg, bad);
+                    LOp::advance(inc, sm.tagg, bad);
                     store_plain(ss.pre + (int64_t)tile * PF, inc);
                     st_release(ss.flags + tile, kFlagPre);
                 }
@@ -1325,7 +1361,7 @@ struct BlockScan {
 // Lemma 5 element from a filtered mean and covariance (k = n when `last`).
 template <int N, int M, class MC>
 KS_DEV void build_selem_from(const MC& mc, const float (&xb)[N], const float (&P)[sym_size(N)],
-                             bool last, SElem<N>& e, bool& bad) {
+                             bool last, SElem<N>& e, Flags& bad) {
     if (last) {  // Lemma 5, k = n: E = 0, g = xbar_n, L = P_n
 #pragma unroll
         for (int a = 0; a < N * N; ++a) e.E[a] = 0.f;
@@ -1345,32 +1381,34 @@ KS_DEV void build_selem_from(const MC& mc, const float (&xb)[N], const float (&P
 // smoothing block aggregate per thread to `sagg` for the reverse scan.
 // With TV the elements are a time-varying model's TVElem records (`el`) and
 // the fused smoothing elements use the next step's transition from `tv`.
-template <int N, int M, int NT, int CH, bool FROM_Y, bool SAGG, bool SEG, bool TV>
-__global__ void __launch_bounds__(NT) filter_scan_kernel(const ModelConst<N, M>* __restrict__ mcg,
-                                                         const float* __restrict__ y,
-                                                         const float* __restrict__ el, int64_t ld,
-                                                         int64_t T, float* __restrict__ fmean,
-                                                         float* __restrict__ fcov, ScanState ss,
-                                                         float* __restrict__ sagg, Segs<N, M> segs,
-                                                         TVArgs tv) {
+// Shared memory of one forward tile: the model constants (single sequence)
+// and the block scan's.
+template <int N, int M, int NT>
+struct FilterSmem {
+    ModelConst<N, M> mc;
+    typename BlockScan<FilterOp<N>, NT>::Smem bsm;
+};
+
+// One forward tile (`tile` of the sequence or segmented axis).  `sm.mc` holds
+// the constants of a single sequence (unused by segmented scans); `dsm` is
+// the staging memory of filter_dyn_smem.
+template <int N, int M, int NT, int CH, bool FROM_Y, bool SAGG, bool SEG, bool TV, int REF = REF_FP64>
+KS_DEV void filter_scan_body(FilterSmem<N, M, NT>& sm, char* dsm, int tile,
+                             const float* __restrict__ y, const float* __restrict__ el, int64_t ld, int64_t T,
+                             float* __restrict__ fmean, float* __restrict__ fcov, const ScanState& ss,
+                             float* __restrict__ sagg, const Segs<N, M>& segs, const TVArgs& tv) {
     static_assert(FROM_Y || !SEG, "segmented scans build their elements from y");
     static_assert(!TV || (!FROM_Y && !SEG), "time-varying elements come materialised");
-    using BS = BlockScan<FilterOp<N>, NT>;
+    using BS = BlockScan<FilterOp<N, REF>, NT>;
     using SG = Stage<N>;
     constexpr int64_t TILE = (int64_t)NT * CH;
     constexpr int OSTR = SG::pad_odd(SG::kBuf);
-    __shared__ ModelConst<N, M> mc;
-    __shared__ typename BS::Smem bsm;
-    __shared__ int s_tile;
-    extern __shared__ __align__(16) char dsm[];
+    const ModelConst<N, M>& mc = sm.mc;
+    typename BS::Smem& bsm = sm.bsm;
     const int tid = threadIdx.x, lane = tid & 31;
-    load_const<N, M>(mcg, mc, tid, NT);
-    if (tid == 0) s_tile = (int)atomicAdd(ss.counter, 1u);
-    __syncthreads();
-    const int tile = s_tile;
     const int64_t k0 = tile * TILE + (int64_t)tid * CH;
     const bool valid = k0 < T;
-    bool bad = false;
+    Flags bad = 0u;
 
     // ---- phase 1: fold this thread's block of steps
     FElem<N> acc;
@@ -1542,7 +1580,38 @@ __global__ void __launch_bounds__(NT) filter_scan_kernel(const ModelConst<N, M>*
         if constexpr (SAGG) store_plain(sagg + (k0 / CH) * (int64_t)(sizeof(SElem<N>) / 4), sacc);
         bad |= !isfinite(probe);
     }
-    if (__any_sync(kFull, bad) && lane == 0) atomicOr(ss.status, ST_NUMERIC);
+    report_flags(ss.status, bad, kFull, lane == 0);
+}
+
+// REF: how the cross-block combines take their inverses.  The fused scans
+// run first with REF_DETECT (FP32 inverses with a condition estimate, which
+// keeps the kernel's registers for its step loops) and then launch a RETRY
+// copy with REF_FP64 that returns at once unless the first run met an
+// ill-conditioned inverse (HDR_NEED); then it repeats the scan with the FP64
+// refinement, on its own tile counter and flags, and overwrites the results.
+template <int N, int M, int NT, int CH, bool FROM_Y, bool SAGG, bool SEG, bool TV, int REF = REF_FP64,
+          bool RETRY = false>
+__global__ void __launch_bounds__(NT) filter_scan_kernel(const ModelConst<N, M>* __restrict__ mcg,
+                                                         const float* __restrict__ y,
+                                                         const float* __restrict__ el, int64_t ld,
+                                                         int64_t T, float* __restrict__ fmean,
+                                                         float* __restrict__ fcov, ScanState ss,
+                                                         float* __restrict__ sagg, Segs<N, M> segs,
+                                                         TVArgs tv) {
+    if constexpr (RETRY) {
+        if (*(volatile uint32_t*)(ss.status + HDR_NEED) == 0u) return;   // the first run needed no refinement
+    }
+    __shared__ FilterSmem<N, M, NT> sm;
+    __shared__ int s_tile;
+    extern __shared__ __align__(16) char dsm[];
+    const int tid = threadIdx.x;
+    load_const<N, M>(mcg, sm.mc, tid, NT);
+    if (tid == 0) s_tile = (int)atomicAdd(ss.counter, 1u);
+    __syncthreads();
+    const int tile = s_tile;
+    if (tile >= (int)gridDim.x) return;   // a tile number past the grid (only when the counter was offset)
+    filter_scan_body<N, M, NT, CH, FROM_Y, SAGG, SEG, TV, REF>(sm, dsm, tile, y, el, ld, T, fmean, fcov, ss, sagg,
+                                                               segs, tv);
 }
 
 // ---------------------------------------------------------------- reverse scan
@@ -1602,40 +1671,38 @@ constexpr int kRevMinBlocks = Stage<N>::kOn ? 2 : 0;
 // otherwise it is folded here from the filtered moments.
 // With TV the elements come from a time-varying model's per-step transitions
 // (`tv`) instead of the constant model.
+// Shared memory of one reverse tile: the model constants (single sequence),
+// the block scan's, and the staged reads' mbarriers (two per thread).
+template <int N, int M, int NT>
+struct SmootherSmem {
+    ModelConst<N, M> mc;
+    typename BlockScan<SmootherOp<N>, NT>::Smem bsm;
+    uint64_t mbars[Stage<N>::kOn ? 2 * NT : 1];
+};
+
+// One reverse tile; the mbarriers of `sm` must be initialised (one arrival)
+// and have no transaction pending, as the body leaves them.
 template <int N, int M, int NT, int CH, bool FROM_AGG, bool SEG, bool TV>
-__global__ void __launch_bounds__(NT, kRevMinBlocks<N>) smoother_scan_kernel(const ModelConst<N, M>* __restrict__ mcg,
-                                                           const float* __restrict__ fmean,
-                                                           const float* __restrict__ fcov, int64_t T,
-                                                           float* __restrict__ smean,
-                                                           float* __restrict__ scov, ScanState ss,
-                                                           const float* __restrict__ sagg, Segs<N, M> segs,
-                                                           TVArgs tv) {
+KS_DEV void smoother_scan_body(SmootherSmem<N, M, NT>& sm, char* dsm, int tile,
+                               const float* __restrict__ fmean, const float* __restrict__ fcov, int64_t T,
+                               float* __restrict__ smean, float* __restrict__ scov, const ScanState& ss,
+                               const float* __restrict__ sagg, const Segs<N, M>& segs, const TVArgs& tv) {
     static_assert(!TV || !SEG, "time-varying models run unsegmented");
     using BS = BlockScan<SmootherOp<N>, NT>;
     using SG = Stage<N>;
     using RR = RevReader<N>;
-    __shared__ ModelConst<N, M> mc;
-    __shared__ typename BS::Smem bsm;
-    __shared__ int s_tile;
-    __shared__ uint64_t mbars[SG::kOn ? 2 * NT : 1];
-    extern __shared__ __align__(16) char dsm[];
+    const ModelConst<N, M>& mc = sm.mc;
+    typename BS::Smem& bsm = sm.bsm;
+    uint64_t* mbars = sm.mbars;
     const int tid = threadIdx.x, lane = tid & 31;
-    load_const<N, M>(mcg, mc, tid, NT);
-    if (tid == 0) s_tile = (int)atomicAdd(ss.counter, 1u);
-    if constexpr (SG::kOn) {
-        mbar_init(&mbars[2 * tid], 1);
-        mbar_init(&mbars[2 * tid + 1], 1);
-        fence_proxy_async();
-    }
-    __syncthreads();
-    const int tile = s_tile;
     const int64_t nblk = (T + CH - 1) / CH;
     const int64_t c = nblk - 1 - ((int64_t)tile * NT + tid);    // forward block index
     const bool valid = c >= 0;
     const int64_t klo = c * CH;
     const int64_t khi = valid ? ((klo + CH < T ? klo + CH : T) - 1) : -1;
     const int cnt = valid ? (int)(khi - klo + 1) : 0;
-    bool bad = false, lost = false;
+    Flags bad = 0u;
+    bool lost = false;
     constexpr uint32_t kWait = 4000000u;
     RR rd;
     if constexpr (SG::kOn) rd.init(dsm + tid * RR::TSTR, &mbars[2 * tid], khi, cnt);
@@ -1780,7 +1847,33 @@ __global__ void __launch_bounds__(NT, kRevMinBlocks<N>) smoother_scan_kernel(con
         bad |= !isfinite(probe);
     }
     if (lost) atomicOr(ss.status, ST_TIMEOUT);
-    if (__any_sync(kFull, bad) && lane == 0) atomicOr(ss.status, ST_NUMERIC);
+    report_flags(ss.status, bad, kFull, lane == 0);
+}
+
+template <int N, int M, int NT, int CH, bool FROM_AGG, bool SEG, bool TV>
+__global__ void __launch_bounds__(NT, kRevMinBlocks<N>) smoother_scan_kernel(const ModelConst<N, M>* __restrict__ mcg,
+                                                           const float* __restrict__ fmean,
+                                                           const float* __restrict__ fcov, int64_t T,
+                                                           float* __restrict__ smean,
+                                                           float* __restrict__ scov, ScanState ss,
+                                                           const float* __restrict__ sagg, Segs<N, M> segs,
+                                                           TVArgs tv) {
+    __shared__ SmootherSmem<N, M, NT> sm;
+    __shared__ int s_tile;
+    extern __shared__ __align__(16) char dsm[];
+    const int tid = threadIdx.x;
+    load_const<N, M>(mcg, sm.mc, tid, NT);
+    if (tid == 0) s_tile = (int)atomicAdd(ss.counter, 1u);
+    if constexpr (Stage<N>::kOn) {
+        mbar_init(&sm.mbars[2 * tid], 1);
+        mbar_init(&sm.mbars[2 * tid + 1], 1);
+        fence_proxy_async();
+    }
+    __syncthreads();
+    const int tile = s_tile;
+    if (tile >= (int)gridDim.x) return;   // a tile number past the grid (only when the counter was offset)
+    smoother_scan_body<N, M, NT, CH, FROM_AGG, SEG, TV>(sm, dsm, tile, fmean, fcov, T, smean, scov, ss, sagg, segs,
+                                                        tv);
 }
 
 // Dynamic shared memory of the two scans (bytes).
@@ -1815,7 +1908,7 @@ template <int N>
 __global__ void filter_combine_batch_kernel(const float* __restrict__ left, const float* __restrict__ right,
                                             float* __restrict__ out, int64_t count, uint32_t* status) {
     constexpr int SZ = 3 * N * N + 2 * N;
-    bool bad = false;
+    Flags bad = 0u;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
          i += (int64_t)gridDim.x * blockDim.x) {
         const FElem<N> r = fcombine<N>(load_packed_f<N>(left + i * SZ), load_packed_f<N>(right + i * SZ), bad);
@@ -1832,7 +1925,7 @@ __global__ void filter_combine_batch_kernel(const float* __restrict__ left, cons
                 o[2 * N * N + 2 * N + a * N + b] = r.J[sidx(a, b)];
             }
     }
-    if (bad) atomicOr(status, ST_NUMERIC);
+    if (bad & FL_BAD) atomicOr(status, ST_NUMERIC);
 }
 
 template <int N>

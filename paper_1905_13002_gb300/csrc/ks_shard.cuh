@@ -66,7 +66,7 @@ template <int N>
 struct FilterFold {
     using Elem = FElem<N>;
     static constexpr int SZ = 3 * N * N + 2 * N;
-    KS_DEV static Elem combine(const Elem& a, const Elem& b, bool& bad) { return fcombine<N>(a, b, bad); }
+    KS_DEV static Elem combine(const Elem& a, const Elem& b, Flags& bad) { return fcombine<N>(a, b, bad); }
     KS_DEV static void identity(Elem& e) { set_identity<N>(e); }
     KS_DEV static Elem load(const float* p) { return load_packed_f<N>(p); }
     KS_DEV static void store(float* p, const Elem& e) { store_packed_f<N>(p, e); }
@@ -75,7 +75,7 @@ template <int N>
 struct SmootherFold {
     using Elem = SElem<N>;
     static constexpr int SZ = 2 * N * N + N;
-    KS_DEV static Elem combine(const Elem& a, const Elem& b, bool&) { return scombine<N>(a, b); }
+    KS_DEV static Elem combine(const Elem& a, const Elem& b, Flags&) { return scombine<N>(a, b); }
     KS_DEV static void identity(Elem& e) { set_identity<N>(e); }
     KS_DEV static Elem load(const float* p) { return load_packed_s<N>(p); }
     KS_DEV static void store(float* p, const Elem& e) { store_packed_s<N>(p, e); }
@@ -85,7 +85,7 @@ struct SmootherFold {
 // Lane pairs at distance d = 1, 2, 4, ... combine (the left lane keeps the
 // result), then thread 0 folds the warps' results in warp order.
 template <class Op, int NT>
-KS_DEV typename Op::Elem block_fold(typename Op::Elem x, typename Op::Elem* wsm, bool& bad) {
+KS_DEV typename Op::Elem block_fold(typename Op::Elem x, typename Op::Elem* wsm, Flags& bad) {
     using E = typename Op::Elem;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(NT) filter_fold_kernel(const ModelConst<N, M>*
     load_const<N, M>(mcg, mc, tid, NT);
     __syncthreads();
     const int64_t k0 = ((int64_t)blockIdx.x * NT + tid) * CH;
-    bool bad = false;
+    Flags bad = 0u;
     FElem<N> acc;
     if (k0 >= T) {
         set_identity<N>(acc);
@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(NT) filter_fold_kernel(const ModelConst<N, M>*
     }
     acc = block_fold<Op, NT>(acc, wsm, bad);
     if (tid == 0) Op::store(blk + (int64_t)blockIdx.x * Op::SZ, acc);
-    if (__any_sync(kFull, bad) && (tid & 31) == 0) atomicOr(status, ST_NUMERIC);
+    report_flags(status, bad, kFull, (tid & 31) == 0);
 }
 
 // Smoothing elements of steps [0, T) from the filtered moments (Lemma 5; the
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(NT) smoother_fold_kernel(const ModelConst<N, M
     load_const<N, M>(mcg, mc, tid, NT);
     __syncthreads();
     const int64_t k0 = ((int64_t)blockIdx.x * NT + tid) * CH;
-    bool bad = false;
+    Flags bad = 0u;
     SElem<N> acc;
     set_identity<N>(acc);
 #pragma unroll 1
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(NT) smoother_fold_kernel(const ModelConst<N, M
     }
     acc = block_fold<Op, NT>(acc, wsm, bad);
     if (tid == 0) Op::store(blk + (int64_t)blockIdx.x * Op::SZ, acc);
-    if (__any_sync(kFull, bad) && (tid & 31) == 0) atomicOr(status, ST_NUMERIC);
+    report_flags(status, bad, kFull, (tid & 31) == 0);
 }
 
 // The nblk packed elements of blk folded in order into `out` (one block).
@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(NT) fold_packed_kernel(const float* __restrict
     const int tid = threadIdx.x;
     const int per = (nblk + NT - 1) / NT;
     const int lo = tid * per, hi = lo + per < nblk ? lo + per : nblk;
-    bool bad = false;
+    Flags bad = 0u;
     typename Op::Elem acc;
     Op::identity(acc);
 #pragma unroll 1
@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(NT) fold_packed_kernel(const float* __restrict
     }
     acc = block_fold<Op, NT>(acc, wsm, bad);
     if (tid == 0) Op::store(out, acc);
-    if (__any_sync(kFull, bad) && (tid & 31) == 0) atomicOr(status, ST_NUMERIC);
+    report_flags(status, bad, kFull, (tid & 31) == 0);
 }
 
 }  // namespace ks

@@ -26,7 +26,6 @@ namespace ks {
 namespace tc {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr float kRefineCond = 1.0e3f;
 
 // Unrolling of the k loop of the tensor-core products (code size against
 // cross-step scheduling).
@@ -56,9 +55,9 @@ template <int N>
 struct Pool {
     float* base;
     uint32_t mask;
-    KS_DEV float* get(bool& bad) {
+    KS_DEV float* get(Flags& bad) {
         if (mask == 0u) {
-            bad = true;
+            bad |= FL_BAD;
             return base;
         }
         const int i = __ffs(mask) - 1;
@@ -320,7 +319,7 @@ struct Rec {
     static constexpr int S = 2 * N * N + N;
 };
 template <int N>
-KS_DEV FE gload_fe(const float* g, Pool<N>& pool, bool& bad) {
+KS_DEV FE gload_fe(const float* g, Pool<N>& pool, Flags& bad) {
     FE e{pool.get(bad), pool.get(bad), pool.get(bad)};
     gload_mat<N>(e.A, g);
     gload_mat<N>(e.C, g + N * N);
@@ -351,7 +350,7 @@ KS_DEV void gstore_fstate(float* g, const float* C) {
     gstore_vec<N>(g + 3 * N * N, vrow<N>(C));
 }
 template <int N>
-KS_DEV SE gload_se(const float* g, Pool<N>& pool, bool& bad) {
+KS_DEV SE gload_se(const float* g, Pool<N>& pool, Flags& bad) {
     SE e{pool.get(bad), pool.get(bad)};
     gload_mat<N>(e.E, g);
     gload_mat<N>(e.L, g + N * N);
@@ -413,14 +412,6 @@ struct VS {
 // from the registers); `ok` is cleared on a zero or non-finite pivot.
 constexpr int GJ_U = 4;
 
-// 1 / x: the hardware approximation refined by one Newton-Raphson step
-// y <- y (2 - x y) (relative error a few ulp).
-KS_DEV float recip(float x) {
-    float y;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y * fmaf(-x, y, 2.f);
-}
-
 template <int N, bool PIVOT = true>
 KS_DEV float gj_inverse(const float* Mx, float* out, VS<N> vs, bool& ok) {
     constexpr int P = TD<N>::P;
@@ -468,7 +459,7 @@ KS_DEV float gj_inverse(const float* Mx, float* out, VS<N> vs, bool& ok) {
             }
             const float pv = rp[u];
             ok = ok && (fabsf(pv) > 1e-30f) && (fabsf(pv) < 3.0e38f);
-            const float ip = recip(pv);
+            const float ip = __frcp_rn(pv);
             // rows are kept unscaled: the true row is scale * w, and a lane
             // takes its scale 1 / pivot when it becomes the pivot row, whose
             // stored values then stay as they are; the update w -= (f / pivot)
@@ -554,14 +545,19 @@ KS_DEV void refine_inverse(const float* Mx, float* X) {
 }
 
 // X = Mx^{-1}, refined once when the condition estimate exceeds kRefineCond.
-// Returns false on a zero or non-finite pivot (then nothing is refined).
+// Returns FL_BAD on a zero or non-finite pivot (then nothing is refined),
+// FL_REFINED when the refinement step ran, else 0.
 // SPD: Mx is symmetric positive definite (no pivot search).
 template <int N, bool SPD = false>
-KS_DEV bool inverse(const float* Mx, float* X, VS<N> vs) {
+KS_DEV Flags inverse(const float* Mx, float* X, VS<N> vs) {
     bool ok = true;
     const float cond = gj_inverse<N, !SPD>(Mx, X, vs, ok);
-    if (ok && cond > kRefineCond && cond < 3.0e38f) refine_inverse<N>(Mx, X);   // warp-uniform
-    return ok;
+    if (!ok) return FL_BAD;
+    if (cond > kRefineCond && cond < 3.0e38f) {   // warp-uniform
+        refine_inverse<N>(Mx, X);
+        return FL_REFINED;
+    }
+    return 0u;
 }
 
 // ---------------------------------------------------------------- model constants
@@ -674,7 +670,7 @@ KS_DEV void first_elem(const ModelConst<N, M>& g, const FConst<N, M>& c, const F
 // PREFIX: acc is a prefix state (A = 0): only b and C are formed.
 template <int N, int M, bool PREFIX>
 KS_DEV void fcomb_meas(FE& acc, const FConst<N, M>& c, float bk, const float (&w)[M], Pool<N>& pool, VS<N> vs,
-                       bool& bad) {
+                       Flags& bad) {
     constexpr int P = TD<N>::P;
     static_assert(4 * M <= P, "thin products share one buffer");
     const int r = lane_id();
@@ -761,14 +757,14 @@ KS_DEV void fcomb_meas(FE& acc, const FConst<N, M>& c, float bk, const float (&w
 // st <- st (x) j for a prefix state st = (b, C) (A = 0): only b and C.
 //   M = I + C J_j,  X = A_j M^{-1},  b <- X (b + C eta_j) + b_j,  C <- X C A_j^T + C_j.
 template <int N>
-KS_DEV void fadvance(FE& st, const FE& j, Pool<N>& pool, VS<N> vs, bool& bad) {
+KS_DEV void fadvance(FE& st, const FE& j, Pool<N>& pool, VS<N> vs, Flags& bad) {
     const int r = lane_id();
     float* s0 = pool.get(bad);
     float* s1 = pool.get(bad);
     mmq<N, false, true>(st.C, j.J, s0);
     add_diag<N>(s0, 1.f);
     vs.v(0)[r] = vrow<N>(st.C)[r] + rdot<N>(st.C, r, vrow<N>(j.J));
-    bad |= !inverse<N>(s0, s1, vs);
+    bad |= inverse<N>(s0, s1, vs);
     mmq<N, false, false>(j.A, s1, s0);                                // X = A_j M^{-1}
     mmq<N, false, true>(s0, st.C, s1);                                // X C
     vrow<N>(st.C)[r] = rdot<N>(s0, r, vs.v(0)) + vrow<N>(j.C)[r];
@@ -783,7 +779,7 @@ KS_DEV void fadvance(FE& st, const FE& j, Pool<N>& pool, VS<N> vs, bool& bad) {
 //   C_o = X C_i A_j^T + C_j,  eta_o = A_i^T M^{-T} (eta_j - J_j b_i) + eta_i,
 //   J_o = A_i^T (M^{-T} J_j) A_i + J_i.
 template <int N>
-KS_DEV FE fcombine(const FE& i, const FE& j, Pool<N>& pool, VS<N> vs, bool& bad) {
+KS_DEV FE fcombine(const FE& i, const FE& j, Pool<N>& pool, VS<N> vs, Flags& bad) {
     const int r = lane_id();
     float* s0 = pool.get(bad);
     mmq<N, false, true>(i.C, j.J, s0);
@@ -791,7 +787,7 @@ KS_DEV FE fcombine(const FE& i, const FE& j, Pool<N>& pool, VS<N> vs, bool& bad)
     vs.v(0)[r] = vrow<N>(i.C)[r] + rdot<N>(i.C, r, vrow<N>(j.J));    // t = b_i + C_i eta_j
     vs.v(1)[r] = vrow<N>(j.J)[r] - rdot<N>(j.J, r, vrow<N>(i.C));    // v = eta_j - J_j b_i
     float* s1 = pool.get(bad);
-    bad |= !inverse<N>(s0, s1, vs);                             // M^{-1}
+    bad |= inverse<N>(s0, s1, vs);                             // M^{-1}
     float* s2 = pool.get(bad);
     float* s3 = pool.get(bad);
     mmq<N, false, false>(j.A, s1, s2);                                // X
@@ -819,7 +815,7 @@ KS_DEV FE fcombine(const FE& i, const FE& j, Pool<N>& pool, VS<N> vs, bool& bad)
 //   k < n: P- = F P F^T + Q,  E = P F^T (P-)^{-1},  g = xbar - E (F xbar + u),
 //          L = P - E F P;     k = n: (0, xbar, P).
 template <int N, int M>
-KS_DEV SE selem(float* Pm, const SConst<N, M>& c, bool last, Pool<N>& pool, VS<N> vs, bool& bad) {
+KS_DEV SE selem(float* Pm, const SConst<N, M>& c, bool last, Pool<N>& pool, VS<N> vs, Flags& bad) {
     const int r = lane_id();
     if (last) {
         float* E = pool.get(bad);
@@ -833,7 +829,7 @@ KS_DEV SE selem(float* Pm, const SConst<N, M>& c, bool last, Pool<N>& pool, VS<N
     mmq<N, false, true>(FP, c.F, Pp, c.Q);                            // P- = F P F^T + Q
     vs.v(0)[r] = rdot<N>(c.F, r, xb) + c.u[r];                        // F xbar + u
     float* Pi = pool.get(bad);
-    bad |= !inverse<N, true>(Pp, Pi, vs);                           // P- is SPD
+    bad |= inverse<N, true>(Pp, Pi, vs);                           // P- is SPD
     mmq<N, true, true>(FP, Pi, Pp);                                   // E = (F P)^T (P-)^{-1}
     mmq<N, false, false>(Pp, FP, Pi, Pm, -1.f);                       // L = P - E F P
     vrow<N>(Pi)[r] = xb[r] - rdot<N>(Pp, r, vs.v(0));                 // g
@@ -849,7 +845,7 @@ KS_DEV SE selem(float* Pm, const SConst<N, M>& c, bool last, Pool<N>& pool, VS<N
 // i.L); STATE: j is a suffix state (E_j = 0) and o.E is null; otherwise o.E is
 // a fresh buffer.  i.E and j are left for the caller to release.
 template <int N, bool STATE>
-KS_DEV SE scombine(const SE& i, const SE& j, Pool<N>& pool, bool& bad) {
+KS_DEV SE scombine(const SE& i, const SE& j, Pool<N>& pool, Flags& bad) {
     const int r = lane_id();
     float* Y = pool.get(bad);
     mmq<N, false, true>(i.E, j.L, Y);                                 // E_i L_j

@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(NW * 32) tfilter_reduce_kernel(const ModelCons
     const bool valid = w < nvalid;
     const int64_t k0 = ch * CH;
     VS<N> vs{sm.vs + w * VS<N>::FLOATS};
-    bool bad = false;
+    Flags bad = 0u;
 
     // ---- chain fold
     if (valid) {
@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(NW * 32) tfilter_reduce_kernel(const ModelCons
         }
         gstore_fe<N>(tb.spine0 + (size_t)tile * FR, run);
     }
-    if (__any_sync(kFull, bad) && lane_id() == 0) atomicOr(status, ST_NUMERIC);
+    report_flags(status, bad, kFull, lane_id() == 0);
 }
 
 // dst[t] = src[t - s] (x) src[t] for t >= s, else src[t].  src[t - s] covers
@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(NWS * 32) tspine_filter_kernel(const float* __
     }
     Pool<N> pool{sm.pool + w * kSpineBufF * TD<N>::MAT, (1u << kSpineBufF) - 1u};
     VS<N> vs{sm.vs + w * VS<N>::FLOATS};
-    bool bad = false;
+    Flags bad = 0u;
     const float* a = src + (size_t)(t - s) * FR;
     const float* b = src + (size_t)t * FR;
     if (t - s < s) {
@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(NWS * 32) tspine_filter_kernel(const float* __
         const FE r = fcombine<N>(i, j, pool, vs, bad);
         gstore_fe<N>(o, r);
     }
-    if (__any_sync(kFull, bad) && lane_id() == 0) atomicOr(status, ST_NUMERIC);
+    report_flags(status, bad, kFull, lane_id() == 0);
 }
 
 // `pre`: the spine's inclusive prefixes (record t covers tiles 0..t).
@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(NW * 32) tfilter_apply_kernel(const ModelConst
     const int64_t k0 = ch * CH;
     const float* chE = tb.chains + (size_t)ch * 2 * FR + FR;
     VS<N> vs{sm.vs + w * VS<N>::FLOATS};
-    bool bad = false;
+    Flags bad = 0u;
     Pool<N> pool{sm.pool + w * KW * MAT, (1u << KW) - 1u};
     FE st{nullptr, pool.get(bad), nullptr};
     bool has = false;
@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(NW * 32) tfilter_apply_kernel(const ModelConst
         probe += vrow<N>(st.C)[r] + st.C[r * TD<N>::P + r];
     }
     bad |= !isfinite(probe);
-    if (__any_sync(kFull, bad) && r == 0) atomicOr(status, ST_NUMERIC);
+    report_flags(status, bad, kFull, r == 0);
 }
 
 // ---------------------------------------------------------------- reverse
@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(NW * 32) tsmoother_reduce_kernel(const ModelCo
     const int64_t klo = cblk * CH;
     const int64_t khi = valid ? ((klo + CH < T ? klo + CH : T) - 1) : -1;
     VS<N> vs{sm.vs + w * VS<N>::FLOATS};
-    bool bad = false;
+    Flags bad = 0u;
 
     // ---- chain fold: a_klo (x) ... (x) a_khi, from the latest step back
     if (valid) {
@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(NW * 32) tsmoother_reduce_kernel(const ModelCo
         }
         gstore_se<N>(tb.spine0 + (size_t)tile * SR, run);
     }
-    if (__any_sync(kFull, bad) && lane_id() == 0) atomicOr(status, ST_NUMERIC);
+    report_flags(status, bad, kFull, lane_id() == 0);
 }
 
 // Scan order (tile 0 = latest time): dst[u] = src[u] (x) src[u - s] in time
@@ -322,7 +322,7 @@ __global__ void __launch_bounds__(NWS * 32) tspine_smoother_kernel(const float* 
         return;
     }
     Pool<N> pool{sm.pool + w * kSpineBufS * TD<N>::MAT, (1u << kSpineBufS) - 1u};
-    bool bad = false;
+    Flags bad = 0u;
     const float* later = src + (size_t)(u - s) * SR;
     const SE i = gload_se<N>(src + (size_t)u * SR, pool, bad);
     if (u - s < s) {
@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(NWS * 32) tspine_smoother_kernel(const float* 
         const SE r = scombine<N, false>(i, j, pool, bad);
         gstore_se<N>(o, r);
     }
-    if (__any_sync(kFull, bad) && lane_id() == 0) atomicOr(status, ST_NUMERIC);
+    report_flags(status, bad, kFull, lane_id() == 0);
 }
 
 // `pre`: the spine's inclusive suffixes (record u covers scan tiles 0..u).
@@ -356,7 +356,7 @@ __global__ void __launch_bounds__(NW * 32) tsmoother_apply_kernel(int64_t T, flo
     const int64_t klo = cblk * CH;
     const int64_t khi = (klo + CH < T ? klo + CH : T) - 1;
     const float* chE = tb.chains + (size_t)u * 2 * SR + SR;
-    bool bad = false;
+    Flags bad = 0u;
     Pool<N> pool{sm.pool + w * KW * MAT, (1u << KW) - 1u};
     float* st = nullptr;                                  // L (g) of the running suffix
     if (tile != 0) {
@@ -391,7 +391,7 @@ __global__ void __launch_bounds__(NW * 32) tsmoother_apply_kernel(int64_t T, flo
         probe += vrow<N>(st)[r] + st[r * TD<N>::P + r];
     }
     bad |= !isfinite(probe);
-    if (__any_sync(kFull, bad) && r == 0) atomicOr(status, ST_NUMERIC);
+    report_flags(status, bad, kFull, r == 0);
 }
 
 }  // namespace tc

@@ -55,8 +55,15 @@ class Request:
 
 def request_bytes(nx: int, ny: int, T: int) -> int:
     """Device bytes a request holds while admitted: measurements, filtered and
-    smoothed moments (FP32), and its share of the segmented workspace."""
-    return 4 * T * ny + 2 * 4 * T * (nx + nx * nx) + workspace_bytes_batch(nx, ny, 1, T)
+    smoothed moments (FP32), its share of the segmented workspace, and its
+    model in the launch's gathered batch (F, Q, H, R in FP32, m0 and P0 in
+    FP64, one int64 offset and one int64 index).
+
+    The budget this counts against is logical: torch's caching allocator may
+    keep freed blocks reserved beyond it, and a launch's handful of small
+    tensors are rounded up to the allocator's block size."""
+    model = 4 * (2 * nx * nx + nx * ny + ny * ny) + 8 * (nx + nx * nx) + 16
+    return 4 * T * ny + 2 * 4 * T * (nx + nx * nx) + workspace_bytes_batch(nx, ny, 1, T) + model
 
 
 @dataclass

@@ -1,11 +1,29 @@
 """Error measures used by the GPU parity tests.
 
-Means are compared normwise per step, relative to the larger of the mean's
-magnitude and the largest posterior standard deviation at that step
-(elementwise relative error is meaningless for components near zero, and the
-positions of a Wiener-velocity model grow like T^1.5).  Covariances are
-compared per step relative to their largest entry.  The reported figure is
-the maximum over steps.
+Two measures for every mean, one for every covariance, each taken per step
+and reported as the maximum over steps:
+
+* ``mean_err`` -- normwise relative: ``|dm_k|_inf / max(|m_k|_inf,
+  max_i sqrt(P_k,ii))``.  Elementwise relative error is meaningless for
+  components near zero, and the positions of a Wiener-velocity model grow
+  like T^1.5, hence the per-step scale.
+* ``sd_err`` -- in posterior standard deviations: ``|dm_k|_2 /
+  sqrt(lambda_min(P_k))``, an upper bound on the Mahalanobis distance of the
+  GPU mean from the exact one under the exact posterior N(m_k, P_k).
+* ``cov_err`` -- ``|dP_k|_max / |P_k|_max``.
+
+An FP32 output cannot sit closer to the exact FP64 mean than half an FP32
+ulp of each component.  In posterior-sd units that floor is
+``ulp_sd(k) = |ulp32(m_k)|_2 / sqrt(lambda_min(P_k))``; at T = 2^20 of the
+Wiener-velocity workload positions reach 2e7 (ulp 2) against a posterior
+sd of 0.32, so the exact mean rounded to FP32 is already 3-4 sd away at
+the last steps.  The sd bound therefore reads
+
+    sd_err(k) <= SD_TOL + ULP_TOL * ulp_sd(k)        for every k,
+
+i.e. within SD_TOL posterior sd where FP32 can resolve that, and within
+ULP_TOL ulps of the value where it cannot.  ``sd_excess`` is the largest
+ratio of the left side to the right side (<= 1 passes).
 """
 import numpy as np
 
@@ -21,6 +39,27 @@ TOL = 1e-4
 # ~1e-5 at most, so the same 1e-4 applies.
 TOL_NX32 = 1e-4
 
+# Posterior-sd bound.  Each FP32 step of the filter and smoother rounds the
+# mean at about eps32 |m|, and the error-propagation maps of the filter,
+# (I - K H) F, and of the smoother, E, contract it at a rate rho < 1 per
+# step, so the steady error is about eps32 |m| / (1 - rho): a fixed number
+# of ulps of the value, 1 / (1 - rho) ~ 10 for the tracking model.  Where
+# |m| is a few hundred sd or less that is below 0.002 sd (measured: 0.0018
+# sd at T = 1024; 1e-5 sd at nx = 8 and 32), so SD_TOL = 0.01 sd.  Where FP32
+# cannot resolve a posterior sd (T = 2^20: one ulp of 2e7 is 6-8 sd) the
+# error is a number of ulps of the value: at most 16 measured (T = 2^20,
+# smoothed means), so ULP_TOL = 24.
+SD_TOL = 0.01
+ULP_TOL = 24.0
+
+# (test id, measure dict) of every check, for the end-of-run parity summary.
+RECORD = []
+
+
+def _lam_min(P):
+    P = np.asarray(P, dtype=np.float64)
+    return np.maximum(np.linalg.eigvalsh(P)[..., 0], np.finfo(np.float64).tiny)
+
 
 def mean_err(got, ref, Pref):
     got = np.asarray(got, dtype=np.float64)
@@ -30,15 +69,82 @@ def mean_err(got, ref, Pref):
     return float((np.abs(got - ref).max(-1) / scale).max())
 
 
+def sd_terms(got, ref, Pref):
+    """Per-step (error in posterior sd, one-ulp floor in posterior sd)."""
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    s = np.sqrt(_lam_min(Pref))
+    err = np.linalg.norm(got - ref, axis=-1) / s
+    ulp = np.spacing(np.abs(ref).astype(np.float32)).astype(np.float64)
+    return err, np.linalg.norm(ulp, axis=-1) / s
+
+
+def sd_err(got, ref, Pref):
+    return float(sd_terms(got, ref, Pref)[0].max())
+
+
+def sd_excess(got, ref, Pref, sd_tol=SD_TOL, ulp_tol=ULP_TOL):
+    err, floor = sd_terms(got, ref, Pref)
+    return float((err / (sd_tol + ulp_tol * floor)).max())
+
+
 def cov_err(got, ref):
     got = np.asarray(got, dtype=np.float64)
     ref = np.asarray(ref, dtype=np.float64)
     return float((np.abs(got - ref).max((-2, -1)) / np.abs(ref).max((-2, -1))).max())
 
 
+def _np(x):
+    return np.asarray(x.detach().cpu().numpy() if hasattr(x, "detach") else x)
+
+
 def errors(gpu, ref):
-    """gpu, ref: (fmean, fcov, smean, scov) tuples -> dict of max errors."""
-    fm, fP, sm, sP = (np.asarray(x.detach().cpu().numpy() if hasattr(x, "detach") else x) for x in gpu)
+    """gpu, ref: (fmean, fcov, smean, scov) tuples -> dict of max relative
+    errors (keys fmean, fcov, smean, scov), to be compared with TOL."""
+    fm, fP, sm, sP = (_np(x) for x in gpu)
     rfm, rfP, rsm, rsP = ref
     return {"fmean": mean_err(fm, rfm, rfP), "fcov": cov_err(fP, rfP),
             "smean": mean_err(sm, rsm, rsP), "scov": cov_err(sP, rsP)}
+
+
+def sd_errors(gpu, ref):
+    """Posterior-sd errors of both means: max sd_err and max sd_excess."""
+    fm, _, sm, _ = (_np(x) for x in gpu)
+    rfm, rfP, rsm, rsP = ref
+    return {"fmean_sd": sd_err(fm, rfm, rfP), "smean_sd": sd_err(sm, rsm, rsP),
+            "fmean_sdx": sd_excess(fm, rfm, rfP), "smean_sdx": sd_excess(sm, rsm, rsP)}
+
+
+def _record(e):
+    import os
+    RECORD.append((os.environ.get("PYTEST_CURRENT_TEST", "?").split(" ")[0], dict(e)))
+
+
+def check_mean(got, ref, Pref, tol=TOL):
+    """Assert both mean measures; returns (relative, sd, sd_excess)."""
+    got = _np(got)
+    rel = mean_err(got, ref, Pref)
+    sd = sd_err(got, ref, Pref)
+    sdx = sd_excess(got, ref, Pref)
+    _record({"mean": rel, "mean_sd": sd, "mean_sdx": sdx})
+    assert rel < tol, ("relative mean error", rel)
+    assert sdx <= 1.0, ("posterior-sd mean error", sd, "excess", sdx)
+    return rel, sd, sdx
+
+
+def check_cov(got, ref, tol=TOL):
+    e = cov_err(_np(got), ref)
+    assert e < tol, ("covariance error", e)
+    return e
+
+
+def check_all(gpu, ref, tol=TOL):
+    """Assert every measure on (fmean, fcov, smean, scov) against the oracle's
+    tuple; returns the merged dict."""
+    e = errors(gpu, ref)
+    e.update(sd_errors(gpu, ref))
+    _record(e)
+    rel = max(e["fmean"], e["fcov"], e["smean"], e["scov"])
+    assert rel < tol, e
+    assert e["fmean_sdx"] <= 1.0 and e["smean_sdx"] <= 1.0, e
+    return e

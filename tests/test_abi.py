@@ -120,3 +120,30 @@ def test_hmm_host_queries_and_argument_errors(ks):
     assert L.ks_hmm_smooth(ctypes.byref(h32), 4, 10, 256, 1 << 30, 16, None, None, None) == ks.KS_EINVAL
     hnull = ks._KsHmm(8, 0, 0, 16)
     assert L.ks_hmm_smooth(ctypes.byref(hnull), 16, 10, 256, 1 << 20, 16, None, None, None) == ks.KS_EINVAL
+
+
+def test_mixed_batch_host_queries(ks):
+    """ks_workspace_bytes_batched reads only the groups' sizes: one region per
+    state size after the header, 0 for a malformed group list."""
+    L = ks.lib()
+
+    def groups(*sizes):
+        arr = (ks._KsBatchGroup * len(sizes))()
+        for i, (nx, ny, B, T) in enumerate(sizes):
+            arr[i].models.nx, arr[i].models.ny, arr[i].models.B = nx, ny, B
+            arr[i].total_T = T
+        return arr
+
+    one = L.ks_workspace_bytes_batched(1, groups((4, 2, 10, 5000)))
+    three = L.ks_workspace_bytes_batched(3, groups((6, 3, 5, 3000), (4, 2, 10, 5000), (2, 1, 7, 900)))
+    assert 0 < one < three
+    assert one >= L.ks_workspace_bytes_batch(4, 2, 10, 5000)
+    assert L.ks_workspace_bytes_batched(0, groups((4, 2, 10, 5000))) == 0
+    assert L.ks_workspace_bytes_batched(2, groups((4, 2, 10, 5000), (4, 2, 3, 300))) == 0   # size twice
+    assert L.ks_workspace_bytes_batched(1, groups((8, 4, 10, 5000))) == 0                  # not a register size
+    assert L.ks_workspace_bytes_batched(1, groups((4, 2, 10, 5))) == 0                     # T < B
+    # argument errors are returned before any CUDA call
+    assert L.ks_smooth_batched(1, groups((4, 2, 10, 5000)), None, 0, None) == ks.KS_EINVAL
+    assert L.ks_smooth_batched(1, groups((8, 4, 10, 5000)), None, 0, None) == ks.KS_EUNSUPPORTED
+    assert L.ks_workspace_set_waits(None, 0, 0, 0, None) == ks.KS_EINVAL
+    assert L.ks_refinements(None, None, None) == ks.KS_EINVAL

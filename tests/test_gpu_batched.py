@@ -41,7 +41,8 @@ def run_and_check(ks, seqs):
     o = 0
     for s in seqs:
         ref = oracle.kf_rts(s.model, s.y)
-        e = parity.errors([x[o:o + s.T] for x in out], ref)
+        e = parity.check_all([x[o:o + s.T] for x in out], ref)
+        e = {k: e[k] for k in ("fmean", "fcov", "smean", "scov")}
         worst = max(worst, max(e.values()))
         o += s.T
     assert worst < parity.TOL, worst
@@ -125,3 +126,75 @@ def test_random_stable_nx32_batch(ks):
         _, y = workloads.simulate(m, T, rng)
         seqs.append(workloads.Sequence(m, y))
     run_and_check(ks, seqs)
+
+
+def run_mixed_and_check(ks, seqs):
+    """All sequences through ks_smooth_batched (one group per state size, one
+    launch per scan); every sequence against its own oracle run."""
+    groups, members = [], []
+    for nx in (6, 4, 2):
+        grp = [s for s in seqs if s.model.nx == nx]
+        if not grp:
+            continue
+        batch = ks.ModelBatch.create([s.model for s in grp], [s.T for s in grp])
+        y = torch.as_tensor(np.concatenate([s.y for s in grp]), dtype=torch.float32, device="cuda")
+        groups.append((batch, y))
+        members.append(grp)
+    sizes = [(b.nx, b.ny, b.B, int(y.shape[0])) for b, y in groups]
+    ws = torch.empty(ks.workspace_bytes_batched(sizes), dtype=torch.uint8, device="cuda")
+    assert ks.lib().ks_workspace_init(ks._p(ws), ws.numel(), ks._stream(None)) == 0
+    outs = ks.smooth_batched(groups, ws)
+    assert ks.status(ws) == ks.KS_OK
+    worst = {}
+    for grp, out in zip(members, outs):
+        out = [t.cpu().numpy() for t in out]
+        w, o = 0.0, 0
+        for s in grp:
+            e = parity.check_all([x[o:o + s.T] for x in out], oracle.kf_rts(s.model, s.y))
+            w = max(w, e["fmean"], e["fcov"], e["smean"], e["scov"])
+            o += s.T
+        worst[grp[0].model.nx] = w
+    return worst
+
+
+def test_batched_workload_full_size(ks):
+    """The whole batched workload in one ks_smooth_batched call (one launch
+    per scan over all three state sizes): 4096 sequences, log-uniform lengths
+    in [256, 16384] (15.9 M steps), nx in {2, 4, 6}, every sequence checked
+    against its own FP64 oracle run."""
+    seqs = workloads.config_batched()
+    assert len(seqs) == 4096
+    worst = run_mixed_and_check(ks, seqs)
+    print("batched workload (one launch per scan), worst relative error per nx", worst)
+
+
+# Mixed-size batches: the three sizes with the edge lengths, two sizes only,
+# one size only, and totals in each steps-per-thread band.
+@pytest.mark.parametrize("dims,extra", [((1, 2, 3), 0), ((1, 3), 0), ((2,), 0), ((1, 2, 3), 60),
+                                        ((2, 3), 250), ((1, 2, 3), 400)])
+def test_mixed_state_sizes(ks, dims, extra):
+    rng = np.random.default_rng(70 + extra + len(dims))
+    seqs = []
+    for dim in dims:
+        lengths = np.concatenate([EDGE, workloads.batch_lengths(extra, rng, 256, 16384)]) if extra else EDGE
+        seqs += make_batch(dim, lengths, 80 + dim + extra)
+    rng.shuffle(seqs)
+    worst = run_mixed_and_check(ks, seqs)
+    print("mixed", dims, sum(s.T for s in seqs), worst)
+
+
+def test_mixed_batch_rejects_unsupported_groups(ks):
+    seqs = make_batch(2, [100, 50], 5)
+    batch = ks.ModelBatch.create([s.model for s in seqs], [s.T for s in seqs])
+    y = torch.as_tensor(np.concatenate([s.y for s in seqs]), dtype=torch.float32, device="cuda")
+    ws = torch.zeros(1 << 20, dtype=torch.uint8, device="cuda")
+    with pytest.raises(ks.KsError) as ei:            # two groups of one size
+        ks.smooth_batched([(batch, y), (batch, y)], ws)
+    assert ei.value.code == ks.KS_EINVAL
+    rng = np.random.default_rng(6)
+    m8 = workloads.random_stable(8, 4, rng)
+    b8 = ks.ModelBatch.create([m8], [10])
+    y8 = torch.zeros((10, 4), dtype=torch.float32, device="cuda")
+    with pytest.raises(ks.KsError) as ei:            # nx = 8 runs on the lane-group kernels
+        ks.smooth_batched([(b8, y8)], ws)
+    assert ei.value.code == ks.KS_EUNSUPPORTED

@@ -62,6 +62,8 @@ def test_mix_equals_alone_and_oracle(ks, setup):
         _, _, rsm, rsc = oracle.kf_rts(m, ys[r.nx][r.model][:r.T].astype(np.float64))
         worst_alone = max(worst_alone, parity.mean_err(sm, am, rsc), parity.cov_err(sc, ac))
         worst_oracle = max(worst_oracle, parity.mean_err(sm, rsm, rsc), parity.cov_err(sc, rsc))
+        parity.check_mean(sm, rsm, rsc)
+        assert parity.sd_excess(sm, am, rsc) <= 1.0
     print("mix vs alone", worst_alone, "mix vs oracle", worst_oracle)
     assert worst_alone < parity.TOL
     assert worst_oracle < parity.TOL
@@ -78,3 +80,30 @@ def test_tight_budget_queues_but_serves_everything(ks, setup):
     assert srv.stats.max_reserved <= budget
     assert srv.stats.launches >= 10
     assert all(r.done >= r.launched >= r.admitted >= r.arrival for r in done)
+
+
+def test_long_nx8_request_in_the_mix(ks, setup):
+    """A served nx = 8 request of 150,000 steps (the serving workload draws T
+    up to 2^18) among short requests of both sizes: each result equals its
+    result alone and the FP64 oracle."""
+    serving, models, ys, sets = setup
+    long_T = 150000
+    m8 = models[8][1]
+    rng = np.random.default_rng(905)
+    _, ylong = workloads.simulate(m8, long_T, rng)
+    reqs = make_requests(serving, models, ys, 12, seed=906)
+    reqs.append(serving.Request(rid=len(reqs), nx=8, ny=4, T=long_T, model=1,
+                                y=torch.from_numpy(np.ascontiguousarray(ylong, dtype=np.float32)).pin_memory(),
+                                arrival=0.0))
+    srv = serving.Server(serving.GpuLauncher(sets, streams=2), budget_bytes=8 << 30, streams=2)
+    done = srv.run(reqs, keep_results=True)
+    assert len(done) == len(reqs)
+    for r in done:
+        sm, sc = (t.cpu().numpy() for t in r.result)
+        m = models[r.nx][r.model]
+        y = ylong if r.T == long_T and r.nx == 8 else ys[r.nx][r.model][:r.T]
+        am, ac = alone(ks, models, r)
+        _, _, rsm, rsc = oracle.kf_rts(m, np.asarray(y, dtype=np.float64))
+        parity.check_mean(sm, rsm, rsc)
+        parity.check_cov(sc, rsc)
+        assert parity.sd_excess(sm, am, rsc) <= 1.0

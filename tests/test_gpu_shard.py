@@ -91,6 +91,5 @@ def test_emulated_ranks_equal_the_oracle(ks, dim, T, world):
     saggs = [p.smoother_aggregate() for p in parts]
     outs = [p.reverse(saggs) for p in parts]
     got = [torch.cat([o[i] for o in outs]).cpu().numpy() for i in range(4)]
-    e = parity.errors(got, oracle.kf_rts(m, y))
+    e = parity.check_all(got, oracle.kf_rts(m, y))
     print(f"nx={n} T={T} world={world} errors", e)
-    assert max(e.values()) < parity.TOL, e
