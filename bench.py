@@ -312,6 +312,26 @@ def main():
     run_single(args, rank, world, local, mode=args.workload)
 
 
+def block_length(ks, nx: int, T: int) -> dict:
+    """Steps per thread the library uses for this call and where the rule
+    came from (the tuner's cache for this device, or the built-in table)."""
+    from paper_1905_13002_gb300 import tune
+    src = os.path.relpath(tune.APPLIED, ROOT) if tune.APPLIED else "built-in table"
+    return {"steps_per_thread": ks.chunk_steps(nx, T) if nx <= 6 else None, "rules": src}
+
+
+def launches_per_call(nx: int, T: int) -> int:
+    """Kernels one ks_smooth call launches: nx <= 6: preparation, forward scan,
+    its refinement retry (returns at once unless needed), reverse scan;
+    nx = 32: preparation, then per scan a reduce, one spine launch per
+    Kogge-Stone level over the tiles of 3 chains x 72 steps, and an apply."""
+    if nx <= 6:
+        return 4
+    tiles = -(-T // (3 * 72))
+    levels = (tiles - 1).bit_length() if tiles > 1 else 0
+    return 1 + 2 * (2 + levels)
+
+
 def run_single(args, rank, world, local, mode):
     import torch
     import torch.distributed as dist
@@ -370,16 +390,38 @@ def run_single(args, rank, world, local, mode):
     if ks.status(ws) != ks.KS_OK:
         raise SystemExit("device status not OK after warm-up")
 
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    # one call captured in a CUDA graph (as a serving loop would run it),
+    # timed with events around each replay
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step()
+    graph.replay()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     clocks = ClockSampler(local)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
     time.sleep(0.3)
+    tot = []
     for i in range(args.steps):
         flush.zero_()                       # L2 flushed between timed steps, outside the events
-        step(evs[i])
+        ev[0].record()
+        graph.replay()
+        ev[3].record()
+        ev[3].synchronize()
+        tot.append(ev[0].elapsed_time(ev[3]))
+    # per-kernel times: the same call launched directly, with events between
+    # the preparation, the forward scan (and its retry) and the reverse scan
+    kel, kf, ksm = [], [], []
+    for i in range(args.steps):
+        flush.zero_()
+        step(ev)
+        ev[3].synchronize()
+        kel.append(ev[0].elapsed_time(ev[1]))
+        kf.append(ev[1].elapsed_time(ev[2]))
+        ksm.append(ev[2].elapsed_time(ev[3]))
     torch.cuda.synchronize()
     time.sleep(0.3)
     clk = clocks.stop()
@@ -388,12 +430,7 @@ def run_single(args, rank, world, local, mode):
     st = ks.status(ws)
     if st != ks.KS_OK:
         raise SystemExit(f"device status {st} after the timed steps")
-
-    tot = [e[0].elapsed_time(e[3]) for e in evs]
     lat = {"p50_ms": float(np.percentile(tot, 50)), "p99_ms": float(np.percentile(tot, 99))}
-    kel = [e[0].elapsed_time(e[1]) for e in evs]
-    kf = [e[1].elapsed_time(e[2]) for e in evs]
-    ksm = [e[2].elapsed_time(e[3]) for e in evs]
     ms = statistics.mean(tot)
     if world > 1:
         t = torch.tensor([ms], device=dev)
@@ -484,9 +521,11 @@ def run_single(args, rank, world, local, mode):
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": wl, "T": T,
                       "sequences_per_gpu": 1, "parallelism": f"replicas{world}",
+                      "launch": "one ks_smooth call replayed as a CUDA graph (kernel times: direct calls)",
+                      "block_length": block_length(ks, nx, T),
                       "l2": "flushed between timed steps (256 MiB memset outside the events)"},
            "clocks": {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
-           "gpu_launches": 3 * args.steps, "latency": lat, "e2e": e2e, "roofline": roof}
+           "gpu_launches": 2 * launches_per_call(nx, T) * args.steps, "latency": lat, "e2e": e2e, "roofline": roof}
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_oracle_rate(seq, args.cpu_seconds)
     if batched is not None:
@@ -811,12 +850,13 @@ def measure_batched(args, rank, world, dev, full: bool) -> dict:
     res = {"value": total * world / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
            "latency": {"p50_ms": float(np.percentile(times, 50)), "p99_ms": float(np.percentile(times, 99))},
            "clocks": {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
-           "gpu_launches": 3 * args.steps,
+           "gpu_launches": 4 * args.steps,
            "config": {"workload": "batched: log-uniform T in [256,16384], nx in {2,4,6} Wiener-velocity, "
                                   "q~U[0.5,2], R=rI r~U[0.1,1]", "sequences": len(seqs), "total_steps": total,
                       "groups": [{"nx": g["nx"], "B": g["B"], "T": g["T"]} for g in groups],
-                      "launch": "ks_smooth_batched: prep + one forward + one reverse launch over all sizes "
-                                "(CUDA graph)",
+                      "launch": "ks_smooth_batched: prep + forward + refinement retry + reverse launches over "
+                                "all sizes (CUDA graph)",
+                      "block_length": block_length(ks, 0, total),
                       "l2": "flushed between timed steps (256 MiB memset outside the events)"}}
 
     # the plain single-sequence scan, one ks_smooth call per sequence, same GPU
@@ -1027,7 +1067,7 @@ def run_serving(args, rank, world, local):
                                "first arrival)); ms_per_step = its p50 latency",
                       "latency": "completion (CUDA event after the request's launch) - scheduled arrival"},
            "clocks": {k: clk_s[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
-           "gpu_launches": 3 * launches,
+           "gpu_launches": 4 * launches,   # a lower bound: nx = 8 calls also run spine launches
            "latency": {"p50_ms": top["p50_ms"], "p99_ms": top["p99_ms"]},
            "rates": per_rate}
     if world == 1 and not args.no_cpu_baseline:

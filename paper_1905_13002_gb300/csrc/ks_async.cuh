@@ -18,6 +18,15 @@ KS_DEV uint32_t smem_addr(const void* p) { return static_cast<uint32_t>(__cvta_g
 // async-proxy (TMA) accesses to the same memory.
 KS_DEV void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialization may start while the kernel before it in the stream drains;
+// pdl_wait() blocks until that kernel has completed and its memory writes are
+// visible (a no-op for a kernel launched without the attribute), and
+// pdl_trigger() lets the next such kernel be scheduled once every block of
+// this grid has triggered or exited.
+KS_DEV void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+KS_DEV void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Global <- shared bulk copy (bytes % 16 == 0, both addresses 16-byte aligned).
 KS_DEV void bulk_store(void* gdst, const void* ssrc, uint32_t bytes) {
     asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;"

@@ -119,7 +119,7 @@ struct GImpl {
             ka<<<L.ntf, NW * 32, smem, st>>>(mconst(ws, L), y, L.T, fm, fc, fb, src, stat, segs);
             if ((rc = launch_status())) return rc;
         }
-        if (ev && ev[2] && cudaEventRecord(static_cast<cudaEvent_t>(ev[2]), st) != cudaSuccess) return KS_ECUDA;
+        if (ev && ev[2] && record_event(ev[2], st) != cudaSuccess) return KS_ECUDA;
         if (smoother) {
             auto kr = grp::gsmoother_reduce_kernel<N, M, NW, CH, SEG, TV>;
             auto ks = grp::gspine_smoother_kernel<N, SW>;
@@ -196,7 +196,7 @@ struct GImpl {
         auto* tvc = reinterpret_cast<ModelConst<N, M>*>(static_cast<char*>(ws) + tv_offset(T));
         const TVArgs tv{m->F, m->u, m->Q, m->H, m->d, m->R, m->m0, m->P0};
         int rc;
-        if (ev && ev[0] && cudaEventRecord(static_cast<cudaEvent_t>(ev[0]), st) != cudaSuccess) return KS_ECUDA;
+        if (ev && ev[0] && record_event(ev[0], st) != cudaSuccess) return KS_ECUDA;
         {
             const int smem = (int)prep_smem();
             auto k = prep_kernel<N, M>;
@@ -212,11 +212,11 @@ struct GImpl {
             tv_const_kernel<N, M><<<blocks, 128, 0, st>>>(tv, T, tvc, status(ws));
             if ((rc = launch_status())) return rc;
         }
-        if (ev && ev[1] && cudaEventRecord(static_cast<cudaEvent_t>(ev[1]), st) != cudaSuccess) return KS_ECUDA;
+        if (ev && ev[1] && record_event(ev[1], st) != cudaSuccess) return KS_ECUDA;
         if ((rc = scans<false, true>(ws, L, y, fm, fc, sm, sc, Segs<N, M>{tvc, nullptr, 1}, st, ev, true,
                                      !filter_only)))
             return rc;
-        if (ev && ev[3] && cudaEventRecord(static_cast<cudaEvent_t>(ev[3]), st) != cudaSuccess) return KS_ECUDA;
+        if (ev && ev[3] && record_event(ev[3], st) != cudaSuccess) return KS_ECUDA;
         return KS_OK;
     }
 
@@ -233,13 +233,13 @@ struct GImpl {
             fm = reinterpret_cast<float*>(static_cast<char*>(ws) + L.off_fmean);
             fc = reinterpret_cast<float*>(static_cast<char*>(ws) + L.off_fcov);
         }
-        if (ev && ev[0] && cudaEventRecord(static_cast<cudaEvent_t>(ev[0]), st) != cudaSuccess) return KS_ECUDA;
+        if (ev && ev[0] && record_event(ev[0], st) != cudaSuccess) return KS_ECUDA;
         if ((rc = prep(m->F, m->u, m->Q, m->H, m->d, m->R, m->m0, m->P0, y, 1, nullptr, ws, L, st))) return rc;
-        if (ev && ev[1] && cudaEventRecord(static_cast<cudaEvent_t>(ev[1]), st) != cudaSuccess) return KS_ECUDA;
+        if (ev && ev[1] && record_event(ev[1], st) != cudaSuccess) return KS_ECUDA;
         if ((rc = scans<false>(ws, L, y, fm, fc, sm, sc, Segs<N, M>{nullptr, nullptr, 1}, st, ev, true,
                                !filter_only)))
             return rc;
-        if (ev && ev[3] && cudaEventRecord(static_cast<cudaEvent_t>(ev[3]), st) != cudaSuccess) return KS_ECUDA;
+        if (ev && ev[3] && record_event(ev[3], st) != cudaSuccess) return KS_ECUDA;
         return KS_OK;
     }
 

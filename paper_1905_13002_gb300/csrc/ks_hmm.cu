@@ -72,7 +72,7 @@ struct HImpl {
         const Const<K>* cg = reinterpret_cast<const Const<K>*>(b + L.off_const);
         float* sblk = reinterpret_cast<float*>(b + L.off_sblk);
         auto rec = [&](int i) {
-            return (ev && ev[i] && cudaEventRecord(static_cast<cudaEvent_t>(ev[i]), st) != cudaSuccess) ? KS_ECUDA
+            return (ev && ev[i] && record_event(ev[i], st) != cudaSuccess) ? KS_ECUDA
                                                                                                         : KS_OK;
         };
         int rc;
@@ -169,7 +169,7 @@ struct WImpl {
         bf.sspine0 = reinterpret_cast<float*>(b + L.off_ssp0);
         bf.sspine1 = reinterpret_cast<float*>(b + L.off_ssp1);
         auto rec = [&](int i) {
-            return (ev && ev[i] && cudaEventRecord(static_cast<cudaEvent_t>(ev[i]), st) != cudaSuccess) ? KS_ECUDA
+            return (ev && ev[i] && record_event(ev[i], st) != cudaSuccess) ? KS_ECUDA
                                                                                                         : KS_OK;
         };
         const int sgrid = (L.ntiles + sgrid_tiles - 1) / sgrid_tiles;

@@ -64,6 +64,25 @@ inline int launch_status() {
     return cudaGetLastError() == cudaSuccess ? KS_OK : KS_ECUDA;
 }
 
+// Launch with programmatic stream serialization: the kernel may be scheduled
+// while the previous kernel of the stream drains (it calls pdl_wait() before
+// reading that kernel's results), which hides the launch gap between the
+// preparation and the scans.
+template <class... KArgs, class... Args>
+inline int launch_pdl(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...) == cudaSuccess ? KS_OK : KS_ECUDA;
+}
+
 // FCH_ = steps per thread of the block scans (one tile = 128 * FCH_ steps).
 template <int N, int M, int FCH_ = 32>
 struct Impl {
@@ -193,13 +212,14 @@ struct Impl {
         auto kr = filter_scan_kernel<N, M, FNT, FCH, true, true, SEG, false, REF_FP64, true>;
         static const bool ok = allow_smem(k, smem) && allow_smem(kr, smem);
         if (!ok) return KS_ECUDA;
-        k<<<L.ntf, FNT, smem, st>>>(mconst(ws, L), y, nullptr, L.ld, L.T, fm, fc, fstate(ws, L), sblk(ws, L),
-                                    segs, TVArgs{});
-        int rc = launch_status();
+        const ModelConst<N, M>* mc = mconst(ws, L);
+        const float* none = nullptr;
+        float* sb = sblk(ws, L);
+        int rc = launch_pdl(k, L.ntf, FNT, smem, st, mc, y, none, L.ld, L.T, fm, fc, fstate(ws, L), sb, segs,
+                            TVArgs{});
         if (rc) return rc;
-        kr<<<L.ntf, FNT, smem, st>>>(mconst(ws, L), y, nullptr, L.ld, L.T, fm, fc, fstate_retry(ws, L),
-                                     sblk(ws, L), segs, TVArgs{});
-        return launch_status();
+        return launch_pdl(kr, L.ntf, FNT, smem, st, mc, y, none, L.ld, L.T, fm, fc, fstate_retry(ws, L), sb, segs,
+                          TVArgs{});
     }
 
     // Time-varying model: elements from the TVElem records `el`, smoothing
@@ -211,13 +231,14 @@ struct Impl {
         auto kr = filter_scan_kernel<N, M, FNT, FCH, false, true, false, true, REF_FP64, true>;
         static const bool ok = allow_smem(k, smem) && allow_smem(kr, smem);
         if (!ok) return KS_ECUDA;
-        k<<<L.ntf, FNT, smem, st>>>(mconst(ws, L), nullptr, el, L.ld, L.T, fm, fc, fstate(ws, L), sblk(ws, L),
-                                    no_segs(), tv);
-        int rc = launch_status();
+        const ModelConst<N, M>* mc = mconst(ws, L);
+        const float* none = nullptr;
+        float* sb = sblk(ws, L);
+        int rc = launch_pdl(k, L.ntf, FNT, smem, st, mc, none, el, L.ld, L.T, fm, fc, fstate(ws, L), sb, no_segs(),
+                            tv);
         if (rc) return rc;
-        kr<<<L.ntf, FNT, smem, st>>>(mconst(ws, L), nullptr, el, L.ld, L.T, fm, fc, fstate_retry(ws, L),
-                                     sblk(ws, L), no_segs(), tv);
-        return launch_status();
+        return launch_pdl(kr, L.ntf, FNT, smem, st, mc, none, el, L.ld, L.T, fm, fc, fstate_retry(ws, L), sb,
+                          no_segs(), tv);
     }
 
     static int launch_filter_soa(void* ws, const Layout& L, const float* el, float* fm, float* fc,
@@ -238,9 +259,9 @@ struct Impl {
         auto k = smoother_scan_kernel<N, M, SNT, SCH, FROM_AGG, SEG, TV>;
         static const bool ok = allow_smem(k, smem);
         if (!ok) return KS_ECUDA;
-        k<<<L.nts, SNT, smem, st>>>(mconst(ws, L), fm, fc, L.T, sm, sc, sstate(ws, L),
-                                    FROM_AGG ? sblk(ws, L) : nullptr, segs, tv);
-        return launch_status();
+        const float* sb = FROM_AGG ? sblk(ws, L) : nullptr;
+        return launch_pdl(k, L.nts, SNT, smem, st, (const ModelConst<N, M>*)mconst(ws, L), (const float*)fm,
+                          (const float*)fc, L.T, sm, sc, sstate(ws, L), sb, segs, tv);
     }
 
     static int build_elements(const ks_model* m, const float* y, int64_t T, void* ws, size_t ws_bytes,
@@ -280,7 +301,7 @@ struct Impl {
 
     static int record(void* const* ev, int i, cudaStream_t st) {
         if (!ev || !ev[i]) return KS_OK;
-        return cudaEventRecord(static_cast<cudaEvent_t>(ev[i]), st) == cudaSuccess ? KS_OK : KS_ECUDA;
+        return record_event(ev[i], st) == cudaSuccess ? KS_OK : KS_ECUDA;
     }
 
     static size_t tv_bytes(int64_t T) { return layout(T).bytes_elements; }

@@ -86,15 +86,28 @@ constexpr size_t mixed_prep_smem() {
     return cmax(cmax(mixed_prep_smem_of<6, 3>(), mixed_prep_smem_of<4, 2>()), mixed_prep_smem_of<2, 1>());
 }
 
+template <int CH, int REF, bool RETRY>
+KS_DEV void mixed_filter_tile(const MG6& g6, const MG4& g4, const MG2& g2, const MixedQueue& q);
+
 // REF / RETRY as for filter_scan_kernel: the first launch detects
 // ill-conditioned inverses, the retry repeats the scan with refinement only
 // when the first met one.
 template <int CH, int REF, bool RETRY>
 __global__ void __launch_bounds__(kMixedThreads) mixed_filter_kernel(MG6 g6, MG4 g4, MG2 g2, MixedQueue q) {
-    constexpr int NT = kMixedThreads;
+    pdl_wait();
     if constexpr (RETRY) {
-        if (*(volatile uint32_t*)(q.status + HDR_NEED) == 0u) return;
+        if (*(volatile uint32_t*)(q.status + HDR_NEED) == 0u) {
+            pdl_trigger();
+            return;
+        }
     }
+    mixed_filter_tile<CH, REF, RETRY>(g6, g4, g2, q);
+    pdl_trigger();
+}
+
+template <int CH, int REF, bool RETRY>
+KS_DEV void mixed_filter_tile(const MG6& g6, const MG4& g4, const MG2& g2, const MixedQueue& q) {
+    constexpr int NT = kMixedThreads;
     __shared__ union {
         FilterSmem<6, 3, NT> s6;
         FilterSmem<4, 2, NT> s4;
@@ -149,14 +162,18 @@ __global__ void __launch_bounds__(kMixedThreads, kRevMinBlocks<4>) mixed_smoothe
     } sm;
     __shared__ int s_tile;
     extern __shared__ __align__(16) char dsm[];
+    pdl_wait();
     if (threadIdx.x == 0) s_tile = (int)atomicAdd(q.scounter, 1u);
     __syncthreads();
     int t = s_tile;
-    if (t < g6.ntiles) { mixed_smoother_one<6, 3, CH>(sm.s6, dsm, t, g6); return; }
-    t -= g6.ntiles;
-    if (t < g4.ntiles) { mixed_smoother_one<4, 2, CH>(sm.s4, dsm, t, g4); return; }
-    t -= g4.ntiles;
-    if (t < g2.ntiles) mixed_smoother_one<2, 1, CH>(sm.s2, dsm, t, g2);
+    if (t < g6.ntiles) {
+        mixed_smoother_one<6, 3, CH>(sm.s6, dsm, t, g6);
+    } else if ((t -= g6.ntiles) < g4.ntiles) {
+        mixed_smoother_one<4, 2, CH>(sm.s4, dsm, t, g4);
+    } else if ((t -= g4.ntiles) < g2.ntiles) {
+        mixed_smoother_one<2, 1, CH>(sm.s2, dsm, t, g2);
+    }
+    pdl_trigger();
 }
 
 constexpr int mixed_filter_smem() {
@@ -258,12 +275,13 @@ struct Mixed {
         mixed_prep_kernel<CH><<<nseq, kPrepThreads, mixed_prep_smem(), st>>>(g6, g4, g2, q);
         int rc = launch_status();
         if (rc) return rc;
-        mixed_filter_kernel<CH, REF_DETECT, false><<<ntiles, kMixedThreads, mixed_filter_smem(), st>>>(g6, g4, g2, q);
-        if ((rc = launch_status())) return rc;
-        mixed_filter_kernel<CH, REF_FP64, true><<<ntiles, kMixedThreads, mixed_filter_smem(), st>>>(g6, g4, g2, q);
-        if ((rc = launch_status())) return rc;
-        mixed_smoother_kernel<CH><<<ntiles, kMixedThreads, mixed_smoother_smem(), st>>>(g6, g4, g2, q);
-        return launch_status();
+        if ((rc = launch_pdl(mixed_filter_kernel<CH, REF_DETECT, false>, ntiles, kMixedThreads, mixed_filter_smem(),
+                             st, g6, g4, g2, q)))
+            return rc;
+        if ((rc = launch_pdl(mixed_filter_kernel<CH, REF_FP64, true>, ntiles, kMixedThreads, mixed_filter_smem(), st,
+                             g6, g4, g2, q)))
+            return rc;
+        return launch_pdl(mixed_smoother_kernel<CH>, ntiles, kMixedThreads, mixed_smoother_smem(), st, g6, g4, g2, q);
     }
 };
 

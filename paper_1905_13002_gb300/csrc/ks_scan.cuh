@@ -24,6 +24,16 @@
 
 namespace ks {
 
+// Record a timing event on `st` (host); inside a stream capture as an
+// external event node, so that every replay of the graph records it.
+inline cudaError_t record_event(void* ev, cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return cudaErrorUnknown;
+    cudaEvent_t e = static_cast<cudaEvent_t>(ev);
+    return cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(e, st, cudaEventRecordExternal)
+                                               : cudaEventRecord(e, st);
+}
+
 constexpr unsigned kFull = 0xffffffffu;
 constexpr uint32_t kFlagAgg = 1u;   // tile aggregate published
 constexpr uint32_t kFlagPre = 2u;   // inclusive prefix published
@@ -705,8 +715,10 @@ __global__ void __launch_bounds__(kPrepThreads) prep_kernel(const float* __restr
                                                    int nzero, const int64_t* __restrict__ off, int64_t T,
                                                    const uint32_t* __restrict__ first_tile = nullptr) {
     extern __shared__ __align__(16) char prep_dsm[];
+    pdl_wait();
     prep_body<N, M>(prep_dsm, (int)blockIdx.x, (int)gridDim.x, F, u, Q, H, d, R, m0, P0, y, out, status, zero, nzero,
                     off, T, first_tile);
+    pdl_trigger();
 }
 
 // ---------------------------------------------------------------- Lemma 3 materialised
@@ -1598,8 +1610,12 @@ __global__ void __launch_bounds__(NT) filter_scan_kernel(const ModelConst<N, M>*
                                                          float* __restrict__ fcov, ScanState ss,
                                                          float* __restrict__ sagg, Segs<N, M> segs,
                                                          TVArgs tv) {
+    pdl_wait();   // the preparation (or the first run) has completed
     if constexpr (RETRY) {
-        if (*(volatile uint32_t*)(ss.status + HDR_NEED) == 0u) return;   // the first run needed no refinement
+        if (*(volatile uint32_t*)(ss.status + HDR_NEED) == 0u) {   // the first run needed no refinement
+            pdl_trigger();
+            return;
+        }
     }
     __shared__ FilterSmem<N, M, NT> sm;
     __shared__ int s_tile;
@@ -1609,9 +1625,10 @@ __global__ void __launch_bounds__(NT) filter_scan_kernel(const ModelConst<N, M>*
     if (tid == 0) s_tile = (int)atomicAdd(ss.counter, 1u);
     __syncthreads();
     const int tile = s_tile;
-    if (tile >= (int)gridDim.x) return;   // a tile number past the grid (only when the counter was offset)
-    filter_scan_body<N, M, NT, CH, FROM_Y, SAGG, SEG, TV, REF>(sm, dsm, tile, y, el, ld, T, fmean, fcov, ss, sagg,
-                                                               segs, tv);
+    if (tile < (int)gridDim.x)   // else a tile number past the grid (only when the counter was offset)
+        filter_scan_body<N, M, NT, CH, FROM_Y, SAGG, SEG, TV, REF>(sm, dsm, tile, y, el, ld, T, fmean, fcov, ss,
+                                                                   sagg, segs, tv);
+    pdl_trigger();
 }
 
 // ---------------------------------------------------------------- reverse scan
@@ -1862,6 +1879,7 @@ __global__ void __launch_bounds__(NT, kRevMinBlocks<N>) smoother_scan_kernel(con
     __shared__ int s_tile;
     extern __shared__ __align__(16) char dsm[];
     const int tid = threadIdx.x;
+    pdl_wait();   // the forward scan has completed
     load_const<N, M>(mcg, sm.mc, tid, NT);
     if (tid == 0) s_tile = (int)atomicAdd(ss.counter, 1u);
     if constexpr (Stage<N>::kOn) {
@@ -1874,6 +1892,7 @@ __global__ void __launch_bounds__(NT, kRevMinBlocks<N>) smoother_scan_kernel(con
     if (tile >= (int)gridDim.x) return;   // a tile number past the grid (only when the counter was offset)
     smoother_scan_body<N, M, NT, CH, FROM_AGG, SEG, TV>(sm, dsm, tile, fmean, fcov, T, smean, scov, ss, sagg, segs,
                                                         tv);
+    pdl_trigger();
 }
 
 // Dynamic shared memory of the two scans (bytes).

@@ -100,7 +100,7 @@ struct TImpl {
             ka<<<L.ntf, NW * 32, sizeof(FSM), st>>>(mc, y, L.T, fm, fc, fb, src, status);
             if ((rc = launch_status())) return rc;
         }
-        if (ev && ev[2] && cudaEventRecord(static_cast<cudaEvent_t>(ev[2]), st) != cudaSuccess) return KS_ECUDA;
+        if (ev && ev[2] && record_event(ev[2], st) != cudaSuccess) return KS_ECUDA;
         if (smoother) {
             auto kr = tc::tsmoother_reduce_kernel<N, M, NW, CH>;
             auto ks = tc::tspine_smoother_kernel<N, SW>;
@@ -165,13 +165,13 @@ struct TImpl {
             fc = reinterpret_cast<float*>(static_cast<char*>(ws) + L.off_fcov);
         }
         if (!vec_ok(fm, fc, filter_only ? fm : sm, filter_only ? fc : sc)) return KS_EINVAL;
-        if (ev && ev[0] && cudaEventRecord(static_cast<cudaEvent_t>(ev[0]), st) != cudaSuccess) return KS_ECUDA;
+        if (ev && ev[0] && record_event(ev[0], st) != cudaSuccess) return KS_ECUDA;
         if ((rc = GImpl<N, M, NW, CH>::prep(m->F, m->u, m->Q, m->H, m->d, m->R, m->m0, m->P0, y, 1, nullptr, ws,
                                             L, st)))
             return rc;
-        if (ev && ev[1] && cudaEventRecord(static_cast<cudaEvent_t>(ev[1]), st) != cudaSuccess) return KS_ECUDA;
+        if (ev && ev[1] && record_event(ev[1], st) != cudaSuccess) return KS_ECUDA;
         if ((rc = scans(ws, L, y, fm, fc, sm, sc, st, ev, true, !filter_only))) return rc;
-        if (ev && ev[3] && cudaEventRecord(static_cast<cudaEvent_t>(ev[3]), st) != cudaSuccess) return KS_ECUDA;
+        if (ev && ev[3] && record_event(ev[3], st) != cudaSuccess) return KS_ECUDA;
         return KS_OK;
     }
 };

@@ -11,7 +11,8 @@ from the call's total number of steps through a rule table per state size
   for nx = 2, 4, 6 (one sequence through ``ks_smooth``) and for mixed-size
   batches (``ks_smooth_batched``, keyed by their total steps), timing each
   call with CUDA events after warm-up, L2 flushed between calls;
-* turns the measurements into rules: the fastest l at each measured size,
+* turns the measurements into rules: the fastest l at each measured size
+  (keeping the smaller size's choice while it is within 2 % of the fastest),
   with the switch between two neighbouring sizes at their geometric mean;
 * writes them to a versioned JSON cache, which the binding loads when the
   library is first used (``load_default``) if it was measured on the same
@@ -40,14 +41,26 @@ TUNING_DIR = os.path.join(HERE, "tuning")
 
 
 # ---------------------------------------------------------------- selection logic
+HYSTERESIS = 0.02   # keep the smaller size's choice while it is within 2 % of the fastest
+
+
 def rules_from(measured: dict) -> list:
     """measured: {size: {steps: ms}} -> [(T_below, steps), ...] (sizes ascending).
-    The fastest block length at each size; where neighbouring sizes disagree
-    the switch sits at their geometric mean; equal neighbours merge."""
+    The fastest block length at each size, except that the choice of the next
+    smaller size is kept while it is within HYSTERESIS of the fastest (timing
+    noise then does not flip the table back and forth); where neighbouring
+    sizes disagree the switch sits at their geometric mean; equal neighbours
+    merge."""
     sizes = sorted(measured)
     if not sizes:
         return []
-    best = [min(measured[T], key=lambda s: (measured[T][s], s)) for T in sizes]
+    best = []
+    for T in sizes:
+        row = measured[T]
+        fastest = min(row, key=lambda s: (row[s], s))
+        if best and best[-1] in row and row[best[-1]] <= (1.0 + HYSTERESIS) * row[fastest]:
+            fastest = best[-1]
+        best.append(fastest)
     rules = []
     for i in range(len(sizes) - 1):
         if best[i] != best[i + 1]:

@@ -36,3 +36,13 @@ def test_recorded_traffic_only_for_its_length_and_sources(tmp_path, monkeypatch)
     assert bench.recorded_traffic("smoother_scan_kernel", 1 << 20) is None
     monkeypatch.setattr(bench, "source_hash", lambda k: "changed")
     assert bench.recorded_traffic(key, 1 << 20) is None
+
+
+def test_launch_counts():
+    """Kernels per ks_smooth call in the bench's gpu_launches: 4 for the fused
+    nx <= 6 path (preparation, forward, refinement retry, reverse); at nx = 32
+    the preparation and per scan a reduce, the spine levels over tiles of 216
+    steps and an apply (T = 65536: 304 tiles, 9 levels)."""
+    assert bench.launches_per_call(4, 1 << 20) == 4
+    assert bench.launches_per_call(32, 65536) == 1 + 2 * (2 + 9)
+    assert bench.launches_per_call(32, 216) == 1 + 2 * 2

@@ -32,6 +32,14 @@ def test_rules_follow_the_fastest_length_with_geometric_switches():
     assert tune.choose(rules, 131071) == 4 and tune.choose(rules, 131072) == 8
 
 
+def test_noise_within_the_hysteresis_keeps_the_previous_choice():
+    meas = {1000: {4: 1.0, 8: 1.2, 16: 2.0, 32: 3.0},
+            2000: {4: 1.01, 8: 1.0, 16: 2.0, 32: 3.0},      # 8 faster by 1 %: keep 4
+            4000: {4: 1.5, 8: 1.0, 16: 1.01, 32: 3.0},      # 8 clearly faster
+            8000: {4: 3.0, 8: 1.0, 16: 0.995, 32: 3.0}}     # 16 faster by 0.5 %: keep 8
+    assert tune.rules_from(meas) == [(2829, 4), (tune.T_NEVER, 8)]
+
+
 def test_ties_go_to_the_shorter_block_and_one_size_gives_one_rule():
     assert tune.rules_from({5000: {4: 1.0, 8: 1.0, 16: 2.0, 32: 3.0}}) == [(tune.T_NEVER, 4)]
     assert tune.rules_from({}) == []
@@ -80,7 +88,7 @@ def test_committed_caches_are_well_formed():
             assert rules and all(s in tune.STEPS for _, s in rules)
             tbs = [tb for tb, _ in rules]
             assert tbs == sorted(tbs) and len(set(tbs)) == len(tbs)
-            # the rules pick the fastest measured length at every measured size
+            # at every measured size the rules pick a length within the hysteresis of the fastest
             meas = {int(T): {int(s): ms for s, ms in row.items()} for T, row in d["measured_ms"][key].items()}
             for T, row in meas.items():
-                assert tune.choose(rules, T) == min(row, key=lambda s: (row[s], s))
+                assert row[tune.choose(rules, T)] <= (1 + tune.HYSTERESIS) * min(row.values()) + 1e-9
