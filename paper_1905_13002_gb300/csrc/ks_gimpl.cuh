@@ -83,7 +83,7 @@ struct GImpl {
         if (!ok) return KS_ECUDA;
         uint32_t* z = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + L.off_flags);
         k<<<B, kPrepThreads, smem, st>>>(F, u, Q, H, d, R, m0, P0, y, mconst(ws, L), status(ws), z,
-                                (int)(L.flags_bytes / 4), off, L.T, nullptr);
+                                (int)(L.flags_bytes / 4), off, L.T, nullptr, nullptr, 0);
         return launch_status();
     }
 
@@ -204,7 +204,7 @@ struct GImpl {
             if (!ok) return KS_ECUDA;
             uint32_t* z = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + L.off_flags);
             k<<<1, kPrepThreads, smem, st>>>(m->F, m->u, m->Q, m->H, m->d, m->R, m->m0, m->P0, y, tvc, status(ws), z,
-                                             (int)(L.flags_bytes / 4), nullptr, T, nullptr);
+                                             (int)(L.flags_bytes / 4), nullptr, T, nullptr, nullptr, 0);
             if ((rc = launch_status())) return rc;
         }
         if (T > 1) {

@@ -22,7 +22,7 @@ struct Layout {
     int64_t T = 0, ld = 0;
     int B = 1;
     int ntf = 0, nts = 0;
-    size_t off_const = 0, off_flags = 0, flags_bytes = 0;
+    size_t off_const = 0, off_coef = 0, off_flags = 0, flags_bytes = 0;
     size_t off_fagg = 0, off_fpre = 0, off_sagg = 0, off_spre = 0, off_sblk = 0;
     size_t off_elems = 0, off_fmean = 0, off_fcov = 0;
     size_t bytes_smooth = 0, bytes_elements = 0;
@@ -103,6 +103,8 @@ struct Impl {
         size_t off = 256;                                   // status word + reserved
         L.off_const = off;                                  // one ModelConst per segment
         off = align_up(off + sizeof(ModelConst<N, M>) * (size_t)B, 256);
+        L.off_coef = off;                                   // one BlockCoef per segment
+        off = align_up(off + sizeof(BlockCoef<N, M>) * (size_t)B, 256);
         L.off_flags = off;   // [fcounter, scounter, retry counter, pad][fflags][sflags][retry fflags]
         L.flags_bytes = 16 + 4 * (size_t)(2 * L.ntf + L.nts);
         off = align_up(off + L.flags_bytes, 256);
@@ -129,6 +131,9 @@ struct Impl {
 
     static ModelConst<N, M>* mconst(void* ws, const Layout& L) {
         return reinterpret_cast<ModelConst<N, M>*>(static_cast<char*>(ws) + L.off_const);
+    }
+    static BlockCoef<N, M>* coef(void* ws, const Layout& L) {
+        return reinterpret_cast<BlockCoef<N, M>*>(static_cast<char*>(ws) + L.off_coef);
     }
     static uint32_t* status(void* ws) { return static_cast<uint32_t*>(ws); }
 
@@ -177,13 +182,15 @@ struct Impl {
         return KS_OK;
     }
 
-    // Model constants (and the k = 1 element when y is given); also zeroes the
+    // Model constants (and the k = 1 element when y is given, with the block
+    // fold's coefficients when the layout has room for them); also zeroes the
     // scans' tile counters and flags, which every scan launch needs.
     static int prep(const ks_model* m, const float* y, void* ws, const Layout& L, cudaStream_t st) {
         uint32_t* z = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + L.off_flags);
         prep_kernel<N, M><<<1, kPrepThreads, prep_smem(), st>>>(m->F, m->u, m->Q, m->H, m->d, m->R, m->m0, m->P0, y,
                                              mconst(ws, L), status(ws), z, (int)(L.flags_bytes / 4), nullptr,
-                                             L.T, status(ws) + HDR_FIRST_TILE);
+                                             L.T, status(ws) + HDR_FIRST_TILE, (y && L.off_coef) ? coef(ws, L) : nullptr,
+                                             FCH);
         return launch_status();
     }
 
@@ -368,7 +375,8 @@ struct Impl {
         if ((rc = record(ev, 0, st))) return rc;
         if ((rc = prep(m, y, ws, L, st))) return rc;
         if ((rc = record(ev, 1, st))) return rc;
-        if ((rc = launch_filter_fused<false>(ws, L, y, fm, fc, no_segs(), st))) return rc;
+        if ((rc = launch_filter_fused<false>(ws, L, y, fm, fc, Segs<N, M>{nullptr, nullptr, 1, coef(ws, L)}, st)))
+            return rc;
         if ((rc = record(ev, 2, st))) return rc;
         if (!filter_only && (rc = launch_smoother<true, false>(ws, L, fm, fc, sm, sc, no_segs(), st))) return rc;
         return record(ev, 3, st);
@@ -388,10 +396,10 @@ struct Impl {
         uint32_t* z = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + L.off_flags);
         prep_kernel<N, M><<<mb->B, kPrepThreads, prep_smem(), st>>>(mb->F, mb->u, mb->Q, mb->H, mb->d, mb->R, mb->m0, mb->P0, y,
                                                  mconst(ws, L), status(ws), z, (int)(L.flags_bytes / 4),
-                                                 mb->offsets, T, status(ws) + HDR_FIRST_TILE);
+                                                 mb->offsets, T, status(ws) + HDR_FIRST_TILE, coef(ws, L), FCH);
         int rc = launch_status();
         if (rc) return rc;
-        const Segs<N, M> segs{mconst(ws, L), mb->offsets, mb->B};
+        const Segs<N, M> segs{mconst(ws, L), mb->offsets, mb->B, coef(ws, L)};
         if ((rc = launch_filter_fused<true>(ws, L, y, fm, fc, segs, st))) return rc;
         return launch_smoother<true, true>(ws, L, fm, fc, sm, sc, segs, st);
     }

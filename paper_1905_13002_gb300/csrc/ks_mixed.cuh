@@ -38,6 +38,7 @@ struct MixedGroup {
     float* sagg = nullptr;  // fused smoothing aggregates, one per forward block
     uint32_t* zero = nullptr;   // the group's flags region
     int nzero = 0;
+    int ch = 0;                 // steps per thread of the launch (block-fold coefficients)
 };
 
 using MG6 = MixedGroup<6, 3>;
@@ -58,7 +59,7 @@ template <int N, int M>
 KS_DEV void mixed_prep_one(char* dsm, int sg, const MixedGroup<N, M>& g) {
     prep_body<N, M>(dsm, sg, g.B, g.F, g.u, g.Q, g.H, g.d, g.R, g.m0, g.P0, g.y,
                     const_cast<ModelConst<N, M>*>(g.segs.mcg), g.fs.status, g.zero, g.nzero, g.segs.off, g.T,
-                    nullptr);
+                    nullptr, const_cast<BlockCoef<N, M>*>(g.segs.coef), g.ch);
 }
 
 // One block per sequence of all groups (nx = 6 sequences first); block 0 also
@@ -105,61 +106,68 @@ __global__ void __launch_bounds__(kMixedThreads) mixed_filter_kernel(MG6 g6, MG4
     pdl_trigger();
 }
 
+// Dynamic shared memory of one size's body: its block-scan state first, its
+// staging buffers after it.  A block carves the layout of its item's size out
+// of one dynamic allocation sized for the largest, so that the big block-scan
+// state of nx = 6 and the staging buffers of nx = 4 never add up.
+__host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) / 16 * 16; }
+template <int N, int M>
+constexpr size_t mixed_filter_smem_of() {
+    return align16(sizeof(FilterSmem<N, M, kMixedThreads>)) + (size_t)filter_dyn_smem<N, kMixedThreads>();
+}
+template <int N, int M>
+constexpr size_t mixed_smoother_smem_of() {
+    return align16(sizeof(SmootherSmem<N, M, kMixedThreads>)) + (size_t)smoother_dyn_smem<N, kMixedThreads>();
+}
+constexpr int mixed_filter_smem() {
+    return (int)cmax(cmax(mixed_filter_smem_of<6, 3>(), mixed_filter_smem_of<4, 2>()), mixed_filter_smem_of<2, 1>());
+}
+constexpr int mixed_smoother_smem() {
+    return (int)cmax(cmax(mixed_smoother_smem_of<6, 3>(), mixed_smoother_smem_of<4, 2>()),
+                     mixed_smoother_smem_of<2, 1>());
+}
+
+template <int N, int M, int CH, int REF, bool RETRY>
+KS_DEV void mixed_filter_one(char* dsm, int t, const MixedGroup<N, M>& g) {
+    auto& sm = *reinterpret_cast<FilterSmem<N, M, kMixedThreads>*>(dsm);
+    char* stage = dsm + align16(sizeof(FilterSmem<N, M, kMixedThreads>));
+    filter_scan_body<N, M, kMixedThreads, CH, true, true, true, false, REF>(
+        sm, stage, t, g.y, nullptr, 0, g.T, g.fmean, g.fcov, RETRY ? g.fs2 : g.fs, g.sagg, g.segs, TVArgs{});
+}
+
 template <int CH, int REF, bool RETRY>
 KS_DEV void mixed_filter_tile(const MG6& g6, const MG4& g4, const MG2& g2, const MixedQueue& q) {
-    constexpr int NT = kMixedThreads;
-    __shared__ union {
-        FilterSmem<6, 3, NT> s6;
-        FilterSmem<4, 2, NT> s4;
-        FilterSmem<2, 1, NT> s2;
-    } sm;
     __shared__ int s_tile;
     extern __shared__ __align__(16) char dsm[];
     if (threadIdx.x == 0) s_tile = (int)atomicAdd(RETRY ? q.fcounter2 : q.fcounter, 1u);
     __syncthreads();
     int t = s_tile;
-    const TVArgs tv{};
     if (t < g6.ntiles) {
-        filter_scan_body<6, 3, NT, CH, true, true, true, false, REF>(sm.s6, dsm, t, g6.y, nullptr, 0, g6.T, g6.fmean,
-                                                                    g6.fcov, RETRY ? g6.fs2 : g6.fs, g6.sagg,
-                                                                    g6.segs, tv);
-        return;
+        mixed_filter_one<6, 3, CH, REF, RETRY>(dsm, t, g6);
+    } else if ((t -= g6.ntiles) < g4.ntiles) {
+        mixed_filter_one<4, 2, CH, REF, RETRY>(dsm, t, g4);
+    } else if ((t -= g4.ntiles) < g2.ntiles) {
+        mixed_filter_one<2, 1, CH, REF, RETRY>(dsm, t, g2);
     }
-    t -= g6.ntiles;
-    if (t < g4.ntiles) {
-        filter_scan_body<4, 2, NT, CH, true, true, true, false, REF>(sm.s4, dsm, t, g4.y, nullptr, 0, g4.T, g4.fmean,
-                                                                    g4.fcov, RETRY ? g4.fs2 : g4.fs, g4.sagg,
-                                                                    g4.segs, tv);
-        return;
-    }
-    t -= g4.ntiles;
-    if (t < g2.ntiles)
-        filter_scan_body<2, 1, NT, CH, true, true, true, false, REF>(sm.s2, dsm, t, g2.y, nullptr, 0, g2.T, g2.fmean,
-                                                                    g2.fcov, RETRY ? g2.fs2 : g2.fs, g2.sagg,
-                                                                    g2.segs, tv);
 }
 
 template <int N, int M, int CH>
-KS_DEV void mixed_smoother_one(SmootherSmem<N, M, kMixedThreads>& sm, char* dsm, int t, const MixedGroup<N, M>& g) {
+KS_DEV void mixed_smoother_one(char* dsm, int t, const MixedGroup<N, M>& g) {
+    auto& sm = *reinterpret_cast<SmootherSmem<N, M, kMixedThreads>*>(dsm);
+    char* stage = dsm + align16(sizeof(SmootherSmem<N, M, kMixedThreads>));
     if constexpr (Stage<N>::kOn) {   // this thread's two staging mbarriers
         mbar_init(&sm.mbars[2 * threadIdx.x], 1);
         mbar_init(&sm.mbars[2 * threadIdx.x + 1], 1);
         fence_proxy_async();
         __syncthreads();
     }
-    smoother_scan_body<N, M, kMixedThreads, CH, true, true, false>(sm, dsm, t, g.fmean, g.fcov, g.T, g.smean,
+    smoother_scan_body<N, M, kMixedThreads, CH, true, true, false>(sm, stage, t, g.fmean, g.fcov, g.T, g.smean,
                                                                    g.scov, g.ss, g.sagg, g.segs, TVArgs{});
 }
 
 template <int CH>
 __global__ void __launch_bounds__(kMixedThreads, kRevMinBlocks<4>) mixed_smoother_kernel(MG6 g6, MG4 g4, MG2 g2,
                                                                                        MixedQueue q) {
-    constexpr int NT = kMixedThreads;
-    __shared__ union {
-        SmootherSmem<6, 3, NT> s6;
-        SmootherSmem<4, 2, NT> s4;
-        SmootherSmem<2, 1, NT> s2;
-    } sm;
     __shared__ int s_tile;
     extern __shared__ __align__(16) char dsm[];
     pdl_wait();
@@ -167,22 +175,13 @@ __global__ void __launch_bounds__(kMixedThreads, kRevMinBlocks<4>) mixed_smoothe
     __syncthreads();
     int t = s_tile;
     if (t < g6.ntiles) {
-        mixed_smoother_one<6, 3, CH>(sm.s6, dsm, t, g6);
+        mixed_smoother_one<6, 3, CH>(dsm, t, g6);
     } else if ((t -= g6.ntiles) < g4.ntiles) {
-        mixed_smoother_one<4, 2, CH>(sm.s4, dsm, t, g4);
+        mixed_smoother_one<4, 2, CH>(dsm, t, g4);
     } else if ((t -= g4.ntiles) < g2.ntiles) {
-        mixed_smoother_one<2, 1, CH>(sm.s2, dsm, t, g2);
+        mixed_smoother_one<2, 1, CH>(dsm, t, g2);
     }
     pdl_trigger();
-}
-
-constexpr int mixed_filter_smem() {
-    return cmax(cmax(filter_dyn_smem<6, kMixedThreads>(), filter_dyn_smem<4, kMixedThreads>()),
-                filter_dyn_smem<2, kMixedThreads>());
-}
-constexpr int mixed_smoother_smem() {
-    return cmax(cmax(smoother_dyn_smem<6, kMixedThreads>(), smoother_dyn_smem<4, kMixedThreads>()),
-                smoother_dyn_smem<2, kMixedThreads>());
 }
 
 // ---------------------------------------------------------------- host side
@@ -226,7 +225,9 @@ struct Mixed {
         o.T = g.total_T;
         o.F = mb.F; o.u = mb.u; o.Q = mb.Q; o.H = mb.H; o.d = mb.d; o.R = mb.R;
         o.m0 = mb.m0; o.P0 = mb.P0;
-        o.segs = Segs<N, M>{reinterpret_cast<const ModelConst<N, M>*>(b + L.off_const), mb.offsets, mb.B};
+        o.segs = Segs<N, M>{reinterpret_cast<const ModelConst<N, M>*>(b + L.off_const), mb.offsets, mb.B,
+                            reinterpret_cast<const BlockCoef<N, M>*>(b + L.off_coef)};
+        o.ch = CH;
         o.y = g.y;
         o.fmean = g.fmean; o.fcov = g.fcov; o.smean = g.smean; o.scov = g.scov;
         uint32_t* status = reinterpret_cast<uint32_t*>(ws);

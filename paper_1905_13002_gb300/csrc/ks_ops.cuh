@@ -892,6 +892,215 @@ KS_DEV void first_element(const ModelConst<N, M>& mc, FElem<N>& e) {
     for (int a = 0; a < sym_size(N); ++a) { e.C[a] = mc.C1[a]; e.J[a] = 0.f; }
 }
 
+// ---------------------------------------------------------------- linear block fold
+// For a time-invariant model every measurement element has the same A, C,
+// J = U^T U (Lemma 3: only b_k and eta_k depend on k), so the fold of a block
+// of l consecutive measurement elements, a_1 (x) ... (x) a_l (Lemma 4), has the
+// same A, C, J for every block, and its (b, eta) is affine in the block's
+// innovations e_i = y_i - H u - d: the rank-ny combine maps (b, eta) of the
+// running aggregate and of the next element linearly, with coefficients that
+// depend only on the matrices.  BlockCoef holds, for blocks of `ch` steps,
+//   b   = bc + sum_i Bc[i] e_i,     eta = ec + sum_i Ec[i] e_i,
+// and the block's A, C, J.  The scans fold a full block with it in 2 N M FMAs
+// per step instead of one rank-ny combine; blocks that hold a sequence's first
+// step, or a ragged end, fold element by element.
+template <int N, int M>
+struct alignas(16) BlockCoef {
+    float Bc[32][N * M];   // position i: row-major N x M
+    float Ec[32][N * M];
+    float bc[N], ec[N];
+    float A[N * N];
+    float C[sym_size(N)];
+    float J[sym_size(N)];
+    int ch;                // block length the coefficients are for (0: none)
+    int pad[3];
+};
+
+// Coefficients of blocks of `ch` steps (a power of two, <= 32), by one warp,
+// by doubling: a block of 2h steps is the Lemma 4 combine of two blocks of h
+// steps, whose matrix parts (A_h, C_h, J_h) are the same.  Every lane runs the
+// matrix combines (the same values; five levels for 32 steps), and lane i
+// keeps the coefficients of position i within its current block.  With
+// M = I + C_h J_h, P = A_h M^{-1}, R = A_h^T M^{-T}:
+//   b = P (b_L + C_h eta_R) + b_R,   eta = R (eta_R - J_h b_L) + eta_L,
+// so a position of the left half maps as Bc <- P Bc, Ec <- Ec - R J_h Bc, one
+// of the right half as Bc <- P C_h Ec + Bc, Ec <- R Ec, and the constants as
+// bc <- P (bc + C_h ec) + bc, ec <- R (ec - J_h bc) + ec.  A block of one step
+// is the measurement element: A, C, J = U^T U, Bc = K, Ec = U^T L_S^{-1},
+// bc = u, ec = 0.  `ch` = 0 is written when an inverse fails (then the scans
+// fold element by element).
+template <int N, int M>
+KS_DEV void block_coef_warp(const ModelConst<N, M>& mc, int ch, BlockCoef<N, M>* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    float Ah[N][N], Ch[N][N], Jh[N][N];
+#pragma unroll
+    for (int a = 0; a < N; ++a)
+#pragma unroll
+        for (int b = 0; b < N; ++b) {
+            Ah[a][b] = mc.A[a * N + b];
+            Ch[a][b] = mc.C[sidx(a, b)];
+            float s = 0.f;
+#pragma unroll
+            for (int q = 0; q < M; ++q) s = fmaf(mc.U[q * N + a], mc.U[q * N + b], s);
+            Jh[a][b] = s;
+        }
+    float bc[N], ec[N];
+#pragma unroll
+    for (int a = 0; a < N; ++a) { bc[a] = mc.u[a]; ec[a] = 0.f; }
+    float Bc[N][M], Ec[N][M];
+#pragma unroll
+    for (int a = 0; a < N; ++a)
+#pragma unroll
+        for (int r = 0; r < M; ++r) {
+            Bc[a][r] = mc.K[a * M + r];
+            float s = 0.f;   // U^T L_S^{-1}
+#pragma unroll
+            for (int q = r; q < M; ++q) s = fmaf(mc.U[q * N + a], mc.Lsi[q * M + r], s);
+            Ec[a][r] = s;
+        }
+    bool ok = ch >= 1 && ch <= 32 && (ch & (ch - 1)) == 0;
+#pragma unroll 1
+    for (int h = 1; ok && h < ch; h <<= 1) {
+        float Mx[N][N], Mi[N][N];
+#pragma unroll
+        for (int a = 0; a < N; ++a)
+#pragma unroll
+            for (int b = 0; b < N; ++b) {
+                float s = (a == b) ? 1.f : 0.f;
+#pragma unroll
+                for (int c = 0; c < N; ++c) s = fmaf(Ch[a][c], Jh[c][b], s);
+                Mx[a][b] = s;
+            }
+        ok = inverse_pp<N>(Mx, Mi);
+        float P[N][N], Rt[N][N], PC[N][N], RJ[N][N];   // Rt = R^T = M^{-1} A_h
+#pragma unroll
+        for (int a = 0; a < N; ++a)
+#pragma unroll
+            for (int b = 0; b < N; ++b) {
+                float s = 0.f, t = 0.f;
+#pragma unroll
+                for (int c = 0; c < N; ++c) {
+                    s = fmaf(Ah[a][c], Mi[c][b], s);
+                    t = fmaf(Mi[a][c], Ah[c][b], t);
+                }
+                P[a][b] = s;
+                Rt[a][b] = t;
+            }
+#pragma unroll
+        for (int a = 0; a < N; ++a)
+#pragma unroll
+            for (int b = 0; b < N; ++b) {
+                float s = 0.f, t = 0.f;
+#pragma unroll
+                for (int c = 0; c < N; ++c) {
+                    s = fmaf(P[a][c], Ch[c][b], s);
+                    t = fmaf(Rt[c][a], Jh[c][b], t);   // (R J_h)[a][b], R = Rt^T
+                }
+                PC[a][b] = s;
+                RJ[a][b] = t;
+            }
+        // this lane's position: left or right half of the new block of 2h
+        const bool right = (lane & h) != 0;
+        {
+            float nB[N][M], nE[N][M];
+#pragma unroll
+            for (int a = 0; a < N; ++a)
+#pragma unroll
+                for (int r = 0; r < M; ++r) {
+                    float sb, se;
+                    if (!right) {
+                        sb = 0.f;
+                        se = Ec[a][r];
+#pragma unroll
+                        for (int c = 0; c < N; ++c) {
+                            sb = fmaf(P[a][c], Bc[c][r], sb);
+                            se = fmaf(-RJ[a][c], Bc[c][r], se);
+                        }
+                    } else {
+                        sb = Bc[a][r];
+                        se = 0.f;
+#pragma unroll
+                        for (int c = 0; c < N; ++c) {
+                            sb = fmaf(PC[a][c], Ec[c][r], sb);
+                            se = fmaf(Rt[c][a], Ec[c][r], se);
+                        }
+                    }
+                    nB[a][r] = sb;
+                    nE[a][r] = se;
+                }
+#pragma unroll
+            for (int a = 0; a < N; ++a)
+#pragma unroll
+                for (int r = 0; r < M; ++r) { Bc[a][r] = nB[a][r]; Ec[a][r] = nE[a][r]; }
+        }
+        {   // constants (both halves have the same)
+            float nb[N], ne[N];
+#pragma unroll
+            for (int a = 0; a < N; ++a) {
+                float sb = bc[a], se = ec[a];
+#pragma unroll
+                for (int c = 0; c < N; ++c) {
+                    sb = fmaf(P[a][c], bc[c], sb);
+                    sb = fmaf(PC[a][c], ec[c], sb);
+                    se = fmaf(Rt[c][a], ec[c], se);
+                    se = fmaf(-RJ[a][c], bc[c], se);
+                }
+                nb[a] = sb;
+                ne[a] = se;
+            }
+#pragma unroll
+            for (int a = 0; a < N; ++a) { bc[a] = nb[a]; ec[a] = ne[a]; }
+        }
+        {   // matrix part: A <- P A_h, C <- P C_h A_h^T + C_h, J <- A_h^T M^{-T} J_h A_h + J_h
+            float nA[N][N], nC[N][N], nJ[N][N];
+#pragma unroll
+            for (int a = 0; a < N; ++a)
+#pragma unroll
+                for (int b = 0; b < N; ++b) {
+                    float sa = 0.f, sc = Ch[a][b], sj = Jh[a][b];
+#pragma unroll
+                    for (int c = 0; c < N; ++c) {
+                        sa = fmaf(P[a][c], Ah[c][b], sa);
+                        sc = fmaf(PC[a][c], Ah[b][c], sc);
+                        sj = fmaf(RJ[a][c], Ah[c][b], sj);
+                    }
+                    nA[a][b] = sa;
+                    nC[a][b] = sc;
+                    nJ[a][b] = sj;
+                }
+#pragma unroll
+            for (int a = 0; a < N; ++a)
+#pragma unroll
+                for (int b = 0; b < N; ++b) {
+                    Ah[a][b] = nA[a][b];
+                    Ch[a][b] = 0.5f * (nC[a][b] + nC[b][a]);
+                    Jh[a][b] = 0.5f * (nJ[a][b] + nJ[b][a]);
+                }
+        }
+    }
+    if (lane < ch) {
+#pragma unroll
+        for (int a = 0; a < N; ++a)
+#pragma unroll
+            for (int r = 0; r < M; ++r) {
+                out->Bc[lane][a * M + r] = Bc[a][r];
+                out->Ec[lane][a * M + r] = Ec[a][r];
+            }
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int a = 0; a < N; ++a) { out->bc[a] = bc[a]; out->ec[a] = ec[a]; }
+#pragma unroll
+        for (int a = 0; a < N; ++a) {
+#pragma unroll
+            for (int b = 0; b < N; ++b) out->A[a * N + b] = Ah[a][b];
+#pragma unroll
+            for (int b = 0; b <= a; ++b) { out->C[sidx(a, b)] = Ch[a][b]; out->J[sidx(a, b)] = Jh[a][b]; }
+        }
+        out->ch = ok ? ch : 0;
+    }
+}
+
 // ---------------------------------------------------------------- Lemma 5
 // Smoothing element for k < n from the filtered (xbar, P):
 //   P- = F P F^T + Q = Lc Lc^T (Cholesky),  E = P F^T (P-)^{-1}  (solved as

@@ -223,6 +223,14 @@ KS_DEV FElem<N> load_soa(const float* __restrict__ el, int64_t ld, int64_t k) {
 }
 
 template <int N, int M>
+KS_DEV void load_coef(const BlockCoef<N, M>* __restrict__ g, BlockCoef<N, M>& s, int tid, int nt) {
+    static_assert(sizeof(BlockCoef<N, M>) % 16 == 0, "vector copy");
+    const float4* src = reinterpret_cast<const float4*>(g);
+    float4* dst = reinterpret_cast<float4*>(&s);
+    for (int i = tid; i < (int)(sizeof(BlockCoef<N, M>) / 16); i += nt) dst[i] = src[i];
+}
+
+template <int N, int M>
 KS_DEV void load_const(const ModelConst<N, M>* __restrict__ g, ModelConst<N, M>& s, int tid, int nt) {
     const float* src = reinterpret_cast<const float*>(g);
     float* dst = reinterpret_cast<float*>(&s);
@@ -244,6 +252,7 @@ struct Segs {
     const ModelConst<N, M>* mcg;   // per-segment constants [B] (batched)
     const int64_t* off;            // [B+1] (batched), else nullptr
     int B;
+    const BlockCoef<N, M>* coef = nullptr;   // block-fold coefficients per segment (null: none)
 };
 
 // With TV the constants are per step (g.mcg[k] for step k of one sequence of
@@ -460,7 +469,8 @@ KS_DEV void prep_body(char* prep_dsm, int sg, int nseg, const float* __restrict_
                       const float* __restrict__ R, const double* __restrict__ m0, const double* __restrict__ P0,
                       const float* __restrict__ y, ModelConst<N, M>* __restrict__ out, uint32_t* __restrict__ status,
                       uint32_t* __restrict__ zero, int nzero, const int64_t* __restrict__ off, int64_t T,
-                      const uint32_t* __restrict__ first_tile) {
+                      const uint32_t* __restrict__ first_tile, BlockCoef<N, M>* __restrict__ coef = nullptr,
+                      int ch = 0) {
     PrepSmem<N, M>& p = *reinterpret_cast<PrepSmem<N, M>*>(prep_dsm);
     ModelConst<N, M>& mc =
         *reinterpret_cast<ModelConst<N, M>*>(prep_dsm + ((sizeof(PrepSmem<N, M>) + 15) / 16) * 16);
@@ -597,6 +607,12 @@ KS_DEV void prep_body(char* prep_dsm, int sg, int nseg, const float* __restrict_
         }
         for (int e = l; e < N; e += 32) mc.u[e] = p.u[e];
         if (l < 4) mc.pad[l] = 0.f;
+        if constexpr (N <= 6) {   // register-path sizes only
+            if (coef != nullptr) {   // the block-fold coefficients, while warp 1 builds the k = 1 element
+                __syncwarp();
+                block_coef_warp<N, M>(mc, ch, coef + sg);
+            }
+        }
     } else if (warp == 1) {
         if (y != nullptr) {
             // ---- k = 1 in FP64: m- = F m0 + u, P- = F P0 F^T + Q, S1 = H P- H^T + R = L1 L1^T,
@@ -713,11 +729,12 @@ __global__ void __launch_bounds__(kPrepThreads) prep_kernel(const float* __restr
                                                    const float* __restrict__ y, ModelConst<N, M>* __restrict__ out,
                                                    uint32_t* __restrict__ status, uint32_t* __restrict__ zero,
                                                    int nzero, const int64_t* __restrict__ off, int64_t T,
-                                                   const uint32_t* __restrict__ first_tile = nullptr) {
+                                                   const uint32_t* __restrict__ first_tile = nullptr,
+                                                   BlockCoef<N, M>* __restrict__ coef = nullptr, int ch = 0) {
     extern __shared__ __align__(16) char prep_dsm[];
     pdl_wait();
     prep_body<N, M>(prep_dsm, (int)blockIdx.x, (int)gridDim.x, F, u, Q, H, d, R, m0, P0, y, out, status, zero, nzero,
-                    off, T, first_tile);
+                    off, T, first_tile, coef, ch);
     pdl_trigger();
 }
 
@@ -1398,6 +1415,7 @@ KS_DEV void build_selem_from(const MC& mc, const float (&xb)[N], const float (&P
 template <int N, int M, int NT>
 struct FilterSmem {
     ModelConst<N, M> mc;
+    BlockCoef<N, M> bc;   // block-fold coefficients of a single sequence
     typename BlockScan<FilterOp<N>, NT>::Smem bsm;
 };
 
@@ -1429,6 +1447,35 @@ KS_DEV void filter_scan_body(FilterSmem<N, M, NT>& sm, char* dsm, int tile,
         set_identity<N>(acc);
     } else if constexpr (FROM_Y) {
         cur.seek(segs, &mc, k0, T);
+        // A full block inside one sequence, not holding its first step, folds
+        // through the block coefficients (the linear block fold).
+        const BlockCoef<N, M>* bcf = nullptr;
+        if (segs.coef != nullptr) bcf = SEG ? segs.coef + cur.s : &sm.bc;
+        const bool lin = bcf != nullptr && bcf->ch == CH && k0 + CH <= T && !cur.first(k0) &&
+                         (!SEG || cur.end >= k0 + CH);
+        if (lin) {
+#pragma unroll
+            for (int a = 0; a < N * N; ++a) acc.A[a] = bcf->A[a];
+#pragma unroll
+            for (int a = 0; a < sym_size(N); ++a) { acc.C[a] = bcf->C[a]; acc.J[a] = bcf->J[a]; }
+#pragma unroll
+            for (int a = 0; a < N; ++a) { acc.b[a] = bcf->bc[a]; acc.eta[a] = bcf->ec[a]; }
+            const ModelConst<N, M>& m1 = *cur.mc;
+#pragma unroll 4
+            for (int i = 0; i < CH; ++i) {
+                float e[M];
+                load_meas<M>(y, k0 + i, e);
+#pragma unroll
+                for (int q = 0; q < M; ++q) e[q] -= m1.hud[q];
+#pragma unroll
+                for (int a = 0; a < N; ++a)
+#pragma unroll
+                    for (int q = 0; q < M; ++q) {
+                        acc.b[a] = fmaf(bcf->Bc[i][a * M + q], e[q], acc.b[a]);
+                        acc.eta[a] = fmaf(bcf->Ec[i][a * M + q], e[q], acc.eta[a]);
+                    }
+            }
+        } else {
         // y of the next step is loaded one step ahead, so that its latency
         // overlaps the current step's combine
         float yn[M];
@@ -1462,6 +1509,7 @@ KS_DEV void filter_scan_body(FilterSmem<N, M, NT>& sm, char* dsm, int tile,
                 meas_element<N, M>(*cur.mc, yk, b, w);
                 acc = fcombine_meas<N, M>(acc, *cur.mc, b, w, bad);
             }
+        }
         }
     } else if constexpr (TV) {
         TVElem<N, M> te;
@@ -1622,6 +1670,7 @@ __global__ void __launch_bounds__(NT) filter_scan_kernel(const ModelConst<N, M>*
     extern __shared__ __align__(16) char dsm[];
     const int tid = threadIdx.x;
     load_const<N, M>(mcg, sm.mc, tid, NT);
+    if (!SEG && segs.coef != nullptr) load_coef<N, M>(segs.coef, sm.bc, tid, NT);
     if (tid == 0) s_tile = (int)atomicAdd(ss.counter, 1u);
     __syncthreads();
     const int tile = s_tile;
