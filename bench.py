@@ -87,15 +87,19 @@ def bytes_per_step(nx: int, ny: int) -> dict:
     return {"filter": 4 * ny + post, "smoother": 2 * post}
 
 
-def flops_per_step(N: int, M: int, fused_smoothing: bool = True) -> dict:
+def flops_per_step(N: int, M: int, fused_smoothing: bool = True, block_fold: bool = None) -> dict:
     """Floating-point operations per step of each kernel's per-step work
     (FMA = 2).  The forward scan folds one measurement element into its block
-    aggregate (rank-M form of Lemma 4), applies it to the running filtered
-    posterior, and -- fused into the same pass -- builds the step's Lemma 5
-    smoothing element from that posterior and folds it into the block's
-    smoothing aggregate (Lemma 6).  The reverse scan rebuilds the Lemma 5
-    element and applies it to the running smoothed posterior.  Block-level
-    scan and look-back overheads are not counted."""
+    aggregate, applies it to the running filtered posterior, and -- fused into
+    the same pass -- builds the step's Lemma 5 smoothing element from that
+    posterior and folds it into the block's smoothing aggregate (Lemma 6).
+    The fold is the linear block fold of a time-invariant model at nx <= 6
+    (the innovation and two N x M products per step; `block_fold`), else the
+    rank-M form of Lemma 4.  The reverse scan rebuilds the Lemma 5 element and
+    applies it to the running smoothed posterior.  Block-level scan, look-back
+    and per-model coefficient work are not counted."""
+    if block_fold is None:
+        block_fold = fused_smoothing
     s = N * (N + 1) // 2
     sm = M * (M + 1) // 2
     chol = M * M * M // 3 + 3 * M
@@ -106,8 +110,10 @@ def flops_per_step(N: int, M: int, fused_smoothing: bool = True) -> dict:
     sel = 2 * (N ** 3 + s * N + N ** 3 // 6 + N * N * (N - 1) + 2 * N * N + s * N) + 2 * N * N + N
     scomb = 2 * (N ** 3 + s * N + N * N + N ** 3)
     sadv = 2 * (N ** 3 + N * N + s * N)
+    lbf = M + 2 * (2 * N * M)
     if fused_smoothing:
-        return {"filter": fold + adv + 2 * meas + sel + scomb, "smoother": sel + sadv}
+        first = lbf if block_fold else fold + meas
+        return {"filter": first + adv + meas + sel + scomb, "smoother": sel + sadv}
     # warp-per-chain kernels (nx >= 8): the reverse scan folds its own blocks
     return {"filter": fold + adv + 2 * meas, "smoother": 2 * sel + scomb + sadv}
 
@@ -499,7 +505,7 @@ def run_single(args, rank, world, local, mode):
         roof = tv_roofline(nx, ny, T, hbm, which, {"elements": statistics.mean(kel), "filter": statistics.mean(kf),
                                                    "smoother": statistics.mean(ksm)})
     bps = bytes_per_step(nx, ny)
-    fps = flops_per_step(nx, ny, fused_smoothing=nx <= 6)
+    fps = flops_per_step(nx, ny, fused_smoothing=nx <= 6, block_fold=nx <= 6 and not tv)
     kernels = {"filter": statistics.mean(kf), "smoother": statistics.mean(ksm)}
     if not tv:
         roof = scan_roofline(nx, ny, T, hbm, which, kernels, bps, fps)

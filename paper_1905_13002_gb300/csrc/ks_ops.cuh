@@ -900,14 +900,20 @@ KS_DEV void first_element(const ModelConst<N, M>& mc, FElem<N>& e) {
 // innovations e_i = y_i - H u - d: the rank-ny combine maps (b, eta) of the
 // running aggregate and of the next element linearly, with coefficients that
 // depend only on the matrices.  BlockCoef holds, for blocks of `ch` steps,
-//   b   = bc + sum_i Bc[i] e_i,     eta = ec + sum_i Ec[i] e_i,
-// and the block's A, C, J.  The scans fold a full block with it in 2 N M FMAs
-// per step instead of one rank-ny combine; blocks that hold a sequence's first
-// step, or a ragged end, fold element by element.
+//   b   = bc + Bs e_0 + sum_{i>0} Bc[i] (y_i - y_0),
+//   eta = ec + Es e_0 + sum_{i>0} Ec[i] (y_i - y_0),
+// with Bs = sum_i Bc[i] and Es = sum_i Ec[i] (the response to one innovation
+// common to all steps, built by the same recursion), and the block's A, C, J.
+// Writing the measurements relative to the block's first one keeps the
+// products small where y is large and the coefficients cancel (eta of a
+// tracking model), as in the element-by-element fold.  The scans fold a full
+// block with it in 2 N M FMAs per step instead of one rank-ny combine; blocks
+// that hold a sequence's first step, or a ragged end, fold element by element.
 template <int N, int M>
 struct alignas(16) BlockCoef {
     float Bc[32][N * M];   // position i: row-major N x M
     float Ec[32][N * M];
+    float Bs[N * M], Es[N * M];   // sums over the positions
     float bc[N], ec[N];
     float A[N * N];
     float C[sym_size(N)];
@@ -958,6 +964,11 @@ KS_DEV void block_coef_warp(const ModelConst<N, M>& mc, int ch, BlockCoef<N, M>*
             for (int q = r; q < M; ++q) s = fmaf(mc.U[q * N + a], mc.Lsi[q * M + r], s);
             Ec[a][r] = s;
         }
+    float Bs[N][M], Es[N][M];   // response to an innovation common to all steps
+#pragma unroll
+    for (int a = 0; a < N; ++a)
+#pragma unroll
+        for (int r = 0; r < M; ++r) { Bs[a][r] = Bc[a][r]; Es[a][r] = Ec[a][r]; }
     bool ok = ch >= 1 && ch <= 32 && (ch & (ch - 1)) == 0;
 #pragma unroll 1
     for (int h = 1; ok && h < ch; h <<= 1) {
@@ -1033,6 +1044,28 @@ KS_DEV void block_coef_warp(const ModelConst<N, M>& mc, int ch, BlockCoef<N, M>*
 #pragma unroll
                 for (int r = 0; r < M; ++r) { Bc[a][r] = nB[a][r]; Ec[a][r] = nE[a][r]; }
         }
+        {   // the common-innovation response: both halves contribute
+            float nB[N][M], nE[N][M];
+#pragma unroll
+            for (int a = 0; a < N; ++a)
+#pragma unroll
+                for (int r = 0; r < M; ++r) {
+                    float sb = Bs[a][r], se = Es[a][r];
+#pragma unroll
+                    for (int c = 0; c < N; ++c) {
+                        sb = fmaf(P[a][c], Bs[c][r], sb);
+                        sb = fmaf(PC[a][c], Es[c][r], sb);
+                        se = fmaf(Rt[c][a], Es[c][r], se);
+                        se = fmaf(-RJ[a][c], Bs[c][r], se);
+                    }
+                    nB[a][r] = sb;
+                    nE[a][r] = se;
+                }
+#pragma unroll
+            for (int a = 0; a < N; ++a)
+#pragma unroll
+                for (int r = 0; r < M; ++r) { Bs[a][r] = nB[a][r]; Es[a][r] = nE[a][r]; }
+        }
         {   // constants (both halves have the same)
             float nb[N], ne[N];
 #pragma unroll
@@ -1090,6 +1123,10 @@ KS_DEV void block_coef_warp(const ModelConst<N, M>& mc, int ch, BlockCoef<N, M>*
     if (lane == 0) {
 #pragma unroll
         for (int a = 0; a < N; ++a) { out->bc[a] = bc[a]; out->ec[a] = ec[a]; }
+#pragma unroll
+        for (int a = 0; a < N; ++a)
+#pragma unroll
+            for (int r = 0; r < M; ++r) { out->Bs[a * M + r] = Bs[a][r]; out->Es[a * M + r] = Es[a][r]; }
 #pragma unroll
         for (int a = 0; a < N; ++a) {
 #pragma unroll

@@ -1458,21 +1458,33 @@ KS_DEV void filter_scan_body(FilterSmem<N, M, NT>& sm, char* dsm, int tile,
             for (int a = 0; a < N * N; ++a) acc.A[a] = bcf->A[a];
 #pragma unroll
             for (int a = 0; a < sym_size(N); ++a) { acc.C[a] = bcf->C[a]; acc.J[a] = bcf->J[a]; }
+            float y0[M], e0[M];
+            load_meas<M>(y, k0, y0);
 #pragma unroll
-            for (int a = 0; a < N; ++a) { acc.b[a] = bcf->bc[a]; acc.eta[a] = bcf->ec[a]; }
-            const ModelConst<N, M>& m1 = *cur.mc;
+            for (int q = 0; q < M; ++q) e0[q] = y0[q] - cur.mc->hud[q];
+#pragma unroll
+            for (int a = 0; a < N; ++a) {
+                float sb = bcf->bc[a], se = bcf->ec[a];
+#pragma unroll
+                for (int q = 0; q < M; ++q) {
+                    sb = fmaf(bcf->Bs[a * M + q], e0[q], sb);
+                    se = fmaf(bcf->Es[a * M + q], e0[q], se);
+                }
+                acc.b[a] = sb;
+                acc.eta[a] = se;
+            }
 #pragma unroll 4
-            for (int i = 0; i < CH; ++i) {
-                float e[M];
-                load_meas<M>(y, k0 + i, e);
+            for (int i = 1; i < CH; ++i) {   // the other steps relative to the first
+                float dy[M];
+                load_meas<M>(y, k0 + i, dy);
 #pragma unroll
-                for (int q = 0; q < M; ++q) e[q] -= m1.hud[q];
+                for (int q = 0; q < M; ++q) dy[q] -= y0[q];
 #pragma unroll
                 for (int a = 0; a < N; ++a)
 #pragma unroll
                     for (int q = 0; q < M; ++q) {
-                        acc.b[a] = fmaf(bcf->Bc[i][a * M + q], e[q], acc.b[a]);
-                        acc.eta[a] = fmaf(bcf->Ec[i][a * M + q], e[q], acc.eta[a]);
+                        acc.b[a] = fmaf(bcf->Bc[i][a * M + q], dy[q], acc.b[a]);
+                        acc.eta[a] = fmaf(bcf->Ec[i][a * M + q], dy[q], acc.eta[a]);
                     }
             }
         } else {

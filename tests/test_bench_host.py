@@ -7,10 +7,13 @@ import bench
 
 def test_flop_model_nx4():
     """Per-step flops of the fused nx = 4, ny = 2 scans (the roofline's
-    algorithmic work): forward 2230 (fold + advance + two measurement
-    elements + Lemma 5 element + fused Lemma 6 fold), reverse 744."""
+    algorithmic work): forward 1402 with the linear block fold (innovation and
+    two 4 x 2 products, advance, measurement element, Lemma 5 element, fused
+    Lemma 6 fold), 2230 when each step is folded by the rank-2 combine instead
+    (time-varying models); reverse 744."""
     f = bench.flops_per_step(4, 2)
-    assert f == {"filter": 2230, "smoother": 744}
+    assert f == {"filter": 1402, "smoother": 744}
+    assert bench.flops_per_step(4, 2, block_fold=False) == {"filter": 2230, "smoother": 744}
     # without the fused smoothing fold the reverse scan builds its elements twice
     g = bench.flops_per_step(4, 2, fused_smoothing=False)
     assert g["filter"] < f["filter"] and g["smoother"] > f["smoother"]
