@@ -897,23 +897,25 @@ KS_DEV void first_element(const ModelConst<N, M>& mc, FElem<N>& e) {
 // J = U^T U (Lemma 3: only b_k and eta_k depend on k), so the fold of a block
 // of l consecutive measurement elements, a_1 (x) ... (x) a_l (Lemma 4), has the
 // same A, C, J for every block, and its (b, eta) is affine in the block's
-// innovations e_i = y_i - H u - d: the rank-ny combine maps (b, eta) of the
-// running aggregate and of the next element linearly, with coefficients that
-// depend only on the matrices.  BlockCoef holds, for blocks of `ch` steps,
-//   b   = bc + Bs e_0 + sum_{i>0} Bc[i] (y_i - y_0),
-//   eta = ec + Es e_0 + sum_{i>0} Ec[i] (y_i - y_0),
-// with Bs = sum_i Bc[i] and Es = sum_i Ec[i] (the response to one innovation
-// common to all steps, built by the same recursion), and the block's A, C, J.
-// Writing the measurements relative to the block's first one keeps the
-// products small where y is large and the coefficients cancel (eta of a
-// tracking model), as in the element-by-element fold.  The scans fold a full
-// block with it in 2 N M FMAs per step instead of one rank-ny combine; blocks
-// that hold a sequence's first step, or a ragged end, fold element by element.
+// measurements: the rank-ny combine maps (b, eta) of the running aggregate and
+// of the next element linearly, with coefficients that depend only on the
+// matrices.  BlockCoef holds, for blocks of `ch` steps,
+//   b   = bc + Bs y_0 + sum_{i>0} Bc[i] (y_i - y_0),
+//   eta = ec + Es y_0 + sum_{i>0} Ec[i] (y_i - y_0),
+// and the block's A, C, J.  Writing the measurements relative to the block's
+// first one keeps the products small where y is large.  Bs (= sum_i Bc[i])
+// then multiplies the large y_0, and the scan adds Bs y_0 to A x_prev, which
+// nearly cancels it in the directions that y tracks; Bs is therefore formed
+// from the block's own A and J rather than summed (see block_coef_warp), so
+// that the cancellation is as exact as in the element-by-element fold.  The
+// scans fold a full block with it in 2 N M FMAs per step instead of one rank-ny
+// combine; blocks that hold a sequence's first step, or a ragged end, fold
+// element by element.
 template <int N, int M>
 struct alignas(16) BlockCoef {
     float Bc[32][N * M];   // position i: row-major N x M
     float Ec[32][N * M];
-    float Bs[N * M], Es[N * M];   // sums over the positions
+    float Bs[N * M], Es[N * M];   // coefficients of y_0
     float bc[N], ec[N];
     float A[N * N];
     float C[sym_size(N)];
@@ -929,14 +931,30 @@ struct alignas(16) BlockCoef {
 // keeps the coefficients of position i within its current block.  With
 // M = I + C_h J_h, P = A_h M^{-1}, R = A_h^T M^{-T}:
 //   b = P (b_L + C_h eta_R) + b_R,   eta = R (eta_R - J_h b_L) + eta_L,
-// so a position of the left half maps as Bc <- P Bc, Ec <- Ec - R J_h Bc, one
-// of the right half as Bc <- P C_h Ec + Bc, Ec <- R Ec, and the constants as
-// bc <- P (bc + C_h ec) + bc, ec <- R (ec - J_h bc) + ec.  A block of one step
-// is the measurement element: A, C, J = U^T U, Bc = K, Ec = U^T L_S^{-1},
-// bc = u, ec = 0.  `ch` = 0 is written when an inverse fails (then the scans
-// fold element by element).
+// so a position of the left half maps as Bc <- P Bc, Ec <- Ec - R J_h Bc, and
+// one of the right half as Bc <- P C_h Ec + Bc, Ec <- R Ec.  A block of one
+// step is the measurement element: A, C, J = U^T U, Bc = K, Ec = U^T L_S^{-1}.
+//
+// The terms in y_0 follow from a noise-free trajectory.  For any state z, the
+// measurements ybar_i = H x_i + d of the trajectory x_i = F x_{i-1} + u from
+// x_prev = z (no noise) are their own prior means, so the block's posterior
+// mean of x_end given x_prev = z is the trajectory's end, and the likelihood's
+// information vector is J z:  b(ybar) = x_end - A z,  eta(ybar) = J z.  With
+// b, eta affine in y and z = L y_0,
+//   b = x_end - A L y_0 + sum_i Bc[i] (y_i - ybar_i),
+//   eta = J L y_0 + sum_i Ec[i] (y_i - ybar_i),
+// where ybar_i = G_i y_0 + g_i, G_i = H F^{i+1} L, g_i = H c_{i+1} + d,
+// c_j = sum_{l<j} F^l u, x_end = F^ch L y_0 + c_ch.  This holds for any L;
+// L = H^T (H H^T)^{-1} puts z on the measured components, and where y follows
+// a stationary direction of F (the positions of a tracking model) then
+// ybar_i = y_0, G_i = I, and Bs = F^ch L - A L, made of the same A the scan
+// multiplies x_prev with.  Lane i forms F^{i+1} L and c_{i+1} from the powers
+// F^h, c_h by the bits of i + 1; the sums over positions are warp reductions.
+// `ch` = 0 is written when an inverse fails (then the scans fold element by
+// element).
 template <int N, int M>
-KS_DEV void block_coef_warp(const ModelConst<N, M>& mc, int ch, BlockCoef<N, M>* __restrict__ out) {
+KS_DEV void block_coef_warp(const ModelConst<N, M>& mc, const float* __restrict__ Hs, int ch,
+                            BlockCoef<N, M>* __restrict__ out) {
     const int lane = threadIdx.x & 31;
     float Ah[N][N], Ch[N][N], Jh[N][N];
 #pragma unroll
@@ -950,9 +968,6 @@ KS_DEV void block_coef_warp(const ModelConst<N, M>& mc, int ch, BlockCoef<N, M>*
             for (int q = 0; q < M; ++q) s = fmaf(mc.U[q * N + a], mc.U[q * N + b], s);
             Jh[a][b] = s;
         }
-    float bc[N], ec[N];
-#pragma unroll
-    for (int a = 0; a < N; ++a) { bc[a] = mc.u[a]; ec[a] = 0.f; }
     float Bc[N][M], Ec[N][M];
 #pragma unroll
     for (int a = 0; a < N; ++a)
@@ -964,11 +979,6 @@ KS_DEV void block_coef_warp(const ModelConst<N, M>& mc, int ch, BlockCoef<N, M>*
             for (int q = r; q < M; ++q) s = fmaf(mc.U[q * N + a], mc.Lsi[q * M + r], s);
             Ec[a][r] = s;
         }
-    float Bs[N][M], Es[N][M];   // response to an innovation common to all steps
-#pragma unroll
-    for (int a = 0; a < N; ++a)
-#pragma unroll
-        for (int r = 0; r < M; ++r) { Bs[a][r] = Bc[a][r]; Es[a][r] = Ec[a][r]; }
     bool ok = ch >= 1 && ch <= 32 && (ch & (ch - 1)) == 0;
 #pragma unroll 1
     for (int h = 1; ok && h < ch; h <<= 1) {
@@ -1044,46 +1054,6 @@ KS_DEV void block_coef_warp(const ModelConst<N, M>& mc, int ch, BlockCoef<N, M>*
 #pragma unroll
                 for (int r = 0; r < M; ++r) { Bc[a][r] = nB[a][r]; Ec[a][r] = nE[a][r]; }
         }
-        {   // the common-innovation response: both halves contribute
-            float nB[N][M], nE[N][M];
-#pragma unroll
-            for (int a = 0; a < N; ++a)
-#pragma unroll
-                for (int r = 0; r < M; ++r) {
-                    float sb = Bs[a][r], se = Es[a][r];
-#pragma unroll
-                    for (int c = 0; c < N; ++c) {
-                        sb = fmaf(P[a][c], Bs[c][r], sb);
-                        sb = fmaf(PC[a][c], Es[c][r], sb);
-                        se = fmaf(Rt[c][a], Es[c][r], se);
-                        se = fmaf(-RJ[a][c], Bs[c][r], se);
-                    }
-                    nB[a][r] = sb;
-                    nE[a][r] = se;
-                }
-#pragma unroll
-            for (int a = 0; a < N; ++a)
-#pragma unroll
-                for (int r = 0; r < M; ++r) { Bs[a][r] = nB[a][r]; Es[a][r] = nE[a][r]; }
-        }
-        {   // constants (both halves have the same)
-            float nb[N], ne[N];
-#pragma unroll
-            for (int a = 0; a < N; ++a) {
-                float sb = bc[a], se = ec[a];
-#pragma unroll
-                for (int c = 0; c < N; ++c) {
-                    sb = fmaf(P[a][c], bc[c], sb);
-                    sb = fmaf(PC[a][c], ec[c], sb);
-                    se = fmaf(Rt[c][a], ec[c], se);
-                    se = fmaf(-RJ[a][c], bc[c], se);
-                }
-                nb[a] = sb;
-                ne[a] = se;
-            }
-#pragma unroll
-            for (int a = 0; a < N; ++a) { bc[a] = nb[a]; ec[a] = ne[a]; }
-        }
         {   // matrix part: A <- P A_h, C <- P C_h A_h^T + C_h, J <- A_h^T M^{-T} J_h A_h + J_h
             float nA[N][N], nC[N][N], nJ[N][N];
 #pragma unroll
@@ -1120,13 +1090,44 @@ KS_DEV void block_coef_warp(const ModelConst<N, M>& mc, int ch, BlockCoef<N, M>*
                 out->Ec[lane][a * M + r] = Ec[a][r];
             }
     }
-    if (lane == 0) {
+    // ---- the lift L = H^T (H H^T)^{-1} (0 if H H^T is singular) and A L, J L
+    float Lf[N][M], AL[N][M], JL[N][M];
+    {
+        float G[M][M], Gi[M][M];
 #pragma unroll
-        for (int a = 0; a < N; ++a) { out->bc[a] = bc[a]; out->ec[a] = ec[a]; }
+        for (int q = 0; q < M; ++q)
+#pragma unroll
+            for (int r = 0; r < M; ++r) {
+                float s = 0.f;
+#pragma unroll
+                for (int c = 0; c < N; ++c) s = fmaf(Hs[q * N + c], Hs[r * N + c], s);
+                G[q][r] = s;
+            }
+        const bool lift = inverse_pp<M>(G, Gi);
 #pragma unroll
         for (int a = 0; a < N; ++a)
 #pragma unroll
-            for (int r = 0; r < M; ++r) { out->Bs[a * M + r] = Bs[a][r]; out->Es[a * M + r] = Es[a][r]; }
+            for (int r = 0; r < M; ++r) {
+                float s = 0.f;
+#pragma unroll
+                for (int q = 0; q < M; ++q) s = fmaf(Hs[q * N + a], Gi[q][r], s);
+                Lf[a][r] = lift ? s : 0.f;
+            }
+#pragma unroll
+        for (int a = 0; a < N; ++a)
+#pragma unroll
+            for (int r = 0; r < M; ++r) {
+                float s = 0.f, t = 0.f;
+#pragma unroll
+                for (int c = 0; c < N; ++c) {
+                    s = fmaf(Ah[a][c], Lf[c][r], s);
+                    t = fmaf(Jh[a][c], Lf[c][r], t);
+                }
+                AL[a][r] = s;
+                JL[a][r] = t;
+            }
+    }
+    if (lane == 0) {
 #pragma unroll
         for (int a = 0; a < N; ++a) {
 #pragma unroll
@@ -1134,6 +1135,145 @@ KS_DEV void block_coef_warp(const ModelConst<N, M>& mc, int ch, BlockCoef<N, M>*
 #pragma unroll
             for (int b = 0; b <= a; ++b) { out->C[sidx(a, b)] = Ch[a][b]; out->J[sidx(a, b)] = Jh[a][b]; }
         }
+    }
+    // ---- lane i: V = F^{i+1} L and c = c_{i+1}, from (F^h, c_h) by the bits of i + 1
+    float V[N][M], cv[N];
+    {
+        float Fp[N][N], cp[N];
+#pragma unroll
+        for (int a = 0; a < N; ++a) {
+            cv[a] = 0.f;
+            cp[a] = mc.u[a];
+#pragma unroll
+            for (int b = 0; b < N; ++b) Fp[a][b] = mc.F[a * N + b];
+#pragma unroll
+            for (int r = 0; r < M; ++r) V[a][r] = Lf[a][r];
+        }
+        const int j = lane + 1;
+#pragma unroll 1
+        for (int h = 1; h <= ch; h <<= 1) {
+            if (j & h) {
+                float nV[N][M], nc[N];
+#pragma unroll
+                for (int a = 0; a < N; ++a) {
+                    float s = cp[a];
+#pragma unroll
+                    for (int c = 0; c < N; ++c) s = fmaf(Fp[a][c], cv[c], s);
+                    nc[a] = s;
+#pragma unroll
+                    for (int r = 0; r < M; ++r) {
+                        float t = 0.f;
+#pragma unroll
+                        for (int c = 0; c < N; ++c) t = fmaf(Fp[a][c], V[c][r], t);
+                        nV[a][r] = t;
+                    }
+                }
+#pragma unroll
+                for (int a = 0; a < N; ++a) {
+                    cv[a] = nc[a];
+#pragma unroll
+                    for (int r = 0; r < M; ++r) V[a][r] = nV[a][r];
+                }
+            }
+            if (2 * h <= ch) {   // (F^2h, c_2h) = (F^h F^h, F^h c_h + c_h)
+                float nF[N][N], nc[N];
+#pragma unroll
+                for (int a = 0; a < N; ++a) {
+                    float s = cp[a];
+#pragma unroll
+                    for (int c = 0; c < N; ++c) s = fmaf(Fp[a][c], cp[c], s);
+                    nc[a] = s;
+#pragma unroll
+                    for (int b = 0; b < N; ++b) {
+                        float t = 0.f;
+#pragma unroll
+                        for (int c = 0; c < N; ++c) t = fmaf(Fp[a][c], Fp[c][b], t);
+                        nF[a][b] = t;
+                    }
+                }
+#pragma unroll
+                for (int a = 0; a < N; ++a) {
+                    cp[a] = nc[a];
+#pragma unroll
+                    for (int b = 0; b < N; ++b) Fp[a][b] = nF[a][b];
+                }
+            }
+        }
+    }
+    // ---- this position's ybar_i - y_0 = (G_i - I) y_0 + g_i and its terms
+    const bool in = lane < ch;
+    float tB[N][M], tE[N][M], tb[N], te[N];
+    {
+        float Gm[M][M], g[M];
+#pragma unroll
+        for (int q = 0; q < M; ++q) {
+            float s = mc.hud[q];   // H c_{i+1} + d = H u + d + H (c_{i+1} - u)
+#pragma unroll
+            for (int c = 0; c < N; ++c) s = fmaf(Hs[q * N + c], cv[c] - mc.u[c], s);
+            g[q] = s;
+#pragma unroll
+            for (int r = 0; r < M; ++r) {
+                float t = (q == r) ? -1.f : 0.f;
+#pragma unroll
+                for (int c = 0; c < N; ++c) t = fmaf(Hs[q * N + c], V[c][r], t);
+                Gm[q][r] = t;
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < N; ++a) {
+            float sb = 0.f, se = 0.f;
+#pragma unroll
+            for (int q = 0; q < M; ++q) {
+                sb = fmaf(Bc[a][q], g[q], sb);
+                se = fmaf(Ec[a][q], g[q], se);
+            }
+            tb[a] = in ? sb : 0.f;
+            te[a] = in ? se : 0.f;
+#pragma unroll
+            for (int r = 0; r < M; ++r) {
+                float s = 0.f, t = 0.f;
+#pragma unroll
+                for (int q = 0; q < M; ++q) {
+                    s = fmaf(Bc[a][q], Gm[q][r], s);
+                    t = fmaf(Ec[a][q], Gm[q][r], t);
+                }
+                tB[a][r] = in ? s : 0.f;
+                tE[a][r] = in ? t : 0.f;
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int a = 0; a < N; ++a) {
+            tb[a] += __shfl_xor_sync(0xffffffffu, tb[a], o);
+            te[a] += __shfl_xor_sync(0xffffffffu, te[a], o);
+#pragma unroll
+            for (int r = 0; r < M; ++r) {
+                tB[a][r] += __shfl_xor_sync(0xffffffffu, tB[a][r], o);
+                tE[a][r] += __shfl_xor_sync(0xffffffffu, tE[a][r], o);
+            }
+        }
+    }
+    // ---- x_end = F^ch L y_0 + c_ch from the block's last position
+    const int last = (ch >= 1 && ch <= 32) ? ch - 1 : 0;
+#pragma unroll
+    for (int a = 0; a < N; ++a) {
+        const float w = __shfl_sync(0xffffffffu, cv[a], last);
+        if (lane == 0) {
+            out->bc[a] = w - tb[a];
+            out->ec[a] = -te[a];
+        }
+#pragma unroll
+        for (int r = 0; r < M; ++r) {
+            const float W = __shfl_sync(0xffffffffu, V[a][r], last);
+            if (lane == 0) {
+                out->Bs[a * M + r] = (W - AL[a][r]) - tB[a][r];
+                out->Es[a * M + r] = JL[a][r] - tE[a][r];
+            }
+        }
+    }
+    if (lane == 0) {
         out->ch = ok ? ch : 0;
     }
 }

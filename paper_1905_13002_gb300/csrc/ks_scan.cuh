@@ -610,7 +610,7 @@ KS_DEV void prep_body(char* prep_dsm, int sg, int nseg, const float* __restrict_
         if constexpr (N <= 6) {   // register-path sizes only
             if (coef != nullptr) {   // the block-fold coefficients, while warp 1 builds the k = 1 element
                 __syncwarp();
-                block_coef_warp<N, M>(mc, ch, coef + sg);
+                block_coef_warp<N, M>(mc, &p.H[0][0], ch, coef + sg);
             }
         }
     } else if (warp == 1) {
@@ -1458,17 +1458,15 @@ KS_DEV void filter_scan_body(FilterSmem<N, M, NT>& sm, char* dsm, int tile,
             for (int a = 0; a < N * N; ++a) acc.A[a] = bcf->A[a];
 #pragma unroll
             for (int a = 0; a < sym_size(N); ++a) { acc.C[a] = bcf->C[a]; acc.J[a] = bcf->J[a]; }
-            float y0[M], e0[M];
+            float y0[M];
             load_meas<M>(y, k0, y0);
-#pragma unroll
-            for (int q = 0; q < M; ++q) e0[q] = y0[q] - cur.mc->hud[q];
 #pragma unroll
             for (int a = 0; a < N; ++a) {
                 float sb = bcf->bc[a], se = bcf->ec[a];
 #pragma unroll
                 for (int q = 0; q < M; ++q) {
-                    sb = fmaf(bcf->Bs[a * M + q], e0[q], sb);
-                    se = fmaf(bcf->Es[a * M + q], e0[q], se);
+                    sb = fmaf(bcf->Bs[a * M + q], y0[q], sb);
+                    se = fmaf(bcf->Es[a * M + q], y0[q], se);
                 }
                 acc.b[a] = sb;
                 acc.eta[a] = se;

@@ -38,12 +38,16 @@ def pytest_terminal_summary(terminalreporter):
         return
     worst = {}
     for tid, e in parity.RECORD:
-        w = worst.setdefault(tid, {"rel": 0.0, "sd": 0.0, "sdx": 0.0})
+        w = worst.setdefault(tid, {"rel": 0.0, "sd": 0.0, "sdx": 0.0, "where": ""})
         w["rel"] = max(w["rel"], *(v for k, v in e.items() if k in ("fmean", "fcov", "smean", "scov", "mean")))
         w["sd"] = max(w["sd"], *(v for k, v in e.items() if k.endswith("_sd")))
-        w["sdx"] = max(w["sdx"], *(v for k, v in e.items() if k.endswith("_sdx")))
+        sdx = max(v for k, v in e.items() if k.endswith("_sdx"))
+        if sdx >= w["sdx"]:
+            w["sdx"], w["where"] = sdx, e.get("where", "")
     tr = terminalreporter
     tr.write_sep("-", "parity summary (max over steps and checks)")
     tr.write_line(f"{'rel':>9} {'sd':>9} {'sd-bound':>9}  test")
     for tid, w in sorted(worst.items(), key=lambda kv: -kv[1]["sdx"]):
         tr.write_line(f"{w['rel']:9.2e} {w['sd']:9.2e} {w['sdx']:9.3f}  {tid}")
+        if w["sdx"] > 0.8 and w["where"]:
+            tr.write_line(f"{'':30}{w['where']}")

@@ -84,8 +84,19 @@ def sd_err(got, ref, Pref):
 
 
 def sd_excess(got, ref, Pref, sd_tol=SD_TOL, ulp_tol=ULP_TOL):
+    return sd_worst(got, ref, Pref, sd_tol, ulp_tol)[0]
+
+
+def sd_worst(got, ref, Pref, sd_tol=SD_TOL, ulp_tol=ULP_TOL):
+    """(sd_excess, step of the maximum, error there in posterior sd, one-ulp
+    floor there in posterior sd): tells a failure in the sd regime (floor
+    small) from one in the ulp regime."""
     err, floor = sd_terms(got, ref, Pref)
-    return float((err / (sd_tol + ulp_tol * floor)).max())
+    use = err / (sd_tol + ulp_tol * floor)
+    if not use.size:
+        return 0.0, 0, 0.0, 0.0
+    k = int(np.argmax(use))
+    return float(use[k]), k, float(err[k]), float(floor[k])
 
 
 def cov_err(got, ref):
@@ -111,8 +122,12 @@ def sd_errors(gpu, ref):
     """Posterior-sd errors of both means: max sd_err and max sd_excess."""
     fm, _, sm, _ = (_np(x) for x in gpu)
     rfm, rfP, rsm, rsP = ref
+    fx, fk, fe, ff = sd_worst(fm, rfm, rfP)
+    sx, sk, se, sf = sd_worst(sm, rsm, rsP)
     return {"fmean_sd": sd_err(fm, rfm, rfP), "smean_sd": sd_err(sm, rsm, rsP),
-            "fmean_sdx": sd_excess(fm, rfm, rfP), "smean_sdx": sd_excess(sm, rsm, rsP)}
+            "fmean_sdx": fx, "smean_sdx": sx,
+            "where": f"nx {fm.shape[-1]}, fmean step {fk}/{len(fm)}: {fe:.2e} sd, ulp {ff:.2e} sd; "
+                     f"smean step {sk}/{len(sm)}: {se:.2e} sd, ulp {sf:.2e} sd"}
 
 
 def _record(e):
