@@ -319,11 +319,13 @@ def main():
 
 
 def block_length(ks, nx: int, T: int) -> dict:
-    """Steps per thread the library uses for this call and where the rule
-    came from (the tuner's cache for this device, or the built-in table)."""
+    """Steps per thread the library uses for this call, whether full blocks
+    go through the linear block fold, and where the rule came from (the
+    tuner's cache for this device, or the built-in table)."""
     from paper_1905_13002_gb300 import tune
     src = os.path.relpath(tune.APPLIED, ROOT) if tune.APPLIED else "built-in table"
-    return {"steps_per_thread": ks.chunk_steps(nx, T) if nx <= 6 else None, "rules": src}
+    return {"steps_per_thread": ks.chunk_steps(nx, T) if nx <= 6 else None,
+            "block_fold": bool(ks.chunk_fold(nx, T)) if nx <= 6 else False, "rules": src}
 
 
 def launches_per_call(nx: int, T: int) -> int:
@@ -505,10 +507,12 @@ def run_single(args, rank, world, local, mode):
         roof = tv_roofline(nx, ny, T, hbm, which, {"elements": statistics.mean(kel), "filter": statistics.mean(kf),
                                                    "smoother": statistics.mean(ksm)})
     bps = bytes_per_step(nx, ny)
-    fps = flops_per_step(nx, ny, fused_smoothing=nx <= 6, block_fold=nx <= 6 and not tv)
+    fps = flops_per_step(nx, ny, fused_smoothing=nx <= 6,
+                         block_fold=nx <= 6 and not tv and ks.chunk_fold(nx, T) == 1)
     kernels = {"filter": statistics.mean(kf), "smoother": statistics.mean(ksm)}
     if not tv:
         roof = scan_roofline(nx, ny, T, hbm, which, kernels, bps, fps)
+        roof["prep_ms"] = round(statistics.mean(kel), 4)   # model constants (and block-fold coefficients)
 
     # the batched workload beside it (the metric's "batched FP32 scan vs plain
     # scan"): one mixed-size launch per scan, and the plain per-sequence scan
@@ -892,7 +896,7 @@ def measure_batched(args, rank, world, dev, full: bool) -> dict:
     nbytes = nflops = 0
     for g in groups:
         bps = bytes_per_step(g["nx"], g["nx"] // 2)
-        fps = flops_per_step(g["nx"], g["nx"] // 2)
+        fps = flops_per_step(g["nx"], g["nx"] // 2, block_fold=ks.chunk_fold(0, total) == 1)
         nbytes += (bps["filter"] + bps["smoother"]) * g["T"]
         nflops += (fps["filter"] + fps["smoother"]) * g["T"]
     dur = ms / 1e3

@@ -220,31 +220,37 @@ int ks_smooth_batch(const ks_model_batch *mb, const float *y, int64_t total_T, v
 
 /*
  * Block length of the fused scans (Section III-C: each thread folds a block
- * of l consecutive steps; a tile is 128 threads).  The nx <= 6 entry points
- * ks_smooth, ks_smooth_traced, ks_smooth_batch and ks_smooth_batched are
- * compiled for l in {4, 8, 16, 32} and pick one per call from the call's
- * total number of steps T.  The built-in choice is 4 below 96 Ki steps, 8
- * below 192 Ki, 16 below 640 Ki and 32 above.  ks_set_chunk_rules replaces it
- * for one state size (nx = 2, 4 or 6; nx = 0: ks_smooth_batched) by `count`
- * rules with strictly increasing T_below: a call uses the steps of the first
- * rule whose T_below exceeds its T, else the last rule's.  count = 0 restores
- * the built-in choice.  steps must be 4, 8, 16 or 32 and count <= 16
- * (KS_EINVAL otherwise).  The table is process state of the library (host
- * memory, guarded by a mutex); results do not depend on it, only speed.  The
- * project's tuner measures the table on the device (package module tune.py).
- * ks_chunk_steps returns the steps per thread a call of T steps would use
+ * of l consecutive steps; a tile is 128 threads) and how a block is folded.
+ * The nx <= 6 entry points ks_smooth, ks_smooth_traced, ks_smooth_batch and
+ * ks_smooth_batched are compiled for l in {4, 8, 16, 32} and pick one per
+ * call from the call's total number of steps T.  For a time-invariant model
+ * a full block can also be folded through per-position coefficients built
+ * once per call and model (the linear block fold: Lemma 3's A, C, J are the
+ * same at every step, so a block's (b, eta) is affine in its measurements)
+ * instead of element by element; `fold` = 1 selects it.  The built-in choice
+ * is 4 steps below 96 Ki steps, 8 below 192 Ki, 16 below 640 Ki and 32 above,
+ * folding with the coefficients at 32 steps for single-size calls.
+ * ks_set_chunk_rules replaces it for one state size (nx = 2, 4 or 6; nx = 0:
+ * ks_smooth_batched) by `count` rules with strictly increasing T_below: a
+ * call uses the first rule whose T_below exceeds its T, else the last one.
+ * count = 0 restores the built-in choice.  steps must be 4, 8, 16 or 32, fold
+ * 0 or 1, and count <= 16 (KS_EINVAL otherwise).  The table is process state
+ * of the library (host memory, guarded by a mutex); results agree to FP32
+ * rounding whichever entry runs.  The project's tuner measures the table on
+ * the device (package module tune.py).  ks_chunk_steps and ks_chunk_fold
+ * return the steps per thread and the fold flag a call of T steps would use
  * (0 for an nx without a table).
  */
 typedef struct ks_chunk_rule {
     int64_t T_below;
     int32_t steps;
-    int32_t reserved;
+    int32_t fold;
 } ks_chunk_rule;
 int ks_set_chunk_rules(int nx, int count, const ks_chunk_rule *rules);
 int ks_chunk_steps(int nx, int64_t T);
+int ks_chunk_fold(int nx, int64_t T);
 
 /*
- * Batched end to end over sequences of different state sizes, in one/*
  * Batched end to end over sequences of different state sizes, in one
  * preparation, one forward-scan and one reverse-scan launch.  The sequences
  * come in G groups (1 <= G <= 3), one per state size, with distinct

@@ -64,7 +64,7 @@ class _KsBatchGroup(ctypes.Structure):
 
 
 class _KsChunkRule(ctypes.Structure):
-    _fields_ = [("T_below", ctypes.c_int64), ("steps", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+    _fields_ = [("T_below", ctypes.c_int64), ("steps", ctypes.c_int32), ("fold", ctypes.c_int32)]
 
 
 class _KsHmm(ctypes.Structure):
@@ -110,6 +110,7 @@ def lib():
             "ks_workspace_bytes_batched": ([i32, ctypes.POINTER(_KsBatchGroup)], sz),
             "ks_set_chunk_rules": ([i32, i32, ctypes.POINTER(_KsChunkRule)], i32),
             "ks_chunk_steps": ([i32, i64], i32),
+            "ks_chunk_fold": ([i32, i64], i32),
             "ks_smooth_batched": ([i32, ctypes.POINTER(_KsBatchGroup), vp, sz, vp], i32),
             "ks_filter_combine_batch": ([i32, i64, vp, vp, vp, vp, sz, vp], i32),
             "ks_smoother_combine_batch": ([i32, i64, vp, vp, vp, vp, sz, vp], i32),
@@ -135,16 +136,23 @@ def lib():
 
 def set_chunk_rules(nx: int, rules) -> None:
     """Block-length table of one state size (``ks_set_chunk_rules``): rules
-    are (T_below, steps) pairs; an empty list restores the built-in table."""
+    are (T_below, steps, fold) triples (fold 1: the linear block fold); an
+    empty list restores the built-in table."""
     arr = (_KsChunkRule * max(len(rules), 1))()
-    for i, (tb, steps) in enumerate(rules):
-        arr[i].T_below, arr[i].steps = int(tb), int(steps)
+    for i, (tb, steps, fold) in enumerate(rules):
+        arr[i].T_below, arr[i].steps, arr[i].fold = int(tb), int(steps), int(fold)
     _check(lib().ks_set_chunk_rules(nx, len(rules), arr), "ks_set_chunk_rules")
 
 
 def chunk_steps(nx: int, T: int) -> int:
     """Steps per thread a call of T steps of state size nx uses (0: mixed batches)."""
     return int(lib().ks_chunk_steps(nx, T))
+
+
+def chunk_fold(nx: int, T: int) -> int:
+    """1 if a call of T steps of state size nx folds full blocks with the
+    linear block fold, else 0."""
+    return int(lib().ks_chunk_fold(nx, T))
 
 
 def _check(rc: int, what: str):

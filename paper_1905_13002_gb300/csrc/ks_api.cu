@@ -37,7 +37,7 @@ constexpr int kMaxRules = 16;
 struct RuleSet {
     int count = 0;   // 0: built-in table
     int64_t below[kMaxRules];
-    int index[kMaxRules];
+    int choice[kMaxRules];   // chunk index | fold << 2
 };
 std::mutex g_rules_mutex;
 RuleSet g_rules[4];
@@ -46,16 +46,16 @@ int rule_slot(int nx) { return nx == 0 ? 0 : nx == 2 ? 1 : nx == 4 ? 2 : nx == 6
 int steps_index(int steps) { return steps == 4 ? 0 : steps == 8 ? 1 : steps == 16 ? 2 : steps == 32 ? 3 : -1; }
 }  // namespace
 
-int chunk_index_for(int nx, int64_t T) {
+int chunk_choice(int nx, int64_t T) {
     const int sl = rule_slot(nx);
     if (sl >= 0) {
         std::lock_guard<std::mutex> lock(g_rules_mutex);
         const RuleSet& r = g_rules[sl];
         for (int i = 0; i < r.count; ++i)
-            if (T < r.below[i]) return r.index[i];
-        if (r.count > 0) return r.index[r.count - 1];
+            if (T < r.below[i]) return r.choice[i];
+        if (r.count > 0) return r.choice[r.count - 1];
     }
-    return builtin_chunk_index(T);
+    return builtin_chunk_index(T) | (builtin_fold(nx, T) ? 4 : 0);
 }
 
 extern const MixedVariant kMixed4, kMixed8, kMixed16, kMixed32;
@@ -253,7 +253,8 @@ int ks_smooth_batched(int G, const ks_batch_group* groups, void* ws, size_t ws_b
     int rc = mixed_slots(G, groups, true, slot, &total);
     if (rc) return rc;
     if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) != 0) return KS_EINVAL;
-    return kMixed[chunk_index_for(0, total)]->run(groups, slot, ws, ws_bytes, static_cast<cudaStream_t>(stream));
+    const int c = chunk_choice(0, total);
+    return kMixed[c & 3]->run(groups, slot, ws, ws_bytes, static_cast<cudaStream_t>(stream), (c & 4) != 0);
 }
 
 int ks_set_chunk_rules(int nx, int count, const ks_chunk_rule* rules) {
@@ -264,8 +265,9 @@ int ks_set_chunk_rules(int nx, int count, const ks_chunk_rule* rules) {
     for (int i = 0; i < count; ++i) {
         const int ix = steps_index(rules[i].steps);
         if (ix < 0 || rules[i].T_below < 1 || (i > 0 && rules[i].T_below <= rules[i - 1].T_below)) return KS_EINVAL;
+        if (rules[i].fold != 0 && rules[i].fold != 1) return KS_EINVAL;
         r.below[i] = rules[i].T_below;
-        r.index[i] = ix;
+        r.choice[i] = ix | (rules[i].fold << 2);
     }
     std::lock_guard<std::mutex> lock(g_rules_mutex);
     g_rules[sl] = r;
@@ -276,6 +278,11 @@ int ks_chunk_steps(int nx, int64_t T) {
     if (rule_slot(nx) < 0 || T < 1) return 0;
     static const int kSteps[4] = {4, 8, 16, 32};
     return kSteps[chunk_index_for(nx, T)];
+}
+
+int ks_chunk_fold(int nx, int64_t T) {
+    if (rule_slot(nx) < 0 || T < 1) return 0;
+    return (chunk_choice(nx, T) & 4) ? 1 : 0;
 }
 
 int ks_status(void* ws, void* stream) {

@@ -52,10 +52,11 @@ struct VTable {
 // The fused end-to-end entry points of one steps-per-thread choice.
 struct ChunkVariant {
     Layout (*layout)(int64_t T, int B);
+    // the last argument: fold full blocks with the linear block fold
     int (*smooth)(const ks_model*, const float*, int64_t, void*, size_t, float*, float*, float*, float*,
-                  cudaStream_t, void* const*);
+                  cudaStream_t, void* const*, bool);
     int (*smooth_batch)(const ks_model_batch*, const float*, int64_t, void*, size_t, float*, float*, float*,
-                        float*, cudaStream_t);
+                        float*, cudaStream_t, bool);
 };
 
 inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
@@ -183,14 +184,16 @@ struct Impl {
     }
 
     // Model constants (and the k = 1 element when y is given, with the block
-    // fold's coefficients when the layout has room for them); also zeroes the
-    // scans' tile counters and flags, which every scan launch needs.
-    static int prep(const ks_model* m, const float* y, void* ws, const Layout& L, cudaStream_t st) {
+    // fold's coefficients when `fold` is set and the layout has room for
+    // them); also zeroes the scans' tile counters and flags, which every scan
+    // launch needs.
+    static int prep(const ks_model* m, const float* y, void* ws, const Layout& L, cudaStream_t st,
+                    bool fold = false) {
         uint32_t* z = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + L.off_flags);
         prep_kernel<N, M><<<1, kPrepThreads, prep_smem(), st>>>(m->F, m->u, m->Q, m->H, m->d, m->R, m->m0, m->P0, y,
                                              mconst(ws, L), status(ws), z, (int)(L.flags_bytes / 4), nullptr,
-                                             L.T, status(ws) + HDR_FIRST_TILE, (y && L.off_coef) ? coef(ws, L) : nullptr,
-                                             FCH);
+                                             L.T, status(ws) + HDR_FIRST_TILE,
+                                             (fold && y && L.off_coef) ? coef(ws, L) : nullptr, FCH);
         return launch_status();
     }
 
@@ -358,6 +361,12 @@ struct Impl {
 
     static int smooth(const ks_model* m, const float* y, int64_t T, void* ws, size_t ws_bytes, float* fm,
                       float* fc, float* sm, float* sc, cudaStream_t st, void* const* ev) {
+        return smooth_v(m, y, T, ws, ws_bytes, fm, fc, sm, sc, st, ev, FCH == 32);
+    }
+    // `fold`: full blocks of a time-invariant model go through the linear
+    // block fold (coefficients built by the preparation), else element by element.
+    static int smooth_v(const ks_model* m, const float* y, int64_t T, void* ws, size_t ws_bytes, float* fm,
+                        float* fc, float* sm, float* sc, cudaStream_t st, void* const* ev, bool fold) {
         if (m && m->time_varying) return smooth_tv(m, y, T, ws, ws_bytes, fm, fc, sm, sc, st, ev);
         const Layout L = layout(T);
         const bool own = (fm == nullptr) || (fc == nullptr);
@@ -373,10 +382,10 @@ struct Impl {
             return KS_EINVAL;
         }
         if ((rc = record(ev, 0, st))) return rc;
-        if ((rc = prep(m, y, ws, L, st))) return rc;
+        if ((rc = prep(m, y, ws, L, st, fold))) return rc;
         if ((rc = record(ev, 1, st))) return rc;
-        if ((rc = launch_filter_fused<false>(ws, L, y, fm, fc, Segs<N, M>{nullptr, nullptr, 1, coef(ws, L)}, st)))
-            return rc;
+        const Segs<N, M> segs{nullptr, nullptr, 1, fold ? coef(ws, L) : nullptr};
+        if ((rc = launch_filter_fused<false>(ws, L, y, fm, fc, segs, st))) return rc;
         if ((rc = record(ev, 2, st))) return rc;
         if (!filter_only && (rc = launch_smoother<true, false>(ws, L, fm, fc, sm, sc, no_segs(), st))) return rc;
         return record(ev, 3, st);
@@ -385,6 +394,10 @@ struct Impl {
     // B sequences laid end to end (offsets in mb->offsets), T steps in total.
     static int smooth_batch(const ks_model_batch* mb, const float* y, int64_t T, void* ws, size_t ws_bytes,
                             float* fm, float* fc, float* sm, float* sc, cudaStream_t st) {
+        return smooth_batch_v(mb, y, T, ws, ws_bytes, fm, fc, sm, sc, st, false);
+    }
+    static int smooth_batch_v(const ks_model_batch* mb, const float* y, int64_t T, void* ws, size_t ws_bytes,
+                              float* fm, float* fc, float* sm, float* sc, cudaStream_t st, bool fold) {
         if (!mb || !mb->F || !mb->Q || !mb->H || !mb->R || !mb->m0 || !mb->P0 || !mb->offsets)
             return KS_EINVAL;
         if (mb->B < 1 || mb->B > T || T < 1 || T > 0x7fffffffLL) return KS_EINVAL;
@@ -396,10 +409,11 @@ struct Impl {
         uint32_t* z = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + L.off_flags);
         prep_kernel<N, M><<<mb->B, kPrepThreads, prep_smem(), st>>>(mb->F, mb->u, mb->Q, mb->H, mb->d, mb->R, mb->m0, mb->P0, y,
                                                  mconst(ws, L), status(ws), z, (int)(L.flags_bytes / 4),
-                                                 mb->offsets, T, status(ws) + HDR_FIRST_TILE, coef(ws, L), FCH);
+                                                 mb->offsets, T, status(ws) + HDR_FIRST_TILE,
+                                                 fold ? coef(ws, L) : nullptr, FCH);
         int rc = launch_status();
         if (rc) return rc;
-        const Segs<N, M> segs{mconst(ws, L), mb->offsets, mb->B, coef(ws, L)};
+        const Segs<N, M> segs{mconst(ws, L), mb->offsets, mb->B, fold ? coef(ws, L) : nullptr};
         if ((rc = launch_filter_fused<true>(ws, L, y, fm, fc, segs, st))) return rc;
         return launch_smoother<true, true>(ws, L, fm, fc, sm, sc, segs, st);
     }
@@ -473,7 +487,7 @@ struct Impl {
         return VTable{N, M, &layout, &build_elements, &filter_scan, &smooth_scan, &smooth, &smooth_batch,
                       &fcomb_batch, &scomb_batch, &agg_bytes, &faggregate, &saggregate, &tv_bytes};
     }
-    static constexpr ChunkVariant chunk_variant() { return ChunkVariant{&layout, &smooth, &smooth_batch}; }
+    static constexpr ChunkVariant chunk_variant() { return ChunkVariant{&layout, &smooth_v, &smooth_batch_v}; }
 };
 
 // Steps per thread of the fused smooth / smooth_batch scans, picked from
@@ -489,10 +503,17 @@ inline int builtin_chunk_index(int64_t T) {
     return T < 96 * 1024 ? 0 : T < 192 * 1024 ? 1 : T < 640 * 1024 ? 2 : 3;
 }
 
-// Chunk index (0..3 for 4, 8, 16, 32 steps per thread) of a call over T steps
-// of state size nx (2, 4 or 6; 0: mixed-size batches), from the table set by
-// ks_set_chunk_rules, else the built-in one (ks_api.cu).
-int chunk_index_for(int nx, int64_t T);
+// Whether the built-in table folds full blocks with the linear block fold:
+// single-size calls with 32 steps per thread (where the per-call coefficient
+// build is small against the scans), not the mixed-size launch.
+inline bool builtin_fold(int nx, int64_t T) { return nx != 0 && builtin_chunk_index(T) == 3; }
+
+// Choice for a call over T steps of state size nx (2, 4 or 6; 0: mixed-size
+// batches), from the table set by ks_set_chunk_rules, else the built-in one
+// (ks_api.cu): bits 0-1 the chunk index (0..3 for 4, 8, 16, 32 steps per
+// thread), bit 2 the block-fold flag.
+int chunk_choice(int nx, int64_t T);
+inline int chunk_index_for(int nx, int64_t T) { return chunk_choice(nx, T) & 3; }
 
 // Per-(nx, ny) table of the four chunk variants; each instantiation file
 // defines it (the 4-, 8- and 16-step variants compile in their own units).
@@ -519,11 +540,13 @@ struct Tuned {
     }
     static int smooth(const ks_model* m, const float* y, int64_t T, void* ws, size_t ws_bytes, float* fm,
                       float* fc, float* sm, float* sc, cudaStream_t st, void* const* ev) {
-        return ChunkTable<N, M>::v[chunk_index_for(N, T)]->smooth(m, y, T, ws, ws_bytes, fm, fc, sm, sc, st, ev);
+        const int c = chunk_choice(N, T);
+        return ChunkTable<N, M>::v[c & 3]->smooth(m, y, T, ws, ws_bytes, fm, fc, sm, sc, st, ev, (c & 4) != 0);
     }
     static int smooth_batch(const ks_model_batch* mb, const float* y, int64_t T, void* ws, size_t ws_bytes,
                             float* fm, float* fc, float* sm, float* sc, cudaStream_t st) {
-        return ChunkTable<N, M>::v[chunk_index_for(N, T)]->smooth_batch(mb, y, T, ws, ws_bytes, fm, fc, sm, sc, st);
+        const int c = chunk_choice(N, T);
+        return ChunkTable<N, M>::v[c & 3]->smooth_batch(mb, y, T, ws, ws_bytes, fm, fc, sm, sc, st, (c & 4) != 0);
     }
     static size_t tv_bytes(int64_t T) { return layout(T, 1).bytes_elements; }
     static constexpr VTable vtable() {

@@ -213,7 +213,7 @@ struct Mixed {
     }
 
     template <int N, int M>
-    static MixedGroup<N, M> group(const ks_batch_group* gs, int slot, char* ws, size_t base) {
+    static MixedGroup<N, M> group(const ks_batch_group* gs, int slot, char* ws, size_t base, bool fold) {
         MixedGroup<N, M> o;
         if (slot < 0) return o;
         const ks_batch_group& g = gs[slot];
@@ -226,8 +226,8 @@ struct Mixed {
         o.F = mb.F; o.u = mb.u; o.Q = mb.Q; o.H = mb.H; o.d = mb.d; o.R = mb.R;
         o.m0 = mb.m0; o.P0 = mb.P0;
         o.segs = Segs<N, M>{reinterpret_cast<const ModelConst<N, M>*>(b + L.off_const), mb.offsets, mb.B,
-                            reinterpret_cast<const BlockCoef<N, M>*>(b + L.off_coef)};
-        o.ch = CH;
+                            fold ? reinterpret_cast<const BlockCoef<N, M>*>(b + L.off_coef) : nullptr};
+        o.ch = fold ? CH : 0;
         o.y = g.y;
         o.fmean = g.fmean; o.fcov = g.fcov; o.smean = g.smean; o.scov = g.scov;
         uint32_t* status = reinterpret_cast<uint32_t*>(ws);
@@ -256,13 +256,14 @@ struct Mixed {
         return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess;
     }
 
-    static int run(const ks_batch_group* gs, const int (&slot)[3], void* ws, size_t ws_bytes, cudaStream_t st) {
+    static int run(const ks_batch_group* gs, const int (&slot)[3], void* ws, size_t ws_bytes, cudaStream_t st,
+                   bool fold) {
         size_t base[3];
         if (regions(gs, slot, base) > ws_bytes) return KS_EINVAL;
         char* w = static_cast<char*>(ws);
-        const MG6 g6 = group<6, 3>(gs, slot[0], w, base[0]);
-        const MG4 g4 = group<4, 2>(gs, slot[1], w, base[1]);
-        const MG2 g2 = group<2, 1>(gs, slot[2], w, base[2]);
+        const MG6 g6 = group<6, 3>(gs, slot[0], w, base[0], fold);
+        const MG4 g4 = group<4, 2>(gs, slot[1], w, base[1], fold);
+        const MG2 g2 = group<2, 1>(gs, slot[2], w, base[2], fold);
         const MixedQueue q{reinterpret_cast<uint32_t*>(w + kMixedQueueOff),
                            reinterpret_cast<uint32_t*>(w + kMixedQueueOff + 4),
                            reinterpret_cast<uint32_t*>(w + kMixedQueueOff + 8), reinterpret_cast<uint32_t*>(w)};
@@ -289,7 +290,7 @@ struct Mixed {
 // Per-chunk-length entry points (ks_mixed{4,8,16,32}.cu).
 struct MixedVariant {
     size_t (*regions)(const ks_batch_group*, const int (&)[3], size_t (&)[3]);
-    int (*run)(const ks_batch_group*, const int (&)[3], void*, size_t, cudaStream_t);
+    int (*run)(const ks_batch_group*, const int (&)[3], void*, size_t, cudaStream_t, bool fold);
 };
 template <int CH>
 constexpr MixedVariant mixed_variant() { return MixedVariant{&Mixed<CH>::regions, &Mixed<CH>::run}; }

@@ -1,19 +1,24 @@
 """Tuner of the fused scans' block length (Section III-C's block-level
-elements: each thread folds l consecutive steps, a tile is 128 threads).
+elements: each thread folds l consecutive steps, a tile is 128 threads) and
+of how a block is folded.
 
 The nx <= 6 kernels are compiled for l in {4, 8, 16, 32}; short inputs need
 short blocks to fill the 152 SMs, long inputs gain from long ones (less
-per-block look-back and prefix work per step).  The library picks l per call
-from the call's total number of steps through a rule table per state size
-(``ks_set_chunk_rules``).  This module
+per-block look-back and prefix work per step).  A full block of a
+time-invariant model can be folded element by element or through
+per-position coefficients built once per call (the linear block fold: fewer
+operations per step, a longer preparation).  The library picks (l, fold) per
+call from the call's total number of steps through a rule table per state
+size (``ks_set_chunk_rules``).  This module
 
-* measures, on the device it runs on, every block length at a grid of sizes
-  for nx = 2, 4, 6 (one sequence through ``ks_smooth``) and for mixed-size
-  batches (``ks_smooth_batched``, keyed by their total steps), timing each
-  call with CUDA events after warm-up, L2 flushed between calls;
-* turns the measurements into rules: the fastest l at each measured size
-  (keeping the smaller size's choice while it is within 2 % of the fastest),
-  with the switch between two neighbouring sizes at their geometric mean;
+* measures, on the device it runs on, every (l, fold) variant at a grid of
+  sizes for nx = 2, 4, 6 (one sequence through ``ks_smooth``) and for
+  mixed-size batches (``ks_smooth_batched``, keyed by their total steps),
+  timing each call with CUDA events after warm-up, L2 flushed between calls;
+* turns the measurements into rules: the fastest variant at each measured
+  size (keeping the smaller size's choice while it is within 2 % of the
+  fastest), with the switch between two neighbouring sizes at their
+  geometric mean;
 * writes them to a versioned JSON cache, which the binding loads when the
   library is first used (``load_default``) if it was measured on the same
   device model and library version; otherwise the library's built-in table
@@ -29,8 +34,9 @@ import math
 import os
 import time
 
-CACHE_VERSION = 1
+CACHE_VERSION = 2
 STEPS = (4, 8, 16, 32)
+VARIANTS = tuple((s, f) for f in (0, 1) for s in STEPS)   # (steps per thread, block fold)
 T_NEVER = 1 << 62                      # T_below of a last rule: "every larger size"
 GRID = [1 << 10, 1 << 12, 1 << 14, 1 << 16, 98304, 1 << 17, 196608, 1 << 18, 1 << 19, 655360, 1 << 20,
         1 << 21, 1 << 22]
@@ -44,9 +50,18 @@ TUNING_DIR = os.path.join(HERE, "tuning")
 HYSTERESIS = 0.02   # keep the smaller size's choice while it is within 2 % of the fastest
 
 
+def vkey(v) -> str:
+    """Cache key of a variant: "32" (element by element) or "32f" (block fold)."""
+    return f"{v[0]}{'f' if v[1] else ''}"
+
+
+def vparse(k: str) -> tuple:
+    return (int(k.rstrip("f")), 1 if k.endswith("f") else 0)
+
+
 def rules_from(measured: dict) -> list:
-    """measured: {size: {steps: ms}} -> [(T_below, steps), ...] (sizes ascending).
-    The fastest block length at each size, except that the choice of the next
+    """measured: {size: {(steps, fold): ms}} -> [(T_below, steps, fold), ...]
+    (sizes ascending).  The fastest variant at each size, except that the choice of the next
     smaller size is kept while it is within HYSTERESIS of the fastest (timing
     noise then does not flip the table back and forth); where neighbouring
     sizes disagree the switch sits at their geometric mean; equal neighbours
@@ -64,23 +79,24 @@ def rules_from(measured: dict) -> list:
     rules = []
     for i in range(len(sizes) - 1):
         if best[i] != best[i + 1]:
-            rules.append((int(math.ceil(math.sqrt(sizes[i] * sizes[i + 1]))), int(best[i])))
-    rules.append((T_NEVER, int(best[-1])))
+            rules.append((int(math.ceil(math.sqrt(sizes[i] * sizes[i + 1]))), int(best[i][0]), int(best[i][1])))
+    rules.append((T_NEVER, int(best[-1][0]), int(best[-1][1])))
     return rules
 
 
-def choose(rules: list, T: int) -> int:
-    """The block length the library uses for T steps under `rules` (the
+def choose(rules: list, T: int) -> tuple:
+    """The (steps, fold) the library uses for T steps under `rules` (the
     first rule whose T_below exceeds T, else the last one's)."""
-    for tb, steps in rules:
+    for tb, steps, fold in rules:
         if T < tb:
-            return steps
-    return rules[-1][1]
+            return steps, fold
+    return rules[-1][1], rules[-1][2]
 
 
-def builtin(T: int) -> int:
-    """The library's built-in choice."""
-    return 4 if T < 96 * 1024 else 8 if T < 192 * 1024 else 16 if T < 640 * 1024 else 32
+def builtin(T: int, nx: int = 4) -> tuple:
+    """The library's built-in (steps, fold) choice (nx = 0: mixed batches)."""
+    steps = 4 if T < 96 * 1024 else 8 if T < 192 * 1024 else 16 if T < 640 * 1024 else 32
+    return steps, int(nx != 0 and steps == 32)
 
 
 def cache_path(device_name: str) -> str:
@@ -96,7 +112,7 @@ def valid_cache(d: dict, device_name: str, lib_version: int) -> bool:
 def apply(d: dict) -> None:
     from . import set_chunk_rules
     for key, rules in d["rules"].items():
-        set_chunk_rules(int(key), [(int(tb), int(s)) for tb, s in rules])
+        set_chunk_rules(int(key), [(int(tb), int(s), int(f)) for tb, s, f in rules])
 
 
 def load_default() -> str | None:
@@ -194,13 +210,13 @@ def measure_single(nx: int, sizes=GRID, reps: int = 7, warmup: int = 2, log=prin
         outs = dict(fmean=torch.empty(T, nx, device=dev), fcov=torch.empty(T, nx, nx, device=dev),
                     smean=torch.empty(T, nx, device=dev), scov=torch.empty(T, nx, nx, device=dev))
         row = {}
-        for steps in STEPS:
-            set_chunk_rules(nx, [(T_NEVER, steps)])
-            row[steps] = timer(lambda: smooth(model, y, ws, **outs))
+        for v in VARIANTS:
+            set_chunk_rules(nx, [(T_NEVER, v[0], v[1])])
+            row[v] = timer(lambda: smooth(model, y, ws, **outs))
         if status(ws) != KS_OK:
             raise RuntimeError(f"device status not OK while tuning nx={nx} T={T}")
         out[T] = row
-        log(f"nx={nx} T={T}: " + ", ".join(f"{s}: {row[s]:.4f} ms" for s in STEPS))
+        log(f"nx={nx} T={T}: " + ", ".join(f"{vkey(v)}: {row[v]:.4f} ms" for v in VARIANTS))
         del ws, outs, y
     set_chunk_rules(nx, [])
     return out
@@ -237,13 +253,13 @@ def measure_mixed(batches=MIXED_B, reps: int = 5, warmup: int = 2, log=print) ->
                  torch.empty(int(y.shape[0]), b.nx, device=dev), torch.empty(int(y.shape[0]), b.nx, b.nx, device=dev))
                 for b, y in groups]
         row = {}
-        for steps in STEPS:
-            set_chunk_rules(0, [(T_NEVER, steps)])
-            row[steps] = timer(lambda: smooth_batched(groups, ws, outs=outs))
+        for v in VARIANTS:
+            set_chunk_rules(0, [(T_NEVER, v[0], v[1])])
+            row[v] = timer(lambda: smooth_batched(groups, ws, outs=outs))
         if status(ws) != KS_OK:
             raise RuntimeError(f"device status not OK while tuning the mixed batch of {B} sequences")
         out[total] = row
-        log(f"mixed B={B} total={total}: " + ", ".join(f"{s}: {row[s]:.4f} ms" for s in STEPS))
+        log(f"mixed B={B} total={total}: " + ", ".join(f"{vkey(v)}: {row[v]:.4f} ms" for v in VARIANTS))
         del ws, outs, groups
     set_chunk_rules(0, [])
     return out
@@ -264,7 +280,7 @@ def tune(quick: bool = False, log=print) -> dict:
             "sm_count": torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count,
             "when": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime()), "seconds": round(time.perf_counter() - t0, 1),
             "rules": rules,
-            "measured_ms": {str(k): {str(T): {str(s): round(ms, 5) for s, ms in row.items()} for T, row in v.items()}
+            "measured_ms": {str(k): {str(T): {vkey(s): round(ms, 5) for s, ms in row.items()} for T, row in v.items()}
                             for k, v in meas.items()}}
 
 
