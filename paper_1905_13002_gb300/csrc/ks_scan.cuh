@@ -452,10 +452,150 @@ struct PrepSmem {
     float HQ[M][N], HF[M][N], S[M][M], Lsi[M][M], tmp[M][N], K[N][M];
     // warp 1: the k = 1 element in FP64
     double mm[N], FP[N][N], Pm[N][N], HP[M][N], S1[M][M], L1[M][M], r1[M], t1[M][N], z[M];
+    // ny <= 3: FP64 copies of the inputs, the inverse of S1 and S1^{-1} H P-
+    struct Small {
+        double F[N][N], Q[N][N], H[M][N], R[M][M], u[N], v[M], Si[M][M], W[M][N];
+    };
+    struct None {};
+    std::conditional_t<(M <= 3), Small, None> x;
     int ok0, ok1;
 };
 
 constexpr int kPrepThreads = 64;
+
+// Row and column of entry e of a packed lower triangle (row-major: (0,0),
+// (1,0), (1,1), (2,0), ...).
+KS_DEV void tri_rc(int e, int& a, int& b) {
+    a = 0;
+    while ((a + 1) * (a + 2) / 2 <= e) ++a;
+    b = e - a * (a + 1) / 2;
+}
+
+// The k = 1 element in FP64 for ny <= 3, by one warp (lane l):
+//   m- = F m0 + u, P- = F P0 F^T + Q, v = y - H m- - d, S1 = H P- H^T + R,
+//   b1 = m- + (H P-)^T S1^{-1} v,  C1 = P- - (H P-)^T S1^{-1} (H P-).
+// GB300 issues one FP64 warp instruction per several tens of cycles, so the
+// chain is kept short: the inputs are widened once, every stage spreads its
+// entries over the lanes (a dot product of length N or M per lane), and
+// S1^{-1} is its adjugate over its determinant (ny <= 3) instead of a
+// Cholesky factorisation, whose pivots would form a serial chain of
+// square roots.  S1 must be positive definite: its leading principal minors
+// are checked (p.ok1 = 0 otherwise).
+template <int N, int M, class PS, class MC>
+KS_DEV void first_element_fp64_small(PS& p, MC& mc, int l) {
+    auto& x = p.x;
+    for (int e = l; e < N * N; e += 32) {
+        const int a = e / N, b = e % N;
+        x.F[a][b] = (double)p.F[a][b];
+        x.Q[a][b] = 0.5 * ((double)p.Q[a][b] + (double)p.Q[b][a]);
+    }
+    for (int e = l; e < M * N; e += 32) x.H[e / N][e % N] = (double)p.H[e / N][e % N];
+    for (int e = l; e < M * M; e += 32) {
+        const int q = e / M, r = e % M;
+        x.R[q][r] = 0.5 * ((double)p.R[q][r] + (double)p.R[r][q]);
+    }
+    for (int e = l; e < N; e += 32) x.u[e] = (double)p.u[e];
+    for (int e = l; e < M; e += 32) x.v[e] = (double)p.y[e] - (double)p.d[e];
+    __syncwarp();
+    for (int e = l; e < N * N + N; e += 32) {          // F P0 and m- = F m0 + u
+        if (e < N * N) {
+            const int a = e / N, b = e % N;
+            double s = 0.0;
+            for (int c = 0; c < N; ++c) s = fma(x.F[a][c], p.P0[c][b], s);
+            p.FP[a][b] = s;
+        } else {
+            const int a = e - N * N;
+            double s = x.u[a];
+            for (int c = 0; c < N; ++c) s = fma(x.F[a][c], p.m0[c], s);
+            p.mm[a] = s;
+        }
+    }
+    __syncwarp();
+    for (int e = l; e < sym_size(N); e += 32) {        // P- (lower triangle, mirrored)
+        int a, b;
+        tri_rc(e, a, b);
+        double s = x.Q[a][b];
+        for (int c = 0; c < N; ++c) s = fma(p.FP[a][c], x.F[b][c], s);
+        p.Pm[a][b] = s;
+        p.Pm[b][a] = s;
+    }
+    __syncwarp();
+    for (int e = l; e < M * N + M; e += 32) {          // H P- and v = y - d - H m-
+        if (e < M * N) {
+            const int q = e / N, a = e % N;
+            double s = 0.0;
+            for (int c = 0; c < N; ++c) s = fma(x.H[q][c], p.Pm[c][a], s);
+            p.HP[q][a] = s;
+        } else {
+            const int q = e - M * N;
+            double s = x.v[q];
+            for (int c = 0; c < N; ++c) s = fma(-x.H[q][c], p.mm[c], s);
+            x.v[q] = s;
+        }
+    }
+    __syncwarp();
+    for (int e = l; e < M * M; e += 32) {              // S1 = H P- H^T + R
+        const int q = e / M, r = e % M;
+        double s = x.R[q][r];
+        for (int c = 0; c < N; ++c) s = fma(p.HP[q][c], x.H[r][c], s);
+        p.S1[q][r] = s;
+    }
+    __syncwarp();
+    {   // S1^{-1} = adj(S1) / det(S1); lane q * M + r forms the cofactor of entry (r, q)
+        const auto& S = p.S1;
+        double cof = 0.0;
+        if (l < M * M) {
+            const int q = l / M, r = l % M;
+            if constexpr (M == 1) {
+                cof = 1.0;
+            } else if constexpr (M == 2) {
+                cof = (q == r) ? S[1 - q][1 - q] : -S[q][r];
+            } else {   // 3 x 3: cyclic minors carry their sign
+                const int r1 = (r + 1) % 3, r2 = (r + 2) % 3, q1 = (q + 1) % 3, q2 = (q + 2) % 3;
+                cof = fma(S[r1][q1], S[r2][q2], -S[r1][q2] * S[r2][q1]);
+            }
+            x.Si[q][r] = cof;
+        }
+        __syncwarp();
+        double det = 0.0;   // expansion along row 0: sum_r S[0][r] cof(0, r), cof(0, r) = adj[r][0]
+        for (int r = 0; r < M; ++r) det = fma(S[0][r], x.Si[r][0], det);
+        bool pd = S[0][0] > 0.0 && det > 0.0;
+        if constexpr (M == 3) pd = pd && x.Si[2][2] > 0.0;   // the leading 2 x 2 minor
+        const double id = 1.0 / (pd ? det : 1.0);
+        __syncwarp();
+        if (l < M * M) x.Si[l / M][l % M] = cof * id;
+        if (l == 0 && !pd) p.ok1 = 0;
+    }
+    __syncwarp();
+    for (int e = l; e < M * N + M; e += 32) {          // W = S1^{-1} H P-, z = S1^{-1} v
+        if (e < M * N) {
+            const int q = e / N, a = e % N;
+            double s = 0.0;
+            for (int r = 0; r < M; ++r) s = fma(x.Si[q][r], p.HP[r][a], s);
+            x.W[q][a] = s;
+        } else {
+            const int q = e - M * N;
+            double s = 0.0;
+            for (int r = 0; r < M; ++r) s = fma(x.Si[q][r], x.v[r], s);
+            p.z[q] = s;
+        }
+    }
+    __syncwarp();
+    for (int e = l; e < sym_size(N) + N; e += 32) {    // C1 = P- - (H P-)^T W, b1 = m- + (H P-)^T z
+        if (e < sym_size(N)) {
+            int a, b;
+            tri_rc(e, a, b);
+            double s = p.Pm[a][b];
+            for (int q = 0; q < M; ++q) s = fma(-p.HP[q][a], x.W[q][b], s);
+            mc.C1[sidx(a, b)] = (float)s;
+        } else {
+            const int a = e - sym_size(N);
+            double s = p.mm[a];
+            for (int q = 0; q < M; ++q) s = fma(p.HP[q][a], p.z[q], s);
+            mc.b1[a] = (float)s;
+        }
+    }
+}
 
 // One block per model (segment).  After one round of loads, warp 0 builds the
 // FP32 constants of Lemma 3 for k > 1 and warp 1, at the same time, the k = 1
@@ -615,88 +755,92 @@ KS_DEV void prep_body(char* prep_dsm, int sg, int nseg, const float* __restrict_
         }
     } else if (warp == 1) {
         if (y != nullptr) {
-            // ---- k = 1 in FP64: m- = F m0 + u, P- = F P0 F^T + Q, S1 = H P- H^T + R = L1 L1^T,
-            // t1 = L1^{-1} H P-, z = L1^{-1} (y - H m- - d), b1 = m- + t1^T z, C1 = P- - t1^T t1.
-            // Each product is spread over the warp's lanes; the triangular solves use the
-            // reciprocal square roots of the Cholesky pivots, so the chain has no division.
-            for (int e = l; e < N * N; e += 32) {
-                const int a = e / N, b = e % N;
-                double s = 0.0;
-                for (int c = 0; c < N; ++c) s = fma((double)p.F[a][c], p.P0[c][b], s);
-                p.FP[a][b] = s;
-            }
-            for (int e = l; e < N; e += 32) {
-                double s = p.u[e];
-                for (int c = 0; c < N; ++c) s = fma((double)p.F[e][c], p.m0[c], s);
-                p.mm[e] = s;
-            }
-            __syncwarp();
-            for (int e = l; e < N * N; e += 32) {
-                const int a = e / N, b = e % N;
-                if (b > a) continue;
-                double s = 0.5 * ((double)p.Q[a][b] + (double)p.Q[b][a]);
-                for (int c = 0; c < N; ++c) s = fma(p.FP[a][c], (double)p.F[b][c], s);
-                p.Pm[a][b] = s;
-                p.Pm[b][a] = s;
-            }
-            __syncwarp();
-            for (int e = l; e < M * N; e += 32) {
-                const int q = e / N, a = e % N;
-                double s = 0.0;
-                for (int c = 0; c < N; ++c) s = fma((double)p.H[q][c], p.Pm[c][a], s);
-                p.HP[q][a] = s;
-            }
-            __syncwarp();
-            for (int e = l; e < M * M; e += 32) {
-                const int q = e / M, r = e % M;
-                double s = 0.5 * ((double)p.R[q][r] + (double)p.R[r][q]);
-                for (int c = 0; c < N; ++c) s = fma(p.HP[q][c], (double)p.H[r][c], s);
-                p.S1[q][r] = s;
-            }
-            __syncwarp();
-            if (l == 0) {                          // Cholesky of S1 (reciprocal pivots), z
-                bool ok = true;
-                for (int j = 0; j < M; ++j) {
-                    double s = p.S1[j][j];
-                    for (int k = 0; k < j; ++k) s = fma(-p.L1[j][k], p.L1[j][k], s);
-                    ok = ok && (s > 0.0);
-                    const double rj = rsqrt(s > 0.0 ? s : 1e-300);
-                    p.L1[j][j] = s * rj;
-                    p.r1[j] = rj;
-                    for (int i = j + 1; i < M; ++i) {
-                        double q = p.S1[i][j];
-                        for (int k = 0; k < j; ++k) q = fma(-p.L1[i][k], p.L1[j][k], q);
-                        p.L1[i][j] = q * rj;
+            if constexpr (M <= 3) {
+                first_element_fp64_small<N, M>(p, mc, l);
+            } else {
+                // ---- k = 1 in FP64: m- = F m0 + u, P- = F P0 F^T + Q, S1 = H P- H^T + R = L1 L1^T,
+                // t1 = L1^{-1} H P-, z = L1^{-1} (y - H m- - d), b1 = m- + t1^T z, C1 = P- - t1^T t1.
+                // Each product is spread over the warp's lanes; the triangular solves use the
+                // reciprocal square roots of the Cholesky pivots, so the chain has no division.
+                for (int e = l; e < N * N; e += 32) {
+                    const int a = e / N, b = e % N;
+                    double s = 0.0;
+                    for (int c = 0; c < N; ++c) s = fma((double)p.F[a][c], p.P0[c][b], s);
+                    p.FP[a][b] = s;
+                }
+                for (int e = l; e < N; e += 32) {
+                    double s = p.u[e];
+                    for (int c = 0; c < N; ++c) s = fma((double)p.F[e][c], p.m0[c], s);
+                    p.mm[e] = s;
+                }
+                __syncwarp();
+                for (int e = l; e < N * N; e += 32) {
+                    const int a = e / N, b = e % N;
+                    if (b > a) continue;
+                    double s = 0.5 * ((double)p.Q[a][b] + (double)p.Q[b][a]);
+                    for (int c = 0; c < N; ++c) s = fma(p.FP[a][c], (double)p.F[b][c], s);
+                    p.Pm[a][b] = s;
+                    p.Pm[b][a] = s;
+                }
+                __syncwarp();
+                for (int e = l; e < M * N; e += 32) {
+                    const int q = e / N, a = e % N;
+                    double s = 0.0;
+                    for (int c = 0; c < N; ++c) s = fma((double)p.H[q][c], p.Pm[c][a], s);
+                    p.HP[q][a] = s;
+                }
+                __syncwarp();
+                for (int e = l; e < M * M; e += 32) {
+                    const int q = e / M, r = e % M;
+                    double s = 0.5 * ((double)p.R[q][r] + (double)p.R[r][q]);
+                    for (int c = 0; c < N; ++c) s = fma(p.HP[q][c], (double)p.H[r][c], s);
+                    p.S1[q][r] = s;
+                }
+                __syncwarp();
+                if (l == 0) {                          // Cholesky of S1 (reciprocal pivots), z
+                    bool ok = true;
+                    for (int j = 0; j < M; ++j) {
+                        double s = p.S1[j][j];
+                        for (int k = 0; k < j; ++k) s = fma(-p.L1[j][k], p.L1[j][k], s);
+                        ok = ok && (s > 0.0);
+                        const double rj = rsqrt(s > 0.0 ? s : 1e-300);
+                        p.L1[j][j] = s * rj;
+                        p.r1[j] = rj;
+                        for (int i = j + 1; i < M; ++i) {
+                            double q = p.S1[i][j];
+                            for (int k = 0; k < j; ++k) q = fma(-p.L1[i][k], p.L1[j][k], q);
+                            p.L1[i][j] = q * rj;
+                        }
+                    }
+                    for (int q = 0; q < M; ++q) {
+                        double s = (double)p.y[q] - (double)p.d[q];
+                        for (int c = 0; c < N; ++c) s = fma(-(double)p.H[q][c], p.mm[c], s);
+                        for (int k = 0; k < q; ++k) s = fma(-p.L1[q][k], p.z[k], s);
+                        p.z[q] = s * p.r1[q];
+                    }
+                    if (!ok) p.ok1 = 0;
+                }
+                __syncwarp();
+                for (int a = l; a < N; a += 32) {      // t1 column a
+                    for (int q = 0; q < M; ++q) {
+                        double s = p.HP[q][a];
+                        for (int k = 0; k < q; ++k) s = fma(-p.L1[q][k], p.t1[k][a], s);
+                        p.t1[q][a] = s * p.r1[q];
                     }
                 }
-                for (int q = 0; q < M; ++q) {
-                    double s = (double)p.y[q] - (double)p.d[q];
-                    for (int c = 0; c < N; ++c) s = fma(-(double)p.H[q][c], p.mm[c], s);
-                    for (int k = 0; k < q; ++k) s = fma(-p.L1[q][k], p.z[k], s);
-                    p.z[q] = s * p.r1[q];
-                }
-                if (!ok) p.ok1 = 0;
-            }
-            __syncwarp();
-            for (int a = l; a < N; a += 32) {      // t1 column a
-                for (int q = 0; q < M; ++q) {
-                    double s = p.HP[q][a];
-                    for (int k = 0; k < q; ++k) s = fma(-p.L1[q][k], p.t1[k][a], s);
-                    p.t1[q][a] = s * p.r1[q];
-                }
-            }
-            __syncwarp();
-            for (int e = l; e < N * N; e += 32) {
-                const int a = e / N, b = e % N;
-                if (b == 0) {
-                    double s = p.mm[a];
-                    for (int q = 0; q < M; ++q) s = fma(p.t1[q][a], p.z[q], s);
-                    mc.b1[a] = (float)s;
-                }
-                if (b <= a) {
-                    double s = p.Pm[a][b];
-                    for (int q = 0; q < M; ++q) s = fma(-p.t1[q][a], p.t1[q][b], s);
-                    mc.C1[sidx(a, b)] = (float)s;
+                __syncwarp();
+                for (int e = l; e < N * N; e += 32) {
+                    const int a = e / N, b = e % N;
+                    if (b == 0) {
+                        double s = p.mm[a];
+                        for (int q = 0; q < M; ++q) s = fma(p.t1[q][a], p.z[q], s);
+                        mc.b1[a] = (float)s;
+                    }
+                    if (b <= a) {
+                        double s = p.Pm[a][b];
+                        for (int q = 0; q < M; ++q) s = fma(-p.t1[q][a], p.t1[q][b], s);
+                        mc.C1[sidx(a, b)] = (float)s;
+                    }
                 }
             }
         } else {
