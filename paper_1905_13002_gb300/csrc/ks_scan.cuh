@@ -450,18 +450,14 @@ struct PrepSmem {
     double m0[N], P0[N][N];
     // warp 0: the FP32 model constants
     float HQ[M][N], HF[M][N], S[M][M], Lsi[M][M], tmp[M][N], K[N][M];
-    // warp 1: the k = 1 element in FP64
-    double mm[N], FP[N][N], Pm[N][N], HP[M][N], S1[M][M], L1[M][M], r1[M], t1[M][N], z[M];
-    // ny <= 3: FP64 copies of the inputs, the inverse of S1 and S1^{-1} H P-
-    struct Small {
-        double F[N][N], Q[N][N], H[M][N], R[M][M], u[N], v[M], Si[M][M], W[M][N];
-    };
-    struct None {};
-    std::conditional_t<(M <= 3), Small, None> x;
+    // warps 1-3: the k = 1 element in FP64 (inputs widened once, S1^{-1}, S1^{-1} H P-)
+    double mm[N], FP[N][N], Pm[N][N], HP[M][N], S1[M][M], z[M];
+    double dF[N][N], dQ[N][N], dH[M][N], dR[M][M], du[N], v[M], Si[M][M], W[M][N];
     int ok0, ok1;
 };
 
-constexpr int kPrepThreads = 64;
+constexpr int kPrepThreads = 128;   // warp 0: FP32 constants; warps 1-3: the FP64 first element
+constexpr int kFirstThreads = 96;
 
 // Row and column of entry e of a packed lower triangle (row-major: (0,0),
 // (1,0), (1,1), (2,0), ...).
@@ -471,81 +467,86 @@ KS_DEV void tri_rc(int e, int& a, int& b) {
     b = e - a * (a + 1) / 2;
 }
 
-// The k = 1 element in FP64 for ny <= 3, by one warp (lane l):
+// Barrier of the three warps that build the first element (named barrier 1).
+KS_DEV void first_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kFirstThreads) : "memory"); }
+
+// The k = 1 element in FP64, by warps 1-3 (thread i of kFirstThreads):
 //   m- = F m0 + u, P- = F P0 F^T + Q, v = y - H m- - d, S1 = H P- H^T + R,
 //   b1 = m- + (H P-)^T S1^{-1} v,  C1 = P- - (H P-)^T S1^{-1} (H P-).
-// GB300 issues one FP64 warp instruction per several tens of cycles, so the
-// chain is kept short: the inputs are widened once, every stage spreads its
-// entries over the lanes (a dot product of length N or M per lane), and
-// S1^{-1} is its adjugate over its determinant (ny <= 3) instead of a
-// Cholesky factorisation, whose pivots would form a serial chain of
-// square roots.  S1 must be positive definite: its leading principal minors
-// are checked (p.ok1 = 0 otherwise).
+// GB300 issues one FP64 warp instruction per several tens of cycles on each
+// SM sub-partition, so the work is spread over three warps (three
+// sub-partitions) and the chain is kept short: the inputs are widened once,
+// every stage spreads its entries over the threads (a dot product of length
+// N or M each), and S1^{-1} is, for ny <= 3, its adjugate over its
+// determinant (leading minors checked), else Gauss-Jordan elimination without
+// pivoting by one warp, lane c holding column c of [S1 | I] (S1 is symmetric
+// positive definite exactly when every pivot is positive).  p.ok1 = 0 when S1
+// is not positive definite.
 template <int N, int M, class PS, class MC>
-KS_DEV void first_element_fp64_small(PS& p, MC& mc, int l) {
-    auto& x = p.x;
-    for (int e = l; e < N * N; e += 32) {
+KS_DEV void first_element_fp64(PS& p, MC& mc, int i) {
+    constexpr int n1 = kFirstThreads;
+    for (int e = i; e < N * N; e += n1) {
         const int a = e / N, b = e % N;
-        x.F[a][b] = (double)p.F[a][b];
-        x.Q[a][b] = 0.5 * ((double)p.Q[a][b] + (double)p.Q[b][a]);
+        p.dF[a][b] = (double)p.F[a][b];
+        p.dQ[a][b] = 0.5 * ((double)p.Q[a][b] + (double)p.Q[b][a]);
     }
-    for (int e = l; e < M * N; e += 32) x.H[e / N][e % N] = (double)p.H[e / N][e % N];
-    for (int e = l; e < M * M; e += 32) {
+    for (int e = i; e < M * N; e += n1) p.dH[e / N][e % N] = (double)p.H[e / N][e % N];
+    for (int e = i; e < M * M; e += n1) {
         const int q = e / M, r = e % M;
-        x.R[q][r] = 0.5 * ((double)p.R[q][r] + (double)p.R[r][q]);
+        p.dR[q][r] = 0.5 * ((double)p.R[q][r] + (double)p.R[r][q]);
     }
-    for (int e = l; e < N; e += 32) x.u[e] = (double)p.u[e];
-    for (int e = l; e < M; e += 32) x.v[e] = (double)p.y[e] - (double)p.d[e];
-    __syncwarp();
-    for (int e = l; e < N * N + N; e += 32) {          // F P0 and m- = F m0 + u
+    for (int e = i; e < N; e += n1) p.du[e] = (double)p.u[e];
+    for (int e = i; e < M; e += n1) p.v[e] = (double)p.y[e] - (double)p.d[e];
+    first_sync();
+    for (int e = i; e < N * N + N; e += n1) {          // F P0 and m- = F m0 + u
         if (e < N * N) {
             const int a = e / N, b = e % N;
             double s = 0.0;
-            for (int c = 0; c < N; ++c) s = fma(x.F[a][c], p.P0[c][b], s);
+            for (int c = 0; c < N; ++c) s = fma(p.dF[a][c], p.P0[c][b], s);
             p.FP[a][b] = s;
         } else {
             const int a = e - N * N;
-            double s = x.u[a];
-            for (int c = 0; c < N; ++c) s = fma(x.F[a][c], p.m0[c], s);
+            double s = p.du[a];
+            for (int c = 0; c < N; ++c) s = fma(p.dF[a][c], p.m0[c], s);
             p.mm[a] = s;
         }
     }
-    __syncwarp();
-    for (int e = l; e < sym_size(N); e += 32) {        // P- (lower triangle, mirrored)
+    first_sync();
+    for (int e = i; e < sym_size(N); e += n1) {        // P- (lower triangle, mirrored)
         int a, b;
         tri_rc(e, a, b);
-        double s = x.Q[a][b];
-        for (int c = 0; c < N; ++c) s = fma(p.FP[a][c], x.F[b][c], s);
+        double s = p.dQ[a][b];
+        for (int c = 0; c < N; ++c) s = fma(p.FP[a][c], p.dF[b][c], s);
         p.Pm[a][b] = s;
         p.Pm[b][a] = s;
     }
-    __syncwarp();
-    for (int e = l; e < M * N + M; e += 32) {          // H P- and v = y - d - H m-
+    first_sync();
+    for (int e = i; e < M * N + M; e += n1) {          // H P- and v = y - d - H m-
         if (e < M * N) {
             const int q = e / N, a = e % N;
             double s = 0.0;
-            for (int c = 0; c < N; ++c) s = fma(x.H[q][c], p.Pm[c][a], s);
+            for (int c = 0; c < N; ++c) s = fma(p.dH[q][c], p.Pm[c][a], s);
             p.HP[q][a] = s;
         } else {
             const int q = e - M * N;
-            double s = x.v[q];
-            for (int c = 0; c < N; ++c) s = fma(-x.H[q][c], p.mm[c], s);
-            x.v[q] = s;
+            double s = p.v[q];
+            for (int c = 0; c < N; ++c) s = fma(-p.dH[q][c], p.mm[c], s);
+            p.v[q] = s;
         }
     }
-    __syncwarp();
-    for (int e = l; e < M * M; e += 32) {              // S1 = H P- H^T + R
+    first_sync();
+    for (int e = i; e < M * M; e += n1) {              // S1 = H P- H^T + R
         const int q = e / M, r = e % M;
-        double s = x.R[q][r];
-        for (int c = 0; c < N; ++c) s = fma(p.HP[q][c], x.H[r][c], s);
+        double s = p.dR[q][r];
+        for (int c = 0; c < N; ++c) s = fma(p.HP[q][c], p.dH[r][c], s);
         p.S1[q][r] = s;
     }
-    __syncwarp();
-    {   // S1^{-1} = adj(S1) / det(S1); lane q * M + r forms the cofactor of entry (r, q)
+    first_sync();
+    if constexpr (M <= 3) {   // S1^{-1} = adj(S1) / det(S1); thread q * M + r forms the cofactor of (r, q)
         const auto& S = p.S1;
         double cof = 0.0;
-        if (l < M * M) {
-            const int q = l / M, r = l % M;
+        if (i < M * M) {
+            const int q = i / M, r = i % M;
             if constexpr (M == 1) {
                 cof = 1.0;
             } else if constexpr (M == 2) {
@@ -554,39 +555,64 @@ KS_DEV void first_element_fp64_small(PS& p, MC& mc, int l) {
                 const int r1 = (r + 1) % 3, r2 = (r + 2) % 3, q1 = (q + 1) % 3, q2 = (q + 2) % 3;
                 cof = fma(S[r1][q1], S[r2][q2], -S[r1][q2] * S[r2][q1]);
             }
-            x.Si[q][r] = cof;
+            p.Si[q][r] = cof;
         }
-        __syncwarp();
+        first_sync();
         double det = 0.0;   // expansion along row 0: sum_r S[0][r] cof(0, r), cof(0, r) = adj[r][0]
-        for (int r = 0; r < M; ++r) det = fma(S[0][r], x.Si[r][0], det);
+        for (int r = 0; r < M; ++r) det = fma(S[0][r], p.Si[r][0], det);
         bool pd = S[0][0] > 0.0 && det > 0.0;
-        if constexpr (M == 3) pd = pd && x.Si[2][2] > 0.0;   // the leading 2 x 2 minor
+        if constexpr (M == 3) pd = pd && p.Si[2][2] > 0.0;   // the leading 2 x 2 minor
         const double id = 1.0 / (pd ? det : 1.0);
-        __syncwarp();
-        if (l < M * M) x.Si[l / M][l % M] = cof * id;
-        if (l == 0 && !pd) p.ok1 = 0;
+        first_sync();
+        if (i < M * M) p.Si[i / M][i % M] = cof * id;
+        if (i == 0 && !pd) p.ok1 = 0;
+    } else if (i < 32) {   // Gauss-Jordan on [S1 | I] by the first of the three warps
+        static_assert(M <= 16, "one lane per column of [S1 | I]");
+        const int c = i;
+        double col[M];
+#pragma unroll
+        for (int r = 0; r < M; ++r) col[r] = c < M ? p.S1[r][c] : (c < 2 * M && r == c - M ? 1.0 : 0.0);
+        bool pd = true;
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+            const double piv = __shfl_sync(0xffffffffu, col[k], k);
+            pd = pd && piv > 0.0;
+            const double rk = col[k] * (1.0 / (piv > 0.0 ? piv : 1.0));
+#pragma unroll
+            for (int r = 0; r < M; ++r) {
+                if (r == k) continue;
+                const double f = __shfl_sync(0xffffffffu, col[r], k);
+                col[r] = fma(-f, rk, col[r]);
+            }
+            col[k] = rk;
+        }
+        if (c >= M && c < 2 * M) {
+#pragma unroll
+            for (int r = 0; r < M; ++r) p.Si[r][c - M] = col[r];
+        }
+        if (c == 0 && !pd) p.ok1 = 0;
     }
-    __syncwarp();
-    for (int e = l; e < M * N + M; e += 32) {          // W = S1^{-1} H P-, z = S1^{-1} v
+    first_sync();
+    for (int e = i; e < M * N + M; e += n1) {          // W = S1^{-1} H P-, z = S1^{-1} v
         if (e < M * N) {
             const int q = e / N, a = e % N;
             double s = 0.0;
-            for (int r = 0; r < M; ++r) s = fma(x.Si[q][r], p.HP[r][a], s);
-            x.W[q][a] = s;
+            for (int r = 0; r < M; ++r) s = fma(p.Si[q][r], p.HP[r][a], s);
+            p.W[q][a] = s;
         } else {
             const int q = e - M * N;
             double s = 0.0;
-            for (int r = 0; r < M; ++r) s = fma(x.Si[q][r], x.v[r], s);
+            for (int r = 0; r < M; ++r) s = fma(p.Si[q][r], p.v[r], s);
             p.z[q] = s;
         }
     }
-    __syncwarp();
-    for (int e = l; e < sym_size(N) + N; e += 32) {    // C1 = P- - (H P-)^T W, b1 = m- + (H P-)^T z
+    first_sync();
+    for (int e = i; e < sym_size(N) + N; e += n1) {    // C1 = P- - (H P-)^T W, b1 = m- + (H P-)^T z
         if (e < sym_size(N)) {
             int a, b;
             tri_rc(e, a, b);
             double s = p.Pm[a][b];
-            for (int q = 0; q < M; ++q) s = fma(-p.HP[q][a], x.W[q][b], s);
+            for (int q = 0; q < M; ++q) s = fma(-p.HP[q][a], p.W[q][b], s);
             mc.C1[sidx(a, b)] = (float)s;
         } else {
             const int a = e - sym_size(N);
@@ -598,9 +624,9 @@ KS_DEV void first_element_fp64_small(PS& p, MC& mc, int l) {
 }
 
 // One block per model (segment).  After one round of loads, warp 0 builds the
-// FP32 constants of Lemma 3 for k > 1 and warp 1, at the same time, the k = 1
-// element (prediction of N(m0, P0) and update with y_1) in FP64; the two
-// chains only meet for the final store.
+// FP32 constants of Lemma 3 for k > 1 (and the block-fold coefficients), and
+// warps 1-3, at the same time, the k = 1 element (prediction of N(m0, P0) and
+// update with y_1) in FP64; the two chains only meet for the final store.
 // Body of the preparation of segment sg of nseg (one thread block); dyn:
 // its dynamic shared memory (PrepSmem and a ModelConst).
 template <int N, int M>
@@ -748,104 +774,17 @@ KS_DEV void prep_body(char* prep_dsm, int sg, int nseg, const float* __restrict_
         for (int e = l; e < N; e += 32) mc.u[e] = p.u[e];
         if (l < 4) mc.pad[l] = 0.f;
         if constexpr (N <= 6) {   // register-path sizes only
-            if (coef != nullptr) {   // the block-fold coefficients, while warp 1 builds the k = 1 element
+            if (coef != nullptr) {   // the block-fold coefficients, while warps 1-3 build the k = 1 element
                 __syncwarp();
                 block_coef_warp<N, M>(mc, &p.H[0][0], ch, coef + sg);
             }
         }
-    } else if (warp == 1) {
+    } else {   // warps 1-3
         if (y != nullptr) {
-            if constexpr (M <= 3) {
-                first_element_fp64_small<N, M>(p, mc, l);
-            } else {
-                // ---- k = 1 in FP64: m- = F m0 + u, P- = F P0 F^T + Q, S1 = H P- H^T + R = L1 L1^T,
-                // t1 = L1^{-1} H P-, z = L1^{-1} (y - H m- - d), b1 = m- + t1^T z, C1 = P- - t1^T t1.
-                // Each product is spread over the warp's lanes; the triangular solves use the
-                // reciprocal square roots of the Cholesky pivots, so the chain has no division.
-                for (int e = l; e < N * N; e += 32) {
-                    const int a = e / N, b = e % N;
-                    double s = 0.0;
-                    for (int c = 0; c < N; ++c) s = fma((double)p.F[a][c], p.P0[c][b], s);
-                    p.FP[a][b] = s;
-                }
-                for (int e = l; e < N; e += 32) {
-                    double s = p.u[e];
-                    for (int c = 0; c < N; ++c) s = fma((double)p.F[e][c], p.m0[c], s);
-                    p.mm[e] = s;
-                }
-                __syncwarp();
-                for (int e = l; e < N * N; e += 32) {
-                    const int a = e / N, b = e % N;
-                    if (b > a) continue;
-                    double s = 0.5 * ((double)p.Q[a][b] + (double)p.Q[b][a]);
-                    for (int c = 0; c < N; ++c) s = fma(p.FP[a][c], (double)p.F[b][c], s);
-                    p.Pm[a][b] = s;
-                    p.Pm[b][a] = s;
-                }
-                __syncwarp();
-                for (int e = l; e < M * N; e += 32) {
-                    const int q = e / N, a = e % N;
-                    double s = 0.0;
-                    for (int c = 0; c < N; ++c) s = fma((double)p.H[q][c], p.Pm[c][a], s);
-                    p.HP[q][a] = s;
-                }
-                __syncwarp();
-                for (int e = l; e < M * M; e += 32) {
-                    const int q = e / M, r = e % M;
-                    double s = 0.5 * ((double)p.R[q][r] + (double)p.R[r][q]);
-                    for (int c = 0; c < N; ++c) s = fma(p.HP[q][c], (double)p.H[r][c], s);
-                    p.S1[q][r] = s;
-                }
-                __syncwarp();
-                if (l == 0) {                          // Cholesky of S1 (reciprocal pivots), z
-                    bool ok = true;
-                    for (int j = 0; j < M; ++j) {
-                        double s = p.S1[j][j];
-                        for (int k = 0; k < j; ++k) s = fma(-p.L1[j][k], p.L1[j][k], s);
-                        ok = ok && (s > 0.0);
-                        const double rj = rsqrt(s > 0.0 ? s : 1e-300);
-                        p.L1[j][j] = s * rj;
-                        p.r1[j] = rj;
-                        for (int i = j + 1; i < M; ++i) {
-                            double q = p.S1[i][j];
-                            for (int k = 0; k < j; ++k) q = fma(-p.L1[i][k], p.L1[j][k], q);
-                            p.L1[i][j] = q * rj;
-                        }
-                    }
-                    for (int q = 0; q < M; ++q) {
-                        double s = (double)p.y[q] - (double)p.d[q];
-                        for (int c = 0; c < N; ++c) s = fma(-(double)p.H[q][c], p.mm[c], s);
-                        for (int k = 0; k < q; ++k) s = fma(-p.L1[q][k], p.z[k], s);
-                        p.z[q] = s * p.r1[q];
-                    }
-                    if (!ok) p.ok1 = 0;
-                }
-                __syncwarp();
-                for (int a = l; a < N; a += 32) {      // t1 column a
-                    for (int q = 0; q < M; ++q) {
-                        double s = p.HP[q][a];
-                        for (int k = 0; k < q; ++k) s = fma(-p.L1[q][k], p.t1[k][a], s);
-                        p.t1[q][a] = s * p.r1[q];
-                    }
-                }
-                __syncwarp();
-                for (int e = l; e < N * N; e += 32) {
-                    const int a = e / N, b = e % N;
-                    if (b == 0) {
-                        double s = p.mm[a];
-                        for (int q = 0; q < M; ++q) s = fma(p.t1[q][a], p.z[q], s);
-                        mc.b1[a] = (float)s;
-                    }
-                    if (b <= a) {
-                        double s = p.Pm[a][b];
-                        for (int q = 0; q < M; ++q) s = fma(-p.t1[q][a], p.t1[q][b], s);
-                        mc.C1[sidx(a, b)] = (float)s;
-                    }
-                }
-            }
+            first_element_fp64<N, M>(p, mc, t - 32);
         } else {
-            for (int e = l; e < N; e += 32) mc.b1[e] = 0.f;
-            for (int e = l; e < sym_size(N); e += 32) mc.C1[e] = 0.f;
+            for (int e = t - 32; e < N; e += kFirstThreads) mc.b1[e] = 0.f;
+            for (int e = t - 32; e < sym_size(N); e += kFirstThreads) mc.C1[e] = 0.f;
         }
     }
     __syncthreads();
