@@ -227,9 +227,11 @@ int ks_smooth_batch(const ks_model_batch *mb, const float *y, int64_t total_T, v
  * a full block can also be folded through per-position coefficients built
  * once per call and model (the linear block fold: Lemma 3's A, C, J are the
  * same at every step, so a block's (b, eta) is affine in its measurements)
- * instead of element by element; `fold` = 1 selects it.  The built-in choice
- * is 4 steps below 96 Ki steps, 8 below 192 Ki, 16 below 640 Ki and 32 above,
- * folding with the coefficients at 32 steps for single-size calls.
+ * instead of element by element; `fold` = 1 selects it for ks_smooth,
+ * ks_smooth_traced and ks_smooth_batched (ks_smooth_batch always folds element
+ * by element).  The built-in choice is 4 steps below 96 Ki steps, 8 below
+ * 192 Ki, 16 below 640 Ki and 32 above, folding with the coefficients at 32
+ * steps for single sequences and never for ks_smooth_batched.
  * ks_set_chunk_rules replaces it for one state size (nx = 2, 4 or 6; nx = 0:
  * ks_smooth_batched) by `count` rules with strictly increasing T_below: a
  * call uses the first rule whose T_below exceeds its T, else the last one.

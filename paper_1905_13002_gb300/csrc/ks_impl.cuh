@@ -190,10 +190,11 @@ struct Impl {
     static int prep(const ks_model* m, const float* y, void* ws, const Layout& L, cudaStream_t st,
                     bool fold = false) {
         uint32_t* z = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + L.off_flags);
-        prep_kernel<N, M><<<1, kPrepThreads, prep_smem(), st>>>(m->F, m->u, m->Q, m->H, m->d, m->R, m->m0, m->P0, y,
-                                             mconst(ws, L), status(ws), z, (int)(L.flags_bytes / 4), nullptr,
-                                             L.T, status(ws) + HDR_FIRST_TILE,
-                                             (fold && y && L.off_coef) ? coef(ws, L) : nullptr, FCH);
+        BlockCoef<N, M>* cf = (fold && y && L.off_coef) ? coef(ws, L) : nullptr;
+        auto k = cf ? prep_kernel<N, M, true> : prep_kernel<N, M, false>;
+        k<<<1, kPrepThreads, prep_smem(), st>>>(m->F, m->u, m->Q, m->H, m->d, m->R, m->m0, m->P0, y, mconst(ws, L),
+                                                status(ws), z, (int)(L.flags_bytes / 4), nullptr, L.T,
+                                                status(ws) + HDR_FIRST_TILE, cf, FCH);
         return launch_status();
     }
 
@@ -407,10 +408,11 @@ struct Impl {
         if (!aligned16(y) || !aligned16(fm) || !aligned16(fc) || !aligned16(sm) || !aligned16(sc))
             return KS_EINVAL;
         uint32_t* z = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + L.off_flags);
-        prep_kernel<N, M><<<mb->B, kPrepThreads, prep_smem(), st>>>(mb->F, mb->u, mb->Q, mb->H, mb->d, mb->R, mb->m0, mb->P0, y,
-                                                 mconst(ws, L), status(ws), z, (int)(L.flags_bytes / 4),
-                                                 mb->offsets, T, status(ws) + HDR_FIRST_TILE,
-                                                 fold ? coef(ws, L) : nullptr, FCH);
+        auto k = fold ? prep_kernel<N, M, true> : prep_kernel<N, M, false>;
+        k<<<mb->B, kPrepThreads, prep_smem(), st>>>(mb->F, mb->u, mb->Q, mb->H, mb->d, mb->R, mb->m0, mb->P0, y,
+                                                    mconst(ws, L), status(ws), z, (int)(L.flags_bytes / 4),
+                                                    mb->offsets, T, status(ws) + HDR_FIRST_TILE,
+                                                    fold ? coef(ws, L) : nullptr, FCH);
         int rc = launch_status();
         if (rc) return rc;
         const Segs<N, M> segs{mconst(ws, L), mb->offsets, mb->B, fold ? coef(ws, L) : nullptr};
@@ -545,8 +547,11 @@ struct Tuned {
     }
     static int smooth_batch(const ks_model_batch* mb, const float* y, int64_t T, void* ws, size_t ws_bytes,
                             float* fm, float* fc, float* sm, float* sc, cudaStream_t st) {
-        const int c = chunk_choice(N, T);
-        return ChunkTable<N, M>::v[c & 3]->smooth_batch(mb, y, T, ws, ws_bytes, fm, fc, sm, sc, st, (c & 4) != 0);
+        // segmented batches fold element by element: every sequence would need its
+        // own coefficients, read from L2 in phase 1 (measured slower in the
+        // mixed-size launch)
+        return ChunkTable<N, M>::v[chunk_index_for(N, T)]->smooth_batch(mb, y, T, ws, ws_bytes, fm, fc, sm, sc, st,
+                                                                         false);
     }
     static size_t tv_bytes(int64_t T) { return layout(T, 1).bytes_elements; }
     static constexpr VTable vtable() {

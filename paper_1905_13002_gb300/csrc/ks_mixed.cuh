@@ -55,17 +55,17 @@ struct MixedQueue {
 
 constexpr int kMixedThreads = 128;
 
-template <int N, int M>
+template <int N, int M, bool FOLD>
 KS_DEV void mixed_prep_one(char* dsm, int sg, const MixedGroup<N, M>& g) {
-    prep_body<N, M>(dsm, sg, g.B, g.F, g.u, g.Q, g.H, g.d, g.R, g.m0, g.P0, g.y,
+    prep_body<N, M, FOLD>(dsm, sg, g.B, g.F, g.u, g.Q, g.H, g.d, g.R, g.m0, g.P0, g.y,
                     const_cast<ModelConst<N, M>*>(g.segs.mcg), g.fs.status, g.zero, g.nzero, g.segs.off, g.T,
                     nullptr, const_cast<BlockCoef<N, M>*>(g.segs.coef), g.ch);
 }
 
 // One block per sequence of all groups (nx = 6 sequences first); block 0 also
 // zeroes the two work-queue counters.  (CH only makes one copy per
-// instantiation unit.)
-template <int CH>
+// instantiation unit; FOLD: build the block-fold coefficients.)
+template <int CH, bool FOLD>
 __global__ void __launch_bounds__(kPrepThreads) mixed_prep_kernel(MG6 g6, MG4 g4, MG2 g2, MixedQueue q) {
     extern __shared__ __align__(16) char prep_dsm[];
     int b = (int)blockIdx.x;
@@ -74,11 +74,11 @@ __global__ void __launch_bounds__(kPrepThreads) mixed_prep_kernel(MG6 g6, MG4 g4
         *q.scounter = 0u;
         *q.fcounter2 = 0u;
     }
-    if (b < g6.B) { mixed_prep_one<6, 3>(prep_dsm, b, g6); return; }
+    if (b < g6.B) { mixed_prep_one<6, 3, FOLD>(prep_dsm, b, g6); return; }
     b -= g6.B;
-    if (b < g4.B) { mixed_prep_one<4, 2>(prep_dsm, b, g4); return; }
+    if (b < g4.B) { mixed_prep_one<4, 2, FOLD>(prep_dsm, b, g4); return; }
     b -= g4.B;
-    if (b < g2.B) mixed_prep_one<2, 1>(prep_dsm, b, g2);
+    if (b < g2.B) mixed_prep_one<2, 1, FOLD>(prep_dsm, b, g2);
 }
 
 template <int N, int M>
@@ -269,12 +269,16 @@ struct Mixed {
                            reinterpret_cast<uint32_t*>(w + kMixedQueueOff + 8), reinterpret_cast<uint32_t*>(w)};
         const int nseq = g6.B + g4.B + g2.B;
         const int ntiles = g6.ntiles + g4.ntiles + g2.ntiles;
-        static const bool ok = allow_smem(mixed_prep_kernel<CH>, (int)mixed_prep_smem()) &&
+        static const bool ok = allow_smem(mixed_prep_kernel<CH, true>, (int)mixed_prep_smem()) &&
+                               allow_smem(mixed_prep_kernel<CH, false>, (int)mixed_prep_smem()) &&
                                allow_smem(mixed_filter_kernel<CH, REF_DETECT, false>, mixed_filter_smem()) &&
                                allow_smem(mixed_filter_kernel<CH, REF_FP64, true>, mixed_filter_smem()) &&
                                allow_smem(mixed_smoother_kernel<CH>, mixed_smoother_smem());
         if (!ok) return KS_ECUDA;
-        mixed_prep_kernel<CH><<<nseq, kPrepThreads, mixed_prep_smem(), st>>>(g6, g4, g2, q);
+        if (fold)
+            mixed_prep_kernel<CH, true><<<nseq, kPrepThreads, mixed_prep_smem(), st>>>(g6, g4, g2, q);
+        else
+            mixed_prep_kernel<CH, false><<<nseq, kPrepThreads, mixed_prep_smem(), st>>>(g6, g4, g2, q);
         int rc = launch_status();
         if (rc) return rc;
         if ((rc = launch_pdl(mixed_filter_kernel<CH, REF_DETECT, false>, ntiles, kMixedThreads, mixed_filter_smem(),

@@ -629,7 +629,9 @@ KS_DEV void first_element_fp64(PS& p, MC& mc, int i) {
 // update with y_1) in FP64; the two chains only meet for the final store.
 // Body of the preparation of segment sg of nseg (one thread block); dyn:
 // its dynamic shared memory (PrepSmem and a ModelConst).
-template <int N, int M>
+// FOLD = false leaves the block-fold coefficient code out (fewer registers
+// for launches that never fold).
+template <int N, int M, bool FOLD = true>
 KS_DEV void prep_body(char* prep_dsm, int sg, int nseg, const float* __restrict__ F, const float* __restrict__ u,
                       const float* __restrict__ Q, const float* __restrict__ H, const float* __restrict__ d,
                       const float* __restrict__ R, const double* __restrict__ m0, const double* __restrict__ P0,
@@ -773,7 +775,7 @@ KS_DEV void prep_body(char* prep_dsm, int sg, int nseg, const float* __restrict_
         }
         for (int e = l; e < N; e += 32) mc.u[e] = p.u[e];
         if (l < 4) mc.pad[l] = 0.f;
-        if constexpr (N <= 6) {   // register-path sizes only
+        if constexpr (N <= 6 && FOLD) {   // register-path sizes only
             if (coef != nullptr) {   // the block-fold coefficients, while warps 1-3 build the k = 1 element
                 __syncwarp();
                 block_coef_warp<N, M>(mc, &p.H[0][0], ch, coef + sg);
@@ -804,7 +806,7 @@ constexpr size_t prep_dyn_smem() {
 
 // One block per model (segment); block 0 also zeroes the scans' counters and
 // flags (`zero`), the first one from *first_tile when given.
-template <int N, int M>
+template <int N, int M, bool FOLD = true>
 __global__ void __launch_bounds__(kPrepThreads) prep_kernel(const float* __restrict__ F, const float* __restrict__ u,
                                                    const float* __restrict__ Q, const float* __restrict__ H,
                                                    const float* __restrict__ d, const float* __restrict__ R,
@@ -816,8 +818,8 @@ __global__ void __launch_bounds__(kPrepThreads) prep_kernel(const float* __restr
                                                    BlockCoef<N, M>* __restrict__ coef = nullptr, int ch = 0) {
     extern __shared__ __align__(16) char prep_dsm[];
     pdl_wait();
-    prep_body<N, M>(prep_dsm, (int)blockIdx.x, (int)gridDim.x, F, u, Q, H, d, R, m0, P0, y, out, status, zero, nzero,
-                    off, T, first_tile, coef, ch);
+    prep_body<N, M, FOLD>(prep_dsm, (int)blockIdx.x, (int)gridDim.x, F, u, Q, H, d, R, m0, P0, y, out, status, zero,
+                          nzero, off, T, first_tile, coef, ch);
     pdl_trigger();
 }
 

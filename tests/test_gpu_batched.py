@@ -183,6 +183,26 @@ def test_mixed_state_sizes(ks, dims, extra):
     print("mixed", dims, sum(s.T for s in seqs), worst)
 
 
+@pytest.mark.parametrize("steps", [8, 32])
+def test_mixed_batch_with_block_fold(ks, steps):
+    """The mixed-size launch with the linear block fold forced on (per-sequence
+    coefficients, segment-relative tables): every sequence against its oracle."""
+    from paper_1905_13002_gb300 import tune
+    rng = np.random.default_rng(90 + steps)
+    seqs = []
+    for dim in (1, 2, 3):
+        lengths = np.concatenate([EDGE, workloads.batch_lengths(30, rng, 256, 16384)])
+        seqs += make_batch(dim, lengths, 95 + dim + steps)
+    rng.shuffle(seqs)
+    ks.set_chunk_rules(0, [(tune.T_NEVER, steps, 1)])
+    try:
+        assert ks.chunk_fold(0, 1 << 20) == 1
+        run_mixed_and_check(ks, seqs)
+    finally:
+        ks.set_chunk_rules(0, [])
+        tune.load_default()
+
+
 def test_mixed_batch_rejects_unsupported_groups(ks):
     seqs = make_batch(2, [100, 50], 5)
     batch = ks.ModelBatch.create([s.model for s in seqs], [s.T for s in seqs])

@@ -89,6 +89,26 @@ def test_chunk_variants(ks, dim, T):
     _, y = workloads.simulate(m, T, rng)
     check(ks, m, y)
 
+# Every (steps per thread, block fold) variant of the fused scans, forced by a
+# one-rule table, on sizes with ragged ends; the table is restored after.
+@pytest.mark.parametrize("dim,T", [(1, 9001), (2, 70001), (3, 30001)])
+@pytest.mark.parametrize("steps,fold", [(4, 1), (8, 1), (16, 1), (32, 1), (32, 0)])
+def test_block_fold_variants(ks, dim, T, steps, fold):
+    from paper_1905_13002_gb300 import tune
+    rng = np.random.default_rng(4100 + T + dim)
+    m = workloads.wiener_velocity(dim, dt=0.1, q=1.3, r=0.4)
+    m.u = rng.standard_normal(2 * dim) * 0.1        # the affine terms of the fold
+    m.d = rng.standard_normal(dim) * 0.1
+    _, y = workloads.simulate(m, T, rng)
+    ks.set_chunk_rules(2 * dim, [(tune.T_NEVER, steps, fold)])
+    try:
+        assert (ks.chunk_steps(2 * dim, T), ks.chunk_fold(2 * dim, T)) == (steps, fold)
+        check(ks, m, y)
+    finally:
+        ks.set_chunk_rules(2 * dim, [])
+        tune.load_default()                       # the device's tuned table, if any
+
+
 def test_single_sequence_T1024(ks):
     seq = workloads.config_single()
     e = check(ks, seq.model, seq.y)
