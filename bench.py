@@ -208,21 +208,48 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- CPU oracle
-def cpu_oracle_rate(seq, seconds: float) -> dict:
+def output_errors(got, ref) -> dict:
+    """Errors of the GPU outputs (fmean, fcov, smean, scov as float arrays)
+    against the oracle's FP64 ones, max over steps: normwise relative
+    (|dm|_inf / max(|m|_inf, max_i sqrt(P_ii)); |dP|_max / |P|_max), and the
+    means' error in posterior standard deviations, |dm|_2 / sqrt(lambda_min(P))."""
+    out = {}
+    for name, g, r, P in (("fmean", got[0], ref[0], ref[1]), ("smean", got[2], ref[2], ref[3])):
+        g = np.asarray(g, dtype=np.float64)
+        d = g - r
+        sd_scale = np.sqrt(np.abs(np.diagonal(P, axis1=-2, axis2=-1))).max(-1)
+        rel = np.abs(d).max(-1) / np.maximum(np.abs(r).max(-1), sd_scale)
+        lam = np.maximum(np.linalg.eigvalsh(P)[..., 0], np.finfo(np.float64).tiny)
+        out[name] = {"rel": float(rel.max()), "sd": float((np.linalg.norm(d, axis=-1) / np.sqrt(lam)).max())}
+    for name, g, r in (("fcov", got[1], ref[1]), ("scov", got[3], ref[3])):
+        d = np.abs(np.asarray(g, dtype=np.float64) - r).max((-2, -1)) / np.abs(r).max((-2, -1))
+        out[name] = {"rel": float(d.max())}
+    return out
+
+
+def cpu_oracle_rate(seq, seconds: float, gpu_out=None) -> dict:
     """The FP64 oracle (sequential KF + RTS, one core) on the same sequence,
-    repeated until `seconds` of CPU work have run (at least once)."""
+    repeated until `seconds` of CPU work have run (at least once).  With the
+    GPU's outputs for this sequence, the first pass's results also give the
+    line's `max_err`."""
     import oracle
     oracle.build()
     t0 = time.perf_counter()
     reps = 0
+    first = None
     while True:
-        oracle.kf_rts(seq.model, seq.y)
+        r = oracle.kf_rts(seq.model, seq.y)
+        if first is None:
+            first = r
         reps += 1
         el = time.perf_counter() - t0
         if el >= seconds:
             break
-    return {"value": reps * seq.T / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{reps} full passes over the T={seq.T} sequence ({el:.1f} s, 1 thread)"}
+    res = {"value": reps * seq.T / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"{reps} full passes over the T={seq.T} sequence ({el:.1f} s, 1 thread)"}
+    if gpu_out is not None:
+        res["_max_err"] = output_errors(gpu_out, first)
+    return res
 
 
 # The sources that define each recorded kernel's code (its traffic record is
@@ -516,6 +543,9 @@ def run_single(args, rank, world, local, mode):
 
     # the batched workload beside it (the metric's "batched FP32 scan vs plain
     # scan"): one mixed-size launch per scan, and the plain per-sequence scan
+    # the outputs of the last timed call, for the error against the oracle
+    want_err = world == 1 and not args.no_cpu_baseline
+    host_out = tuple(t.cpu().numpy() for t in (fm, fP, sm, sP)) if want_err else None
     batched = None
     if mode == "long" and not args.no_batched:
         del fm, fP, sm, sP, ws, flush
@@ -537,7 +567,8 @@ def run_single(args, rank, world, local, mode):
            "clocks": {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
            "gpu_launches": 2 * launches_per_call(nx, T) * args.steps, "latency": lat, "e2e": e2e, "roofline": roof}
     if world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_oracle_rate(seq, args.cpu_seconds)
+        out["cpu_baseline"] = cpu_oracle_rate(seq, args.cpu_seconds, host_out)
+        out["max_err"] = out["cpu_baseline"].pop("_max_err")
     if batched is not None:
         out["batched"] = batched
     print(json.dumps(out))
