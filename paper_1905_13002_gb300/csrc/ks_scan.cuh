@@ -1533,6 +1533,23 @@ KS_DEV void build_selem_from(const MC& mc, const float (&xb)[N], const float (&P
     }
 }
 
+// A reverse step's Lemma 5 element: from the gain the forward scan stored for
+// it (GAIN, and `gain` given), else built from the filtered moments.
+template <int N, int M, int CH, bool GAIN, bool TV>
+KS_DEV void rev_element(const ModelConst<N, M>* mc, const float* __restrict__ gain, const TVArgs& tv, int64_t k,
+                        int64_t T, bool last, const float (&xb)[N], const float (&P)[sym_size(N)], SElem<N>& e,
+                        Flags& bad) {
+    if constexpr (GAIN) {
+        if (gain != nullptr) {
+            float E[N * N];
+            load_gain<N, CH>(gain, k, E);
+            smoother_element_from_gain<N>(*mc, E, xb, P, e);
+            return;
+        }
+    }
+    build_selem_flat<N, M, TV>(mc, tv, k, T, last, xb, P, e, bad);
+}
+
 // ---------------------------------------------------------------- forward scan
 // With SAGG the same pass also builds each step's Lemma 5 smoothing element
 // from the posterior it has just produced and folds the thread's block of
@@ -1978,16 +1995,6 @@ KS_DEV void smoother_scan_body(SmootherSmem<N, M, NT>& sm, char* dsm, int tile,
         float probe = 0.f;
         Cursor<N, M, SEG> cur;
         cur.seek(segs, &mc, khi, T);
-        // Stored gains are read one or two steps ahead of their use (gA: the
-        // next step's, gB: the one after), so their latency overlaps a step.
-        const bool use_gain = GAIN && ss.gain != nullptr;
-        float gA[GAIN ? N * N : 1], gB[GAIN ? N * N : 1];
-        if constexpr (GAIN) {
-            if (use_gain) {
-                load_gain<N, CH>(ss.gain, khi, gA);
-                if (khi - 1 >= klo) load_gain<N, CH>(ss.gain, khi - 1, gB);
-            }
-        }
         if constexpr (SG::kOn) {
             rd.fetch(fmean, fcov, 0);
             rd.fetch(fmean, fcov, 1);
@@ -2020,23 +2027,8 @@ KS_DEV void smoother_scan_body(SmootherSmem<N, M, NT>& sm, char* dsm, int tile,
                     const ModelConst<N, M>* mcc = cur.mc;
                     const bool lc = TV ? (kc == T - 1) : cur.last(kc);
                     SElem<N> ea, ec;
-                    if constexpr (GAIN) {
-                        if (use_gain) {
-                            float Ea[N * N], Ec[N * N];
-#pragma unroll
-                            for (int q = 0; q < N * N; ++q) { Ea[q] = gA[q]; Ec[q] = gB[q]; }
-                            if (ka - 2 >= klo) load_gain<N, CH>(ss.gain, ka - 2, gA);
-                            if (ka - 3 >= klo) load_gain<N, CH>(ss.gain, ka - 3, gB);
-                            smoother_element_from_gain<N>(*ma, Ea, xa, Pa, ea);
-                            smoother_element_from_gain<N>(*mcc, Ec, xc, Pc, ec);
-                        } else {
-                            build_selem_flat<N, M, TV>(ma, tv, ka, T, la, xa, Pa, ea, bad);
-                            build_selem_flat<N, M, TV>(mcc, tv, kc, T, lc, xc, Pc, ec, bad);
-                        }
-                    } else {
-                        build_selem_flat<N, M, TV>(ma, tv, ka, T, la, xa, Pa, ea, bad);
-                        build_selem_flat<N, M, TV>(mcc, tv, kc, T, lc, xc, Pc, ec, bad);
-                    }
+                    rev_element<N, M, CH, GAIN, TV>(ma, ss.gain, tv, ka, T, la, xa, Pa, ea, bad);
+                    rev_element<N, M, CH, GAIN, TV>(mcc, ss.gain, tv, kc, T, lc, xc, Pc, ec, bad);
                     if (!has) { st = SmootherOp<N>::state_of(ea); has = true; }   // only k = T-1
                     else sadvance<N>(ea, st);
                     stage_write<N>(b, s, st.g, st.L);     // the slot's input is already in registers
@@ -2055,12 +2047,8 @@ KS_DEV void smoother_scan_body(SmootherSmem<N, M, NT>& sm, char* dsm, int tile,
                     stage_read<N>(b, 0, xb, P);
                     cur.backward(segs, lo);
                     SElem<N> e;
-                    if constexpr (GAIN) {
-                        if (use_gain) smoother_element_from_gain<N>(*cur.mc, gA, xb, P, e);   // the block's first step
-                        else build_selem_flat<N, M, TV>(cur.mc, tv, lo, T, cur.last(lo), xb, P, e, bad);
-                    } else {
-                        build_selem_flat<N, M, TV>(cur.mc, tv, lo, T, TV ? (lo == T - 1) : cur.last(lo), xb, P, e, bad);
-                    }
+                    rev_element<N, M, CH, GAIN, TV>(cur.mc, ss.gain, tv, lo, T, TV ? (lo == T - 1) : cur.last(lo), xb,
+                                                    P, e, bad);
                     if (!has) { st = SmootherOp<N>::state_of(e); has = true; }
                     else sadvance<N>(e, st);
                     stage_write<N>(b, 0, st.g, st.L);
@@ -2081,19 +2069,8 @@ KS_DEV void smoother_scan_body(SmootherSmem<N, M, NT>& sm, char* dsm, int tile,
                 load_posterior<N>(fmean, fcov, k, xb, P);
                 cur.backward(segs, k);
                 SElem<N> e;
-                if constexpr (GAIN) {
-                    if (use_gain) {
-                        float Ek[N * N];
-#pragma unroll
-                        for (int q = 0; q < N * N; ++q) Ek[q] = gA[q];
-                        if (k - 1 >= klo) load_gain<N, CH>(ss.gain, k - 1, gA);
-                        smoother_element_from_gain<N>(*cur.mc, Ek, xb, P, e);
-                    } else {
-                        build_selem_flat<N, M, TV>(cur.mc, tv, k, T, cur.last(k), xb, P, e, bad);
-                    }
-                } else {
-                    build_selem_flat<N, M, TV>(cur.mc, tv, k, T, TV ? (k == T - 1) : cur.last(k), xb, P, e, bad);
-                }
+                rev_element<N, M, CH, GAIN, TV>(cur.mc, ss.gain, tv, k, T, TV ? (k == T - 1) : cur.last(k), xb, P,
+                                                e, bad);
                 if (!has) { st = SmootherOp<N>::state_of(e); has = true; }
                 else sadvance<N>(e, st);
                 store_posterior<N>(smean, scov, k, st.g, st.L);
