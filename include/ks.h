@@ -144,11 +144,7 @@ const char *ks_strerror(int code);
  * (only m->nx, m->ny and m->time_varying are read; host pointer).
  * purpose = KS_WS_SMOOTH or KS_WS_ELEMENTS.  Returns 0 for invalid
  * arguments, and for a time-varying model of an (nx, ny) whose smoother
- * does not take one.  For a time-invariant model with nx <= 6, KS_WS_SMOOTH
- * includes nx * nx floats per step in which ks_smooth's forward scan keeps
- * each step's Lemma 5 gain E_k for its reverse scan; ks_smooth also runs in
- * a workspace too small for them (down to the size without them) and then
- * forms the gains again in the reverse scan, with the same results.
+ * does not take one.
  */
 size_t ks_workspace_bytes(const ks_model *m, int64_t T, int purpose);
 

@@ -25,8 +25,6 @@ struct Layout {
     size_t off_const = 0, off_coef = 0, off_flags = 0, flags_bytes = 0;
     size_t off_fagg = 0, off_fpre = 0, off_sagg = 0, off_spre = 0, off_sblk = 0;
     size_t off_elems = 0, off_fmean = 0, off_fcov = 0;
-    size_t off_gain = 0;            // per-step smoother gains of a single sequence (0: none)
-    size_t bytes_smooth_min = 0;    // the fused smooth without the stored gains
     size_t bytes_smooth = 0, bytes_elements = 0;
 };
 
@@ -96,13 +94,6 @@ struct Impl {
 
     static constexpr size_t prep_smem() { return sizeof(PrepSmem<N, M>) + sizeof(ModelConst<N, M>) + 16; }
 
-    // Stored gains: N x N floats per step, in groups of 32 consecutive thread
-    // blocks of FCH steps (gain_index), so whole groups of blocks are allocated.
-    static size_t gain_bytes(int64_t T) {
-        const int64_t grp = (T + 32 * (int64_t)FCH - 1) / (32 * (int64_t)FCH);
-        return 4 * (size_t)N * N * (size_t)grp * 32 * FCH;
-    }
-
     static Layout layout(int64_t T, int B = 1) {
         Layout L;
         L.T = T;
@@ -128,11 +119,6 @@ struct Impl {
         off = align_up(off + sizeof(SState<N>) * (size_t)L.nts, 256);
         L.off_sblk = off;                                   // smoothing aggregate per forward block
         off = align_up(off + sizeof(SElem<N>) * (size_t)((T + FCH - 1) / FCH), 256);
-        L.bytes_smooth_min = off;
-        if (B == 1) {   // each step's Lemma 5 gain E_k, written by the forward scan for the reverse scan
-            L.off_gain = off;
-            off = align_up(off + gain_bytes(T), 256);
-        }
         L.bytes_smooth = off;
         L.off_elems = off;
         off = align_up(off + 4 * (size_t)NCOMP * (size_t)L.ld, 256);
@@ -231,7 +217,7 @@ struct Impl {
 
     template <bool SEG>
     static int launch_filter_fused(void* ws, const Layout& L, const float* y, float* fm, float* fc,
-                                   Segs<N, M> segs, cudaStream_t st, float* gain = nullptr) {
+                                   Segs<N, M> segs, cudaStream_t st) {
         constexpr int smem = filter_dyn_smem<N, FNT>();
         auto k = filter_scan_kernel<N, M, FNT, FCH, true, true, SEG, false, REF_DETECT, false>;
         auto kr = filter_scan_kernel<N, M, FNT, FCH, true, true, SEG, false, REF_FP64, true>;
@@ -240,11 +226,11 @@ struct Impl {
         const ModelConst<N, M>* mc = mconst(ws, L);
         const float* none = nullptr;
         float* sb = sblk(ws, L);
-        ScanState fs = fstate(ws, L), fr = fstate_retry(ws, L);
-        fs.gain = fr.gain = gain;
-        int rc = launch_pdl(k, L.ntf, FNT, smem, st, mc, y, none, L.ld, L.T, fm, fc, fs, sb, segs, TVArgs{});
+        int rc = launch_pdl(k, L.ntf, FNT, smem, st, mc, y, none, L.ld, L.T, fm, fc, fstate(ws, L), sb, segs,
+                            TVArgs{});
         if (rc) return rc;
-        return launch_pdl(kr, L.ntf, FNT, smem, st, mc, y, none, L.ld, L.T, fm, fc, fr, sb, segs, TVArgs{});
+        return launch_pdl(kr, L.ntf, FNT, smem, st, mc, y, none, L.ld, L.T, fm, fc, fstate_retry(ws, L), sb, segs,
+                          TVArgs{});
     }
 
     // Time-varying model: elements from the TVElem records `el`, smoothing
@@ -279,17 +265,14 @@ struct Impl {
 
     template <bool FROM_AGG, bool SEG, bool TV = false>
     static int launch_smoother(void* ws, const Layout& L, const float* fm, const float* fc, float* sm,
-                               float* sc, Segs<N, M> segs, cudaStream_t st, TVArgs tv = TVArgs{},
-                               float* gain = nullptr) {
+                               float* sc, Segs<N, M> segs, cudaStream_t st, TVArgs tv = TVArgs{}) {
         constexpr int smem = smoother_dyn_smem<N, SNT>();
         auto k = smoother_scan_kernel<N, M, SNT, SCH, FROM_AGG, SEG, TV>;
         static const bool ok = allow_smem(k, smem);
         if (!ok) return KS_ECUDA;
         const float* sb = FROM_AGG ? sblk(ws, L) : nullptr;
-        ScanState ss = sstate(ws, L);
-        ss.gain = gain;
         return launch_pdl(k, L.nts, SNT, smem, st, (const ModelConst<N, M>*)mconst(ws, L), (const float*)fm,
-                          (const float*)fc, L.T, sm, sc, ss, sb, segs, tv);
+                          (const float*)fc, L.T, sm, sc, sstate(ws, L), sb, segs, tv);
     }
 
     static int build_elements(const ks_model* m, const float* y, int64_t T, void* ws, size_t ws_bytes,
@@ -319,7 +302,7 @@ struct Impl {
     static int smooth_scan(const ks_model* m, int64_t T, const float* fm, const float* fc, void* ws,
                            size_t ws_bytes, float* sm, float* sc, cudaStream_t st) {
         const Layout L = layout(T);
-        int rc = check_common(m, T, ws, ws_bytes, L.bytes_smooth_min);
+        int rc = check_common(m, T, ws, ws_bytes, L.bytes_smooth);
         if (rc) return rc;
         if (!fm || !fc || !sm || !sc || !aligned16(fm) || !aligned16(fc) || !aligned16(sm) || !aligned16(sc))
             return KS_EINVAL;
@@ -389,7 +372,7 @@ struct Impl {
         const Layout L = layout(T);
         const bool own = (fm == nullptr) || (fc == nullptr);
         const bool filter_only = (sm == nullptr) && (sc == nullptr);
-        int rc = check_common(m, T, ws, ws_bytes, own ? L.bytes_elements : L.bytes_smooth_min);
+        int rc = check_common(m, T, ws, ws_bytes, own ? L.bytes_elements : L.bytes_smooth);
         if (rc) return rc;
         if (!y || !aligned16(y) || (filter_only && own)) return KS_EINVAL;
         if (!filter_only && (!sm || !sc || !aligned16(sm) || !aligned16(sc))) return KS_EINVAL;
@@ -403,16 +386,9 @@ struct Impl {
         if ((rc = prep(m, y, ws, L, st, fold))) return rc;
         if ((rc = record(ev, 1, st))) return rc;
         const Segs<N, M> segs{nullptr, nullptr, 1, fold ? coef(ws, L) : nullptr};
-        // With room for them, the forward scan keeps each step's Lemma 5 gain
-        // for the reverse scan, which then skips the factorisation of P-.
-        float* gain = (!filter_only && L.off_gain && ws_bytes >= L.bytes_smooth)
-                          ? reinterpret_cast<float*>(static_cast<char*>(ws) + L.off_gain)
-                          : nullptr;
-        if ((rc = launch_filter_fused<false>(ws, L, y, fm, fc, segs, st, gain))) return rc;
+        if ((rc = launch_filter_fused<false>(ws, L, y, fm, fc, segs, st))) return rc;
         if ((rc = record(ev, 2, st))) return rc;
-        if (!filter_only &&
-            (rc = launch_smoother<true, false>(ws, L, fm, fc, sm, sc, no_segs(), st, TVArgs{}, gain)))
-            return rc;
+        if (!filter_only && (rc = launch_smoother<true, false>(ws, L, fm, fc, sm, sc, no_segs(), st))) return rc;
         return record(ev, 3, st);
     }
 
@@ -427,7 +403,7 @@ struct Impl {
             return KS_EINVAL;
         if (mb->B < 1 || mb->B > T || T < 1 || T > 0x7fffffffLL) return KS_EINVAL;
         const Layout L = layout(T, mb->B);
-        if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) != 0 || ws_bytes < L.bytes_smooth_min) return KS_EINVAL;
+        if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) != 0 || ws_bytes < L.bytes_smooth) return KS_EINVAL;
         if (!y || !fm || !fc || !sm || !sc) return KS_EINVAL;
         if (!aligned16(y) || !aligned16(fm) || !aligned16(fc) || !aligned16(sm) || !aligned16(sc))
             return KS_EINVAL;
@@ -560,7 +536,6 @@ struct Tuned {
         for (int i = 0; i < 4; ++i) {
             const Layout Li = ChunkTable<N, M>::v[i]->layout(T, B);
             L.bytes_smooth = std::max(L.bytes_smooth, Li.bytes_smooth);
-            L.bytes_smooth_min = std::max(L.bytes_smooth_min, Li.bytes_smooth_min);
             L.bytes_elements = std::max(L.bytes_elements, Li.bytes_elements);
         }
         return L;

@@ -43,7 +43,7 @@ extern "C" int ks_smooth_noalloc(const ks_model* m, const float* y, int64_t T, f
     if (!fmean || !fcov) return KS_EINVAL;
     if ((smean == nullptr) != (scov == nullptr)) return KS_EINVAL;   // both NULL: filtering only
     const VTable* v = &kImpl32_4_2;   // 32 steps per thread: the smallest scratch layout
-    if (v->layout(T, 1).bytes_smooth_min > (size_t)KS_NOALLOC_SCRATCH_BYTES) return KS_EINVAL;
+    if (v->layout(T, 1).bytes_smooth > (size_t)KS_NOALLOC_SCRATCH_BYTES) return KS_EINVAL;
     void* ws = nullptr;
     int rc = scratch_on_current_device(&ws);
     if (rc) return rc;

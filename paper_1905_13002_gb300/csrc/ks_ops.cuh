@@ -1379,51 +1379,6 @@ KS_DEV void smoother_element(const MC& mc, const float (&xbar)[N],
         }
 }
 
-// Lemma 5 element from a gain E computed before from the same filtered
-// (xbar, P) (by smoother_element in the forward scan): the rest of the element
-// in the same arithmetic, g = xbar - E (F xbar + u), L = P - E (F P), so the
-// result equals smoother_element's.
-template <int N, class MC>
-KS_DEV void smoother_element_from_gain(const MC& mc, const float (&E)[N * N], const float (&xbar)[N],
-                                       const float (&P)[sym_size(N)], SElem<N>& e) {
-#pragma unroll
-    for (int a = 0; a < N * N; ++a) e.E[a] = E[a];
-    float fx[N];
-#pragma unroll
-    for (int a = 0; a < N; ++a) {
-        float s = mc.u[a];
-#pragma unroll
-        for (int c = 0; c < N; ++c) s = fmaf(mc.F[a * N + c], xbar[c], s);
-        fx[a] = s;
-    }
-#pragma unroll
-    for (int a = 0; a < N; ++a) {
-        float s = xbar[a];
-#pragma unroll
-        for (int c = 0; c < N; ++c) s = fmaf(-E[a * N + c], fx[c], s);
-        e.g[a] = s;
-    }
-    float FP[N][N];
-#pragma unroll
-    for (int a = 0; a < N; ++a)
-#pragma unroll
-        for (int b = 0; b < N; ++b) {
-            float s = 0.f;
-#pragma unroll
-            for (int c = 0; c < N; ++c) s = fmaf(mc.F[a * N + c], P[sidx(c, b)], s);
-            FP[a][b] = s;
-        }
-#pragma unroll
-    for (int a = 0; a < N; ++a)
-#pragma unroll
-        for (int b = 0; b <= a; ++b) {
-            float s = P[sidx(a, b)];
-#pragma unroll
-            for (int c = 0; c < N; ++c) s = fmaf(-E[a * N + c], FP[c][b], s);
-            e.L[sidx(a, b)] = s;
-        }
-}
-
 // ---------------------------------------------------------------- Lemma 6
 // a_i (x) a_j with a_i the earlier time step:
 //   E_ij = E_i E_j,  g_ij = E_i g_j + g_i,  L_ij = E_i L_j E_i^T + L_i.

@@ -45,52 +45,7 @@ struct ScanState {
     float* pre;          // per-tile inclusive prefixes
     uint32_t* status;    // device status word (workspace header, see below)
     uint32_t spin_limit; // look-back polls before giving up (~1 s)
-    float* gain = nullptr;   // single sequence: each step's Lemma 5 gain (gain_index), or none
 };
-
-// Position of step k's N x N gain in the stored-gains array: the thread
-// blocks of CH steps are taken in groups of 32 (a warp's), and within a group
-// step j of every block is contiguous, so the 32 threads of a warp that write
-// (forward scan) or read (reverse scan) step j of their blocks touch one
-// contiguous run of 32 gains.
-template <int N, int CH>
-KS_DEV int64_t gain_index(int64_t k) {
-    const int64_t blk = k / CH;
-    const int64_t j = k - blk * CH;
-    return (((blk >> 5) * CH + j) * 32 + (blk & 31)) * (int64_t)(N * N);
-}
-
-template <int N, int CH>
-KS_DEV void store_gain(float* __restrict__ gain, int64_t k, const float (&E)[N * N]) {
-    static_assert((N * N) % 4 == 0 || N == 2 || N == 6, "float4 or float2 rows");
-    float* p = gain + gain_index<N, CH>(k);
-    if constexpr ((N * N) % 4 == 0) {
-#pragma unroll
-        for (int i = 0; i < N * N; i += 4)
-            *reinterpret_cast<float4*>(p + i) = make_float4(E[i], E[i + 1], E[i + 2], E[i + 3]);
-    } else {
-#pragma unroll
-        for (int i = 0; i < N * N; i += 2) *reinterpret_cast<float2*>(p + i) = make_float2(E[i], E[i + 1]);
-    }
-}
-
-template <int N, int CH>
-KS_DEV void load_gain(const float* __restrict__ gain, int64_t k, float (&E)[N * N]) {
-    const float* p = gain + gain_index<N, CH>(k);
-    if constexpr ((N * N) % 4 == 0) {
-#pragma unroll
-        for (int i = 0; i < N * N; i += 4) {
-            const float4 t = __ldg(reinterpret_cast<const float4*>(p + i));
-            E[i] = t.x; E[i + 1] = t.y; E[i + 2] = t.z; E[i + 3] = t.w;
-        }
-    } else {
-#pragma unroll
-        for (int i = 0; i < N * N; i += 2) {
-            const float2 t = __ldg(reinterpret_cast<const float2*>(p + i));
-            E[i] = t.x; E[i + 1] = t.y;
-        }
-    }
-}
 
 KS_DEV uint32_t wait_limit(const ScanState& ss) {
     const uint32_t o = ss.status[HDR_WAIT];
@@ -1533,23 +1488,6 @@ KS_DEV void build_selem_from(const MC& mc, const float (&xb)[N], const float (&P
     }
 }
 
-// A reverse step's Lemma 5 element: from the gain the forward scan stored for
-// it (GAIN, and `gain` given), else built from the filtered moments.
-template <int N, int M, int CH, bool GAIN, bool TV>
-KS_DEV void rev_element(const ModelConst<N, M>* mc, const float* __restrict__ gain, const TVArgs& tv, int64_t k,
-                        int64_t T, bool last, const float (&xb)[N], const float (&P)[sym_size(N)], SElem<N>& e,
-                        Flags& bad) {
-    if constexpr (GAIN) {
-        if (gain != nullptr) {
-            float E[N * N];
-            load_gain<N, CH>(gain, k, E);
-            smoother_element_from_gain<N>(*mc, E, xb, P, e);
-            return;
-        }
-    }
-    build_selem_flat<N, M, TV>(mc, tv, k, T, last, xb, P, e, bad);
-}
-
 // ---------------------------------------------------------------- forward scan
 // With SAGG the same pass also builds each step's Lemma 5 smoothing element
 // from the posterior it has just produced and folds the thread's block of
@@ -1763,19 +1701,12 @@ KS_DEV void filter_scan_body(FilterSmem<N, M, NT>& sm, char* dsm, int tile,
                 if (i >= 1) {   // step k - 1 < T - 1: never the last step
                     SElem<N> e;
                     smoother_element<N, M>(*cur.mc, prev.b, prev.C, e, bad);
-                    if (ss.gain) store_gain<N, CH>(ss.gain, k - 1, e.E);
                     sacc = (i == 1) ? e : scombine<N>(sacc, e);
                 }
             } else if constexpr (SAGG) {
                 SElem<N> e;
-                if constexpr (TV) {
-                    build_selem_tv<N, M>(tv, k, T, st.b, st.C, e, bad);
-                } else {
-                    build_selem_from<N, M>(*cur.mc, st.b, st.C, cur.last(k), e, bad);
-                    if constexpr (!SEG) {
-                        if (ss.gain) store_gain<N, CH>(ss.gain, k, e.E);
-                    }
-                }
+                if constexpr (TV) build_selem_tv<N, M>(tv, k, T, st.b, st.C, e, bad);
+                else build_selem_from<N, M>(*cur.mc, st.b, st.C, cur.last(k), e, bad);
                 sacc = (i == 0) ? e : scombine<N>(sacc, e);
             }
             if constexpr (SG::kOn) {
@@ -1796,7 +1727,6 @@ KS_DEV void filter_scan_body(FilterSmem<N, M, NT>& sm, char* dsm, int tile,
             const int64_t kl = k0 + nsteps - 1;
             SElem<N> e;
             build_selem_from<N, M>(*cur.mc, st.b, st.C, kl == T - 1, e, bad);
-            if (ss.gain) store_gain<N, CH>(ss.gain, kl, e.E);
             sacc = (nsteps == 1) ? e : scombine<N>(sacc, e);
         }
         if constexpr (SG::kOn) {
@@ -1920,8 +1850,6 @@ KS_DEV void smoother_scan_body(SmootherSmem<N, M, NT>& sm, char* dsm, int tile,
                                const float* __restrict__ sagg, const Segs<N, M>& segs, const TVArgs& tv) {
     static_assert(!TV || !SEG, "time-varying models run unsegmented");
     using BS = BlockScan<SmootherOp<N>, NT>;
-    // a single sequence after the fused forward scan: its stored gains, if any
-    constexpr bool GAIN = FROM_AGG && !SEG && !TV;
     using SG = Stage<N>;
     using RR = RevReader<N>;
     const ModelConst<N, M>& mc = sm.mc;
@@ -2027,8 +1955,8 @@ KS_DEV void smoother_scan_body(SmootherSmem<N, M, NT>& sm, char* dsm, int tile,
                     const ModelConst<N, M>* mcc = cur.mc;
                     const bool lc = TV ? (kc == T - 1) : cur.last(kc);
                     SElem<N> ea, ec;
-                    rev_element<N, M, CH, GAIN, TV>(ma, ss.gain, tv, ka, T, la, xa, Pa, ea, bad);
-                    rev_element<N, M, CH, GAIN, TV>(mcc, ss.gain, tv, kc, T, lc, xc, Pc, ec, bad);
+                    build_selem_flat<N, M, TV>(ma, tv, ka, T, la, xa, Pa, ea, bad);
+                    build_selem_flat<N, M, TV>(mcc, tv, kc, T, lc, xc, Pc, ec, bad);
                     if (!has) { st = SmootherOp<N>::state_of(ea); has = true; }   // only k = T-1
                     else sadvance<N>(ea, st);
                     stage_write<N>(b, s, st.g, st.L);     // the slot's input is already in registers
@@ -2047,8 +1975,8 @@ KS_DEV void smoother_scan_body(SmootherSmem<N, M, NT>& sm, char* dsm, int tile,
                     stage_read<N>(b, 0, xb, P);
                     cur.backward(segs, lo);
                     SElem<N> e;
-                    rev_element<N, M, CH, GAIN, TV>(cur.mc, ss.gain, tv, lo, T, TV ? (lo == T - 1) : cur.last(lo), xb,
-                                                    P, e, bad);
+                    if constexpr (TV) build_selem_tv<N, M>(tv, lo, T, xb, P, e, bad);
+                    else build_selem_from<N, M>(*cur.mc, xb, P, cur.last(lo), e, bad);
                     if (!has) { st = SmootherOp<N>::state_of(e); has = true; }
                     else sadvance<N>(e, st);
                     stage_write<N>(b, 0, st.g, st.L);
@@ -2069,8 +1997,8 @@ KS_DEV void smoother_scan_body(SmootherSmem<N, M, NT>& sm, char* dsm, int tile,
                 load_posterior<N>(fmean, fcov, k, xb, P);
                 cur.backward(segs, k);
                 SElem<N> e;
-                rev_element<N, M, CH, GAIN, TV>(cur.mc, ss.gain, tv, k, T, TV ? (k == T - 1) : cur.last(k), xb, P,
-                                                e, bad);
+                if constexpr (TV) build_selem_tv<N, M>(tv, k, T, xb, P, e, bad);
+                else build_selem_from<N, M>(*cur.mc, xb, P, cur.last(k), e, bad);
                 if (!has) { st = SmootherOp<N>::state_of(e); has = true; }
                 else sadvance<N>(e, st);
                 store_posterior<N>(smean, scov, k, st.g, st.L);
