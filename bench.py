@@ -211,16 +211,22 @@ class ClockSampler:
 def output_errors(got, ref) -> dict:
     """Errors of the GPU outputs (fmean, fcov, smean, scov as float arrays)
     against the oracle's FP64 ones, max over steps: normwise relative
-    (|dm|_inf / max(|m|_inf, max_i sqrt(P_ii)); |dP|_max / |P|_max), and the
-    means' error in posterior standard deviations, |dm|_2 / sqrt(lambda_min(P))."""
+    (|dm|_inf / max(|m|_inf, max_i sqrt(P_ii)); |dP|_max / |P|_max), the
+    means' error in posterior standard deviations, |dm|_2 / sqrt(lambda_min(P)),
+    and the largest use of the bound 0.01 sd + 24 ulps of the value (an FP32
+    output cannot resolve less than its own ulp; at T = 2^20 one ulp of the
+    position is several posterior sd)."""
     out = {}
     for name, g, r, P in (("fmean", got[0], ref[0], ref[1]), ("smean", got[2], ref[2], ref[3])):
         g = np.asarray(g, dtype=np.float64)
         d = g - r
         sd_scale = np.sqrt(np.abs(np.diagonal(P, axis1=-2, axis2=-1))).max(-1)
         rel = np.abs(d).max(-1) / np.maximum(np.abs(r).max(-1), sd_scale)
-        lam = np.maximum(np.linalg.eigvalsh(P)[..., 0], np.finfo(np.float64).tiny)
-        out[name] = {"rel": float(rel.max()), "sd": float((np.linalg.norm(d, axis=-1) / np.sqrt(lam)).max())}
+        s = np.sqrt(np.maximum(np.linalg.eigvalsh(P)[..., 0], np.finfo(np.float64).tiny))
+        e = np.linalg.norm(d, axis=-1) / s
+        ulp = np.linalg.norm(np.spacing(np.abs(r).astype(np.float32)).astype(np.float64), axis=-1) / s
+        out[name] = {"rel": float(rel.max()), "sd": float(e.max()),
+                     "sd_bound_use": float((e / (0.01 + 24.0 * ulp)).max())}
     for name, g, r in (("fcov", got[1], ref[1]), ("scov", got[3], ref[3])):
         d = np.abs(np.asarray(g, dtype=np.float64) - r).max((-2, -1)) / np.abs(r).max((-2, -1))
         out[name] = {"rel": float(d.max())}

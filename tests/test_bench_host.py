@@ -49,3 +49,25 @@ def test_launch_counts():
     assert bench.launches_per_call(4, 1 << 20) == 4
     assert bench.launches_per_call(32, 65536) == 1 + 2 * (2 + 9)
     assert bench.launches_per_call(32, 216) == 1 + 2 * 2
+
+
+def test_output_errors_measure_the_means_in_posterior_sd():
+    """The bench line's max_err: FP32 rounding of the oracle's own outputs
+    stays far inside the sd bound; a mean moved by one posterior sd along the
+    least certain direction reads as 1 sd."""
+    import numpy as np
+    import oracle
+    import workloads
+    seq = workloads.tracking_sequence(2000, seed=9)
+    ref = oracle.kf_rts(seq.model, seq.y)
+    got = [np.asarray(x, dtype=np.float32) for x in ref]
+    e = bench.output_errors(got, ref)
+    assert e["fmean"]["rel"] < 1e-6 and e["scov"]["rel"] < 1e-6
+    assert e["fmean"]["sd_bound_use"] < 0.2 and e["smean"]["sd_bound_use"] < 0.2
+    k = 1234
+    w, V = np.linalg.eigh(ref[1][k])
+    moved = got[0].astype(np.float64)
+    moved[k] += np.sqrt(w[0]) * V[:, 0]
+    e = bench.output_errors([moved, got[1], got[2], got[3]], ref)
+    assert abs(e["fmean"]["sd"] - 1.0) < 1e-3
+    assert e["fmean"]["sd_bound_use"] > 1.0
