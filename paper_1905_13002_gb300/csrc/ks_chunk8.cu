@@ -1,5 +1,5 @@
 // The 8-steps-per-thread variants of the fused smooth / smooth_batch for
-// nx = 2, 4 and 6 (chosen per call by chunk_index_for, ks_api.cu).
+// nx = 2, 4 and 6 (chosen per call by chunk_choice, ks_api.cu).
 #include "ks_impl.cuh"
 
 namespace ks {
