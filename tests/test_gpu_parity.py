@@ -275,6 +275,26 @@ def test_non_finite_measurement_is_reported(ks):
     assert ks.status(ws) == ks.KS_OK          # the status word was cleared
 
 
+@pytest.mark.parametrize("nx,ny", [(2, 1), (4, 2), (6, 3), (8, 4)])
+def test_non_positive_first_innovation_covariance_is_reported(ks, nx, ny):
+    """The FP64 k = 1 element checks that S1 = H P- H^T + R is positive
+    definite (leading minors for ny <= 3, pivots of the unpivoted elimination
+    above): a prior covariance P0 = -10 I, which no valid model has, makes S1
+    negative definite while S = H Q H^T + R of the later steps stays valid."""
+    rng = np.random.default_rng(nx)
+    if nx <= 6:
+        m = workloads.wiener_velocity(nx // 2, dt=0.1, q=1.0, r=0.5)
+    else:
+        m = workloads.random_stable(nx, ny, rng)
+    m.P0 = -10.0 * np.eye(nx)
+    y = rng.standard_normal((300, ny))
+    model = gpu_model(ks, m)
+    yt = torch.as_tensor(np.asarray(y), dtype=torch.float32, device="cuda")
+    ws = ks.alloc_workspace(model, 300)
+    ks.smooth(model, yt, ws)
+    assert ks.status(ws) == ks.KS_ENUMERIC
+
+
 def test_bad_arguments_raise(ks):
     seq = workloads.tracking_sequence(100, seed=4)
     model = gpu_model(ks, seq.model)
